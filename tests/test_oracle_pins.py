@@ -1,0 +1,435 @@
+"""Pins of the FP64 oracle against facts fixed by the paper or by mathematics.
+
+Each test checks the oracle against something other than itself: values the
+paper prints or implies, closed forms, physical invariants, special cases that
+reduce to a textbook result, the published Philox known-answer vectors, or a
+statistical law.  A plausible slip in the oracle (dropped term, wrong sign or
+index, transposed operand) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, signal, stats
+
+from oracle import gateau_oracle as O
+from paper_2604_23305_b300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+GHZ = 1e9
+KB, H = O.K_BOLTZMANN, O.H_PLANCK
+
+
+def golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split()[:2]
+                vals[k] = float(v)
+    return vals
+
+
+# ---------------------------------------------------------------- constants / stages
+
+def test_stage_efficiency_values():
+    g = golden("efficiencies.txt")
+    assert O.reflection_efficiency(3.41) == pytest.approx(g["refl"], abs=6e-6)
+    assert O.refraction_efficiency(4e-3, 3.41, 1e-4, 300 * GHZ) == pytest.approx(g["refr_300GHz"], abs=6e-6)
+    assert O.ohmic_efficiency(0.0025, 840 * GHZ, 350 * GHZ) == pytest.approx(g["ohmic_350GHz"], abs=6e-7)
+    assert O.ruze_efficiency(42e-6, 350 * GHZ) == pytest.approx(g["ruze_350GHz"], abs=6e-6)
+    assert O.kid_cutoff_hz(188e-6 * O.E_CHARGE) / GHZ == pytest.approx(g["cutoff_GHz"], abs=6e-3)
+
+
+def test_refractive_stage_expansion():
+    nu = np.array([300 * GHZ])
+    st = dict(kind="refractive", d=4e-3, n=3.41, tan_delta=1e-4, T=290.0, T_refl=100.0)
+    prim = O.expand_stage(st, nu)
+    assert len(prim) == 3
+    assert [p[1] for p in prim] == [100.0, 290.0, 100.0]
+    assert prim[0][0][0] == pytest.approx(0.70135, abs=1e-5)
+    assert len(O.expand_stage(dict(st, ar=True), nu)) == 1
+
+
+# ---------------------------------------------------------------- Johnson-Nyquist
+
+def test_johnson_nyquist_limits():
+    # Rayleigh-Jeans: h nu << k T gives k T (1 - x/2 + x^2/12).
+    T, nu = 1e4, 1 * GHZ
+    x = H * nu / (KB * T)
+    assert O.johnson_nyquist(T, nu) == pytest.approx(KB * T * (1 - x / 2 + x * x / 12), rel=1e-12)
+    # Wien: h nu >> k T gives h nu exp(-x).
+    T, nu = 1.0, 1000 * GHZ
+    x = H * nu / (KB * T)
+    assert O.johnson_nyquist(T, nu) == pytest.approx(H * nu * math.exp(-x), rel=1e-12)
+    assert O.johnson_nyquist(0.0, 300 * GHZ) == 0.0
+
+
+def test_johnson_nyquist_total_power():
+    # Single-mode blackbody: int_0^inf h nu/(e^{h nu/kT}-1) d nu = (pi^2/6) (kT)^2 / h.
+    for T in (2.725, 40.0, 290.0):
+        total, _ = integrate.quad(lambda v: float(O.johnson_nyquist(T, v)), 0, 60 * KB * T / H,
+                                  limit=400)
+        assert total == pytest.approx(math.pi ** 2 / 6 * (KB * T) ** 2 / H, rel=1e-8)
+
+
+# ---------------------------------------------------------------- cascade invariants
+
+def _mixed_stages(T):
+    return [dict(kind="reflective", eta=0.93, T=T),
+            dict(kind="ohmic", eps_ref=0.0025, nu_ref=840 * GHZ, T=T),
+            dict(kind="reflective", eta=0.85, T="sky"),
+            dict(kind="refractive", d=10e-3, n=3.4, tan_delta=1e-3, T=T, T_refl=T),
+            dict(kind="refractive", d=4e-3, n=3.41, tan_delta=1e-4, T=T, ar=True),
+            dict(kind="reflective", eta=np.linspace(0.5, 0.9, 64), T=T)]
+
+
+def test_thermal_equilibrium_invariant():
+    """All stages, the sky and the CMB at one T, no source: P_nu = B(T, nu) for any eta."""
+    nu = np.linspace(90 * GHZ, 900 * GHZ, 64)
+    rng = np.random.default_rng(3)
+    eta_atm = rng.uniform(0.01, 0.99, (5, 64))
+    for T in (4.0, 150.0, 290.0):
+        prim = O.expand_cascade(_mixed_stages(T), nu)
+        P = O.cascade(np.zeros((5, 64)), eta_atm, nu, prim, T, T, 0.85,
+                      O.ruze_efficiency(42e-6, nu), 0.5)
+        np.testing.assert_allclose(P, np.broadcast_to(O.johnson_nyquist(T, nu), P.shape), rtol=1e-12)
+
+
+def test_transparent_passthrough():
+    """eta == 1 everywhere and a transparent sky: P_nu = eta_t eta_surf eta_pol P_src + B(T_cmb)."""
+    nu = np.linspace(220 * GHZ, 440 * GHZ, 50)
+    prim = O.expand_cascade([dict(kind="reflective", eta=1.0, T=290.0),
+                             dict(kind="reflective", eta=1.0, T="sky")], nu)
+    P_src = np.random.default_rng(0).uniform(0, 1e-22, (3, 50))
+    es = O.ruze_efficiency(42e-6, nu)
+    P = O.cascade(P_src, np.ones((3, 50)), nu, prim, 273.0, 2.725, 0.85, es, 0.5)
+    np.testing.assert_allclose(P, 0.85 * es * 0.5 * P_src + O.johnson_nyquist(2.725, nu), rtol=1e-14)
+
+
+def test_cold_cascade_is_product_of_efficiencies():
+    """With every temperature at 0 K only the source survives, scaled by the product of all etas."""
+    nu = np.linspace(220 * GHZ, 440 * GHZ, 40)
+    stages = _mixed_stages(0.0)[:5]
+    prim = O.expand_cascade(stages, nu)
+    eta_atm = np.random.default_rng(1).uniform(0.2, 0.95, (4, 40))
+    P_src = np.random.default_rng(2).uniform(1e-23, 1e-22, (4, 40))
+    es = O.ruze_efficiency(42e-6, nu)
+    P = O.cascade(P_src, eta_atm, nu, prim, 0.0, 0.0, 0.85, es, 0.5)
+    n = 3.4
+    refl = 1 - ((1 - n) / (1 + n)) ** 2
+    prod = (0.93 * (1 - 0.0025 * np.sqrt(nu / (840 * GHZ))) * 0.85 * refl ** 2
+            * np.exp(-2 * np.pi * 10e-3 * 3.4 * 1e-3 * nu / O.C_LIGHT)
+            * np.exp(-2 * np.pi * 4e-3 * 3.41 * 1e-4 * nu / O.C_LIGHT))
+    np.testing.assert_allclose(P, eta_atm * prod * 0.85 * es * 0.5 * P_src, rtol=1e-13)
+
+
+def test_single_stage_emission_only():
+    """No source, CMB at 0 K, one stage: P = (1-eta_atm) eta_1 B(T_atm) + (1-eta_1) B(T_1)."""
+    nu = np.array([150 * GHZ, 350 * GHZ])
+    eta_atm = np.array([[0.8, 0.6]])
+    prim = O.expand_cascade([dict(kind="reflective", eta=0.9, T=40.0)], nu)
+    P = O.cascade(np.zeros((1, 2)), eta_atm, nu, prim, 273.0, 0.0, 0.85, np.ones(2), 0.5)
+    # Planck values by the textbook closed form at these two points, written out separately.
+    B273 = np.array([H * v / math.expm1(H * v / (KB * 273.0)) for v in nu])
+    B40 = np.array([H * v / math.expm1(H * v / (KB * 40.0)) for v in nu])
+    np.testing.assert_allclose(P[0], 0.9 * (1 - eta_atm[0]) * B273 + 0.1 * B40, rtol=1e-13)
+
+
+# ---------------------------------------------------------------- dispersive element
+
+def test_lorentzian_closed_form_integral():
+    """Grating channel on a flat unit PSD: trapezoid sum = eta_p (f/2R)[atan 2R(nu/f-1)]_a^b."""
+    nu = O.frequency_grid(220 * GHZ, 440 * GHZ, 20001)
+    w = O.trapezoid_weights(nu)
+    f_c = np.array([250 * GHZ, 331.7 * GHZ, 410 * GHZ])
+    R = np.array([500.0, 300.0, 50.0])
+    eta = O.filter_efficiency("lorentzian", f_c, R, 0.16, nu, 188e-6 * O.E_CHARGE)
+    got = O.kid_power(eta, w, np.ones((1, nu.size)))[0]
+    a, b = nu[0], nu[-1]
+    exact = 0.16 * f_c / (2 * R) * (np.arctan(2 * R * (b / f_c - 1)) - np.arctan(2 * R * (a / f_c - 1)))
+    np.testing.assert_allclose(got, exact, rtol=2e-7)
+
+
+def test_nep_closed_forms_flat_psd():
+    """Eq. 17 on a flat PSD P0 for a grating channel, against the closed-form integrals of
+    L, L^2 and nu L (x = 2R(nu/f - 1))."""
+    nu = O.frequency_grid(200 * GHZ, 500 * GHZ, 60001)
+    w = O.trapezoid_weights(nu)
+    f, R, ep = 300 * GHZ, 400.0, 0.3
+    dal, epb = 188e-6 * O.E_CHARGE, 0.4
+    eta = O.filter_efficiency("lorentzian", [f], [R], ep, nu, dal)
+    P0 = 7e-22
+    got = O.nep_squared(eta, w, np.full((1, nu.size), P0), nu, dal, epb)[0, 0]
+    xa, xb = 2 * R * (nu[0] / f - 1), 2 * R * (nu[-1] / f - 1)
+    s = f / (2 * R)
+    i_L = ep * s * (math.atan(xb) - math.atan(xa))
+    prim2 = lambda x: x / (2 * (1 + x * x)) + math.atan(x) / 2
+    i_L2 = ep * ep * s * (prim2(xb) - prim2(xa))
+    primnu = lambda x: math.atan(x) + math.log1p(x * x) / (4 * R)
+    i_nuL = ep * s * f * (primnu(xb) - primnu(xa))
+    exact = 2 * (H * P0 * i_nuL + P0 * P0 * i_L2 + (2 * dal / epb) * P0 * i_L)
+    assert got == pytest.approx(exact, rel=1e-7)
+
+
+def test_filterbank_telescoping_identity():
+    """Constant eta_peak: sum over channels of Eq. 7 = eta_p (1 - prod_ch (1 - L_ch)); all >= 0;
+    the recursion order follows centre frequency, not input order."""
+    nu = np.linspace(200 * GHZ, 460 * GHZ, 3001)
+    f_c = W.geometric_channels(220 * GHZ, 440 * GHZ, 101)
+    R = np.full(101, 300.0)
+    eta = O.filter_efficiency("filterbank", f_c, R, 0.16, nu, 188e-6 * O.E_CHARGE)
+    prod = np.ones_like(nu)
+    for f in f_c:
+        prod *= 1 - 1 / (1 + 4 * 300.0 ** 2 * (nu / f - 1) ** 2)
+    np.testing.assert_allclose(eta.sum(axis=0), 0.16 * (1 - prod), rtol=1e-12, atol=1e-15)
+    assert (eta >= 0).all()
+    perm = np.random.default_rng(0).permutation(101)
+    eta_p = O.filter_efficiency("filterbank", f_c[perm], R, 0.16, nu, 188e-6 * O.E_CHARGE)
+    np.testing.assert_array_equal(eta_p, eta[perm])
+    # The highest channel sees the bare Lorentzian (nothing upstream).
+    top = int(np.argmax(f_c))
+    np.testing.assert_allclose(eta[top], 0.16 / (1 + 4 * 300.0 ** 2 * (nu / f_c[top] - 1) ** 2), rtol=1e-15)
+
+
+def test_cutoff_masks_low_frequencies():
+    nu = np.linspace(80 * GHZ, 120 * GHZ, 401)
+    eta = O.filter_efficiency("lorentzian", [95 * GHZ], [20.0], 1.0, nu, 188e-6 * O.E_CHARGE)
+    below = nu < 90.92e9 - 1e7
+    assert (eta[0, below] == 0).all() and (eta[0, nu > 90.93e9] > 0).all()
+
+
+def test_half_power_channels_reproduce_paper_count():
+    """R = 20 over 90-180 GHz with half-power spacing gives the 15 channels of Sect. 4.1."""
+    assert W.half_power_channels(90 * GHZ, 180 * GHZ, 20.0).size == 15
+    assert W.half_power_channels(220 * GHZ, 440 * GHZ, 500.0).size == 347
+
+
+# ---------------------------------------------------------------- atmosphere
+
+def test_airmass_special_elevations():
+    tau = np.array([[0.3, 1.2, 0.05]])
+    np.testing.assert_allclose(O.atmospheric_transmission(tau, np.array([math.pi / 2])), np.exp(-tau), rtol=1e-15)
+    np.testing.assert_allclose(O.atmospheric_transmission(tau, np.array([math.pi / 6])), np.exp(-tau) ** 2, rtol=1e-14)
+
+
+def test_screen_uniform_linear_and_periodic():
+    nx, ny, pitch = 16, 12, 0.5
+    assert np.all(O.screen_bilinear(np.full((ny, nx), 0.8), np.array([-3.1, 7.7]), np.array([2.2, -9.0]), pitch) == 0.8)
+    ix, iy = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    lin = 0.3 + 0.01 * ix + 0.02 * iy
+    # Points inside the non-wrapping interior: bilinear reproduces a linear field exactly.
+    gx = np.array([1.25, 5.5, 10.75, 13.0])
+    gy = np.array([2.5, 0.0, 9.9, 7.25])
+    x = (gx - nx / 2) * pitch
+    y = (gy - ny / 2) * pitch
+    np.testing.assert_allclose(O.screen_bilinear(lin, x, y, pitch), 0.3 + 0.01 * gx + 0.02 * gy, rtol=1e-14)
+    rnd = np.random.default_rng(0).uniform(size=(ny, nx))
+    xs = np.random.default_rng(1).uniform(-20, 20, 50)
+    ys = np.random.default_rng(2).uniform(-20, 20, 50)
+    np.testing.assert_allclose(O.screen_bilinear(rnd, xs + 3 * nx * pitch, ys - 2 * ny * pitch, pitch),
+                               O.screen_bilinear(rnd, xs, ys, pitch), rtol=1e-12)
+    # Grid nodes return the node value; cell (0,0) sits at (-nx/2, -ny/2) * pitch.
+    np.testing.assert_allclose(O.screen_bilinear(rnd, np.array([-nx / 2 * pitch, 0.0]),
+                                                 np.array([-ny / 2 * pitch, 0.0]), pitch),
+                               [rnd[0, 0], rnd[ny // 2, nx // 2]], rtol=1e-15)
+
+
+def test_frozen_flow_coordinates():
+    """Eq. 9: a stare drifts with the wind along x only; y depends on elevation offset only."""
+    t = np.array([0.0, 1.0, 10.0])
+    x, y = O.screen_coordinates(0.0, 0.0, 0.0, 0.0, t, 1537.0, 10.0)
+    np.testing.assert_allclose(x, 10.0 * t)
+    np.testing.assert_allclose(y, 0.0)
+    x, y = O.screen_coordinates(0.0, 0.0, 1e-3, 2e-3, t, 1000.0, 0.0)
+    np.testing.assert_allclose(x, 1000 * math.tan(1e-3))
+    np.testing.assert_allclose(y, 1000 * math.tan(2e-3))
+
+
+def test_opacity_interpolation_and_clamp():
+    nu = np.linspace(220 * GHZ, 440 * GHZ, 7)
+    pw = np.arange(11) * 0.5
+    tab = 0.02 + np.outer(pw, np.linspace(0.05, 0.2, 7))          # exactly linear in PWV
+    got = O.zenith_opacity(tab, 0.0, 0.5, np.array([0.0, 1.3, 2.75, 5.0]))
+    want = 0.02 + np.outer([0.0, 1.3, 2.75, 5.0], np.linspace(0.05, 0.2, 7))
+    np.testing.assert_allclose(got, want, rtol=1e-14)
+    np.testing.assert_allclose(O.zenith_opacity(tab, 0.0, 0.5, np.array([-1.0, 9.0])), tab[[0, -1]], rtol=1e-15)
+    np.testing.assert_allclose(O.eta_to_opacity(np.exp(-tab)), tab, rtol=1e-12)
+
+
+def test_epl_conversion():
+    np.testing.assert_allclose(O.epl_to_pwv(np.array([0.0, 6.587]), 1.0), [1.0, 2.0])
+
+
+# ---------------------------------------------------------------- source and scan
+
+def test_source_bilinear_linear_cube_and_outside():
+    n_az, n_el, nf = 6, 5, 3
+    ia, ie = np.meshgrid(np.arange(n_az), np.arange(n_el), indexing="ij")
+    cube = (1.0 + 2.0 * ia + 3.0 * ie)[:, :, None] * np.array([1.0, 0.5, 0.25])
+    az0, daz, el0, de = -0.5, 0.25, 0.75, 0.125       # exactly representable grid: edges are exact
+    u = np.array([0.0, 2.5, 5.0, 4.9, 3.3])
+    v = np.array([0.0, 1.25, 4.0, 0.1, 3.999])
+    got = O.source_bilinear(cube, az0, daz, el0, de, az0 + u * daz, el0 + v * de)
+    np.testing.assert_allclose(got, (1 + 2 * u + 3 * v)[:, None] * np.array([1.0, 0.5, 0.25]), rtol=1e-13)
+    out = O.source_bilinear(cube, az0, daz, el0, de, np.array([az0 - 1e-6, az0, az0 + 6 * daz]),
+                            np.array([el0, el0 - 1e-6, el0]))
+    assert (out == 0).all()
+
+
+def test_scan_patterns():
+    t = np.linspace(0, 100, 1001)
+    phi, th = O.scan_pattern("daisy", (1e-4, 2 * math.pi * 1.54, 2 * math.pi * 1.54 / 50), t)
+    assert phi[0] == 0 and th[0] == 0
+    assert np.all(np.hypot(phi, th) <= 1e-4 + 1e-18)
+    phi, th = O.scan_pattern("raster", (1e-3, 2e-4, 1e-4, 5), t)
+    assert np.all(np.abs(phi) <= 1e-3 + 1e-15)
+    assert set(np.round(th / 1e-4, 9)) <= {-2, -1, 0, 1, 2}
+    # first row runs +phi, second row -phi, rows step by one position
+    assert phi[1] > phi[0] and phi[101] < phi[100] and th[101] - th[99] == pytest.approx(1e-4)
+    tab = np.random.default_rng(0).uniform(size=(20, 2))
+    p, q = O.scan_pattern("custom", None, np.zeros(3), np.array([0, 7, 19]), tab)
+    np.testing.assert_array_equal(np.stack([p, q], 1), tab[[0, 7, 19]])
+
+
+# ---------------------------------------------------------------- random numbers
+
+def test_philox_known_answers():
+    """Known-answer vectors of Philox4x32-10 from the Random123 distribution (Salmon et al. 2011)."""
+    cases = [
+        ((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+        ((0xFFFFFFFF,) * 4, (0xFFFFFFFF, 0xFFFFFFFF), (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+        ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+         (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
+    ]
+    for ctr, key, want in cases:
+        got = O.philox4x32_10(*ctr, *key)
+        assert tuple(int(g) for g in got) == want
+
+
+def test_normals_are_standard_gaussian():
+    n = np.arange(1 << 16)
+    zw = O.white_normals(5, n[:, None], 3, np.arange(4)[None, :]).ravel()
+    zp = O.pink_normals(5, n, 3, 11)
+    for z in (zw, zp):
+        assert abs(z.mean()) < 5 / math.sqrt(z.size)
+        assert abs(z.var() - 1) < 5 * math.sqrt(2 / z.size)
+        assert stats.kstest(z, "norm").pvalue > 1e-4
+    # distinct streams are uncorrelated
+    zw2 = O.white_normals(5, n, 3, 11)
+    assert abs(np.corrcoef(zw2, zp)[0, 1]) < 5 / math.sqrt(n.size)
+    assert abs(np.corrcoef(zp[:-1], zp[1:])[0, 1]) < 5 / math.sqrt(n.size)
+
+
+def test_white_noise_variance_matches_sigma():
+    """Eqs. 18-19: the sample variance of sigma z_w is sigma^2 within a chi^2 99.99% band,
+    and the one-sided white PSD equals NEP^2."""
+    sigma = 3e-17
+    z = O.white_normals(9, np.arange(40000), 0, 2)
+    x = sigma * z
+    lo, hi = stats.chi2.ppf([5e-5, 1 - 5e-5], x.size - 1) / (x.size - 1)
+    assert lo < x.var() / sigma ** 2 < hi
+    fs = 160.0
+    f, pxx = signal.welch(x, fs=fs, nperseg=1024)
+    nep2 = sigma ** 2 / (0.5 * fs)
+    assert np.mean(pxx[1:-1]) == pytest.approx(nep2, rel=0.03)
+
+
+# ---------------------------------------------------------------- pink noise
+
+def test_pink_partial_fractions_equal_product_form():
+    for alpha in (0.5, 1.0, 1.5):
+        d = O.pink_design(alpha, 1e-34, 1 / 1200, 160.0)
+        f = np.logspace(-4, math.log10(80), 50)
+        zinv = np.exp(-2j * np.pi * f / 160.0)
+        H_par = d.d + np.sum(d.r[None, :] / (1 - d.a[None, :] * zinv[:, None]), axis=1)
+        np.testing.assert_allclose(H_par, O.pink_transfer(d.a, d.b, f, 160.0), rtol=1e-10)
+
+
+def test_pink_alpha_zero_is_white_at_level_A():
+    d = O.pink_design(0.0, 4e-34, 1 / 600, 160.0)
+    assert d.d == pytest.approx(1.0) and np.allclose(d.r, 0)
+    z = O.pink_normals(1, np.arange(1000), 0, 0)
+    y, _ = O.pink_filter_run(d, z)
+    np.testing.assert_allclose(y, d.g * z, rtol=1e-12)
+    assert 2 * d.g ** 2 / 160.0 == pytest.approx(4e-34)
+
+
+def test_pink_design_follows_power_law():
+    fs, fmin = 160.0, 1 / 1200
+    for alpha in (0.5, 1.0, 1.5):
+        d = O.pink_design(alpha, 1e-34, fmin, fs)
+        f = np.logspace(math.log10(10 * fmin), math.log10(fs / 20), 200)
+        S = 2 / fs * d.g ** 2 * np.abs(O.pink_transfer(d.a, d.b, f, fs)) ** 2
+        slope = np.polyfit(np.log10(f), np.log10(S), 1)[0]
+        assert slope == pytest.approx(-alpha, abs=0.05)
+        # ripple around the power law A f^-alpha stays within 1.5 dB in that band
+        assert np.max(np.abs(10 * np.log10(S / (1e-34 * f ** -alpha)))) < 1.5
+
+
+def test_pink_output_psd_matches_transfer_function():
+    """Welch PSD of the filtered pink stream against (2/f_s) g^2 |H|^2 (Eq. 20 level and slope)."""
+    fs = 160.0
+    d = O.pink_design(1.2, 2e-34, 0.05, fs)
+    n = 1 << 17
+    z = O.pink_normals(3, np.arange(n), 2, 5)
+    y, _ = O.pink_filter_run(d, z)
+    y = y[4096:]                      # drop the start-up transient of the zero initial state
+    f, pxx = signal.welch(y, fs=fs, nperseg=4096)
+    sel = (f > 0.5) & (f < 60)
+    S = 2 / fs * d.g ** 2 * np.abs(O.pink_transfer(d.a, d.b, f[sel], fs)) ** 2
+    ratio = pxx[sel] / S
+    assert np.median(ratio) == pytest.approx(1.0, abs=0.08)
+    assert np.all(np.abs(np.log(ratio)) < 0.6)
+
+
+def test_pink_state_carry_equals_one_pass():
+    d = O.pink_design(1.0, 1e-34, 0.01, 160.0)
+    z = O.pink_normals(0, np.arange(3000), 0, 0)
+    y_all, s_all = O.pink_filter_run(d, z)
+    y1, s1 = O.pink_filter_run(d, z[:1234])
+    y2, s2 = O.pink_filter_run(d, z[1234:], s1)
+    np.testing.assert_allclose(np.concatenate([y1, y2]), y_all, rtol=1e-13)
+    np.testing.assert_allclose(s2, s_all, rtol=1e-13)
+
+
+# ---------------------------------------------------------------- whole path
+
+def _uniform_stare_scenario():
+    sc = W.scenario("single_pixel_small", nt_total=64)
+    sc["atmosphere"]["screen"] = np.full((32, 32), 1.2, dtype=np.float32)
+    sc["source"]["cube"] = np.zeros_like(sc["source"]["cube"])
+    return sc
+
+
+def test_uniform_sky_stare_is_constant_in_time():
+    sc = _uniform_stare_scenario()
+    parts = O.simulate(sc, 0, 64, white=False, pink=False, return_parts=True)
+    pk = parts["p_kid"][:, 0, :]
+    np.testing.assert_allclose(pk, np.broadcast_to(pk[0], pk.shape), rtol=1e-13)
+    assert np.allclose(parts["pwv"], 1.2)
+
+
+def test_whole_path_thermal_equilibrium_gives_filter_weighted_planck():
+    """Everything at one temperature, no source: P_KID = sum_nu w eta_filt B(T) for any sky."""
+    sc = W.scenario("single_pixel_small", nt_total=32)
+    T = 200.0
+    sc["T_cmb"] = T
+    sc["atmosphere"]["T_atm"] = T
+    sc["cascade"] = [dict(s, T=(T if s["T"] != "sky" else "sky")) for s in sc["cascade"]]
+    sc["source"]["cube"] = np.zeros_like(sc["source"]["cube"])
+    parts = O.simulate(sc, 0, 32, white=False, pink=False, return_parts=True)
+    inst = O.build_instrument(sc)
+    B = np.array([H * v / math.expm1(H * v / (KB * T)) for v in inst.nu])
+    want = (inst.eta_filt * inst.w) @ B
+    np.testing.assert_allclose(parts["p_kid"][:, 0, :], np.broadcast_to(want, (32, want.size)), rtol=1e-12)
+
+
+def test_chunked_simulation_equals_single_pass():
+    sc = W.scenario("single_pixel_small", nt_total=200)
+    full = O.simulate(sc, 0, 200, return_parts=True)
+    a = O.simulate(sc, 0, 77, return_parts=True)
+    b = O.simulate(sc, 77, 123, pink_state=a["pink_state"], return_parts=True)
+    np.testing.assert_allclose(np.concatenate([a["total"], b["total"]]), full["total"], rtol=1e-12)
