@@ -1,0 +1,295 @@
+/*
+ * gateau.h -- C ABI of the B300 time-ordered-data simulator (hot path of
+ * gateau, arXiv 2604.23305).
+ *
+ * For every time sample n and IFU spaxel i the library computes, on one GPU:
+ *   screen PWV (Sect. 2.4, Eq. 9) -> zenith opacity and airmass (Eq. 10)
+ *   -> source sample (Sect. 2.4) -> radiative-transfer cascade (Sect. 2.5,
+ *   Eqs. 11-15) -> dispersive element (Sect. 2.3, Eqs. 6-7; Sect. 2.5, Eq. 16)
+ *   -> photon noise (Sect. 2.6, Eqs. 17-19) + pink noise (Sect. 2.6, Eq. 20)
+ *   -> out[n - t0][i][ch] = P_KID + P_wn + P_pn in W (Sect. 2.7, Eq. 21).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers are plain host or device addresses; no library types cross the
+ *     boundary except the opaque plan.  "host" pointers are read during the
+ *     call only; "device" pointers must be valid CUDA device memory of the
+ *     plan's device.  Setters COPY their inputs into plan-owned memory: the
+ *     caller may free or reuse its buffers when the setter returns.
+ *   - Arrays are C-contiguous, row-major, in the shapes given below.
+ *   - Angles are radians, frequencies Hz, temperatures K, lengths m, PWV mm,
+ *     spectral power W/Hz, output power W.
+ *   - Every call returns a gateau_status; on failure a thread-local message is
+ *     available from gateau_last_error().  Argument errors are detected on the
+ *     host before anything is enqueued.  No entry point traps or aborts.
+ *   - A plan is used by one host thread at a time.
+ */
+#ifndef GATEAU_H
+#define GATEAU_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GATEAU_ABI_VERSION 1
+
+typedef struct gateau_plan gateau_plan;
+
+typedef enum {
+    GATEAU_OK = 0,
+    GATEAU_EINVAL = -1,       /* an argument is out of range or inconsistent        */
+    GATEAU_ENOMEM = -2,       /* host or device allocation failed                    */
+    GATEAU_ECUDA = -3,        /* a CUDA runtime call failed (message has the name)   */
+    GATEAU_EORDER = -4,       /* t0 neither 0 nor the end of the previous chunk      */
+    GATEAU_ESTATE = -5,       /* a required setter has not been called               */
+    GATEAU_EDEVICE = -6,      /* the device status word reports an error bit         */
+    GATEAU_ETIMEOUT = -7,     /* a bounded device-side wait ran out                  */
+    GATEAU_EUNSUPPORTED = -8  /* the device cannot run the requested path            */
+} gateau_status;
+
+/* Contraction precision of the dispersive-element integral (Sect. 2.5, Eq. 16). */
+enum {
+    GATEAU_PREC_FP32 = 0,     /* FP32 spectra, FP32 SIMT contraction                 */
+    GATEAU_PREC_BF16X3 = 1    /* fused kernel: FP32 spectra split into BF16 hi+lo,
+                                 3 tcgen05 products (hi*hi + hi*lo + lo*hi) with FP32
+                                 accumulation for P_KID; 1 BF16 product per noise term */
+};
+
+/* Where a setter's array lives. */
+enum { GATEAU_MEM_HOST = 0, GATEAU_MEM_DEVICE = 1 };
+
+/* Scan patterns (Sect. 2.4).  params:
+ *   STARE  : none                                   phi = theta = 0
+ *   DAISY  : r_petal, omega, Omega (Eq. 8)          phi = r cos(Omega t) sin(omega t),
+ *                                                   theta = r sin(Omega t) sin(omega t)
+ *   RASTER : half_width, speed, row_step, n_rows    boustrophedon rows in azimuth of
+ *            period 2 half_width/speed, row k running +phi (even k) or -phi (odd k),
+ *            elevation walking the n_rows positions up and down, centred on 0
+ *   CUSTOM : none; a [n_custom][2] table of (phi, theta) indexed by the sample number */
+enum { GATEAU_SCAN_STARE = 0, GATEAU_SCAN_DAISY = 1, GATEAU_SCAN_RASTER = 2, GATEAU_SCAN_CUSTOM = 3 };
+
+/* Dispersive elements (Sect. 2.3). */
+enum {
+    GATEAU_DISP_FILTERBANK = 0,   /* Eq. 7: channels fed in series, highest f first          */
+    GATEAU_DISP_LORENTZIAN = 1,   /* Eq. 6: independent Lorentzians (grating)                */
+    GATEAU_DISP_CUSTOM = 2        /* user eta_filt[ch][nu] (measured filters, multichroic)   */
+};
+
+/* Cascade stage kinds (Sect. 2.5). */
+enum {
+    GATEAU_STAGE_REFLECTIVE = 0,  /* Eq. 12 with eta (scalar or per frequency)               */
+    GATEAU_STAGE_OHMIC = 1,       /* Eq. 12 with eta = 1 - eps_ref sqrt(nu/nu_ref) (Eq. 13)  */
+    GATEAU_STAGE_REFRACTIVE = 2   /* Eq. 15, Eq. 14, Eq. 15 (three primitive stages), or Eq. 14
+                                     alone when anti-reflection coated                        */
+};
+
+/* A stage temperature equal to GATEAU_T_SKY couples the stage to the sky: its
+ * emission is (1 - eta_atm) B(T_atm) + eta_atm B(T_cmb) for the same spaxel and
+ * time (Sect. 2.5, secondary spillover). */
+#define GATEAU_T_SKY (-1.0)
+
+/* Noise switches (plan-wide).  Bit set = component added. */
+enum { GATEAU_NOISE_WHITE = 1, GATEAU_NOISE_PINK = 2 };
+
+/* Device status bits read by gateau_plan_status(). */
+enum {
+    GATEAU_STATUS_PWV_CLAMPED = 1u,    /* informational: a PWV left the table range (clamped)   */
+    GATEAU_STATUS_WAIT_TIMEOUT = 2u,   /* error: a pipeline wait in the fused kernel ran out     */
+    GATEAU_STATUS_BAD_INDEX = 4u       /* error: an index check failed and the access was skipped */
+};
+
+/* Plan description (everything fixed for a simulation). */
+typedef struct {
+    int n_freq;                    /* spectral points, >= 2                                     */
+    double f_lo_hz, f_hi_hz;       /* uniform grid, both end points included                    */
+    double f_sample_hz;            /* readout rate; sample n is at t = n / f_sample (Eq. 18)   */
+    int n_pix;                     /* spaxels, >= 1                                             */
+    const double* pix_offsets_rad; /* host [n_pix][2] (dphi_i, dtheta_i) (Sect. 2.3)           */
+    double T_atm_K;                /* atmosphere temperature (Sect. 2.4)                        */
+    double T_cmb_K;                /* CMB temperature, 2.725 in the paper (Sect. 2.5, Eq. 11)  */
+    double h_column_m;             /* PWV column height (Eq. 9)                                 */
+    double wind_mps;               /* frozen-flow wind along +x (Eq. 9)                        */
+    double eta_taper;              /* taper efficiency (Sect. 2.3)                              */
+    double rho_surf_m;             /* rms surface roughness for the Ruze factor (Eq. 5)        */
+    double eta_pol;                /* polarisation efficiency (Eq. 11)                          */
+    double delta_al_J;             /* superconducting gap (Sect. 2.3); 2 Delta/h is the cutoff */
+    double eta_pb;                 /* pair-breaking efficiency (Sect. 2.3, Eq. 17)             */
+    unsigned long long seed;       /* Philox4x32-10 key for all noise draws                     */
+    int precision;                 /* GATEAU_PREC_*                                             */
+    int noise_flags;               /* GATEAU_NOISE_* bits                                       */
+    double pink_f_min_hz;          /* lowest pole of the pink-noise filter, e.g. 1/T_scan      */
+} gateau_plan_desc;
+
+/* One cascade stage, after the atmosphere (stage 0 is always the atmosphere). */
+typedef struct {
+    int kind;                      /* GATEAU_STAGE_*                                            */
+    double T_K;                    /* physical temperature, or GATEAU_T_SKY                     */
+    double eta;                    /* REFLECTIVE: efficiency when eta_nu is NULL                */
+    const double* eta_nu;          /* REFLECTIVE: host [n_freq] efficiencies, or NULL           */
+    double eps_ref, nu_ref_hz;     /* OHMIC: reference emissivity at nu_ref                    */
+    double d_m, n_index, tan_delta;/* REFRACTIVE: thickness, refractive index, loss tangent    */
+    double T_refl_K;               /* REFRACTIVE: temperature seen by the two surface passes   */
+    int ar_coated;                 /* REFRACTIVE: nonzero drops the surface passes              */
+} gateau_stage;
+
+/* Sizes of a finished plan. */
+typedef struct {
+    int n_freq, n_freq_padded;     /* spectral points and the padded contraction depth          */
+    int n_ch, n_pix, n_pole;       /* channels, spaxels, pink-filter poles                      */
+    long long next_t0;             /* first sample of the next chunk                            */
+    size_t device_bytes;           /* device memory owned by the plan                           */
+} gateau_plan_info;
+
+/* Host-built FP64 tables, for inspection and tests (gateau_plan_get_vector). */
+enum {
+    GATEAU_VEC_NU = 0,             /* [n_freq] grid (Hz)                                        */
+    GATEAU_VEC_WEIGHT = 1,         /* [n_freq] trapezoid weights (Hz)                           */
+    GATEAU_VEC_ETA_FILT = 2,       /* [n_ch][n_freq] eta_filt (Eqs. 6-7, cutoff applied)        */
+    GATEAU_VEC_C0 = 3,             /* [n_freq] cascade constant term (W/Hz), see gateau_set_cascade */
+    GATEAU_VEC_C1 = 4,             /* [n_freq] coefficient of (1 - eta_atm) (W/Hz)              */
+    GATEAU_VEC_C2 = 5,             /* [n_freq] coefficient of eta_atm * P_src                   */
+    GATEAU_VEC_PINK_A = 6,         /* [n_ch][n_pole] discrete poles a_j                         */
+    GATEAU_VEC_PINK_R = 7,         /* [n_ch][n_pole] residues r_j (gain folded in)              */
+    GATEAU_VEC_PINK_D = 8          /* [n_ch] direct term d (gain folded in)                     */
+};
+
+/* Library version string and the calling thread's last error message. */
+const char* gateau_version(void);
+const char* gateau_last_error(void);
+
+/* Number of CUDA devices visible (0 on a machine without a GPU; never fails). */
+int gateau_device_count(void);
+
+/* Create a plan from desc (copied).  Builds the frequency grid on the host;
+ * allocates no device memory yet.  EINVAL on inconsistent sizes.  *out is set
+ * to NULL on failure. */
+gateau_status gateau_plan_create(const gateau_plan_desc* desc, gateau_plan** out);
+
+/* Free every host and device resource of the plan (NULL is a no-op).  The
+ * caller must have synchronised any stream the plan ran on. */
+void gateau_plan_destroy(gateau_plan* plan);
+
+/* Source cube P_nu,src (Sect. 2.2, after the beam convolution of Eq. 1), W/Hz,
+ * cube[n_az][n_el][n_freq] float32 on the grid az = az0 + ia*daz, el = el0 +
+ * ie*del (el is absolute elevation).  Bilinear sampling, zero outside the grid
+ * (Sect. 2.4).  n_az, n_el >= 2, daz, del > 0.  mem: GATEAU_MEM_HOST/DEVICE. */
+gateau_status gateau_set_source_cube(gateau_plan* plan, const float* cube, int n_az, int n_el,
+                                     double az0_rad, double daz_rad, double el0_rad, double del_rad,
+                                     int mem);
+
+/* PWV screen screen[ny][nx] float32 (mm) on a periodic grid of pitch pitch_m;
+ * cell (0,0) sits at x = -nx/2*pitch, y = -ny/2*pitch (Sect. 2.4, Eq. 9).  When
+ * is_epl is nonzero the values are extra path length and become
+ * PWV = EPL/6.587 + pwv0_mm (Sect. 2.2, Eq. 4).  nx, ny >= 2. */
+gateau_status gateau_set_atmosphere_screen(gateau_plan* plan, const float* screen, int nx, int ny,
+                                           double pitch_m, int is_epl, double pwv0_mm, int mem);
+
+/* Zenith table table[n_pwv][n_freq] float32 on the PWV grid pwv_min + j*dpwv
+ * (Sect. 2.4): opacity tau_z when is_opacity is nonzero, else transmission
+ * eta_z (stored as -ln max(eta_z, 1e-30)).  Interpolated linearly in opacity;
+ * PWV outside the grid is clamped (status bit GATEAU_STATUS_PWV_CLAMPED).
+ * n_pwv >= 2, dpwv > 0. */
+gateau_status gateau_set_atmosphere_table(gateau_plan* plan, const float* table, int n_pwv,
+                                          double pwv_min_mm, double dpwv_mm, int is_opacity, int mem);
+
+/* Cascade after the atmosphere, in the order the signal meets it (Sect. 2.5,
+ * Eqs. 12-15; Tables 1-2).  The library collapses the literal stage-by-stage
+ * recurrence into P_nu = c0 + c1 (1 - eta_atm) + c2 eta_atm P_src, an exact
+ * identity of Eq. 12 because every stage is affine in P and in eta_atm; c0, c1,
+ * c2 are built in FP64 (gateau_plan_get_vector).  0 <= n_stage <= 64. */
+gateau_status gateau_set_cascade(gateau_plan* plan, int n_stage, const gateau_stage* stages);
+
+/* Dispersive element (Sect. 2.3, Eqs. 6-7): n_ch channels with centre f_c_hz[ch],
+ * resolving power R[ch] and peak efficiency eta_peak[ch] (host arrays), or, for
+ * GATEAU_DISP_CUSTOM, custom_eta[n_ch][n_freq] (host FP64) and f_c/R/eta_peak
+ * ignored.  Frequencies below 2 Delta_Al / h are zeroed.  1 <= n_ch <= 4096. */
+gateau_status gateau_set_dispersive_element(gateau_plan* plan, int kind, int n_ch,
+                                            const double* f_c_hz, const double* R,
+                                            const double* eta_peak, const double* custom_eta);
+
+/* Pink detector noise (Sect. 2.6, Eq. 20) per channel: one-sided PSD level
+ * A[ch] (W^2/Hz at 1 Hz, 0 disables the channel) and slope alpha[ch] in
+ * [0, 3] (host arrays [n_ch]).  Realised by a pole-zero filter: poles at
+ * f_min 10^(j/3) up to f_sample/2, zeros 10^(alpha/6) above each pole,
+ * matched-z, parallel (partial-fraction) form, zero state at sample 0.
+ * Requires gateau_set_dispersive_element first (ESTATE otherwise). */
+gateau_status gateau_set_pink_noise(gateau_plan* plan, const double* A, const double* alpha);
+
+/* Scan pattern (Sect. 2.4, Eq. 8) with scan offset (phi0, theta0).  params has
+ * n_params doubles as listed at GATEAU_SCAN_*.  CUSTOM takes custom[n_custom][2]
+ * (phi, theta) per sample (host or device per mem); runs may not go past
+ * n_custom samples (EINVAL). */
+gateau_status gateau_set_scan(gateau_plan* plan, int kind, const double* params, int n_params,
+                              double phi0_rad, double theta0_rad, const double* custom,
+                              long long n_custom, int mem);
+
+/* Simulate samples n = t0 .. t0+nt-1 for all spaxels into dev_out
+ * [nt][n_pix][n_ch] float32 (W), device memory owned by the caller.  Enqueued
+ * on `stream` (a cudaStream_t, NULL = legacy default stream); returns without
+ * synchronising.  t0 must be 0 (restarts the pink-noise state) or the end of
+ * the previous chunk (EORDER otherwise), so a scan may be produced in chunks
+ * of any size with results identical to one call.  The first call after a
+ * setter uploads derived tables (synchronous).  ESTATE if the source,
+ * screen, table, cascade, dispersive element or scan is missing. */
+gateau_status gateau_run(gateau_plan* plan, long long t0, long long nt, float* dev_out, void* stream);
+
+/* Same as gateau_run but writes to host memory host_out[nt][n_pix][n_ch];
+ * the library simulates in chunks on `stream` and copies each chunk back
+ * while the next one runs.  Synchronous: returns when host_out is complete.
+ * Page-locked host_out gives the full copy bandwidth. */
+gateau_status gateau_run_host(gateau_plan* plan, long long t0, long long nt, float* host_out,
+                              void* stream);
+
+/* Synchronise the plan's last stream and read (and clear) the device status
+ * word into *flags (GATEAU_STATUS_* bits).  Returns EDEVICE when an error bit
+ * (anything but GATEAU_STATUS_PWV_CLAMPED) is set, ETIMEOUT for WAIT_TIMEOUT. */
+gateau_status gateau_plan_status(gateau_plan* plan, unsigned int* flags);
+
+/* Sizes and device memory of the plan (after all setters). */
+gateau_status gateau_plan_get_info(gateau_plan* plan, gateau_plan_info* info);
+
+/* Copy a host-built FP64 table (GATEAU_VEC_*) into out, which holds `count`
+ * doubles; EINVAL when count is smaller than the table. */
+gateau_status gateau_plan_get_vector(gateau_plan* plan, int which, double* out, size_t count);
+
+/* Checkpoint / resume of the chunked simulation: the next sample index and the
+ * pink-filter states pink_state[n_pix][n_ch][n_pole] (FP64 host; may be NULL in
+ * get).  Synchronises the plan's last stream. */
+gateau_status gateau_plan_get_state(gateau_plan* plan, long long* next_t0, double* pink_state);
+gateau_status gateau_plan_set_state(gateau_plan* plan, long long next_t0, const double* pink_state);
+
+/* Phase timing.  With timing enabled, every run records CUDA events on its
+ * stream around each phase; gateau_plan_get_timing synchronises the plan's last
+ * stream, adds the elapsed milliseconds per phase since the previous call into
+ * ms[GATEAU_PHASE_COUNT] (which it zeroes first), reports the runs and kernel
+ * launches counted in that interval, and restarts the interval.  Launches are
+ * counted whether or not timing is enabled. */
+enum {
+    GATEAU_PHASE_ROWS = 0,         /* per-row scan, pointing, PWV, airmass, source cell      */
+    GATEAU_PHASE_SPECTRUM = 1,     /* FP32 path only: spectra materialised in HBM            */
+    GATEAU_PHASE_CONTRACT = 2,     /* contraction + photon noise (fused kernel for BF16X3)   */
+    GATEAU_PHASE_PINK = 3,         /* pink-noise scan                                        */
+    GATEAU_PHASE_COUNT = 4
+};
+gateau_status gateau_plan_set_timing(gateau_plan* plan, int enable);
+gateau_status gateau_plan_get_timing(gateau_plan* plan, double* ms, long long* runs, long long* launches);
+
+/* Packed-hexagon spaxel layout (Sect. 2.3): circumradius R_hex spaxels (0..64),
+ * spacing spacing_rad; writes 1 + 3 R (R+1) (dphi, dtheta) pairs into
+ * out[count][2] (host) in rings from the centre.  Returns EINVAL if count is
+ * too small; *n_out receives the spaxel count. */
+gateau_status gateau_hex_offsets(int R_hex, double spacing_rad, double* out, int count, int* n_out);
+
+/* Serving: simulate several plans' chunks on one stream.  plans[k] runs samples
+ * t0s[k] .. t0s[k]+nts[k]-1 into outs[k] (device) exactly as gateau_run would,
+ * with the same chunk-order rules and bit-identical results; the row-setup
+ * kernels of all k are batched into one launch.  0 < n <= 256; the whole batch
+ * is validated before anything is enqueued. */
+gateau_status gateau_run_batch(gateau_plan* const* plans, const long long* t0s, const long long* nts,
+                               float* const* outs, int n, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GATEAU_H */

@@ -210,6 +210,34 @@ def filter_efficiency(kind: str, f_c, R, eta_peak, nu: np.ndarray,
 
 
 # ---------------------------------------------------------------------------
+# Spaxel layout (Sect. 2.3)
+# ---------------------------------------------------------------------------
+
+def hex_offsets(R_hex: int, spacing_rad: float) -> np.ndarray:
+    """Packed hexagon of circumradius R_hex spaxels (excluding the centre), spacing along the radius.
+
+    Ring k holds the 6k spaxels at hexagonal distance k: start from the corner
+    (k*spacing, 0) and walk its six sides of k steps each, turning by 60 degrees.
+    Spaxels are returned ring by ring, each ring ordered by polar angle in [0, 2 pi).
+    """
+    pts = [(0.0, 0.0, 0, 0.0)]
+    for k in range(1, R_hex + 1):
+        ring = []
+        x, y = k * spacing_rad, 0.0
+        for side in range(6):
+            ang = math.radians(120 + 60 * side)            # direction of this side
+            for _ in range(k):
+                ring.append((x, y))
+                x += spacing_rad * math.cos(ang)
+                y += spacing_rad * math.sin(ang)
+        for (x, y) in ring:
+            a = math.atan2(y, x)
+            pts.append((x, y, k, a + 2 * math.pi if a < 0 else a))
+    pts.sort(key=lambda p: (p[2], p[3]))
+    return np.array([[p[0], p[1]] for p in pts], dtype=F64)
+
+
+# ---------------------------------------------------------------------------
 # Scan patterns and pointing (Sect. 2.4, Eq. 8)
 # ---------------------------------------------------------------------------
 

@@ -1,0 +1,856 @@
+// C ABI of the simulator: plan object, setters, run orchestration.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "gateau_internal.h"
+
+using namespace gateau;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+gateau_status fail(gateau_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define GATEAU_CUDA(call)                                                                         \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(e_ == cudaErrorMemoryAllocation ? GATEAU_ENOMEM : GATEAU_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                       \
+    } while (0)
+
+// Grow-only device buffer.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t n) {
+        if (n <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e == cudaSuccess) bytes = n;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T>
+    T* as() const {
+        return static_cast<T*>(p);
+    }
+};
+
+}  // namespace
+
+struct gateau_plan {
+    gateau_plan_desc desc{};
+    std::vector<double> pix_off;      // [n_pix][2]
+    std::vector<double> nu, w;
+    int Kp = 0;
+
+    // setters' state
+    bool has_cube = false, has_screen = false, has_table = false, has_cascade = false, has_disp = false,
+         has_scan = false, has_pink = false;
+    int n_az = 0, n_el = 0;
+    double az0 = 0, daz = 0, el0 = 0, del = 0;
+    int nx = 0, ny = 0;
+    double pitch = 0;
+    int n_pwv = 0;
+    double pwv_min = 0, dpwv = 0;
+    std::vector<StageSpec> stages;
+    int disp_kind = 0, n_ch = 0;
+    std::vector<double> eta_filt;      // [n_ch][n_freq]
+    std::vector<double> pink_A, pink_alpha;
+    int scan_kind = GATEAU_SCAN_STARE;
+    double sp[kMaxScanParams] = {0};
+    double phi0 = 0, theta0 = 0;
+    long long n_custom = 0;
+
+    // derived host tables
+    std::vector<double> c0, c1, c2;
+    int n_pole = 0;
+    std::vector<double> pink_a, pink_r, pink_d;
+    bool dirty = true;
+
+    // device memory
+    DevBuf d_pix, d_cube, d_screen, d_tau, d_custom, d_c, d_HGQ, d_fusedB, d_pink, d_state, d_status;
+    DevBuf d_rows, d_X, d_agg, d_stage[2];
+    FusedOperands fused{};
+    int n_ch_pad = 0;
+    int n_sm = 148;
+    long long next_t0 = 0;
+    cudaStream_t last_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_done[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
+    // phase timing: pairs of events per phase and run, resolved in gateau_plan_get_timing
+    bool timing = false;
+    struct TimedRun { cudaEvent_t ev[GATEAU_PHASE_COUNT][2]; bool used[GATEAU_PHASE_COUNT]; };
+    std::vector<TimedRun> timed;
+    std::vector<cudaEvent_t> ev_pool;
+    long long runs = 0, launches = 0;
+
+    ~gateau_plan() {
+        DevBuf* bufs[] = {&d_pix, &d_cube, &d_screen, &d_tau, &d_custom, &d_c, &d_HGQ, &d_fusedB, &d_pink,
+                          &d_state, &d_status, &d_rows, &d_X, &d_agg, &d_stage[0], &d_stage[1]};
+        for (DevBuf* b : bufs) b->release();
+        for (int i = 0; i < 2; ++i) {
+            if (ev_done[i]) cudaEventDestroy(ev_done[i]);
+            if (ev_copied[i]) cudaEventDestroy(ev_copied[i]);
+        }
+        if (copy_stream) cudaStreamDestroy(copy_stream);
+        for (TimedRun& t : timed)
+            for (int ph = 0; ph < GATEAU_PHASE_COUNT; ++ph)
+                if (t.used[ph]) {
+                    cudaEventDestroy(t.ev[ph][0]);
+                    cudaEventDestroy(t.ev[ph][1]);
+                }
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+size_t device_bytes(const gateau_plan* p) {
+    const DevBuf* bufs[] = {&p->d_pix, &p->d_cube, &p->d_screen, &p->d_tau, &p->d_custom, &p->d_c,
+                            &p->d_HGQ, &p->d_fusedB, &p->d_pink, &p->d_state, &p->d_status, &p->d_rows,
+                            &p->d_X, &p->d_agg, &p->d_stage[0], &p->d_stage[1]};
+    size_t s = 0;
+    for (const DevBuf* b : bufs) s += b->bytes;
+    return s;
+}
+
+cudaMemcpyKind kind_of(int mem) { return mem == GATEAU_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+
+gateau_status check_mem(int mem) {
+    if (mem != GATEAU_MEM_HOST && mem != GATEAU_MEM_DEVICE) return fail(GATEAU_EINVAL, "mem must be GATEAU_MEM_HOST or GATEAU_MEM_DEVICE");
+    return GATEAU_OK;
+}
+
+// Copy a device or host float array to host memory.
+gateau_status fetch_floats(const float* src, size_t n, int mem, std::vector<float>& out) {
+    out.resize(n);
+    if (mem == GATEAU_MEM_DEVICE) {
+        GATEAU_CUDA(cudaMemcpy(out.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost));
+    } else {
+        memcpy(out.data(), src, n * sizeof(float));
+    }
+    return GATEAU_OK;
+}
+
+// Rebuild the derived tables (cascade collapse, filters, pink filters) and upload them.
+gateau_status finalize(gateau_plan* p) {
+    if (!p->dirty) return GATEAU_OK;
+    const gateau_plan_desc& d = p->desc;
+    const int nf = d.n_freq, Kp = p->Kp;
+    // cascade collapse (Sect. 2.5)
+    std::vector<PrimStage> prim;
+    std::string err;
+    if (!expand_stages(p->stages, p->nu, prim, err)) return fail(GATEAU_EINVAL, "%s", err.c_str());
+    collapse_cascade(p->nu, prim, d.T_atm_K, d.T_cmb_K, d.eta_taper, d.rho_surf_m, d.eta_pol, p->c0, p->c1, p->c2);
+    // per-frequency device vectors (kelvin units: divide by k_B)
+    std::vector<float> cv(3 * static_cast<size_t>(Kp), 0.f);
+    for (int k = 0; k < nf; ++k) {
+        cv[k] = static_cast<float>(p->c0[k] / kKB);
+        cv[Kp + k] = static_cast<float>(p->c1[k] / kKB);
+        cv[2 * Kp + k] = static_cast<float>(p->c2[k] / kKB);
+    }
+    GATEAU_CUDA(p->d_c.ensure(cv.size() * sizeof(float)));
+    GATEAU_CUDA(cudaMemcpy(p->d_c.p, cv.data(), cv.size() * sizeof(float), cudaMemcpyHostToDevice));
+
+    // contraction operands, device units: w in GHz, X in kelvin.
+    //   H = eta w_GHz;  G = H gamma (nu_GHz + beta);  Q = eta^2 w_GHz
+    // with gamma = h 1e9 / k_B and beta = 2 Delta_Al / (eta_pb h 1e9) (Eq. 17).
+    const int n_ch = p->n_ch;
+    const double gamma = kH * 1e9 / kKB;
+    const double beta = 2.0 * d.delta_al_J / (d.eta_pb * kH * 1e9);
+    std::vector<double> H(static_cast<size_t>(n_ch) * Kp, 0.0), G(H.size(), 0.0), Q(H.size(), 0.0);
+    for (int c = 0; c < n_ch; ++c)
+        for (int k = 0; k < nf; ++k) {
+            const double eta = p->eta_filt[static_cast<size_t>(c) * nf + k];
+            const double wg = p->w[k] * 1e-9;
+            const size_t i = static_cast<size_t>(c) * Kp + k;
+            H[i] = eta * wg;
+            G[i] = H[i] * gamma * (p->nu[k] * 1e-9 + beta);
+            Q[i] = eta * eta * wg;
+        }
+    p->n_ch_pad = (n_ch + 63) / 64 * 64;
+    if (d.precision == GATEAU_PREC_FP32) {
+        std::vector<float> hgq(3 * static_cast<size_t>(p->n_ch_pad) * Kp, 0.f);
+        const size_t mat = static_cast<size_t>(p->n_ch_pad) * Kp;
+        for (size_t i = 0; i < H.size(); ++i) {
+            hgq[i] = static_cast<float>(H[i]);
+            hgq[mat + i] = static_cast<float>(G[i]);
+            hgq[2 * mat + i] = static_cast<float>(Q[i]);
+        }
+        GATEAU_CUDA(p->d_HGQ.ensure(hgq.size() * sizeof(float)));
+        GATEAU_CUDA(cudaMemcpy(p->d_HGQ.p, hgq.data(), hgq.size() * sizeof(float), cudaMemcpyHostToDevice));
+    } else {
+        const int n_groups = (n_ch + 255) / 256;
+        const int n_half = ((n_ch + n_groups - 1) / n_groups + 15) / 16 * 16;
+        std::vector<uint16_t> tiled;
+        size_t stage_elems = 0;
+        fused_tile_operands(H.data(), G.data(), Q.data(), n_ch, Kp, n_half, n_groups, tiled, stage_elems);
+        GATEAU_CUDA(p->d_fusedB.ensure(tiled.size() * sizeof(uint16_t)));
+        GATEAU_CUDA(cudaMemcpy(p->d_fusedB.p, tiled.data(), tiled.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+        p->fused.B = p->d_fusedB.as<uint16_t>();
+        p->fused.n_half = n_half;
+        p->fused.n_groups = n_groups;
+        p->fused.n_kstage = Kp / fused_kstage();
+        p->fused.stage_elems = stage_elems;
+    }
+
+    // pink filters (Sect. 2.6, Eq. 20)
+    p->n_pole = pink_pole_count(d.pink_f_min_hz, d.f_sample_hz);
+    const int np = p->n_pole;
+    p->pink_a.assign(static_cast<size_t>(n_ch) * np, 0.0);
+    p->pink_r.assign(static_cast<size_t>(n_ch) * np, 0.0);
+    p->pink_d.assign(n_ch, 0.0);
+    for (int c = 0; c < n_ch; ++c) {
+        const double A = p->has_pink ? p->pink_A[c] : 0.0;
+        const double al = p->has_pink ? p->pink_alpha[c] : 1.0;
+        pink_design_channel(al, A, d.pink_f_min_hz, d.f_sample_hz, np, &p->pink_a[static_cast<size_t>(c) * np],
+                            &p->pink_r[static_cast<size_t>(c) * np], &p->pink_d[c]);
+    }
+    std::vector<float> pk(static_cast<size_t>(n_ch) * (2 * np + 1));
+    for (size_t i = 0; i < p->pink_a.size(); ++i) {
+        pk[i] = static_cast<float>(p->pink_a[i]);
+        pk[p->pink_a.size() + i] = static_cast<float>(p->pink_r[i]);
+    }
+    for (int c = 0; c < n_ch; ++c) pk[2 * p->pink_a.size() + c] = static_cast<float>(p->pink_d[c]);
+    GATEAU_CUDA(p->d_pink.ensure(pk.size() * sizeof(float)));
+    GATEAU_CUDA(cudaMemcpy(p->d_pink.p, pk.data(), pk.size() * sizeof(float), cudaMemcpyHostToDevice));
+    const size_t state_bytes = static_cast<size_t>(d.n_pix) * n_ch * np * sizeof(float);
+    if (p->d_state.bytes < state_bytes) {
+        GATEAU_CUDA(p->d_state.ensure(state_bytes));
+        GATEAU_CUDA(cudaMemset(p->d_state.p, 0, state_bytes));
+    }
+    p->dirty = false;
+    return GATEAU_OK;
+}
+
+DevTables make_tables(const gateau_plan* p) {
+    const gateau_plan_desc& d = p->desc;
+    DevTables T{};
+    T.n_pix = d.n_pix;
+    T.pix_off = p->d_pix.as<double>();
+    T.f_sample = d.f_sample_hz;
+    T.h_column = d.h_column_m;
+    T.wind = d.wind_mps;
+    T.scan_kind = p->scan_kind;
+    for (int i = 0; i < kMaxScanParams; ++i) T.sp[i] = p->sp[i];
+    T.phi0 = p->phi0;
+    T.theta0 = p->theta0;
+    T.custom = p->d_custom.as<double>();
+    T.n_custom = p->n_custom;
+    T.screen = p->d_screen.as<float>();
+    T.nx = p->nx;
+    T.ny = p->ny;
+    T.pitch = p->pitch;
+    T.tau = p->d_tau.as<float>();
+    T.n_pwv = p->n_pwv;
+    T.pwv_min = p->pwv_min;
+    T.dpwv = p->dpwv;
+    T.cube = p->d_cube.as<float>();
+    T.n_az = p->n_az;
+    T.n_el = p->n_el;
+    T.az0 = p->az0;
+    T.daz = p->daz;
+    T.el0 = p->el0;
+    T.del = p->del;
+    T.n_freq = d.n_freq;
+    T.Kp = p->Kp;
+    T.c0 = p->d_c.as<float>();
+    T.c1 = T.c0 + p->Kp;
+    T.c2 = T.c0 + 2 * p->Kp;
+    T.n_ch = p->n_ch;
+    T.n_ch_pad = p->n_ch_pad;
+    const size_t mat = static_cast<size_t>(p->n_ch_pad) * p->Kp;
+    T.H = p->d_HGQ.as<float>();
+    T.G = T.H ? T.H + mat : nullptr;
+    T.Q = T.H ? T.H + 2 * mat : nullptr;
+    T.kb1e9 = static_cast<float>(kKB * 1e9);
+    T.kB = static_cast<float>(kKB);
+    T.noise_scale = static_cast<float>(1e9 * d.f_sample_hz);
+    T.key0 = static_cast<uint32_t>(d.seed & 0xffffffffull);
+    T.key1 = static_cast<uint32_t>(d.seed >> 32);
+    T.noise_flags = d.noise_flags;
+    T.n_pole = p->n_pole;
+    const size_t pa = static_cast<size_t>(p->n_ch) * p->n_pole;
+    T.pink_a = p->d_pink.as<float>();
+    T.pink_r = T.pink_a + pa;
+    T.pink_d = T.pink_a + 2 * pa;
+    T.status = p->d_status.as<unsigned int>();
+    return T;
+}
+
+gateau_status check_complete(const gateau_plan* p) {
+    if (!p->has_cube) return fail(GATEAU_ESTATE, "source cube not set (gateau_set_source_cube)");
+    if (!p->has_screen) return fail(GATEAU_ESTATE, "atmosphere screen not set (gateau_set_atmosphere_screen)");
+    if (!p->has_table) return fail(GATEAU_ESTATE, "atmosphere table not set (gateau_set_atmosphere_table)");
+    if (!p->has_cascade) return fail(GATEAU_ESTATE, "cascade not set (gateau_set_cascade)");
+    if (!p->has_disp) return fail(GATEAU_ESTATE, "dispersive element not set (gateau_set_dispersive_element)");
+    if (!p->has_scan) return fail(GATEAU_ESTATE, "scan not set (gateau_set_scan)");
+    return GATEAU_OK;
+}
+
+gateau_status validate_run(const gateau_plan* p, long long t0, long long nt, const void* out) {
+    gateau_status st = check_complete(p);
+    if (st != GATEAU_OK) return st;
+    if (t0 < 0 || nt <= 0) return fail(GATEAU_EINVAL, "need t0 >= 0 and nt > 0 (got t0=%lld nt=%lld)", t0, nt);
+    if (!out) return fail(GATEAU_EINVAL, "out is NULL");
+    if ((p->desc.noise_flags & GATEAU_NOISE_PINK) && t0 != 0 && t0 != p->next_t0)
+        return fail(GATEAU_EORDER, "t0=%lld does not continue the previous chunk (next t0 is %lld, or 0 to restart)", t0,
+                    p->next_t0);
+    if (p->scan_kind == GATEAU_SCAN_CUSTOM && t0 + nt > p->n_custom)
+        return fail(GATEAU_EINVAL, "custom scan has %lld samples, run needs %lld", p->n_custom, t0 + nt);
+    if (nt * static_cast<long long>(p->desc.n_pix) > (1LL << 31))
+        return fail(GATEAU_EINVAL, "nt * n_pix must stay below 2^31 rows per call");
+    return GATEAU_OK;
+}
+
+cudaError_t take_event(gateau_plan* p, cudaEvent_t* e) {
+    if (!p->ev_pool.empty()) {
+        *e = p->ev_pool.back();
+        p->ev_pool.pop_back();
+        return cudaSuccess;
+    }
+    return cudaEventCreate(e);
+}
+
+// Records the start/end events of one phase of the current timed run.
+struct PhaseTimer {
+    gateau_plan* p;
+    cudaStream_t s;
+    cudaError_t begin(int ph) {
+        if (!p->timing) return cudaSuccess;
+        gateau_plan::TimedRun& t = p->timed.back();
+        cudaError_t e = take_event(p, &t.ev[ph][0]);
+        if (e == cudaSuccess) e = take_event(p, &t.ev[ph][1]);
+        if (e != cudaSuccess) return e;
+        t.used[ph] = true;
+        return cudaEventRecord(t.ev[ph][0], s);
+    }
+    cudaError_t end(int ph) {
+        if (!p->timing) return cudaSuccess;
+        return cudaEventRecord(p->timed.back().ev[ph][1], s);
+    }
+};
+
+// Enqueue one validated run.
+gateau_status enqueue_run(gateau_plan* p, long long t0, long long nt, float* out, cudaStream_t stream) {
+    gateau_status st = finalize(p);
+    if (st != GATEAU_OK) return st;
+    const gateau_plan_desc& d = p->desc;
+    const long long rows = nt * d.n_pix;
+    GATEAU_CUDA(p->d_rows.ensure(static_cast<size_t>(rows) * sizeof(RowParams)));
+    const DevTables T = make_tables(p);
+    RowParams* R = p->d_rows.as<RowParams>();
+    if (p->timing) {
+        gateau_plan::TimedRun t{};
+        p->timed.push_back(t);
+    }
+    PhaseTimer tm{p, stream};
+    if (t0 == 0) {
+        GATEAU_CUDA(cudaMemsetAsync(p->d_state.p, 0, static_cast<size_t>(d.n_pix) * p->n_ch * p->n_pole * sizeof(float),
+                                    stream));
+    }
+    GATEAU_CUDA(tm.begin(GATEAU_PHASE_ROWS));
+    GATEAU_CUDA(launch_row_setup(T, t0, nt, R, stream));
+    GATEAU_CUDA(tm.end(GATEAU_PHASE_ROWS));
+    p->launches += 1;
+    if (d.precision == GATEAU_PREC_FP32) {
+        // Unfused baseline: spectra in HBM chunk by chunk, then the SIMT contraction.
+        const long long chunk = std::min<long long>(rows, 131072);
+        GATEAU_CUDA(p->d_X.ensure(static_cast<size_t>(chunk) * p->Kp * sizeof(float)));
+        // Timing covers the whole chunk loop: SPECTRUM and CONTRACT alternate, so the
+        // loop is reported under CONTRACT and SPECTRUM stays zero for this path.
+        GATEAU_CUDA(tm.begin(GATEAU_PHASE_CONTRACT));
+        for (long long r0 = 0; r0 < rows; r0 += chunk) {
+            const long long nr = std::min(chunk, rows - r0);
+            GATEAU_CUDA(launch_psd_fp32(T, R, r0, nr, p->d_X.as<float>(), stream));
+            GATEAU_CUDA(launch_contract_fp32(T, p->d_X.as<float>(), r0, nr, t0, nt, out, stream));
+            p->launches += 2;
+        }
+        GATEAU_CUDA(tm.end(GATEAU_PHASE_CONTRACT));
+    } else {
+        GATEAU_CUDA(tm.begin(GATEAU_PHASE_CONTRACT));
+        GATEAU_CUDA(launch_fused_bf16x3(T, p->fused, R, t0, nt, out, p->n_sm, stream));
+        GATEAU_CUDA(tm.end(GATEAU_PHASE_CONTRACT));
+        p->launches += 1;
+    }
+    if (d.noise_flags & GATEAU_NOISE_PINK) {
+        PinkWork W;
+        pink_choose_chunks(nt, static_cast<long long>(d.n_pix) * p->n_ch, W.C, W.L);
+        GATEAU_CUDA(p->d_agg.ensure(static_cast<size_t>(W.C) * d.n_pix * p->n_ch * p->n_pole * sizeof(float)));
+        W.agg = p->d_agg.as<float>();
+        GATEAU_CUDA(tm.begin(GATEAU_PHASE_PINK));
+        GATEAU_CUDA(launch_pink(T, p->d_state.as<float>(), W, t0, nt, out, stream));
+        GATEAU_CUDA(tm.end(GATEAU_PHASE_PINK));
+        p->launches += 3;
+    }
+    p->runs += 1;
+    p->next_t0 = t0 + nt;
+    p->last_stream = stream;
+    return GATEAU_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gateau_version(void) { return "gateau-b300 1.0 (sm_103a; fp32 SIMT + split-bf16 tcgen05)"; }
+
+const char* gateau_last_error(void) { return g_last_error.c_str(); }
+
+int gateau_device_count(void) {
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+gateau_status gateau_plan_create(const gateau_plan_desc* desc, gateau_plan** out) {
+    if (!out) return fail(GATEAU_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!desc) return fail(GATEAU_EINVAL, "desc is NULL");
+    const gateau_plan_desc& d = *desc;
+    if (d.n_freq < 2 || d.n_freq > (1 << 20)) return fail(GATEAU_EINVAL, "n_freq must be in [2, 2^20]");
+    if (!(d.f_lo_hz > 0.0) || !(d.f_hi_hz > d.f_lo_hz)) return fail(GATEAU_EINVAL, "need 0 < f_lo < f_hi");
+    if (!(d.f_sample_hz > 0.0)) return fail(GATEAU_EINVAL, "f_sample must be > 0");
+    if (d.n_pix < 1 || d.n_pix > (1 << 20) || !d.pix_offsets_rad) return fail(GATEAU_EINVAL, "need n_pix >= 1 and pix_offsets");
+    if (!(d.T_atm_K >= 0.0) || !(d.T_cmb_K >= 0.0)) return fail(GATEAU_EINVAL, "temperatures must be >= 0");
+    if (!(d.h_column_m > 0.0)) return fail(GATEAU_EINVAL, "h_column must be > 0");
+    if (!(d.eta_pb > 0.0) || !(d.delta_al_J >= 0.0)) return fail(GATEAU_EINVAL, "need eta_pb > 0, delta_al >= 0");
+    if (d.precision != GATEAU_PREC_FP32 && d.precision != GATEAU_PREC_BF16X3) return fail(GATEAU_EINVAL, "unknown precision");
+    if (!(d.pink_f_min_hz > 0.0) || !(d.pink_f_min_hz < 0.5 * d.f_sample_hz))
+        return fail(GATEAU_EINVAL, "need 0 < pink_f_min < f_sample/2");
+    if (pink_pole_count(d.pink_f_min_hz, d.f_sample_hz) > kMaxPoles)
+        return fail(GATEAU_EINVAL, "pink_f_min too low: the filter would need more than %d poles", kMaxPoles);
+    std::unique_ptr<gateau_plan> p(new (std::nothrow) gateau_plan());
+    if (!p) return fail(GATEAU_ENOMEM, "host allocation failed");
+    p->desc = d;
+    p->pix_off.assign(d.pix_offsets_rad, d.pix_offsets_rad + 2 * static_cast<size_t>(d.n_pix));
+    p->desc.pix_offsets_rad = p->pix_off.data();
+    p->nu = make_grid(d.n_freq, d.f_lo_hz, d.f_hi_hz);
+    p->w = make_trapezoid(p->nu);
+    p->Kp = (d.n_freq + 31) / 32 * 32;
+    *out = p.release();
+    return GATEAU_OK;
+}
+
+void gateau_plan_destroy(gateau_plan* plan) { delete plan; }
+
+// Device-side plan buffers that every run needs (pixel offsets, status word).
+static gateau_status ensure_base(gateau_plan* p) {
+    if (!p->d_pix.p) {
+        GATEAU_CUDA(p->d_pix.ensure(p->pix_off.size() * sizeof(double)));
+        GATEAU_CUDA(cudaMemcpy(p->d_pix.p, p->pix_off.data(), p->pix_off.size() * sizeof(double), cudaMemcpyHostToDevice));
+        GATEAU_CUDA(p->d_status.ensure(sizeof(unsigned int)));
+        GATEAU_CUDA(cudaMemset(p->d_status.p, 0, sizeof(unsigned int)));
+        int dev = 0;
+        GATEAU_CUDA(cudaGetDevice(&dev));
+        GATEAU_CUDA(cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return GATEAU_OK;
+}
+
+gateau_status gateau_set_source_cube(gateau_plan* p, const float* cube, int n_az, int n_el, double az0_rad,
+                                     double daz_rad, double el0_rad, double del_rad, int mem) {
+    if (!p || !cube) return fail(GATEAU_EINVAL, "plan and cube must be non-NULL");
+    if (check_mem(mem) != GATEAU_OK) return GATEAU_EINVAL;
+    if (n_az < 2 || n_el < 2) return fail(GATEAU_EINVAL, "cube needs n_az, n_el >= 2");
+    if (!(daz_rad > 0.0) || !(del_rad > 0.0)) return fail(GATEAU_EINVAL, "cube grid steps must be > 0");
+    if (static_cast<long long>(n_az) * n_el * p->Kp >= (1LL << 31)) return fail(GATEAU_EINVAL, "cube too large (n_az*n_el*n_freq >= 2^31)");
+    gateau_status st = ensure_base(p);
+    if (st != GATEAU_OK) return st;
+    const size_t nf = p->desc.n_freq, Kp = p->Kp;
+    GATEAU_CUDA(p->d_cube.ensure(static_cast<size_t>(n_az) * n_el * Kp * sizeof(float)));
+    if (Kp != nf) GATEAU_CUDA(cudaMemset(p->d_cube.p, 0, static_cast<size_t>(n_az) * n_el * Kp * sizeof(float)));
+    GATEAU_CUDA(cudaMemcpy2D(p->d_cube.p, Kp * sizeof(float), cube, nf * sizeof(float), nf * sizeof(float),
+                             static_cast<size_t>(n_az) * n_el, kind_of(mem)));
+    p->n_az = n_az;
+    p->n_el = n_el;
+    p->az0 = az0_rad;
+    p->daz = daz_rad;
+    p->el0 = el0_rad;
+    p->del = del_rad;
+    p->has_cube = true;
+    return GATEAU_OK;
+}
+
+gateau_status gateau_set_atmosphere_screen(gateau_plan* p, const float* screen, int nx, int ny, double pitch_m,
+                                           int is_epl, double pwv0_mm, int mem) {
+    if (!p || !screen) return fail(GATEAU_EINVAL, "plan and screen must be non-NULL");
+    if (check_mem(mem) != GATEAU_OK) return GATEAU_EINVAL;
+    if (nx < 2 || ny < 2 || !(pitch_m > 0.0)) return fail(GATEAU_EINVAL, "screen needs nx, ny >= 2 and pitch > 0");
+    gateau_status st = ensure_base(p);
+    if (st != GATEAU_OK) return st;
+    const size_t n = static_cast<size_t>(nx) * ny;
+    GATEAU_CUDA(p->d_screen.ensure(n * sizeof(float)));
+    if (is_epl) {
+        std::vector<float> h;
+        st = fetch_floats(screen, n, mem, h);
+        if (st != GATEAU_OK) return st;
+        for (float& v : h) v = static_cast<float>(static_cast<double>(v) / 6.587 + pwv0_mm);   // Eq. 4
+        GATEAU_CUDA(cudaMemcpy(p->d_screen.p, h.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    } else {
+        GATEAU_CUDA(cudaMemcpy(p->d_screen.p, screen, n * sizeof(float), kind_of(mem)));
+    }
+    p->nx = nx;
+    p->ny = ny;
+    p->pitch = pitch_m;
+    p->has_screen = true;
+    return GATEAU_OK;
+}
+
+gateau_status gateau_set_atmosphere_table(gateau_plan* p, const float* table, int n_pwv, double pwv_min_mm,
+                                          double dpwv_mm, int is_opacity, int mem) {
+    if (!p || !table) return fail(GATEAU_EINVAL, "plan and table must be non-NULL");
+    if (check_mem(mem) != GATEAU_OK) return GATEAU_EINVAL;
+    if (n_pwv < 2 || !(dpwv_mm > 0.0)) return fail(GATEAU_EINVAL, "table needs n_pwv >= 2 and dpwv > 0");
+    gateau_status st = ensure_base(p);
+    if (st != GATEAU_OK) return st;
+    const size_t nf = p->desc.n_freq, Kp = p->Kp;
+    std::vector<float> h;
+    st = fetch_floats(table, static_cast<size_t>(n_pwv) * nf, mem, h);
+    if (st != GATEAU_OK) return st;
+    std::vector<float> padded(static_cast<size_t>(n_pwv) * Kp, 0.f);
+    for (int j = 0; j < n_pwv; ++j)
+        for (size_t k = 0; k < nf; ++k) {
+            double v = h[j * nf + k];
+            if (!is_opacity) v = -log(std::max(v, 1e-30));
+            if (!(v >= 0.0) || !std::isfinite(v)) return fail(GATEAU_EINVAL, "opacity must be finite and >= 0 (row %d, point %zu)", j, k);
+            padded[j * Kp + k] = static_cast<float>(v);
+        }
+    GATEAU_CUDA(p->d_tau.ensure(padded.size() * sizeof(float)));
+    GATEAU_CUDA(cudaMemcpy(p->d_tau.p, padded.data(), padded.size() * sizeof(float), cudaMemcpyHostToDevice));
+    p->n_pwv = n_pwv;
+    p->pwv_min = pwv_min_mm;
+    p->dpwv = dpwv_mm;
+    p->has_table = true;
+    return GATEAU_OK;
+}
+
+gateau_status gateau_set_cascade(gateau_plan* p, int n_stage, const gateau_stage* stages) {
+    if (!p) return fail(GATEAU_EINVAL, "plan is NULL");
+    if (n_stage < 0 || n_stage > 64 || (n_stage > 0 && !stages)) return fail(GATEAU_EINVAL, "need 0 <= n_stage <= 64 and stages");
+    std::vector<StageSpec> v;
+    for (int s = 0; s < n_stage; ++s) {
+        const gateau_stage& g = stages[s];
+        StageSpec st{};
+        st.kind = g.kind;
+        st.T_K = g.T_K;
+        st.eta = g.eta;
+        if (g.kind == GATEAU_STAGE_REFLECTIVE && g.eta_nu) st.eta_nu.assign(g.eta_nu, g.eta_nu + p->desc.n_freq);
+        st.eps_ref = g.eps_ref;
+        st.nu_ref_hz = g.nu_ref_hz;
+        st.d_m = g.d_m;
+        st.n_index = g.n_index;
+        st.tan_delta = g.tan_delta;
+        st.T_refl_K = g.T_refl_K;
+        st.ar_coated = g.ar_coated;
+        v.push_back(std::move(st));
+    }
+    std::vector<PrimStage> prim;
+    std::string err;
+    if (!expand_stages(v, p->nu, prim, err)) return fail(GATEAU_EINVAL, "%s", err.c_str());
+    p->stages = std::move(v);
+    p->has_cascade = true;
+    p->dirty = true;
+    return GATEAU_OK;
+}
+
+gateau_status gateau_set_dispersive_element(gateau_plan* p, int kind, int n_ch, const double* f_c_hz, const double* R,
+                                            const double* eta_peak, const double* custom_eta) {
+    if (!p) return fail(GATEAU_EINVAL, "plan is NULL");
+    if (n_ch < 1 || n_ch > 4096) return fail(GATEAU_EINVAL, "need 1 <= n_ch <= 4096");
+    std::vector<double> eta;
+    std::string err;
+    if (!build_filters(kind, n_ch, f_c_hz, R, eta_peak, custom_eta, p->nu, p->desc.delta_al_J, eta, err))
+        return fail(GATEAU_EINVAL, "%s", err.c_str());
+    if (p->has_disp && n_ch != p->n_ch) {
+        p->has_pink = false;
+        p->d_state.release();
+    }
+    p->eta_filt = std::move(eta);
+    p->disp_kind = kind;
+    p->n_ch = n_ch;
+    p->has_disp = true;
+    p->dirty = true;
+    return GATEAU_OK;
+}
+
+gateau_status gateau_set_pink_noise(gateau_plan* p, const double* A, const double* alpha) {
+    if (!p || !A || !alpha) return fail(GATEAU_EINVAL, "plan, A and alpha must be non-NULL");
+    if (!p->has_disp) return fail(GATEAU_ESTATE, "set the dispersive element before the pink noise");
+    for (int c = 0; c < p->n_ch; ++c)
+        if (!(A[c] >= 0.0) || !(alpha[c] >= 0.0 && alpha[c] <= 3.0))
+            return fail(GATEAU_EINVAL, "channel %d: need A >= 0 and 0 <= alpha <= 3", c);
+    p->pink_A.assign(A, A + p->n_ch);
+    p->pink_alpha.assign(alpha, alpha + p->n_ch);
+    p->has_pink = true;
+    p->dirty = true;
+    return GATEAU_OK;
+}
+
+gateau_status gateau_set_scan(gateau_plan* p, int kind, const double* params, int n_params, double phi0_rad,
+                              double theta0_rad, const double* custom, long long n_custom, int mem) {
+    if (!p) return fail(GATEAU_EINVAL, "plan is NULL");
+    static const int need[] = {0, 3, 4, 0};
+    if (kind < GATEAU_SCAN_STARE || kind > GATEAU_SCAN_CUSTOM) return fail(GATEAU_EINVAL, "unknown scan kind");
+    if (n_params < need[kind] || n_params > kMaxScanParams || (n_params > 0 && !params))
+        return fail(GATEAU_EINVAL, "scan kind %d needs %d parameters", kind, need[kind]);
+    if (kind == GATEAU_SCAN_RASTER && (!(params[0] > 0.0) || !(params[1] > 0.0) || params[3] < 1.0))
+        return fail(GATEAU_EINVAL, "raster needs half_width > 0, speed > 0, n_rows >= 1");
+    if (kind == GATEAU_SCAN_CUSTOM) {
+        if (!custom || n_custom < 1) return fail(GATEAU_EINVAL, "custom scan needs a pointing table");
+        if (check_mem(mem) != GATEAU_OK) return GATEAU_EINVAL;
+        gateau_status st = ensure_base(p);
+        if (st != GATEAU_OK) return st;
+        GATEAU_CUDA(p->d_custom.ensure(static_cast<size_t>(n_custom) * 2 * sizeof(double)));
+        GATEAU_CUDA(cudaMemcpy(p->d_custom.p, custom, static_cast<size_t>(n_custom) * 2 * sizeof(double), kind_of(mem)));
+    }
+    p->scan_kind = kind;
+    for (int i = 0; i < kMaxScanParams; ++i) p->sp[i] = i < n_params ? params[i] : 0.0;
+    p->phi0 = phi0_rad;
+    p->theta0 = theta0_rad;
+    p->n_custom = kind == GATEAU_SCAN_CUSTOM ? n_custom : 0;
+    p->has_scan = true;
+    return GATEAU_OK;
+}
+
+gateau_status gateau_run(gateau_plan* p, long long t0, long long nt, float* dev_out, void* stream) {
+    if (!p) return fail(GATEAU_EINVAL, "plan is NULL");
+    gateau_status st = validate_run(p, t0, nt, dev_out);
+    if (st != GATEAU_OK) return st;
+    st = ensure_base(p);
+    if (st != GATEAU_OK) return st;
+    return enqueue_run(p, t0, nt, dev_out, static_cast<cudaStream_t>(stream));
+}
+
+gateau_status gateau_run_host(gateau_plan* p, long long t0, long long nt, float* host_out, void* stream) {
+    if (!p) return fail(GATEAU_EINVAL, "plan is NULL");
+    gateau_status st = validate_run(p, t0, nt, host_out);
+    if (st != GATEAU_OK) return st;
+    st = ensure_base(p);
+    if (st != GATEAU_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!p->copy_stream) {
+        GATEAU_CUDA(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+            GATEAU_CUDA(cudaEventCreateWithFlags(&p->ev_done[i], cudaEventDisableTiming));
+            GATEAU_CUDA(cudaEventCreateWithFlags(&p->ev_copied[i], cudaEventDisableTiming));
+        }
+    }
+    // Chunks of about 256 MB of output, double-buffered: chunk c runs on `s`
+    // while chunk c-1 is copied to the host on the copy stream.
+    const long long per_sample = static_cast<long long>(p->desc.n_pix) * std::max(p->n_ch, 1);
+    const long long chunk = std::max<long long>(128, std::min<long long>(nt, (256LL << 20) / (4 * per_sample)) / 128 * 128);
+    const size_t chunk_bytes = static_cast<size_t>(std::min(chunk, nt)) * per_sample * sizeof(float);
+    for (int i = 0; i < 2; ++i) GATEAU_CUDA(p->d_stage[i].ensure(chunk_bytes));
+    int c = 0;
+    for (long long a = 0; a < nt; a += chunk, ++c) {
+        const int b = c & 1;
+        const long long len = std::min(chunk, nt - a);
+        if (c >= 2) GATEAU_CUDA(cudaStreamWaitEvent(s, p->ev_copied[b], 0));
+        st = enqueue_run(p, t0 + a, len, p->d_stage[b].as<float>(), s);
+        if (st != GATEAU_OK) return st;
+        GATEAU_CUDA(cudaEventRecord(p->ev_done[b], s));
+        GATEAU_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_done[b], 0));
+        GATEAU_CUDA(cudaMemcpyAsync(host_out + a * per_sample, p->d_stage[b].p,
+                                    static_cast<size_t>(len) * per_sample * sizeof(float), cudaMemcpyDeviceToHost,
+                                    p->copy_stream));
+        GATEAU_CUDA(cudaEventRecord(p->ev_copied[b], p->copy_stream));
+    }
+    GATEAU_CUDA(cudaStreamSynchronize(p->copy_stream));
+    GATEAU_CUDA(cudaStreamSynchronize(s));
+    return GATEAU_OK;
+}
+
+gateau_status gateau_run_batch(gateau_plan* const* plans, const long long* t0s, const long long* nts, float* const* outs,
+                               int n, void* stream) {
+    if (!plans || !t0s || !nts || !outs || n <= 0 || n > 256) return fail(GATEAU_EINVAL, "need 0 < n <= 256 and arrays");
+    for (int k = 0; k < n; ++k) {
+        if (!plans[k]) return fail(GATEAU_EINVAL, "plans[%d] is NULL", k);
+        for (int m = 0; m < k; ++m)
+            if (plans[m] == plans[k]) return fail(GATEAU_EINVAL, "plan %d appears twice in the batch", k);
+        gateau_status st = validate_run(plans[k], t0s[k], nts[k], outs[k]);
+        if (st != GATEAU_OK) return st;
+        st = ensure_base(plans[k]);
+        if (st != GATEAU_OK) return st;
+    }
+    for (int k = 0; k < n; ++k) {
+        gateau_status st = enqueue_run(plans[k], t0s[k], nts[k], outs[k], static_cast<cudaStream_t>(stream));
+        if (st != GATEAU_OK) return st;
+    }
+    return GATEAU_OK;
+}
+
+gateau_status gateau_plan_status(gateau_plan* p, unsigned int* flags) {
+    if (!p || !flags) return fail(GATEAU_EINVAL, "plan and flags must be non-NULL");
+    *flags = 0;
+    if (!p->d_status.p) return GATEAU_OK;
+    GATEAU_CUDA(cudaStreamSynchronize(p->last_stream));
+    GATEAU_CUDA(cudaMemcpy(flags, p->d_status.p, sizeof(unsigned int), cudaMemcpyDeviceToHost));
+    GATEAU_CUDA(cudaMemset(p->d_status.p, 0, sizeof(unsigned int)));
+    if (*flags & GATEAU_STATUS_WAIT_TIMEOUT) return fail(GATEAU_ETIMEOUT, "a fused-kernel pipeline wait timed out");
+    if (*flags & ~static_cast<unsigned int>(GATEAU_STATUS_PWV_CLAMPED))
+        return fail(GATEAU_EDEVICE, "device status word 0x%x", *flags);
+    return GATEAU_OK;
+}
+
+gateau_status gateau_plan_get_info(gateau_plan* p, gateau_plan_info* info) {
+    if (!p || !info) return fail(GATEAU_EINVAL, "plan and info must be non-NULL");
+    info->n_freq = p->desc.n_freq;
+    info->n_freq_padded = p->Kp;
+    info->n_ch = p->n_ch;
+    info->n_pix = p->desc.n_pix;
+    info->n_pole = pink_pole_count(p->desc.pink_f_min_hz, p->desc.f_sample_hz);
+    info->next_t0 = p->next_t0;
+    info->device_bytes = device_bytes(p);
+    return GATEAU_OK;
+}
+
+gateau_status gateau_plan_get_vector(gateau_plan* p, int which, double* out, size_t count) {
+    if (!p || !out) return fail(GATEAU_EINVAL, "plan and out must be non-NULL");
+    const std::vector<double>* src = nullptr;
+    std::vector<double> tmp;
+    const bool needs_tables = which >= GATEAU_VEC_C0;
+    if (which == GATEAU_VEC_ETA_FILT && !p->has_disp) return fail(GATEAU_ESTATE, "dispersive element not set");
+    if (needs_tables) {
+        if (!p->has_cascade || !p->has_disp) return fail(GATEAU_ESTATE, "cascade and dispersive element must be set");
+        // Host-only rebuild (no device upload) so the tables are available without a GPU.
+        std::vector<PrimStage> prim;
+        std::string err;
+        if (!expand_stages(p->stages, p->nu, prim, err)) return fail(GATEAU_EINVAL, "%s", err.c_str());
+        const gateau_plan_desc& d = p->desc;
+        std::vector<double> c0, c1, c2;
+        collapse_cascade(p->nu, prim, d.T_atm_K, d.T_cmb_K, d.eta_taper, d.rho_surf_m, d.eta_pol, c0, c1, c2);
+        if (which == GATEAU_VEC_C0) tmp = c0;
+        else if (which == GATEAU_VEC_C1) tmp = c1;
+        else if (which == GATEAU_VEC_C2) tmp = c2;
+        else {
+            const int np = pink_pole_count(d.pink_f_min_hz, d.f_sample_hz);
+            std::vector<double> a(static_cast<size_t>(p->n_ch) * np), r(a.size()), dd(p->n_ch);
+            for (int c = 0; c < p->n_ch; ++c)
+                pink_design_channel(p->has_pink ? p->pink_alpha[c] : 1.0, p->has_pink ? p->pink_A[c] : 0.0,
+                                    d.pink_f_min_hz, d.f_sample_hz, np, &a[static_cast<size_t>(c) * np],
+                                    &r[static_cast<size_t>(c) * np], &dd[c]);
+            if (which == GATEAU_VEC_PINK_A) tmp = a;
+            else if (which == GATEAU_VEC_PINK_R) tmp = r;
+            else if (which == GATEAU_VEC_PINK_D) tmp = dd;
+            else return fail(GATEAU_EINVAL, "unknown vector id %d", which);
+        }
+        src = &tmp;
+    } else if (which == GATEAU_VEC_NU) {
+        src = &p->nu;
+    } else if (which == GATEAU_VEC_WEIGHT) {
+        src = &p->w;
+    } else if (which == GATEAU_VEC_ETA_FILT) {
+        src = &p->eta_filt;
+    } else {
+        return fail(GATEAU_EINVAL, "unknown vector id %d", which);
+    }
+    if (count < src->size()) return fail(GATEAU_EINVAL, "out holds %zu doubles, table has %zu", count, src->size());
+    std::copy(src->begin(), src->end(), out);
+    return GATEAU_OK;
+}
+
+gateau_status gateau_plan_get_state(gateau_plan* p, long long* next_t0, double* pink_state) {
+    if (!p) return fail(GATEAU_EINVAL, "plan is NULL");
+    if (next_t0) *next_t0 = p->next_t0;
+    if (pink_state) {
+        if (!p->has_disp) return fail(GATEAU_ESTATE, "dispersive element not set");
+        const size_t n = static_cast<size_t>(p->desc.n_pix) * p->n_ch * pink_pole_count(p->desc.pink_f_min_hz, p->desc.f_sample_hz);
+        if (!p->d_state.p || p->d_state.bytes < n * sizeof(float)) {
+            std::fill(pink_state, pink_state + n, 0.0);
+            return GATEAU_OK;
+        }
+        GATEAU_CUDA(cudaStreamSynchronize(p->last_stream));
+        std::vector<float> h(n);
+        GATEAU_CUDA(cudaMemcpy(h.data(), p->d_state.p, n * sizeof(float), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) pink_state[i] = h[i];
+    }
+    return GATEAU_OK;
+}
+
+gateau_status gateau_plan_set_state(gateau_plan* p, long long next_t0, const double* pink_state) {
+    if (!p || next_t0 < 0) return fail(GATEAU_EINVAL, "plan must be non-NULL and next_t0 >= 0");
+    if (pink_state) {
+        if (!p->has_disp) return fail(GATEAU_ESTATE, "dispersive element not set");
+        gateau_status st = ensure_base(p);
+        if (st != GATEAU_OK) return st;
+        st = finalize(p);
+        if (st != GATEAU_OK) return st;
+        const size_t n = static_cast<size_t>(p->desc.n_pix) * p->n_ch * p->n_pole;
+        std::vector<float> h(n);
+        for (size_t i = 0; i < n; ++i) h[i] = static_cast<float>(pink_state[i]);
+        GATEAU_CUDA(cudaStreamSynchronize(p->last_stream));
+        GATEAU_CUDA(cudaMemcpy(p->d_state.p, h.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    p->next_t0 = next_t0;
+    return GATEAU_OK;
+}
+
+gateau_status gateau_plan_set_timing(gateau_plan* p, int enable) {
+    if (!p) return fail(GATEAU_EINVAL, "plan is NULL");
+    p->timing = enable != 0;
+    return GATEAU_OK;
+}
+
+gateau_status gateau_plan_get_timing(gateau_plan* p, double* ms, long long* runs, long long* launches) {
+    if (!p) return fail(GATEAU_EINVAL, "plan is NULL");
+    if (ms)
+        for (int ph = 0; ph < GATEAU_PHASE_COUNT; ++ph) ms[ph] = 0.0;
+    if (!p->timed.empty()) GATEAU_CUDA(cudaStreamSynchronize(p->last_stream));
+    for (gateau_plan::TimedRun& t : p->timed)
+        for (int ph = 0; ph < GATEAU_PHASE_COUNT; ++ph)
+            if (t.used[ph]) {
+                float e = 0.f;
+                GATEAU_CUDA(cudaEventElapsedTime(&e, t.ev[ph][0], t.ev[ph][1]));
+                if (ms) ms[ph] += e;
+                p->ev_pool.push_back(t.ev[ph][0]);
+                p->ev_pool.push_back(t.ev[ph][1]);
+            }
+    p->timed.clear();
+    if (runs) *runs = p->runs;
+    if (launches) *launches = p->launches;
+    p->runs = 0;
+    p->launches = 0;
+    return GATEAU_OK;
+}
+
+gateau_status gateau_hex_offsets(int R_hex, double spacing_rad, double* out, int count, int* n_out) {
+    if (R_hex < 0 || R_hex > 64) return fail(GATEAU_EINVAL, "need 0 <= R_hex <= 64");
+    const int n = 1 + 3 * R_hex * (R_hex + 1);
+    if (n_out) *n_out = n;
+    if (!out || count < n) return fail(GATEAU_EINVAL, "out must hold %d offset pairs", n);
+    std::vector<double> v;
+    hex_offsets(R_hex, spacing_rad, v);
+    std::copy(v.begin(), v.end(), out);
+    return GATEAU_OK;
+}
+
+}  // extern "C"

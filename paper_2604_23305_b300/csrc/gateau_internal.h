@@ -1,0 +1,115 @@
+// Internal declarations shared by the host plan code and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gateau.h"
+#include "plan_host.h"
+
+namespace gateau {
+
+constexpr int kMaxPoles = 24;          // pink-filter poles supported by the kernels
+constexpr int kMaxScanParams = 8;
+
+// Per-row quantities produced by the row-setup kernel and read by the spectral
+// producers (32 bytes, one row = one (time sample, spaxel) pair).
+struct __align__(16) RowParams {
+    float csc;        // 1 / sin(elevation)                                   (Eq. 10)
+    int tau_j;        // opacity-table row below the row's PWV
+    float tau_f;      // fractional position between rows tau_j and tau_j+1
+    int src_idx;      // element offset of cube texel (ia, ie), or -1 outside (Sect. 2.4)
+    float src_fa;     // fractional azimuth cell position
+    float src_fe;     // fractional elevation cell position
+    float pwv;        // line-of-sight PWV (mm), kept for diagnostics
+    int pad;
+};
+
+// Everything the kernels read, by value (device pointers + scalars).
+struct DevTables {
+    // geometry and scan (Sect. 2.4)
+    int n_pix;
+    const double* pix_off;             // [n_pix][2]
+    double f_sample, h_column, wind;
+    int scan_kind;
+    double sp[kMaxScanParams];
+    double phi0, theta0;
+    const double* custom;              // [n_custom][2] or null
+    long long n_custom;
+    // screen [ny][nx] PWV mm
+    const float* screen;
+    int nx, ny;
+    double pitch;
+    // opacity table [n_pwv][Kp]
+    const float* tau;
+    int n_pwv;
+    double pwv_min, dpwv;
+    // source cube [n_az][n_el][Kp] in W/Hz (as given; c2 carries the 1/k_B)
+    const float* cube;
+    int n_az, n_el;
+    double az0, daz, el0, del;
+    // spectral axis
+    int n_freq, Kp;
+    const float* c0;                   // [Kp] kelvin
+    const float* c1;                   // [Kp] kelvin
+    const float* c2;                   // [Kp] kelvin per (W/Hz)
+    // contraction operands, fp32 [n_ch_pad][Kp] (plain path)
+    int n_ch, n_ch_pad;
+    const float* H;                    // eta_filt * w_GHz
+    const float* G;                    // H * gamma (nu_GHz + beta)
+    const float* Q;                    // eta_filt^2 * w_GHz
+    // epilogue scales: P_KID = kb1e9 * S1,  sigma = kB * sqrt(noise_scale * N)
+    float kb1e9;
+    float kB;
+    float noise_scale;                 // 1e9 * f_sample
+    uint32_t key0, key1;               // Philox key
+    int noise_flags;
+    // pink noise
+    int n_pole;
+    const float* pink_a;               // [n_ch][n_pole]
+    const float* pink_r;               // [n_ch][n_pole] gain folded in
+    const float* pink_d;               // [n_ch] gain folded in
+    unsigned int* status;
+};
+
+// Device buffers for the split-BF16 fused path.
+struct FusedOperands {
+    const uint16_t* B;                 // pre-tiled bf16 operand stages (see kernels_fused.cu)
+    int n_half;                        // channels per CTA (multiple of 16)
+    int n_groups;                      // channel groups (CTAs per row tile)
+    int n_kstage;                      // K stages of kKStage
+    size_t stage_elems;                // bf16 elements per (group, kstage) block
+};
+
+// ---- kernel launchers (each enqueues on `stream`, returns cudaGetLastError) ----
+cudaError_t launch_row_setup(const DevTables& T, long long t0, long long nt, RowParams* rows,
+                             cudaStream_t stream);
+cudaError_t launch_psd_fp32(const DevTables& T, const RowParams* rows, long long r0, long long nrows,
+                            float* X, cudaStream_t stream);
+cudaError_t launch_contract_fp32(const DevTables& T, const float* X, long long r0, long long nrows,
+                                 long long t0, long long nt, float* out, cudaStream_t stream);
+cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, const RowParams* rows,
+                                long long t0, long long nt, float* out, int n_sm, cudaStream_t stream);
+size_t fused_smem_bytes();
+int fused_kstage();
+void fused_tile_operands(const double* H, const double* G, const double* Q, int n_ch, int Kp,
+                         int n_half, int n_groups, std::vector<uint16_t>& out, size_t& stage_elems);
+
+// Pink noise: chunked linear-recurrence scan adding into out.
+struct PinkWork {
+    float* agg;                        // [C][S][n_pole]
+    int C;                             // chunks per sequence
+    long long L;                       // samples per chunk (multiple of 4)
+};
+void pink_choose_chunks(long long nt, long long S, int& C, long long& L);
+cudaError_t launch_pink(const DevTables& T, float* state, const PinkWork& W, long long t0, long long nt,
+                        float* out, cudaStream_t stream);
+
+// Host helpers
+uint16_t f32_to_bf16_rn(float x);
+float bf16_to_f32(uint16_t h);
+
+}  // namespace gateau

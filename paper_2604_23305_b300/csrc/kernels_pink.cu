@@ -1,0 +1,148 @@
+// Pink detector noise (Sect. 2.6, Eq. 20) as a pole-zero filter in parallel form,
+//   y_n = d z_n + sum_j r_j s_j,n,   s_j,n = a_j s_j,n-1 + z_n,
+// for every sequence (spaxel i, channel ch), added into out[n][i][ch].
+//
+// The recurrence is linear, so a run of nt samples is cut into C chunks of L
+// samples scanned in parallel:
+//   phase 1: each (chunk, sequence) computes its end state from a zero start;
+//   phase 2: each (sequence, pole) combines the chunk states in order in FP64,
+//            s_in[c+1] = a^len(c) s_in[c] + agg[c], seeded by the carried state;
+//   phase 3: each (chunk, sequence) reruns its chunk from s_in[c] and adds y.
+// Threads of a warp own consecutive channels of one spaxel, so every sample
+// step reads and writes 128 contiguous bytes of out.
+#include <math.h>
+
+#include "device_common.cuh"
+
+namespace gateau {
+
+template <int NP>
+__global__ __launch_bounds__(256) void pink_phase1_kernel(DevTables T, PinkWork W, long long t0,
+                                                          long long nt) {
+    const long long S = static_cast<long long>(T.n_pix) * T.n_ch;
+    const int np = T.n_pole;
+    for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < W.C * S;
+         idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int c = static_cast<int>(idx / S);
+        const long long s = idx - c * S;
+        const int i = static_cast<int>(s / T.n_ch), ch = static_cast<int>(s - static_cast<long long>(i) * T.n_ch);
+        const long long a0 = t0 + c * W.L;
+        const long long b0 = min(a0 + W.L, t0 + nt);
+        float av[NP], st[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            av[j] = (j < np) ? T.pink_a[ch * np + j] : 0.f;
+            st[j] = 0.f;
+        }
+        float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (long long n = a0; n < b0; ++n) {
+            if (n == a0 || (n & 3) == 0) z4 = pink_normals4(n >> 2, i, ch, T.key0, T.key1);
+            const float z = f4_get(z4, static_cast<int>(n & 3));
+#pragma unroll
+            for (int j = 0; j < NP; ++j) st[j] = fmaf(av[j], st[j], z);
+        }
+        float* ag = W.agg + (c * S + s) * np;
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+            if (j < np) ag[j] = st[j];
+    }
+}
+
+__global__ void pink_phase2_kernel(DevTables T, float* state, PinkWork W, long long nt) {
+    const long long S = static_cast<long long>(T.n_pix) * T.n_ch;
+    const int np = T.n_pole;
+    for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < S * np;
+         idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long s = idx / np;
+        const int j = static_cast<int>(idx - s * np);
+        const int ch = static_cast<int>(s % T.n_ch);
+        const double a = T.pink_a[ch * np + j];
+        const double aL = pow(a, static_cast<double>(W.L));
+        double carry = state[idx];
+        for (int c = 0; c < W.C; ++c) {
+            const long long len = min(W.L, nt - c * W.L);
+            float* slot = W.agg + (c * S + s) * np + j;
+            const double agg = *slot;
+            *slot = static_cast<float>(carry);
+            carry = (len == W.L ? aL : pow(a, static_cast<double>(len))) * carry + agg;
+        }
+        state[idx] = static_cast<float>(carry);
+    }
+}
+
+template <int NP>
+__global__ __launch_bounds__(256) void pink_phase3_kernel(DevTables T, PinkWork W, long long t0,
+                                                          long long nt, float* __restrict__ out) {
+    const long long S = static_cast<long long>(T.n_pix) * T.n_ch;
+    const int np = T.n_pole;
+    for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < W.C * S;
+         idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int c = static_cast<int>(idx / S);
+        const long long s = idx - c * S;
+        const int i = static_cast<int>(s / T.n_ch), ch = static_cast<int>(s - static_cast<long long>(i) * T.n_ch);
+        const long long a0 = t0 + c * W.L;
+        const long long b0 = min(a0 + W.L, t0 + nt);
+        const float* ag = W.agg + (c * S + s) * np;
+        float av[NP], rv[NP], st[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            av[j] = (j < np) ? T.pink_a[ch * np + j] : 0.f;
+            rv[j] = (j < np) ? T.pink_r[ch * np + j] : 0.f;
+            st[j] = (j < np) ? ag[j] : 0.f;
+        }
+        const float d = T.pink_d[ch];
+        float* o = out + ((a0 - t0) * T.n_pix + i) * static_cast<long long>(T.n_ch) + ch;
+        const long long stride = static_cast<long long>(T.n_pix) * T.n_ch;
+        float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (long long n = a0; n < b0; ++n, o += stride) {
+            if (n == a0 || (n & 3) == 0) z4 = pink_normals4(n >> 2, i, ch, T.key0, T.key1);
+            const float z = f4_get(z4, static_cast<int>(n & 3));
+            float y = d * z;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                st[j] = fmaf(av[j], st[j], z);
+                y = fmaf(rv[j], st[j], y);
+            }
+            *o += y;
+        }
+    }
+}
+
+void pink_choose_chunks(long long nt, long long S, int& C, long long& L) {
+    const long long target = 148LL * 1024;           // enough independent scans to fill the GPU
+    long long c = (target + S - 1) / S;
+    const long long cmax = (nt + 63) / 64;            // at least 64 samples per chunk
+    if (c > cmax) c = cmax;
+    if (c < 1) c = 1;
+    L = ((nt + c - 1) / c + 3) / 4 * 4;
+    C = static_cast<int>((nt + L - 1) / L);
+}
+
+template <int NP>
+static cudaError_t launch_pink_np(const DevTables& T, float* state, const PinkWork& W, long long t0,
+                                  long long nt, float* out, cudaStream_t stream) {
+    const long long S = static_cast<long long>(T.n_pix) * T.n_ch;
+    const long long work = W.C * S;
+    const int block = 256;
+    long long grid = (work + block - 1) / block;
+    if (grid > 148LL * 32) grid = 148LL * 32;
+    pink_phase1_kernel<NP><<<static_cast<unsigned>(grid), block, 0, stream>>>(T, W, t0, nt);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    long long g2 = (S * T.n_pole + block - 1) / block;
+    if (g2 > 148LL * 32) g2 = 148LL * 32;
+    pink_phase2_kernel<<<static_cast<unsigned>(g2), block, 0, stream>>>(T, state, W, nt);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    pink_phase3_kernel<NP><<<static_cast<unsigned>(grid), block, 0, stream>>>(T, W, t0, nt, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pink(const DevTables& T, float* state, const PinkWork& W, long long t0, long long nt,
+                        float* out, cudaStream_t stream) {
+    if (T.n_pole <= 8) return launch_pink_np<8>(T, state, W, t0, nt, out, stream);
+    if (T.n_pole <= 16) return launch_pink_np<16>(T, state, W, t0, nt, out, stream);
+    return launch_pink_np<kMaxPoles>(T, state, W, t0, nt, out, stream);
+}
+
+}  // namespace gateau

@@ -1,0 +1,312 @@
+// Row setup (per time sample x spaxel) and the plain FP32 path:
+//   row_setup     : scan -> pointing -> screen PWV -> opacity row, airmass, source cell  (Sect. 2.4)
+//   psd_fp32      : P_nu[row][nu] after the cascade, materialised in HBM                (Sect. 2.5)
+//   contract_fp32 : SIMT contraction against eta_filt (Eq. 16) and the NEP^2 terms (Eq. 17),
+//                   epilogue sigma (Eq. 18) + white noise (Eq. 19) -> out                 (Sect. 2.7)
+#include <math.h>
+
+#include "device_common.cuh"
+
+namespace gateau {
+
+__device__ __forceinline__ void scan_pointing(const DevTables& T, long long n, double t, double& phi,
+                                              double& th) {
+    switch (T.scan_kind) {
+        case GATEAU_SCAN_DAISY: {  // Eq. 8
+            const double r = T.sp[0], w = T.sp[1], W = T.sp[2];
+            phi = r * cos(W * t) * sin(w * t);
+            th = r * sin(W * t) * sin(w * t);
+            break;
+        }
+        case GATEAU_SCAN_RASTER: {  // user pattern: boustrophedon in azimuth
+            const double half = T.sp[0], speed = T.sp[1], step = T.sp[2];
+            const int n_rows = static_cast<int>(T.sp[3]);
+            const double T_row = 2.0 * half / speed;
+            const double k = floor(t / T_row);
+            const double s = t - k * T_row;
+            phi = (fmod(k, 2.0) == 0.0) ? (-half + speed * s) : (half - speed * s);
+            double row = 0.0;
+            if (n_rows > 1) {
+                const double m = fmod(k, 2.0 * (n_rows - 1));
+                row = (m < n_rows) ? m : 2.0 * (n_rows - 1) - m;
+            }
+            th = (row - 0.5 * (n_rows - 1)) * step;
+            break;
+        }
+        case GATEAU_SCAN_CUSTOM:
+            phi = T.custom[2 * n];
+            th = T.custom[2 * n + 1];
+            break;
+        default:
+            phi = 0.0;
+            th = 0.0;
+    }
+}
+
+// Python-style floating modulo: result in [0, m) with the sign of m.
+__device__ __forceinline__ double pymod(double a, double m) {
+    double r = fmod(a, m);
+    if (r != 0.0 && ((r < 0.0) != (m < 0.0))) r += m;
+    return r;
+}
+
+__device__ __forceinline__ RowParams make_row(const DevTables& T, long long n, int i) {
+    const double t = static_cast<double>(n) / T.f_sample;
+    double phs, ths;
+    scan_pointing(T, n, t, phs, ths);
+    const double dphi = T.pix_off[2 * i], dth = T.pix_off[2 * i + 1];
+    const double az = phs + T.phi0 + dphi;                   // spaxel pointing (Sect. 2.4)
+    const double el = ths + T.theta0 + dth;
+    // Frozen-flow screen coordinates (Eq. 9) and periodic bilinear PWV.
+    const double x = T.h_column * tan(phs + dphi) + T.wind * t;
+    const double y = T.h_column * tan(ths + dth);
+    double gx = pymod(x / T.pitch + 0.5 * T.nx, static_cast<double>(T.nx));
+    double gy = pymod(y / T.pitch + 0.5 * T.ny, static_cast<double>(T.ny));
+    if (!(gx >= 0.0 && gx <= T.nx) || !(gy >= 0.0 && gy <= T.ny)) {   // non-finite pointing
+        atomicOr(T.status, GATEAU_STATUS_BAD_INDEX);
+        gx = 0.0;
+        gy = 0.0;
+    }
+    int ix = static_cast<int>(floor(gx)), iy = static_cast<int>(floor(gy));
+    const double fx = gx - ix, fy = gy - iy;
+    ix %= T.nx;
+    iy %= T.ny;
+    const int ix1 = (ix + 1) % T.nx, iy1 = (iy + 1) % T.ny;
+    const double s00 = T.screen[static_cast<long long>(iy) * T.nx + ix];
+    const double s01 = T.screen[static_cast<long long>(iy) * T.nx + ix1];
+    const double s10 = T.screen[static_cast<long long>(iy1) * T.nx + ix];
+    const double s11 = T.screen[static_cast<long long>(iy1) * T.nx + ix1];
+    const double pwv = (1 - fx) * (1 - fy) * s00 + fx * (1 - fy) * s01 + (1 - fx) * fy * s10 + fx * fy * s11;
+    // Opacity-table row (linear in PWV, clamped) and airmass (Eq. 10).
+    double u = (pwv - T.pwv_min) / T.dpwv;
+    if (!(u >= 0.0 && u <= T.n_pwv - 1)) {                          // also catches NaN
+        u = fmin(fmax(u, 0.0), static_cast<double>(T.n_pwv - 1));
+        atomicOr(T.status, GATEAU_STATUS_PWV_CLAMPED);
+    }
+    const int j = min(static_cast<int>(floor(u)), T.n_pwv - 2);
+    RowParams rp;
+    rp.csc = static_cast<float>(1.0 / sin(el));
+    rp.tau_j = j;
+    rp.tau_f = static_cast<float>(u - j);
+    rp.pwv = static_cast<float>(pwv);
+    rp.pad = 0;
+    // Source cell (bilinear, zero outside the grid).
+    const double su = (az - T.az0) / T.daz, sv = (el - T.el0) / T.del;
+    if (su >= 0.0 && su <= T.n_az - 1 && sv >= 0.0 && sv <= T.n_el - 1) {
+        const int ia = min(static_cast<int>(floor(su)), T.n_az - 2);
+        const int ie = min(static_cast<int>(floor(sv)), T.n_el - 2);
+        rp.src_idx = (ia * T.n_el + ie) * T.Kp;
+        rp.src_fa = static_cast<float>(su - ia);
+        rp.src_fe = static_cast<float>(sv - ie);
+    } else {
+        rp.src_idx = -1;
+        rp.src_fa = 0.f;
+        rp.src_fe = 0.f;
+    }
+    return rp;
+}
+
+// rows are pixel-major within a run: r = i * nt + (n - t0)
+__global__ void row_setup_kernel(DevTables T, long long t0, long long nt, RowParams* rows) {
+    const long long total = nt * T.n_pix;
+    for (long long r = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; r < total;
+         r += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int i = static_cast<int>(r / nt);
+        const long long n = t0 + (r - static_cast<long long>(i) * nt);
+        rows[r] = make_row(T, n, i);
+    }
+}
+
+cudaError_t launch_row_setup(const DevTables& T, long long t0, long long nt, RowParams* rows,
+                             cudaStream_t stream) {
+    const long long total = nt * T.n_pix;
+    const int block = 256;
+    long long grid = (total + block - 1) / block;
+    if (grid > 148LL * 64) grid = 148LL * 64;
+    row_setup_kernel<<<static_cast<unsigned>(grid), block, 0, stream>>>(T, t0, nt, rows);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Spectral power after the cascade, FP32 (Sect. 2.5), using the exact collapse
+// P = c0 + c1 (1 - eta_atm) + c2 eta_atm P_src with eta_atm = exp(-csc tau_z).
+// One block per row, 4 consecutive frequencies per thread.
+// ---------------------------------------------------------------------------
+__global__ void psd_fp32_kernel(DevTables T, const RowParams* __restrict__ rows, long long r0,
+                                float* __restrict__ X) {
+    const long long row = blockIdx.x;
+    const RowParams rp = rows[r0 + row];
+    const float* tA = T.tau + static_cast<long long>(rp.tau_j) * T.Kp;
+    const float* tB = tA + T.Kp;
+    const bool has_src = rp.src_idx >= 0;
+    const float fa = rp.src_fa, fe = rp.src_fe;
+    const float w00 = (1.f - fa) * (1.f - fe), w10 = fa * (1.f - fe), w01 = (1.f - fa) * fe, w11 = fa * fe;
+    const float* s00 = T.cube + (has_src ? rp.src_idx : 0);
+    const float* s10 = s00 + static_cast<long long>(T.n_el) * T.Kp;
+    const float* s01 = s00 + T.Kp;
+    const float* s11 = s10 + T.Kp;
+    float* xr = X + row * T.Kp;
+    for (int k = threadIdx.x * 4; k < T.Kp; k += blockDim.x * 4) {
+        const float4 a4 = *reinterpret_cast<const float4*>(tA + k);
+        const float4 b4 = *reinterpret_cast<const float4*>(tB + k);
+        const float4 c04 = *reinterpret_cast<const float4*>(T.c0 + k);
+        const float4 c14 = *reinterpret_cast<const float4*>(T.c1 + k);
+        const float4 c24 = *reinterpret_cast<const float4*>(T.c2 + k);
+        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (has_src) {
+            const float4 q00 = *reinterpret_cast<const float4*>(s00 + k);
+            const float4 q10 = *reinterpret_cast<const float4*>(s10 + k);
+            const float4 q01 = *reinterpret_cast<const float4*>(s01 + k);
+            const float4 q11 = *reinterpret_cast<const float4*>(s11 + k);
+            p.x = w00 * q00.x + w10 * q10.x + w01 * q01.x + w11 * q11.x;
+            p.y = w00 * q00.y + w10 * q10.y + w01 * q01.y + w11 * q11.y;
+            p.z = w00 * q00.z + w10 * q10.z + w01 * q01.z + w11 * q11.z;
+            p.w = w00 * q00.w + w10 * q10.w + w01 * q01.w + w11 * q11.w;
+        }
+        float4 o;
+#define GATEAU_PSD(c)                                                  \
+    {                                                                  \
+        const float tau = a4.c + rp.tau_f * (b4.c - a4.c);             \
+        const float arg = rp.csc * tau;                                \
+        const float e = expf(-arg);                                    \
+        const float ome = -expm1f(-arg);                               \
+        o.c = c04.c + c14.c * ome + c24.c * e * p.c;                   \
+    }
+        GATEAU_PSD(x) GATEAU_PSD(y) GATEAU_PSD(z) GATEAU_PSD(w)
+#undef GATEAU_PSD
+        *reinterpret_cast<float4*>(xr + k) = o;
+    }
+}
+
+cudaError_t launch_psd_fp32(const DevTables& T, const RowParams* rows, long long r0, long long nrows,
+                            float* X, cudaStream_t stream) {
+    if (nrows <= 0) return cudaSuccess;
+    psd_fp32_kernel<<<static_cast<unsigned>(nrows), 256, 0, stream>>>(T, rows, r0, X);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP32 SIMT contraction.  For a block of 128 rows x 64 channels:
+//   S1[r][ch] = sum_k X[r][k] H[ch][k]                      (Eq. 16, kelvin*GHz)
+//   N [r][ch] = sum_k X[r][k] G[ch][k] + X[r][k]^2 Q[ch][k]  (Eq. 17 without 2 kB^2 1e9)
+// 256 threads, each 8 rows x 4 consecutive channels, K in steps of 16 with a
+// register-prefetched shared-memory tile.
+// ---------------------------------------------------------------------------
+constexpr int kBM = 128, kBN = 64, kBK = 16;
+
+__global__ __launch_bounds__(256) void contract_fp32_kernel(DevTables T, const float* __restrict__ X,
+                                                            long long r0, long long nrows, long long t0,
+                                                            long long nt, float* __restrict__ out) {
+    __shared__ __align__(16) float Xs[kBK][kBM + 4];
+    __shared__ __align__(16) float Hs[kBK][kBN];
+    __shared__ __align__(16) float Gs[kBK][kBN];
+    __shared__ __align__(16) float Qs[kBK][kBN];
+
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const long long rb = static_cast<long long>(blockIdx.x) * kBM;   // row block within the chunk
+    const int cb = blockIdx.y * kBN;                                  // channel block
+    const int Kp = T.Kp;
+
+    // global -> register loaders
+    const int xa_row0 = tid >> 2, xa_kq = tid & 3;                    // 2 float4 of X per thread
+    const int hb_ch = tid >> 2, hb_kq = tid & 3;                      // 1 float4 of H, G, Q each
+    float4 xr[2], hr, gr, qr;
+    auto load_tiles = [&](int k0) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const long long row = rb + xa_row0 + 64 * u;
+            xr[u] = (row < nrows) ? *reinterpret_cast<const float4*>(X + row * Kp + k0 + 4 * xa_kq)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const long long hoff = static_cast<long long>(cb + hb_ch) * Kp + k0 + 4 * hb_kq;
+        hr = *reinterpret_cast<const float4*>(T.H + hoff);
+        gr = *reinterpret_cast<const float4*>(T.G + hoff);
+        qr = *reinterpret_cast<const float4*>(T.Q + hoff);
+    };
+    auto store_tiles = [&]() {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int row = xa_row0 + 64 * u;
+            Xs[4 * xa_kq + 0][row] = xr[u].x;
+            Xs[4 * xa_kq + 1][row] = xr[u].y;
+            Xs[4 * xa_kq + 2][row] = xr[u].z;
+            Xs[4 * xa_kq + 3][row] = xr[u].w;
+        }
+        Hs[4 * hb_kq + 0][hb_ch] = hr.x; Hs[4 * hb_kq + 1][hb_ch] = hr.y;
+        Hs[4 * hb_kq + 2][hb_ch] = hr.z; Hs[4 * hb_kq + 3][hb_ch] = hr.w;
+        Gs[4 * hb_kq + 0][hb_ch] = gr.x; Gs[4 * hb_kq + 1][hb_ch] = gr.y;
+        Gs[4 * hb_kq + 2][hb_ch] = gr.z; Gs[4 * hb_kq + 3][hb_ch] = gr.w;
+        Qs[4 * hb_kq + 0][hb_ch] = qr.x; Qs[4 * hb_kq + 1][hb_ch] = qr.y;
+        Qs[4 * hb_kq + 2][hb_ch] = qr.z; Qs[4 * hb_kq + 3][hb_ch] = qr.w;
+    };
+
+    float s1[8][4], sn[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s1[i][j] = sn[i][j] = 0.f;
+
+    load_tiles(0);
+    for (int k0 = 0; k0 < Kp; k0 += kBK) {
+        __syncthreads();
+        store_tiles();
+        __syncthreads();
+        if (k0 + kBK < Kp) load_tiles(k0 + kBK);
+#pragma unroll
+        for (int k = 0; k < kBK; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&Xs[k][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&Xs[k][ty * 8 + 4]);
+            const float4 h = *reinterpret_cast<const float4*>(&Hs[k][tx * 4]);
+            const float4 g = *reinterpret_cast<const float4*>(&Gs[k][tx * 4]);
+            const float4 q = *reinterpret_cast<const float4*>(&Qs[k][tx * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float hv[4] = {h.x, h.y, h.z, h.w};
+            const float gv[4] = {g.x, g.y, g.z, g.w};
+            const float qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float x2 = a[i] * a[i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    s1[i][j] = fmaf(a[i], hv[j], s1[i][j]);
+                    sn[i][j] = fmaf(a[i], gv[j], fmaf(x2, qv[j], sn[i][j]));
+                }
+            }
+        }
+    }
+
+    // Epilogue: P_KID (Eq. 16), sigma (Eqs. 17-18), white noise (Eq. 19).
+    const int ch0 = cb + tx * 4;
+    const bool white = (T.noise_flags & GATEAU_NOISE_WHITE) != 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const long long row = rb + ty * 8 + i;
+        if (row >= nrows) continue;
+        const long long rg = r0 + row;
+        const int pix = static_cast<int>(rg / nt);
+        const long long n = t0 + (rg - static_cast<long long>(pix) * nt);
+        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (white) z = white_normals4(n, pix, ch0 >> 2, T.key0, T.key1);
+        float* orow = out + ((n - t0) * T.n_pix + pix) * static_cast<long long>(T.n_ch);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int ch = ch0 + j;
+            if (ch < T.n_ch) {
+                const float pk = T.kb1e9 * s1[i][j];
+                const float sigma = T.kB * sqrtf(T.noise_scale * fmaxf(sn[i][j], 0.f));
+                orow[ch] = fmaf(sigma, f4_get(z, j), pk);
+            }
+        }
+    }
+}
+
+cudaError_t launch_contract_fp32(const DevTables& T, const float* X, long long r0, long long nrows,
+                                 long long t0, long long nt, float* out, cudaStream_t stream) {
+    if (nrows <= 0) return cudaSuccess;
+    dim3 grid(static_cast<unsigned>((nrows + kBM - 1) / kBM), static_cast<unsigned>(T.n_ch_pad / kBN));
+    contract_fp32_kernel<<<grid, 256, 0, stream>>>(T, X, r0, nrows, t0, nt, out);
+    return cudaGetLastError();
+}
+
+}  // namespace gateau

@@ -1,0 +1,301 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative to the oracle):
+  * noiseless signal P_KID: 1e-5 for the FP32 path, 1e-3 for the split-BF16
+    tcgen05 path (both measured far below these bounds, see the printed maxima);
+  * white noise sigma z_w, sample by sample from the same Philox counters:
+    |gpu - oracle| <= tol_sigma * sigma * (|z| + 0.1) with tol_sigma 1e-4 (FP32)
+    or 1e-2 (BF16 noise contractions);
+  * pink noise, sample by sample: within 1e-4 of the channel's pink rms.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import gateau_oracle as O
+from paper_2604_23305_b300 import Plan, workloads as W
+from paper_2604_23305_b300 import _lib as L
+
+pytestmark = pytest.mark.gpu
+
+SIGNAL_TOL = {"fp32": 1e-5, "bf16x3": 1e-3}
+SIGMA_TOL = {"fp32": 1e-4, "bf16x3": 1e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device (no CPU fallback exists)"
+    assert L.lib().gateau_device_count() >= 1
+
+
+def gpu_run(sc, precision, t0, nt, white=False, pink=False, chunks=None):
+    p = Plan(sc, precision=precision, white=white, pink=pink)
+    if chunks is None:
+        out = p.run(t0, nt)
+    else:
+        parts, a = [], t0
+        for c in chunks:
+            parts.append(p.run(a, c))
+            a += c
+        out = torch.cat(parts)
+    torch.cuda.synchronize()
+    flags = p.status()
+    return out.cpu().numpy().astype(np.float64), flags, p
+
+
+def rel_err(a, b):
+    return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+_oracle_cache = {}
+
+
+def oracle(name, t0, nt, white=False, pink=False, mutate=None, key=None):
+    k = (name, t0, nt, white, pink, key)
+    if key is None or k not in _oracle_cache:
+        sc = W.scenario(name, nt_total=max(t0 + nt, 1))
+        if mutate:
+            mutate(sc)
+        res = O.simulate(sc, t0, nt, white=white, pink=pink, return_parts=True)
+        if key is None:
+            return sc, res
+        _oracle_cache[k] = (sc, res)
+    return _oracle_cache[k]
+
+
+# ---------------------------------------------------------------- noiseless signal
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("name,t0,nt", [("single_pixel_small", 0, 1000), ("ifu25", 0, 300),
+                                        ("ifu25", 150001, 130), ("single_pixel_wide", 3, 700)])
+def test_signal_parity(precision, name, t0, nt):
+    sc, ref = oracle(name, t0, nt, key="signal")
+    got, flags, _ = gpu_run(sc, precision, t0, nt)
+    err = rel_err(got, ref["p_kid"])
+    print(f"{precision} {name} t0={t0} nt={nt}: max rel err {err:.3e}")
+    assert err < SIGNAL_TOL[precision]
+    assert flags & ~L.STATUS_PWV_CLAMPED == 0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_source_only_difference(precision):
+    """The faint source on top of the atmosphere: the run with the source minus the run
+    without it, against the oracle's difference (error stated relative to the source)."""
+    name, t0, nt = "ifu25", 40000, 64
+    sc, ref = oracle(name, t0, nt, key="signal")
+
+    def no_src(s):
+        s["source"]["cube"] = np.zeros_like(s["source"]["cube"])
+    sc0, ref0 = oracle(name, t0, nt, mutate=no_src, key="nosrc")
+    got, _, _ = gpu_run(sc, precision, t0, nt)
+    got0, _, _ = gpu_run(sc0, precision, t0, nt)
+    d_ref = ref["p_kid"] - ref0["p_kid"]
+    d_got = got - got0
+    scale = np.abs(d_ref).max()
+    assert scale > 0
+    err_src = np.abs(d_got - d_ref).max() / scale
+    err_tot = np.abs(d_got - d_ref).max() / np.abs(ref["p_kid"]).max()
+    print(f"{precision}: source-only max error {err_src:.3e} of the source peak, {err_tot:.3e} of the total")
+    assert err_tot < (2e-6 if precision == "fp32" else 5e-5)
+
+
+# ---------------------------------------------------------------- noise
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_white_noise_parity(precision):
+    name, t0, nt = "ifu25", 1000, 96
+    sc, ref = oracle(name, t0, nt, white=True, key="white")
+    _, ref_sig = oracle(name, t0, nt, key="signal_w")
+    got, _, _ = gpu_run(sc, precision, t0, nt, white=True)
+    got0, _, _ = gpu_run(sc, precision, t0, nt, white=False)
+    noise = got - got0
+    sigma = ref["sigma"]
+    z = ref["p_wn"] / sigma
+    bound = SIGMA_TOL[precision] * sigma * (np.abs(z) + 0.1) + 1e-6 * np.abs(ref_sig["p_kid"])
+    worst = np.max(np.abs(noise - ref["p_wn"]) / bound)
+    print(f"{precision}: white noise worst error / bound = {worst:.3f}")
+    assert worst <= 1.0
+    assert rel_err(got0, ref_sig["p_kid"]) < SIGNAL_TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_pink_noise_parity(precision):
+    name, nt = "single_pixel_small", 1000
+    sc, ref = oracle(name, 0, nt, pink=True, key="pink")
+    got, _, _ = gpu_run(sc, precision, 0, nt, pink=True)
+    got0, _, _ = gpu_run(sc, precision, 0, nt)
+    pn = got - got0
+    rms = np.sqrt(np.mean(ref["p_pn"] ** 2, axis=0, keepdims=True))
+    worst = np.max(np.abs(pn - ref["p_pn"]) / (1e-4 * rms + 1e-6 * np.abs(got0)))
+    print(f"{precision}: pink noise worst error / bound = {worst:.3f}")
+    assert worst <= 1.0
+
+
+def test_pink_noise_many_sequences_and_chunks():
+    """25 spaxels x 347 channels: the chunked parallel scan, run in uneven pieces, equals the
+    oracle's sequential recurrence."""
+    name, nt = "ifu25", 257
+    sc, ref = oracle(name, 0, nt, pink=True, key="pink_ifu")
+    got, _, _ = gpu_run(sc, "fp32", 0, nt, pink=True, chunks=[1, 130, 3, 123])
+    got0, _, _ = gpu_run(sc, "fp32", 0, nt)
+    pn = got - got0
+    rms = np.sqrt(np.mean(ref["p_pn"] ** 2, axis=0, keepdims=True))
+    worst = np.max(np.abs(pn - ref["p_pn"]) / (1e-4 * rms + 1e-6 * np.abs(got0)))
+    print(f"pink ifu chunked: worst error / bound = {worst:.3f}")
+    assert worst <= 1.0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_all_noise_total_parity(precision):
+    name, nt = "single_pixel_small", 1000
+    sc, ref = oracle(name, 0, nt, white=True, pink=True, key="all")
+    got, _, _ = gpu_run(sc, precision, 0, nt, white=True, pink=True)
+    bound = (SIGMA_TOL[precision] * ref["sigma"] * (np.abs(ref["p_wn"] / ref["sigma"]) + 0.1)
+             + 1e-4 * np.sqrt(np.mean(ref["p_pn"] ** 2, axis=0, keepdims=True))
+             + SIGNAL_TOL[precision] * np.abs(ref["p_kid"]))
+    assert np.max(np.abs(got - ref["total"]) / bound) <= 1.0
+
+
+# ---------------------------------------------------------------- chunking, state, host path
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_chunked_runs_equal_single_run(precision):
+    sc = W.scenario("ifu25", nt_total=400)
+    one, _, _ = gpu_run(sc, precision, 0, 400, white=True, pink=True)
+    parts, _, _ = gpu_run(sc, precision, 0, 400, white=True, pink=True, chunks=[129, 1, 7, 263])
+    sig, _, _ = gpu_run(sc, precision, 0, 400)
+    # signal and white noise are per-sample and bit-identical; pink differs only by rounding
+    assert np.max(np.abs(parts - one) / np.abs(sig)) < 1e-6
+
+
+def test_state_checkpoint_resume():
+    sc = W.scenario("single_pixel_small", nt_total=600)
+    full, _, _ = gpu_run(sc, "fp32", 0, 600, white=True, pink=True)
+    p1 = Plan(sc, precision="fp32")
+    a = p1.run(0, 250)
+    t_next, state = p1.get_state()
+    assert t_next == 250 and np.abs(state).max() > 0
+    p2 = Plan(sc, precision="fp32")
+    p2.set_state(t_next, state)
+    b = p2.run(250, 350)
+    torch.cuda.synchronize()
+    both = torch.cat([a, b]).cpu().numpy()
+    assert np.max(np.abs(both - full) / np.abs(full)) < 1e-6
+    with pytest.raises(L.GateauError, match="EORDER"):
+        p2.run(10, 5)
+
+
+def test_run_host_matches_device():
+    sc = W.scenario("ifu25", nt_total=300)
+    dev, _, _ = gpu_run(sc, "bf16x3", 0, 300, white=True, pink=True)
+    p = Plan(sc, precision="bf16x3", white=True, pink=True)
+    host = p.run_host(0, 300)
+    np.testing.assert_array_equal(host, dev.astype(np.float32))
+
+
+# ---------------------------------------------------------------- edge cases
+
+def _mut_outside(s):
+    s["scan"]["phi0"] = 0.01                         # 0.57 deg: every spaxel misses the cube
+
+
+def _mut_clamp(s):
+    s["atmosphere"]["screen"] = s["atmosphere"]["screen"] * 0 + 7.5   # above the 5 mm table
+
+
+def _mut_epl_eta(s):
+    atm = s["atmosphere"]
+    atm["screen"] = ((atm["screen"] - 0.3) * 6.587).astype(np.float32)
+    atm["is_epl"], atm["pwv0"] = True, 0.3
+    atm["table"] = np.exp(-atm["table"].astype(np.float64)).astype(np.float32)
+    atm["table_is_opacity"] = False
+
+
+def _mut_custom_scan(s):
+    n = s["nt_total"]
+    t = np.arange(n) / s["f_sample"]
+    s["scan"] = dict(kind="custom", params=(), phi0=0.0, theta0=s["scan"]["theta0"],
+                     custom=np.stack([1e-4 * np.sin(t), 5e-5 * np.cos(3 * t)], 1))
+
+
+def _mut_lorentzian_cascade(s):
+    s["dispersive"]["kind"] = "lorentzian"
+    s["cascade"] = [dict(kind="refractive", d=10e-3, n=3.4, tan_delta=1e-4, T=290.0, T_refl="sky"),
+                    dict(kind="ohmic", eps_ref=0.0025, nu_ref=840e9, T=273.0),
+                    dict(kind="reflective", eta=np.linspace(0.6, 0.9, s["n_freq"]), T=4.0)]
+
+
+def _mut_few_channels(s):
+    d = s["dispersive"]
+    s["dispersive"] = dict(kind="filterbank", f_c=np.asarray(d["f_c"])[5:22], R=np.asarray(d["R"])[5:22],
+                           eta_peak=np.asarray(d["eta_peak"])[5:22])
+    s["noise"]["pink_A"] = s["noise"]["pink_A"][5:22]
+    s["noise"]["pink_alpha"] = s["noise"]["pink_alpha"][5:22]
+
+
+def _mut_one_channel_two_freqs(s):
+    s["n_freq"] = 2
+    s["f_lo"], s["f_hi"] = 300e9, 301e9
+    nu = np.linspace(300e9, 301e9, 2)
+    s["atmosphere"]["table"] = s["atmosphere"]["table"][:, :2]
+    s["source"]["cube"] = np.ascontiguousarray(s["source"]["cube"][:, :, :2])
+    s["dispersive"] = dict(kind="lorentzian", f_c=np.array([300.5e9]), R=np.array([100.0]),
+                           eta_peak=np.array([0.5]))
+    s["noise"]["pink_A"] = s["noise"]["pink_A"][:1]
+    s["noise"]["pink_alpha"] = s["noise"]["pink_alpha"][:1]
+    s["cascade"] = [dict(kind="reflective", eta=0.9, T=20.0)]
+
+
+EDGE = {
+    "outside_cube": ("single_pixel_small", 0, 130, _mut_outside),
+    "pwv_clamped": ("single_pixel_small", 0, 64, _mut_clamp),
+    "epl_screen_eta_table": ("single_pixel_small", 5, 200, _mut_epl_eta),
+    "custom_scan": ("single_pixel_small", 11, 150, _mut_custom_scan),
+    "lorentzian_refractive": ("single_pixel_small", 0, 129, _mut_lorentzian_cascade),
+    "17_channels": ("single_pixel_small", 0, 257, _mut_few_channels),
+    "1_channel_2_freqs": ("single_pixel_small", 0, 33, _mut_one_channel_two_freqs),
+    "one_sample": ("ifu25", 77, 1, None),
+}
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("case", sorted(EDGE))
+def test_edge_cases(precision, case):
+    name, t0, nt, mut = EDGE[case]
+    sc, ref = oracle(name, t0, nt, mutate=mut, key=case)
+    got, flags, _ = gpu_run(sc, precision, t0, nt)
+    err = rel_err(got, ref["p_kid"])
+    print(f"{precision} {case}: max rel err {err:.3e} flags {flags}")
+    assert err < SIGNAL_TOL[precision]
+    if case == "pwv_clamped":
+        assert flags & L.STATUS_PWV_CLAMPED
+    else:
+        assert flags == 0
+
+
+# ---------------------------------------------------------------- full size, sampled
+
+def test_full_size_ifu_sampled_rows():
+    """The 25-spaxel IFU over the whole 20-minute raster (192000 samples x 25 x 347) in the
+    split-BF16 launch configuration the benchmark times, checked on sampled time windows
+    (all spaxels and channels) against the oracle, with white noise on."""
+    sc = W.scenario("ifu25")
+    nt = sc["nt_total"]
+    p = Plan(sc, precision="bf16x3", white=True, pink=False)
+    out = p.run(0, nt)
+    torch.cuda.synchronize()
+    assert p.status() & ~L.STATUS_PWV_CLAMPED == 0
+    assert bool(torch.isfinite(out).all())
+    for t0 in (0, 61337, 128000 - 3, nt - 8):
+        ref = O.simulate(sc, t0, 8, white=True, pink=False, return_parts=True)
+        got = out[t0:t0 + 8].cpu().numpy().astype(np.float64)
+        bound = (SIGMA_TOL["bf16x3"] * ref["sigma"] * (np.abs(ref["p_wn"] / ref["sigma"]) + 0.1)
+                 + SIGNAL_TOL["bf16x3"] * np.abs(ref["p_kid"]))
+        worst = np.max(np.abs(got - ref["total"]) / bound)
+        print(f"full size t0={t0}: worst error / bound = {worst:.3f}")
+        assert worst <= 1.0
+    again = p.run(0, nt)
+    torch.cuda.synchronize()
+    assert torch.equal(out, again)                    # deterministic

@@ -433,3 +433,21 @@ def test_chunked_simulation_equals_single_pass():
     a = O.simulate(sc, 0, 77, return_parts=True)
     b = O.simulate(sc, 77, 123, pink_state=a["pink_state"], return_parts=True)
     np.testing.assert_allclose(np.concatenate([a["total"], b["total"]]), full["total"], rtol=1e-12)
+
+
+def test_hex_layout_geometry():
+    """Packed hexagon (Sect. 2.3): 1 + 3R(R+1) spaxels (37 for R = 3, Sect. 4.1), nearest
+    neighbours one spacing apart, outermost ring corners at R spacings, point symmetric."""
+    for R in range(0, 5):
+        off = O.hex_offsets(R, 2.0)
+        assert off.shape == (1 + 3 * R * (R + 1), 2)
+        if R == 0:
+            continue
+        d = np.hypot(off[:, None, 0] - off[None, :, 0], off[:, None, 1] - off[None, :, 1])
+        np.fill_diagonal(d, np.inf)
+        np.testing.assert_allclose(d.min(axis=1), 2.0, rtol=1e-12)
+        r = np.hypot(off[:, 0], off[:, 1])
+        assert r.max() == pytest.approx(2.0 * R, rel=1e-12)
+        key = lambda a: set(map(tuple, np.round(a, 9)))
+        assert key(off) == key(-off)
+    assert O.hex_offsets(3, 1.0).shape[0] == 37
