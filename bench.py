@@ -193,6 +193,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--ref-samples", type=int, default=48)
+    ap.add_argument("--nt", type=int, default=None, help="shorter scan (profiling runs); default: the whole scan")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -219,7 +220,7 @@ def main():
         return float(t.item())
 
     # Each rank simulates an independent copy of the workload (its own screen / noise seeds).
-    sc = W.scenario(args.workload, seed=rank, noise_seed=1 + rank)
+    sc = W.scenario(args.workload, nt_total=args.nt, seed=rank, noise_seed=1 + rank)
     nt = sc["nt_total"]
     per_step = W.detector_samples(sc)
     plan = Plan(sc, precision=args.precision, white=True, pink=True)
