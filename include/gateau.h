@@ -289,6 +289,33 @@ gateau_status gateau_hex_offsets(int R_hex, double spacing_rad, double* out, int
 gateau_status gateau_run_batch(gateau_plan* const* plans, const long long* t0s, const long long* nts,
                                float* const* outs, int n, void* stream);
 
+/* Allocation-free pink-noise scan.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory while they run
+ * (an embedding runtime that owns a fixed memory pool, a real-time loop where
+ * cudaMalloc's device synchronisation and unbounded latency are not allowed,
+ * or a process whose memory was all reserved at start-up).  It adds the pink
+ * noise of samples t0 .. t0+nt-1 into out, exactly like the pink phase of
+ * gateau_run, using only buffers the caller passes plus 4 MiB of scratch that
+ * the library reserves as a static device array on every GPU that loads it
+ * (held until the process exits).  It calls no allocator.
+ *   pink_a, pink_r : device [n_ch][n_pole] poles and residues (gain folded in),
+ *                    e.g. the GATEAU_VEC_PINK_A / GATEAU_VEC_PINK_R tables as float
+ *   pink_d         : device [n_ch] direct terms (GATEAU_VEC_PINK_D as float)
+ *   state          : device [n_pix][n_ch][n_pole] filter state before sample t0
+ *                    (zeros at the start of a scan), updated in place
+ *   out            : device [nt][n_pix][n_ch], the noise is added in place
+ *   seed           : the plan seed (Philox key), so the draws match gateau_run
+ * Sizes with n_pix * n_ch * n_pole above 1048576 are rejected (EINVAL) before
+ * anything is enqueued.  The first call on a device looks up the scratch
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the scratch and leave their
+ * chunk states in it (nothing in it needs to start at zero: every state is
+ * written before it is read), so calls whose kernels overlap on the GPU --
+ * on different streams, or from different threads -- race; serialise them. */
+gateau_status gateau_pink_noise_noalloc(const float* pink_a, const float* pink_r, const float* pink_d,
+                                        int n_pix, int n_ch, int n_pole, unsigned long long seed,
+                                        long long t0, long long nt, float* state, float* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,9 @@ SIGNATURES = {
     "gateau_hex_offsets": (C.c_int, [C.c_int, C.c_double, dp, C.c_int, C.POINTER(C.c_int)]),
     "gateau_plan_set_timing": (C.c_int, [PlanP, C.c_int]),
     "gateau_plan_get_timing": (C.c_int, [PlanP, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+    "gateau_pink_noise_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                            C.c_ulonglong, C.c_longlong, C.c_longlong, C.c_void_p, C.c_void_p,
+                                            C.c_void_p]),
 }
 
 

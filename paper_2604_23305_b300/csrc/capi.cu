@@ -62,6 +62,11 @@ struct DevBuf {
 
 }  // namespace
 
+namespace gateau {
+// Lets other translation units report through gateau_last_error().
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace gateau
+
 struct gateau_plan {
     gateau_plan_desc desc{};
     std::vector<double> pix_off;      // [n_pix][2]

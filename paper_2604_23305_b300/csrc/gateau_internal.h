@@ -109,6 +109,7 @@ cudaError_t launch_pink(const DevTables& T, float* state, const PinkWork& W, lon
                         float* out, cudaStream_t stream);
 
 // Host helpers
+void set_last_error(const std::string& msg);
 uint16_t f32_to_bf16_rn(float x);
 float bf16_to_f32(uint16_t h);
 
