@@ -279,7 +279,8 @@ def main():
                          if args.precision == "bf16x3" else "FP32 SIMT",
                          "l2": "working set > L2: 197 MB source cube read and 6.66 GB output written per step",
                          "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
-              "roofline": roofline, "gpu_launches": launches, "clocks": clk.summary(), "status_flags": flags}
+              "roofline": roofline, "gpu_launches": launches, "clocks": clk.summary(), "status_flags": flags,
+              "staged_inputs": info.staged_inputs}
 
     # plain FP32 path on the same workload and GPU (the baseline the fused path is measured against)
     if not args.skip_fp32 and args.precision == "bf16x3":

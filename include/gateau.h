@@ -139,6 +139,8 @@ typedef struct {
     int n_ch, n_pix, n_pole;       /* channels, spaxels, pink-filter poles                      */
     long long next_t0;             /* first sample of the next chunk                            */
     size_t device_bytes;           /* device memory owned by the plan                           */
+    int staged_inputs;             /* 1 when the fused kernel stages its gathers by tensor copies
+                                      (set by the first BF16X3 run; 0 before it or on fallback)   */
 } gateau_plan_info;
 
 /* Host-built FP64 tables, for inspection and tests (gateau_plan_get_vector). */

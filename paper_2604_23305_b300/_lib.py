@@ -45,7 +45,8 @@ class Stage(C.Structure):
 
 class PlanInfo(C.Structure):
     _fields_ = [("n_freq", C.c_int), ("n_freq_padded", C.c_int), ("n_ch", C.c_int), ("n_pix", C.c_int),
-                ("n_pole", C.c_int), ("next_t0", C.c_longlong), ("device_bytes", C.c_size_t)]
+                ("n_pole", C.c_int), ("next_t0", C.c_longlong), ("device_bytes", C.c_size_t),
+                ("staged_inputs", C.c_int)]
 
 
 PlanP = C.c_void_p

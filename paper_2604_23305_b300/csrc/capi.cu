@@ -99,8 +99,10 @@ struct gateau_plan {
 
     // device memory
     DevBuf d_pix, d_cube, d_screen, d_tau, d_custom, d_c, d_HGQ, d_fusedB, d_pink, d_state, d_status;
-    DevBuf d_rows, d_X, d_agg, d_stage[2];
+    DevBuf d_rows, d_tiles, d_X, d_agg, d_stage[2];
     FusedOperands fused{};
+    TensorMapBytes tm_tau{}, tm_cube{};
+    bool maps_dirty = true;
     int n_ch_pad = 0;
     int n_sm = 148;
     long long next_t0 = 0;
@@ -116,7 +118,7 @@ struct gateau_plan {
 
     ~gateau_plan() {
         DevBuf* bufs[] = {&d_pix, &d_cube, &d_screen, &d_tau, &d_custom, &d_c, &d_HGQ, &d_fusedB, &d_pink,
-                          &d_state, &d_status, &d_rows, &d_X, &d_agg, &d_stage[0], &d_stage[1]};
+                          &d_state, &d_status, &d_rows, &d_tiles, &d_X, &d_agg, &d_stage[0], &d_stage[1]};
         for (DevBuf* b : bufs) b->release();
         for (int i = 0; i < 2; ++i) {
             if (ev_done[i]) cudaEventDestroy(ev_done[i]);
@@ -138,7 +140,7 @@ namespace {
 size_t device_bytes(const gateau_plan* p) {
     const DevBuf* bufs[] = {&p->d_pix, &p->d_cube, &p->d_screen, &p->d_tau, &p->d_custom, &p->d_c,
                             &p->d_HGQ, &p->d_fusedB, &p->d_pink, &p->d_state, &p->d_status, &p->d_rows,
-                            &p->d_X, &p->d_agg, &p->d_stage[0], &p->d_stage[1]};
+                            &p->d_tiles, &p->d_X, &p->d_agg, &p->d_stage[0], &p->d_stage[1]};
     size_t s = 0;
     for (const DevBuf* b : bufs) s += b->bytes;
     return s;
@@ -179,8 +181,14 @@ gateau_status finalize(gateau_plan* p) {
         cv[Kp + k] = static_cast<float>(p->c1[k] / kKB);
         cv[2 * Kp + k] = static_cast<float>(p->c2[k] / kKB);
     }
+    // The same vectors regrouped per 16-point stage, [Kp/16][c0, c1, c2][16], for the fused kernel.
+    const int ks = fused_kstage();
+    for (int b = 0; b < Kp / ks; ++b)
+        for (int m = 0; m < 3; ++m)
+            for (int k = 0; k < ks; ++k) cv.push_back(cv[static_cast<size_t>(m) * Kp + b * ks + k]);
     GATEAU_CUDA(p->d_c.ensure(cv.size() * sizeof(float)));
     GATEAU_CUDA(cudaMemcpy(p->d_c.p, cv.data(), cv.size() * sizeof(float), cudaMemcpyHostToDevice));
+    p->fused.c_tiled = p->d_c.as<float>() + 3 * static_cast<size_t>(Kp);
 
     // contraction operands, device units: w in GHz, X in kelvin.
     //   H = eta w_GHz;  G = H gamma (nu_GHz + beta);  Q = eta^2 w_GHz
@@ -379,8 +387,22 @@ gateau_status enqueue_run(gateau_plan* p, long long t0, long long nt, float* out
         GATEAU_CUDA(cudaMemsetAsync(p->d_state.p, 0, static_cast<size_t>(d.n_pix) * p->n_ch * p->n_pole * sizeof(float),
                                     stream));
     }
+    TileInfo* tiles = nullptr;
+    if (d.precision == GATEAU_PREC_BF16X3) {
+        const long long n_tiles = (nt + kTileRows - 1) / kTileRows * d.n_pix;
+        GATEAU_CUDA(p->d_tiles.ensure(static_cast<size_t>(n_tiles) * sizeof(TileInfo)));
+        tiles = p->d_tiles.as<TileInfo>();
+        if (p->maps_dirty) {
+            std::string err;
+            p->fused.tma_inputs = fused_encode_input_maps(p->d_tau.as<float>(), p->n_pwv, p->d_cube.as<float>(),
+                                                          p->n_az, p->n_el, p->Kp, &p->tm_tau, &p->tm_cube, err)
+                                      ? 1
+                                      : 0;
+            p->maps_dirty = false;
+        }
+    }
     GATEAU_CUDA(tm.begin(GATEAU_PHASE_ROWS));
-    GATEAU_CUDA(launch_row_setup(T, t0, nt, R, stream));
+    GATEAU_CUDA(launch_row_setup(T, t0, nt, R, tiles, stream));
     GATEAU_CUDA(tm.end(GATEAU_PHASE_ROWS));
     p->launches += 1;
     if (d.precision == GATEAU_PREC_FP32) {
@@ -399,7 +421,7 @@ gateau_status enqueue_run(gateau_plan* p, long long t0, long long nt, float* out
         GATEAU_CUDA(tm.end(GATEAU_PHASE_CONTRACT));
     } else {
         GATEAU_CUDA(tm.begin(GATEAU_PHASE_CONTRACT));
-        GATEAU_CUDA(launch_fused_bf16x3(T, p->fused, R, t0, nt, out, p->n_sm, stream));
+        GATEAU_CUDA(launch_fused_bf16x3(T, p->fused, p->tm_tau, p->tm_cube, R, tiles, t0, nt, out, p->n_sm, stream));
         GATEAU_CUDA(tm.end(GATEAU_PHASE_CONTRACT));
         p->launches += 1;
     }
@@ -485,7 +507,7 @@ gateau_status gateau_set_source_cube(gateau_plan* p, const float* cube, int n_az
                                      double daz_rad, double el0_rad, double del_rad, int mem) {
     if (!p || !cube) return fail(GATEAU_EINVAL, "plan and cube must be non-NULL");
     if (check_mem(mem) != GATEAU_OK) return GATEAU_EINVAL;
-    if (n_az < 2 || n_el < 2) return fail(GATEAU_EINVAL, "cube needs n_az, n_el >= 2");
+    if (n_az < 2 || n_el < 2 || n_az > 65535 || n_el > 65535) return fail(GATEAU_EINVAL, "cube needs 2 <= n_az, n_el <= 65535");
     if (!(daz_rad > 0.0) || !(del_rad > 0.0)) return fail(GATEAU_EINVAL, "cube grid steps must be > 0");
     if (static_cast<long long>(n_az) * n_el * p->Kp >= (1LL << 31)) return fail(GATEAU_EINVAL, "cube too large (n_az*n_el*n_freq >= 2^31)");
     gateau_status st = ensure_base(p);
@@ -502,6 +524,7 @@ gateau_status gateau_set_source_cube(gateau_plan* p, const float* cube, int n_az
     p->el0 = el0_rad;
     p->del = del_rad;
     p->has_cube = true;
+    p->maps_dirty = true;
     return GATEAU_OK;
 }
 
@@ -555,6 +578,7 @@ gateau_status gateau_set_atmosphere_table(gateau_plan* p, const float* table, in
     p->pwv_min = pwv_min_mm;
     p->dpwv = dpwv_mm;
     p->has_table = true;
+    p->maps_dirty = true;
     return GATEAU_OK;
 }
 
@@ -735,6 +759,7 @@ gateau_status gateau_plan_get_info(gateau_plan* p, gateau_plan_info* info) {
     info->n_pole = pink_pole_count(p->desc.pink_f_min_hz, p->desc.f_sample_hz);
     info->next_t0 = p->next_t0;
     info->device_bytes = device_bytes(p);
+    info->staged_inputs = p->fused.tma_inputs;
     return GATEAU_OK;
 }
 

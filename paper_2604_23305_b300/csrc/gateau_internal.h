@@ -25,7 +25,20 @@ struct __align__(16) RowParams {
     float src_fa;     // fractional azimuth cell position
     float src_fe;     // fractional elevation cell position
     float pwv;        // line-of-sight PWV (mm), kept for diagnostics
-    int pad;
+    int src_cell;     // ia * 65536 + ie of the cube cell, or -1 outside
+};
+
+// Per-tile summary written by the row setup for the fused kernel: the range of
+// opacity-table rows and the cube texel box that the tile's 128 rows touch, so
+// that both can be staged in shared memory by tensor copies.
+constexpr int kTileRows = 128;
+constexpr int kTauBoxRows = 8;                // opacity rows per staged box
+constexpr int kCubeBoxAz = 16, kCubeBoxEl = 8; // cube texels per staged box
+enum { TILE_TAU_FITS = 1, TILE_CUBE_FITS = 2, TILE_HAS_SOURCE = 4 };
+struct __align__(16) TileInfo {
+    int j0;           // lowest opacity row of the tile
+    int ia0, ie0;     // lowest cube cell of the tile's source rows
+    int flags;        // TILE_* bits
 };
 
 // Everything the kernels read, by value (device pointers + scalars).
@@ -80,19 +93,31 @@ struct FusedOperands {
     const uint16_t* B;                 // pre-tiled bf16 operand stages (see kernels_fused.cu)
     int n_half;                        // channels per CTA (multiple of 16)
     int n_groups;                      // channel groups (CTAs per row tile)
-    int n_kstage;                      // K stages of kKStage
+    int n_kstage;                      // K stages of fused_kstage() points
     size_t stage_elems;                // bf16 elements per (group, kstage) block
+    int tma_inputs;                    // 1: opacity rows and cube texels are staged by tensor copies
+    const float* c_tiled;              // [Kp/16][3][16] c0, c1, c2 per stage (kelvin)
+};
+
+// Opaque 128-byte tensor-map descriptors (CUtensorMap) for the staged inputs.
+struct __align__(64) TensorMapBytes {
+    unsigned char b[128];
 };
 
 // ---- kernel launchers (each enqueues on `stream`, returns cudaGetLastError) ----
 cudaError_t launch_row_setup(const DevTables& T, long long t0, long long nt, RowParams* rows,
-                             cudaStream_t stream);
+                             TileInfo* tiles, cudaStream_t stream);
 cudaError_t launch_psd_fp32(const DevTables& T, const RowParams* rows, long long r0, long long nrows,
                             float* X, cudaStream_t stream);
 cudaError_t launch_contract_fp32(const DevTables& T, const float* X, long long r0, long long nrows,
                                  long long t0, long long nt, float* out, cudaStream_t stream);
-cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, const RowParams* rows,
+cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, const TensorMapBytes& tm_tau,
+                                const TensorMapBytes& tm_cube, const RowParams* rows, const TileInfo* tiles,
                                 long long t0, long long nt, float* out, int n_sm, cudaStream_t stream);
+// Encodes the tensor maps of the opacity table [n_pwv][Kp] and the cube [n_az][n_el][Kp]
+// (driver entry point looked up at run time); false if the driver cannot.
+bool fused_encode_input_maps(const float* tau, int n_pwv, const float* cube, int n_az, int n_el, int Kp,
+                             TensorMapBytes* tm_tau, TensorMapBytes* tm_cube, std::string& err);
 size_t fused_smem_bytes();
 int fused_kstage();
 void fused_tile_operands(const double* H, const double* G, const double* Q, int n_ch, int Kp,

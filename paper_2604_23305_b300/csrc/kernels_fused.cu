@@ -14,38 +14,59 @@
 // epilogue turns S into P_KID (Eq. 16) and N into sigma (Eqs. 17-18), draws the
 // white noise (Eq. 19) from Philox and writes out[n][i][ch].
 //
-// Warp roles (320 threads, one CTA per SM, persistent over work items):
-//   warp 0      : bulk-copy producer of the pre-tiled filter operands (TMA engine)
-//   warp 1      : TMEM allocator + single-thread tcgen05.mma issuer
-//   warps 2..5  : spectrum producers, one thread per tile row
-//   warps 6..9  : epilogue, one thread per TMEM lane (= tile row)
+// Warp roles (448 threads, one CTA per SM, persistent over work items):
+//   warp 0 lane 0 : bulk copies of the pre-tiled filter operands (TMA engine), A/B ring
+//   warp 0 lane 1 : tensor copies of the tile's opacity rows and cube texel box, input ring
+//   warp 1        : TMEM allocator + single-thread tcgen05.mma issuer
+//   warps 2..9    : spectrum producers, one thread per (tile row, half of the 16-point slice)
+//   warps 10..13  : epilogue, one thread per TMEM lane (= tile row)
+// The input ring runs ahead of the producers, the A/B ring behind them, so the
+// producers read their gathers from shared memory.  Tiles whose opacity rows or
+// cube texels do not fit the staged boxes fall back to global loads.
 // Every wait is bounded: on time-out the kernel records GATEAU_STATUS_WAIT_TIMEOUT,
 // stops all roles, waits (bounded) for its own copies and MMAs, frees TMEM and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <math.h>
+#include <string.h>
 
 #include "device_common.cuh"
 
 namespace gateau {
 
-constexpr int kTileM = 128;          // rows per tile (TMEM lanes)
-constexpr int kKStage = 32;          // spectral points per pipeline stage
+constexpr int kTileM = kTileRows;    // rows per tile (TMEM lanes)
+constexpr int kKStage = 16;          // spectral points per pipeline stage (one K=16 MMA step)
 constexpr int kAMats = 3;            // X_hi, X_lo, bf16(X^2)
 constexpr int kBMats = 4;            // H_hi, H_lo, G, Q
-constexpr int kThreads = 320;
+constexpr int kProdWarps = 8;
+constexpr int kProdThreads = kProdWarps * 32;
+constexpr int kEpiWarp0 = 2 + kProdWarps;
+constexpr int kThreads = (kEpiWarp0 + 4) * 32;
 constexpr int kMaxSmem = 227 * 1024;
+constexpr int kInSlots = 5;          // input-ring depth (stages of staged gathers)
+// Staged rows are 20 points wide (80 B): the 16 points of the stage plus 4 that
+// are never read.  With a 20-word row stride, successive texels start on
+// different shared-memory banks, so lanes reading different texels at the same
+// point do not conflict.
+constexpr int kBoxW = 20;
+constexpr int kCubeBoxBytes = kCubeBoxAz * kCubeBoxEl * kBoxW * 4;    // 10240
+constexpr int kTauBoxBytes = kTauBoxRows * kBoxW * 4;                 // 640
+constexpr int kConstBytes = 3 * kKStage * 4;                          // c0, c1, c2 of the stage
+constexpr int kTauOff = kCubeBoxBytes;
+constexpr int kConstOff = kCubeBoxBytes + kTauBoxBytes;
+constexpr int kInSlotBytes = (kConstOff + kConstBytes + 127) / 128 * 128;
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
 int fused_kstage() { return kKStage; }
 
 // ---- operand layout ---------------------------------------------------------
-// One (matrix, stage) block holds R rows x 32 spectral points of bf16 in
-// "core matrices" of 8 rows x 16 bytes (8 points), ordered
-//   [k16 step (2)][row group (R/8)][8-point chunk within the step (2)][8 rows][8 points]
-// so element (r, k) sits at byte
-//   (k/16)*(R/8)*256 + (r/8)*256 + ((k%16)/8)*128 + (r%8)*16 + (k%8)*2.
-// For one K=16 MMA the core matrices adjacent along K are 128 B apart (leading
-// byte offset) and those adjacent along rows 256 B apart (stride byte offset).
+// One (matrix, stage) block holds R rows x 16 spectral points of bf16 in "core
+// matrices" of 8 rows x 16 bytes (8 points), ordered
+//   [row group (R/8)][8-point half of the slice (2)][8 rows][8 points]
+// so element (r, k) sits at byte (r/8)*256 + (k/8)*128 + (r%8)*16 + (k%8)*2.
+// For the K=16 MMA the core matrices adjacent along K are 128 B apart (leading
+// byte offset) and those adjacent along rows 256 B apart (stride byte offset);
+// either reading of the two offsets stays inside the block.
 __host__ __device__ constexpr size_t core_offset(int r, int k, int R) {
     return static_cast<size_t>(k / 16) * (R / 8) * 256 + static_cast<size_t>(r / 8) * 256 +
            ((k % 16) / 8) * 128 + (r % 8) * 16 + (k % 8) * 2;
@@ -94,10 +115,57 @@ void fused_tile_operands(const double* H, const double* G, const double* Q, int 
         }
 }
 
+// Host: tensor maps of the opacity table and the cube for the staged gathers.
+bool fused_encode_input_maps(const float* tau, int n_pwv, const float* cube, int n_az, int n_el, int Kp,
+                             TensorMapBytes* tm_tau, TensorMapBytes* tm_cube, std::string& err) {
+    static_assert(sizeof(CUtensorMap) == sizeof(TensorMapBytes), "tensor map size");
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        err = "cuTensorMapEncodeTiled unavailable";
+        return false;
+    }
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    Encode encode = reinterpret_cast<Encode>(fn);
+    const cuuint32_t estr[3] = {1, 1, 1};
+    {
+        const cuuint64_t dims[2] = {static_cast<cuuint64_t>(Kp), static_cast<cuuint64_t>(n_pwv)};
+        const cuuint64_t strides[1] = {static_cast<cuuint64_t>(Kp) * 4};
+        const cuuint32_t box[2] = {kBoxW, kTauBoxRows};
+        CUresult r = encode(reinterpret_cast<CUtensorMap*>(tm_tau), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                            const_cast<float*>(tau), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            err = "tensor map of the opacity table: CUresult " + std::to_string(static_cast<int>(r));
+            return false;
+        }
+    }
+    {
+        const cuuint64_t dims[3] = {static_cast<cuuint64_t>(Kp), static_cast<cuuint64_t>(n_el),
+                                    static_cast<cuuint64_t>(n_az)};
+        const cuuint64_t strides[2] = {static_cast<cuuint64_t>(Kp) * 4, static_cast<cuuint64_t>(Kp) * 4 * n_el};
+        const cuuint32_t box[3] = {kBoxW, kCubeBoxEl, kCubeBoxAz};
+        CUresult r = encode(reinterpret_cast<CUtensorMap*>(tm_cube), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                            const_cast<float*>(cube), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            err = "tensor map of the cube: CUresult " + std::to_string(static_cast<int>(r));
+            return false;
+        }
+    }
+    return true;
+}
+
 // ---- shared-memory plan -------------------------------------------------------
 struct SmemPlan {
     int n_stages;
-    size_t a_bytes, b_bytes, stage_bytes, bar_off, total;
+    size_t a_bytes, b_bytes, stage_bytes, in_off, bar_off, total;
 };
 
 __host__ __device__ inline SmemPlan smem_plan(int n_half) {
@@ -105,11 +173,13 @@ __host__ __device__ inline SmemPlan smem_plan(int n_half) {
     p.a_bytes = static_cast<size_t>(kAMats) * kTileM * kKStage * 2;
     p.b_bytes = static_cast<size_t>(kBMats) * n_half * kKStage * 2;
     p.stage_bytes = p.a_bytes + p.b_bytes;
-    const size_t bar_reserve = 256;
-    int ns = static_cast<int>((kMaxSmem - 1024 - bar_reserve) / p.stage_bytes);
-    if (ns > 4) ns = 4;
+    const size_t bar_reserve = 512;
+    const size_t in_bytes = static_cast<size_t>(kInSlots) * kInSlotBytes;
+    int ns = static_cast<int>((kMaxSmem - 1024 - bar_reserve - in_bytes) / p.stage_bytes);
+    if (ns > 6) ns = 6;
     p.n_stages = ns;
-    p.bar_off = p.stage_bytes * ns;
+    p.in_off = p.stage_bytes * ns;
+    p.bar_off = p.in_off + in_bytes;
     p.total = p.bar_off + bar_reserve + 1024;   // + alignment slack
     return p;
 }
@@ -162,6 +232,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
+// Bounded wait used on the exit path (no abort check).
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+    const long long t_start = clock64();
+    while (!mbar_try_wait(bar, parity) && clock64() - t_start < kWaitCycles) {
+    }
+}
+
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -170,6 +247,22 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
         "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tensor2d_g2s(uint32_t dst, const void* tmap, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tensor3d_g2s(uint32_t dst, const void* tmap, int x, int y, int z, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
 }
 
@@ -234,14 +327,17 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
     return *reinterpret_cast<const uint32_t*>(&v);
 }
 
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
 // ---- work decomposition ------------------------------------------------------
 struct Work {
     long long tiles_per_pix, n_items;
 };
 
-__device__ __forceinline__ void item_coords(const Work& w, int n_groups, long long it, int& pix,
+// Item it = tile * n_groups + group; tile = pix * tiles_per_pix + tile-in-pixel.
+__device__ __forceinline__ void item_coords(const Work& w, int n_groups, long long it, long long& tile, int& pix,
                                             long long& row0, int& nrows, int& grp, long long nt) {
-    const long long tile = it / n_groups;
+    tile = it / n_groups;
     grp = static_cast<int>(it - tile * n_groups);
     pix = static_cast<int>(tile / w.tiles_per_pix);
     const long long tl = tile - static_cast<long long>(pix) * w.tiles_per_pix;
@@ -251,31 +347,39 @@ __device__ __forceinline__ void item_coords(const Work& w, int n_groups, long lo
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-    fused_bf16x3_kernel(DevTables T, FusedOperands F, const RowParams* __restrict__ rows, long long t0,
-                        long long nt, Work work, float* __restrict__ out) {
+    fused_bf16x3_kernel(const __grid_constant__ CUtensorMap tm_tau, const __grid_constant__ CUtensorMap tm_cube,
+                        DevTables T, FusedOperands F, const RowParams* __restrict__ rows,
+                        const TileInfo* __restrict__ tiles, long long t0, long long nt, Work work,
+                        float* __restrict__ out) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int NH = F.n_half;
     const SmemPlan sp = smem_plan(NH);
     const int NS = sp.n_stages;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + sp.bar_off);
-    // barrier slots: full_a[NS], full_b[NS], empty[NS], acc_full, acc_empty
     const uint32_t bar_base = smem_u32(bars);
     auto full_a = [&](int s) { return bar_base + 8u * s; };
     auto full_b = [&](int s) { return bar_base + 8u * (NS + s); };
     auto empty_bar = [&](int s) { return bar_base + 8u * (2 * NS + s); };
-    const uint32_t acc_full = bar_base + 8u * (3 * NS);
-    const uint32_t acc_empty = bar_base + 8u * (3 * NS + 1);
-    const uint32_t drain_bar = bar_base + 8u * (3 * NS + 2);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + sp.bar_off + 8 * (3 * NS + 3));
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + sp.bar_off + 8 * (3 * NS + 3) + 8);
+    auto full_in = [&](int s) { return bar_base + 8u * (3 * NS + s); };
+    auto empty_in = [&](int s) { return bar_base + 8u * (3 * NS + kInSlots + s); };
+    const int nb = 3 * NS + 2 * kInSlots;
+    const uint32_t acc_full = bar_base + 8u * nb;
+    const uint32_t acc_empty = bar_base + 8u * (nb + 1);
+    const uint32_t drain_bar = bar_base + 8u * (nb + 2);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + sp.bar_off + 8 * (nb + 3));
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + sp.bar_off + 8 * (nb + 3) + 8);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
-            mbar_init(full_a(s), 128);
+            mbar_init(full_a(s), kProdThreads);
             mbar_init(full_b(s), 1);
             mbar_init(empty_bar(s), 1);
+        }
+        for (int s = 0; s < kInSlots; ++s) {
+            mbar_init(full_in(s), 1);
+            mbar_init(empty_in(s), kProdThreads);
         }
         mbar_init(acc_full, 1);
         mbar_init(acc_empty, 128);
@@ -301,40 +405,72 @@ __global__ void __launch_bounds__(kThreads, 1)
                                    : 0;
 
     if (warp == 0) {
-        // ---------------- filter-operand producer (bulk copies) ----------------
         if (lane == 0) {
-            long long g = 0;     // global stage counter
+            // ---------------- filter operands: one bulk copy per stage (A/B ring) ----------------
+            long long g = 0;
+            int s = 0;
+            uint32_t ph = 0;           // parity of the current pass over the ring
             const uint32_t bytes = static_cast<uint32_t>(sp.b_bytes);
             for (long long j = 0; j < my_items && !*abort_flag; ++j) {
                 const long long it = blockIdx.x + j * gridDim.x;
                 const int grp = static_cast<int>(it % F.n_groups);
                 const uint16_t* src = F.B + static_cast<size_t>(grp) * n_ks * F.stage_elems;
-                for (int ks = 0; ks < n_ks; ++ks, ++g) {
-                    const int s = static_cast<int>(g % NS);
-                    const long long u = g / NS;
-                    if (u > 0 && !mbar_wait(empty_bar(s), static_cast<uint32_t>((u - 1) & 1), abort_flag, T.status))
+                bool ok = true;
+                for (int ks = 0; ks < n_ks; ++ks) {
+                    if (g >= NS && !mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, T.status)) {
+                        ok = false;
                         break;
+                    }
                     mbar_arrive_expect_tx(full_b(s), bytes);
                     bulk_g2s(smem_u32(smem + s * sp.stage_bytes + sp.a_bytes), src + ks * F.stage_elems, bytes,
                              full_b(s));
+                    ++g;
+                    if (++s == NS) { s = 0; ph ^= 1u; }
                 }
+                if (!ok) break;
             }
-            // Drain: every copy issued lands on its full_b barrier; wait for the
-            // last NS of them (bounded) so no copy is in flight at exit.
-            const long long issued = g;
-            for (long long q = (issued > NS ? issued - NS : 0); q < issued; ++q) {
-                const int s = static_cast<int>(q % NS);
-                const uint32_t par = static_cast<uint32_t>((q / NS) & 1);
-                const long long t_start = clock64();
-                while (!mbar_try_wait(full_b(s), par) && clock64() - t_start < kWaitCycles) {
+            for (long long q = (g > NS ? g - NS : 0); q < g; ++q)    // no copy in flight at exit
+                mbar_drain(full_b(static_cast<int>(q % NS)), static_cast<uint32_t>((q / NS) & 1));
+        } else if (lane == 1) {
+            // ---------------- staged gathers: opacity rows + cube box per stage (input ring) ----------------
+            long long g = 0;
+            int s = 0;
+            uint32_t ph = 0;
+            for (long long j = 0; j < my_items && !*abort_flag; ++j) {
+                const long long it = blockIdx.x + j * gridDim.x;
+                long long tile, row0;
+                int pix, nrows, grp;
+                item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
+                const TileInfo ti = tiles[tile];
+                const bool tau_box = F.tma_inputs && (ti.flags & TILE_TAU_FITS);
+                const bool cube_box = F.tma_inputs && (ti.flags & TILE_CUBE_FITS);
+                const uint32_t bytes = kConstBytes + (tau_box ? kTauBoxBytes : 0) + (cube_box ? kCubeBoxBytes : 0);
+                bool ok = true;
+                for (int ks = 0; ks < n_ks; ++ks) {
+                    if (g >= kInSlots && !mbar_wait(empty_in(s), ph ^ 1u, abort_flag, T.status)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* slot = smem + sp.in_off + static_cast<size_t>(s) * kInSlotBytes;
+                    mbar_arrive_expect_tx(full_in(s), bytes);
+                    bulk_g2s(smem_u32(slot + kConstOff), F.c_tiled + static_cast<size_t>(ks) * 3 * kKStage,
+                             kConstBytes, full_in(s));
+                    if (cube_box) tensor3d_g2s(smem_u32(slot), &tm_cube, ks * kKStage, ti.ie0, ti.ia0, full_in(s));
+                    if (tau_box) tensor2d_g2s(smem_u32(slot + kTauOff), &tm_tau, ks * kKStage, ti.j0, full_in(s));
+                    ++g;
+                    if (++s == kInSlots) { s = 0; ph ^= 1u; }
                 }
+                if (!ok) break;
             }
+            for (long long q = (g > kInSlots ? g - kInSlots : 0); q < g; ++q)
+                mbar_drain(full_in(static_cast<int>(q % kInSlots)), static_cast<uint32_t>((q / kInSlots) & 1));
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             const uint32_t idesc = make_idesc(NH);
-            long long g = 0;
+            int s = 0;
+            uint32_t par = 0;
             bool ok = true;
             for (long long j = 0; j < my_items && ok; ++j) {
                 if (j > 0) {
@@ -342,9 +478,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!ok) break;
                     tc_fence_after();
                 }
-                for (int ks = 0; ks < n_ks; ++ks, ++g) {
-                    const int s = static_cast<int>(g % NS);
-                    const uint32_t par = static_cast<uint32_t>((g / NS) & 1);
+                for (int ks = 0; ks < n_ks; ++ks) {
                     if (!mbar_wait(full_b(s), par, abort_flag, T.status) ||
                         !mbar_wait(full_a(s), par, abort_flag, T.status)) {
                         ok = false;
@@ -355,122 +489,151 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t b0 = a0 + static_cast<uint32_t>(sp.a_bytes);
                     const uint32_t a_mat = kTileM * kKStage * 2;            // bytes per A matrix
                     const uint32_t b_mat = static_cast<uint32_t>(NH) * kKStage * 2;
-#pragma unroll
-                    for (int kk = 0; kk < kKStage / 16; ++kk) {
-                        const uint32_t a_k = kk * (kTileM / 8) * 256;
-                        const uint32_t b_k = kk * (NH / 8) * 256;
-                        const uint64_t xhi = smem_desc(a0 + 0 * a_mat + a_k, 128, 256);
-                        const uint64_t xlo = smem_desc(a0 + 1 * a_mat + a_k, 128, 256);
-                        const uint64_t xsq = smem_desc(a0 + 2 * a_mat + a_k, 128, 256);
-                        const uint64_t hhi = smem_desc(b0 + 0 * b_mat + b_k, 128, 256);
-                        const uint64_t hlo = smem_desc(b0 + 1 * b_mat + b_k, 128, 256);
-                        const uint64_t gmat = smem_desc(b0 + 2 * b_mat + b_k, 128, 256);
-                        const uint64_t qmat = smem_desc(b0 + 3 * b_mat + b_k, 128, 256);
-                        const uint32_t acc = (ks > 0 || kk > 0) ? 1u : 0u;
-                        tc_mma(d_sig, xhi, hhi, idesc, acc);
-                        tc_mma(d_sig, xlo, hhi, idesc, 1u);
-                        tc_mma(d_sig, xhi, hlo, idesc, 1u);
-                        tc_mma(d_noi, xhi, gmat, idesc, acc);
-                        tc_mma(d_noi, xsq, qmat, idesc, 1u);
-                    }
+                    const uint64_t xhi = smem_desc(a0 + 0 * a_mat, 128, 256);
+                    const uint64_t xlo = smem_desc(a0 + 1 * a_mat, 128, 256);
+                    const uint64_t xsq = smem_desc(a0 + 2 * a_mat, 128, 256);
+                    const uint64_t hhi = smem_desc(b0 + 0 * b_mat, 128, 256);
+                    const uint64_t hlo = smem_desc(b0 + 1 * b_mat, 128, 256);
+                    const uint64_t gmat = smem_desc(b0 + 2 * b_mat, 128, 256);
+                    const uint64_t qmat = smem_desc(b0 + 3 * b_mat, 128, 256);
+                    const uint32_t acc = ks > 0 ? 1u : 0u;
+                    tc_mma(d_sig, xhi, hhi, idesc, acc);
+                    tc_mma(d_sig, xlo, hhi, idesc, 1u);
+                    tc_mma(d_sig, xhi, hlo, idesc, 1u);
+                    tc_mma(d_noi, xhi, gmat, idesc, acc);
+                    tc_mma(d_noi, xsq, qmat, idesc, 1u);
                     tc_commit(empty_bar(s));          // stage s free once these MMAs finish
+                    if (++s == NS) { s = 0; par ^= 1u; }
                 }
                 if (!ok) break;
                 tc_commit(acc_full);                  // accumulators of item j complete
             }
-            // Make sure no MMA is in flight at exit (bounded).
-            tc_commit(drain_bar);
-            const long long t_start = clock64();
-            while (!mbar_try_wait(drain_bar, 0) && clock64() - t_start < kWaitCycles) {
-            }
+            tc_commit(drain_bar);                     // no MMA in flight at exit (bounded)
+            mbar_drain(drain_bar, 0);
         }
-    } else if (warp < 6) {
-        // ---------------- spectrum producers: thread = tile row ----------------
-        const int r = (warp - 2) * 32 + lane;
+    } else if (warp < kEpiWarp0) {
+        // ---------------- spectrum producers: thread = (tile row, 8-point half) ----------------
+        const int pw = warp - 2;
+        const int r = (pw & 3) * 32 + lane;
+        const int kh = (pw >> 2) * 8;               // point offset of this thread within the stage
         long long g = 0;
+        int s = 0, si = 0;
+        uint32_t ph = 0, phi = 0;
         bool ok = true;
         for (long long j = 0; j < my_items && ok; ++j) {
             const long long it = blockIdx.x + j * gridDim.x;
+            long long tile, row0;
             int pix, nrows, grp;
-            long long row0;
-            item_coords(work, F.n_groups, it, pix, row0, nrows, grp, nt);
+            item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
+            const TileInfo ti = tiles[tile];
             const bool valid = r < nrows;
             RowParams rp;
             if (valid) {
                 rp = rows[static_cast<long long>(pix) * nt + row0 + r];
             } else {
-                rp.csc = 1.f; rp.tau_j = 0; rp.tau_f = 0.f; rp.src_idx = -1; rp.src_fa = 0.f; rp.src_fe = 0.f;
+                rp.csc = 1.f; rp.tau_j = ti.j0; rp.tau_f = 0.f; rp.src_idx = -1; rp.src_fa = 0.f; rp.src_fe = 0.f;
+                rp.src_cell = -1;
             }
             if (rp.tau_j < 0 || rp.tau_j > T.n_pwv - 2) {
                 atomicOr(T.status, GATEAU_STATUS_BAD_INDEX);
                 rp.tau_j = 0;
             }
-            const float* tA = T.tau + static_cast<long long>(rp.tau_j) * T.Kp;
-            const float* tB = tA + T.Kp;
             const bool has_src = valid && rp.src_idx >= 0;
+            // staged boxes, with a range check that sends a row to the global path otherwise
+            const int dj = rp.tau_j - ti.j0;
+            const bool tau_box = F.tma_inputs && (ti.flags & TILE_TAU_FITS) && dj >= 0 && dj <= kTauBoxRows - 2;
+            const int da = has_src ? (rp.src_cell >> 16) - ti.ia0 : 0;
+            const int de = has_src ? (rp.src_cell & 0xffff) - ti.ie0 : 0;
+            const bool cube_box = has_src && F.tma_inputs && (ti.flags & TILE_CUBE_FITS) && da >= 0 &&
+                                  da <= kCubeBoxAz - 2 && de >= 0 && de <= kCubeBoxEl - 2;
+            const float* gA = T.tau + static_cast<long long>(rp.tau_j) * T.Kp;
+            const float* gB = gA + T.Kp;
             const float fa = rp.src_fa, fe = rp.src_fe;
             const float w00 = (1.f - fa) * (1.f - fe), w10 = fa * (1.f - fe), w01 = (1.f - fa) * fe, w11 = fa * fe;
-            const float* s00 = T.cube + (has_src ? rp.src_idx : 0);
-            const float* s10 = s00 + static_cast<long long>(T.n_el) * T.Kp;
-            const float* s01 = s00 + T.Kp;
-            const float* s11 = s10 + T.Kp;
+            const float* g00 = T.cube + (has_src ? rp.src_idx : 0);
+            const float* g10 = g00 + static_cast<long long>(T.n_el) * T.Kp;
+            const float* g01 = g00 + T.Kp;
+            const float* g11 = g10 + T.Kp;
+            const int sA = dj * kBoxW + kh;                                      // float offsets inside a slot
+            const int sC00 = (da * kCubeBoxEl + de) * kBoxW + kh;
+            const int sC10 = sC00 + kCubeBoxEl * kBoxW;
+            const int sC01 = sC00 + kBoxW;
+            const int sC11 = sC10 + kBoxW;
             const float csc = rp.csc, tf = rp.tau_f;
-            for (int ks = 0; ks < n_ks; ++ks, ++g) {
-                const int s = static_cast<int>(g % NS);
-                const long long u = g / NS;
-                if (u > 0 && !mbar_wait(empty_bar(s), static_cast<uint32_t>((u - 1) & 1), abort_flag, T.status)) {
+            for (int ks = 0; ks < n_ks; ++ks) {
+                if ((g >= NS && !mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, T.status)) ||
+                    !mbar_wait(full_in(si), phi, abort_flag, T.status)) {
                     ok = false;
                     break;
                 }
-                uint8_t* a0 = smem + s * sp.stage_bytes;
+                const float* slot = reinterpret_cast<const float*>(smem + sp.in_off + static_cast<size_t>(si) * kInSlotBytes);
+                const float* stau = slot + kTauOff / 4;
+                const float* scon = slot + kConstOff / 4 + kh;
+                const int k = ks * kKStage + kh;
+                float x[8];
 #pragma unroll
-                for (int kc = 0; kc < kKStage / 8; ++kc) {
-                    const int k = ks * kKStage + kc * 8;
-                    float x[8];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int kq = k + 4 * h;
-                        const float4 ta = *reinterpret_cast<const float4*>(tA + kq);
-                        const float4 tb = *reinterpret_cast<const float4*>(tB + kq);
-                        const float4 c0 = __ldg(reinterpret_cast<const float4*>(T.c0 + kq));
-                        const float4 c1 = __ldg(reinterpret_cast<const float4*>(T.c1 + kq));
-                        const float4 c2 = __ldg(reinterpret_cast<const float4*>(T.c2 + kq));
-                        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (has_src) {
-                            const float4 q00 = *reinterpret_cast<const float4*>(s00 + kq);
-                            const float4 q10 = *reinterpret_cast<const float4*>(s10 + kq);
-                            const float4 q01 = *reinterpret_cast<const float4*>(s01 + kq);
-                            const float4 q11 = *reinterpret_cast<const float4*>(s11 + kq);
-                            p.x = w00 * q00.x + w10 * q10.x + w01 * q01.x + w11 * q11.x;
-                            p.y = w00 * q00.y + w10 * q10.y + w01 * q01.y + w11 * q11.y;
-                            p.z = w00 * q00.z + w10 * q10.z + w01 * q01.z + w11 * q11.z;
-                            p.w = w00 * q00.w + w10 * q10.w + w01 * q01.w + w11 * q11.w;
+                for (int h = 0; h < 2; ++h) {
+                    const int kq = k + 4 * h;
+                    float4 ta, tb;
+                    if (tau_box) {
+                        ta = ld4(stau + sA + 4 * h);
+                        tb = ld4(stau + sA + kBoxW + 4 * h);
+                    } else {
+                        ta = ld4(gA + kq);
+                        tb = ld4(gB + kq);
+                    }
+                    const float4 c0 = ld4(scon + 4 * h);
+                    const float4 c1 = ld4(scon + kKStage + 4 * h);
+                    const float4 c2 = ld4(scon + 2 * kKStage + 4 * h);
+                    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (has_src) {
+                        float4 q00, q10, q01, q11;
+                        if (cube_box) {
+                            q00 = ld4(slot + sC00 + 4 * h);
+                            q10 = ld4(slot + sC10 + 4 * h);
+                            q01 = ld4(slot + sC01 + 4 * h);
+                            q11 = ld4(slot + sC11 + 4 * h);
+                        } else {
+                            q00 = ld4(g00 + kq);
+                            q10 = ld4(g10 + kq);
+                            q01 = ld4(g01 + kq);
+                            q11 = ld4(g11 + kq);
                         }
+                        p.x = w00 * q00.x + w10 * q10.x + w01 * q01.x + w11 * q11.x;
+                        p.y = w00 * q00.y + w10 * q10.y + w01 * q01.y + w11 * q11.y;
+                        p.z = w00 * q00.z + w10 * q10.z + w01 * q01.z + w11 * q11.z;
+                        p.w = w00 * q00.w + w10 * q10.w + w01 * q01.w + w11 * q11.w;
+                    }
 #define GATEAU_FX(i, c)                                          \
     {                                                            \
         const float tau = ta.c + tf * (tb.c - ta.c);             \
         const float e = __expf(-csc * tau);                      \
         x[4 * h + i] = c0.c + c1.c * (1.f - e) + c2.c * e * p.c; \
     }
-                        GATEAU_FX(0, x) GATEAU_FX(1, y) GATEAU_FX(2, z) GATEAU_FX(3, w)
+                    GATEAU_FX(0, x) GATEAU_FX(1, y) GATEAU_FX(2, z) GATEAU_FX(3, w)
 #undef GATEAU_FX
-                    }
-                    uint32_t hi[4], lo[4], sq[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float xa = x[2 * q], xb = x[2 * q + 1];
-                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(xa, xb);
-                        hi[q] = *reinterpret_cast<const uint32_t*>(&h2);
-                        lo[q] = pack_bf16(xa - __low2float(h2), xb - __high2float(h2));
-                        sq[q] = pack_bf16(xa * xa, xb * xb);
-                    }
-                    const size_t off = core_offset(r, kc * 8, kTileM);
-                    *reinterpret_cast<uint4*>(a0 + 0 * (kTileM * kKStage * 2) + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                    *reinterpret_cast<uint4*>(a0 + 1 * (kTileM * kKStage * 2) + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-                    *reinterpret_cast<uint4*>(a0 + 2 * (kTileM * kKStage * 2) + off) = make_uint4(sq[0], sq[1], sq[2], sq[3]);
                 }
+                uint32_t hi[4], lo[4], sq[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float xa = x[2 * q], xb = x[2 * q + 1];
+                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(xa, xb);
+                    hi[q] = *reinterpret_cast<const uint32_t*>(&h2);
+                    lo[q] = pack_bf16(xa - __low2float(h2), xb - __high2float(h2));
+                    sq[q] = pack_bf16(xa * xa, xb * xb);
+                }
+                uint8_t* a0 = smem + s * sp.stage_bytes;
+                const size_t off = core_offset(r, kh, kTileM);
+                constexpr int amat = kTileM * kKStage * 2;
+                *reinterpret_cast<uint4*>(a0 + 0 * amat + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<uint4*>(a0 + 1 * amat + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                *reinterpret_cast<uint4*>(a0 + 2 * amat + off) = make_uint4(sq[0], sq[1], sq[2], sq[3]);
                 fence_proxy_async();
                 mbar_arrive(full_a(s));
+                mbar_arrive(empty_in(si));
+                ++g;
+                if (++s == NS) { s = 0; ph ^= 1u; }
+                if (++si == kInSlots) { si = 0; phi ^= 1u; }
             }
         }
     } else {
@@ -484,9 +647,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
             const long long it = blockIdx.x + j * gridDim.x;
+            long long tile, row0;
             int pix, nrows, grp;
-            long long row0;
-            item_coords(work, F.n_groups, it, pix, row0, nrows, grp, nt);
+            item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
             const long long n = t0 + row0 + r;
             float* orow = out + ((row0 + r) * T.n_pix + pix) * static_cast<long long>(T.n_ch);
             const int ch_base = grp * NH;
@@ -529,8 +692,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, const RowParams* rows, long long t0,
-                                long long nt, float* out, int n_sm, cudaStream_t stream) {
+cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, const TensorMapBytes& tm_tau,
+                                const TensorMapBytes& tm_cube, const RowParams* rows, const TileInfo* tiles,
+                                long long t0, long long nt, float* out, int n_sm, cudaStream_t stream) {
     const SmemPlan sp = smem_plan(F.n_half);
     if (sp.n_stages < 2) return cudaErrorInvalidConfiguration;
     Work w;
@@ -540,8 +704,12 @@ cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, cons
     cudaError_t e = cudaFuncSetAttribute(fused_bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(sp.total));
     if (e != cudaSuccess) return e;
+    CUtensorMap mt, mc;
+    memcpy(&mt, &tm_tau, sizeof(mt));
+    memcpy(&mc, &tm_cube, sizeof(mc));
     long long grid = w.n_items < n_sm ? w.n_items : n_sm;
-    fused_bf16x3_kernel<<<static_cast<unsigned>(grid), kThreads, sp.total, stream>>>(T, F, rows, t0, nt, w, out);
+    fused_bf16x3_kernel<<<static_cast<unsigned>(grid), kThreads, sp.total, stream>>>(mt, mc, T, F, rows, tiles, t0,
+                                                                                     nt, w, out);
     return cudaGetLastError();
 }
 

@@ -89,7 +89,6 @@ __device__ __forceinline__ RowParams make_row(const DevTables& T, long long n, i
     rp.tau_j = j;
     rp.tau_f = static_cast<float>(u - j);
     rp.pwv = static_cast<float>(pwv);
-    rp.pad = 0;
     // Source cell (bilinear, zero outside the grid).
     const double su = (az - T.az0) / T.daz, sv = (el - T.el0) / T.del;
     if (su >= 0.0 && su <= T.n_az - 1 && sv >= 0.0 && sv <= T.n_el - 1) {
@@ -98,32 +97,72 @@ __device__ __forceinline__ RowParams make_row(const DevTables& T, long long n, i
         rp.src_idx = (ia * T.n_el + ie) * T.Kp;
         rp.src_fa = static_cast<float>(su - ia);
         rp.src_fe = static_cast<float>(sv - ie);
+        rp.src_cell = ia * 65536 + ie;
     } else {
         rp.src_idx = -1;
         rp.src_fa = 0.f;
         rp.src_fe = 0.f;
+        rp.src_cell = -1;
     }
     return rp;
 }
 
-// rows are pixel-major within a run: r = i * nt + (n - t0)
-__global__ void row_setup_kernel(DevTables T, long long t0, long long nt, RowParams* rows) {
-    const long long total = nt * T.n_pix;
-    for (long long r = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; r < total;
-         r += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int i = static_cast<int>(r / nt);
-        const long long n = t0 + (r - static_cast<long long>(i) * nt);
-        rows[r] = make_row(T, n, i);
+// One block of kTileRows threads per tile of kTileRows consecutive samples of one
+// spaxel; rows are pixel-major within a run (r = i * nt + (n - t0)).  With a tile
+// buffer, the block also reduces the opacity-row range and the cube box of the tile.
+__global__ void __launch_bounds__(kTileRows) row_setup_kernel(DevTables T, long long t0, long long nt,
+                                                              RowParams* rows, TileInfo* tiles) {
+    __shared__ int s_jmin, s_jmax, s_amin, s_amax, s_emin, s_emax, s_nsrc;
+    const long long tpp = (nt + kTileRows - 1) / kTileRows;
+    const long long n_tiles = tpp * T.n_pix;
+    for (long long b = blockIdx.x; b < n_tiles; b += gridDim.x) {
+        const int i = static_cast<int>(b / tpp);
+        const long long r = (b - static_cast<long long>(i) * tpp) * kTileRows + threadIdx.x;
+        if (tiles && threadIdx.x == 0) {
+            s_jmin = s_amin = s_emin = 0x7fffffff;
+            s_jmax = s_amax = s_emax = -1;
+            s_nsrc = 0;
+        }
+        __syncthreads();
+        if (r < nt) {
+            const RowParams rp = make_row(T, t0 + r, i);
+            rows[static_cast<long long>(i) * nt + r] = rp;
+            if (tiles) {
+                atomicMin(&s_jmin, rp.tau_j);
+                atomicMax(&s_jmax, rp.tau_j);
+                if (rp.src_cell >= 0) {
+                    atomicMin(&s_amin, rp.src_cell >> 16);
+                    atomicMax(&s_amax, rp.src_cell >> 16);
+                    atomicMin(&s_emin, rp.src_cell & 0xffff);
+                    atomicMax(&s_emax, rp.src_cell & 0xffff);
+                    atomicAdd(&s_nsrc, 1);
+                }
+            }
+        }
+        __syncthreads();
+        if (tiles && threadIdx.x == 0) {
+            TileInfo ti;
+            ti.j0 = s_jmin;
+            ti.ia0 = s_nsrc ? s_amin : 0;
+            ti.ie0 = s_nsrc ? s_emin : 0;
+            int f = 0;
+            if (s_jmax + 1 - s_jmin <= kTauBoxRows - 1) f |= TILE_TAU_FITS;
+            if (s_nsrc) {
+                f |= TILE_HAS_SOURCE;
+                if (s_amax + 1 - s_amin <= kCubeBoxAz - 1 && s_emax + 1 - s_emin <= kCubeBoxEl - 1) f |= TILE_CUBE_FITS;
+            }
+            ti.flags = f;
+            tiles[b] = ti;
+        }
+        __syncthreads();
     }
 }
 
-cudaError_t launch_row_setup(const DevTables& T, long long t0, long long nt, RowParams* rows,
+cudaError_t launch_row_setup(const DevTables& T, long long t0, long long nt, RowParams* rows, TileInfo* tiles,
                              cudaStream_t stream) {
-    const long long total = nt * T.n_pix;
-    const int block = 256;
-    long long grid = (total + block - 1) / block;
-    if (grid > 148LL * 64) grid = 148LL * 64;
-    row_setup_kernel<<<static_cast<unsigned>(grid), block, 0, stream>>>(T, t0, nt, rows);
+    const long long n_tiles = (nt + kTileRows - 1) / kTileRows * T.n_pix;
+    long long grid = n_tiles < 148LL * 16 ? n_tiles : 148LL * 16;
+    row_setup_kernel<<<static_cast<unsigned>(grid), kTileRows, 0, stream>>>(T, t0, nt, rows, tiles);
     return cudaGetLastError();
 }
 
