@@ -98,7 +98,8 @@ struct gateau_plan {
     bool dirty = true;
 
     // device memory
-    DevBuf d_pix, d_cube, d_screen, d_tau, d_custom, d_c, d_HGQ, d_fusedB, d_pink, d_state, d_status;
+    DevBuf d_pix, d_cube, d_cube_raw, d_screen, d_tau, d_custom, d_c, d_HGQ, d_fusedB, d_pink, d_state, d_status;
+    bool cube_scale_dirty = true;    // d_cube = d_cube_raw * c2 / k_B must be recomputed
     DevBuf d_rows, d_tiles, d_X, d_agg, d_stage[2];
     FusedOperands fused{};
     TensorMapBytes tm_tau{}, tm_cube{};
@@ -117,7 +118,7 @@ struct gateau_plan {
     long long runs = 0, launches = 0;
 
     ~gateau_plan() {
-        DevBuf* bufs[] = {&d_pix, &d_cube, &d_screen, &d_tau, &d_custom, &d_c, &d_HGQ, &d_fusedB, &d_pink,
+        DevBuf* bufs[] = {&d_pix, &d_cube, &d_cube_raw, &d_screen, &d_tau, &d_custom, &d_c, &d_HGQ, &d_fusedB, &d_pink,
                           &d_state, &d_status, &d_rows, &d_tiles, &d_X, &d_agg, &d_stage[0], &d_stage[1]};
         for (DevBuf* b : bufs) b->release();
         for (int i = 0; i < 2; ++i) {
@@ -138,7 +139,7 @@ struct gateau_plan {
 namespace {
 
 size_t device_bytes(const gateau_plan* p) {
-    const DevBuf* bufs[] = {&p->d_pix, &p->d_cube, &p->d_screen, &p->d_tau, &p->d_custom, &p->d_c,
+    const DevBuf* bufs[] = {&p->d_pix, &p->d_cube, &p->d_cube_raw, &p->d_screen, &p->d_tau, &p->d_custom, &p->d_c,
                             &p->d_HGQ, &p->d_fusedB, &p->d_pink, &p->d_state, &p->d_status, &p->d_rows,
                             &p->d_tiles, &p->d_X, &p->d_agg, &p->d_stage[0], &p->d_stage[1]};
     size_t s = 0;
@@ -181,14 +182,19 @@ gateau_status finalize(gateau_plan* p) {
         cv[Kp + k] = static_cast<float>(p->c1[k] / kKB);
         cv[2 * Kp + k] = static_cast<float>(p->c2[k] / kKB);
     }
-    // The same vectors regrouped per 16-point stage, [Kp/16][c0, c1, c2][16], for the fused kernel.
+    // Regrouped per 16-point stage for the fused kernel: [Kp/16][c0 + c1, c1][16].
     const int ks = fused_kstage();
-    for (int b = 0; b < Kp / ks; ++b)
-        for (int m = 0; m < 3; ++m)
-            for (int k = 0; k < ks; ++k) cv.push_back(cv[static_cast<size_t>(m) * Kp + b * ks + k]);
+    for (int b = 0; b < Kp / ks; ++b) {
+        for (int k = 0; k < ks; ++k) {
+            const int kk = b * ks + k;
+            cv.push_back(kk < nf ? static_cast<float>((p->c0[kk] + p->c1[kk]) / kKB) : 0.f);
+        }
+        for (int k = 0; k < ks; ++k) cv.push_back(cv[static_cast<size_t>(Kp) + b * ks + k]);
+    }
     GATEAU_CUDA(p->d_c.ensure(cv.size() * sizeof(float)));
     GATEAU_CUDA(cudaMemcpy(p->d_c.p, cv.data(), cv.size() * sizeof(float), cudaMemcpyHostToDevice));
     p->fused.c_tiled = p->d_c.as<float>() + 3 * static_cast<size_t>(Kp);
+    p->cube_scale_dirty = true;
 
     // contraction operands, device units: w in GHz, X in kelvin.
     //   H = eta w_GHz;  G = H gamma (nu_GHz + beta);  Q = eta^2 w_GHz
@@ -387,6 +393,12 @@ gateau_status enqueue_run(gateau_plan* p, long long t0, long long nt, float* out
         GATEAU_CUDA(cudaMemsetAsync(p->d_state.p, 0, static_cast<size_t>(d.n_pix) * p->n_ch * p->n_pole * sizeof(float),
                                     stream));
     }
+    if (p->cube_scale_dirty) {
+        GATEAU_CUDA(launch_scale_cube(p->d_cube_raw.as<float>(), T.c2, static_cast<long long>(p->n_az) * p->n_el,
+                                      p->Kp, p->d_cube.as<float>(), stream));
+        p->launches += 1;
+        p->cube_scale_dirty = false;
+    }
     TileInfo* tiles = nullptr;
     if (d.precision == GATEAU_PREC_BF16X3) {
         const long long n_tiles = (nt + kTileRows - 1) / kTileRows * d.n_pix;
@@ -513,9 +525,12 @@ gateau_status gateau_set_source_cube(gateau_plan* p, const float* cube, int n_az
     gateau_status st = ensure_base(p);
     if (st != GATEAU_OK) return st;
     const size_t nf = p->desc.n_freq, Kp = p->Kp;
-    GATEAU_CUDA(p->d_cube.ensure(static_cast<size_t>(n_az) * n_el * Kp * sizeof(float)));
-    if (Kp != nf) GATEAU_CUDA(cudaMemset(p->d_cube.p, 0, static_cast<size_t>(n_az) * n_el * Kp * sizeof(float)));
-    GATEAU_CUDA(cudaMemcpy2D(p->d_cube.p, Kp * sizeof(float), cube, nf * sizeof(float), nf * sizeof(float),
+    const size_t cube_bytes = static_cast<size_t>(n_az) * n_el * Kp * sizeof(float);
+    if (p->d_cube.bytes < cube_bytes || p->n_az != n_az || p->n_el != n_el) p->maps_dirty = true;
+    GATEAU_CUDA(p->d_cube.ensure(cube_bytes));
+    GATEAU_CUDA(p->d_cube_raw.ensure(cube_bytes));
+    if (Kp != nf) GATEAU_CUDA(cudaMemset(p->d_cube_raw.p, 0, cube_bytes));
+    GATEAU_CUDA(cudaMemcpy2D(p->d_cube_raw.p, Kp * sizeof(float), cube, nf * sizeof(float), nf * sizeof(float),
                              static_cast<size_t>(n_az) * n_el, kind_of(mem)));
     p->n_az = n_az;
     p->n_el = n_el;
@@ -524,7 +539,7 @@ gateau_status gateau_set_source_cube(gateau_plan* p, const float* cube, int n_az
     p->el0 = el0_rad;
     p->del = del_rad;
     p->has_cube = true;
-    p->maps_dirty = true;
+    p->cube_scale_dirty = true;
     return GATEAU_OK;
 }
 
@@ -564,13 +579,21 @@ gateau_status gateau_set_atmosphere_table(gateau_plan* p, const float* table, in
     std::vector<float> h;
     st = fetch_floats(table, static_cast<size_t>(n_pwv) * nf, mem, h);
     if (st != GATEAU_OK) return st;
-    std::vector<float> padded(static_cast<size_t>(n_pwv) * Kp, 0.f);
+    // Interleaved [n_pwv][2][Kp]: row 2j holds tau_j, row 2j+1 tau_{j+1} - tau_j (0 for the last j).
+    std::vector<double> tau(static_cast<size_t>(n_pwv) * nf);
     for (int j = 0; j < n_pwv; ++j)
         for (size_t k = 0; k < nf; ++k) {
             double v = h[j * nf + k];
             if (!is_opacity) v = -log(std::max(v, 1e-30));
             if (!(v >= 0.0) || !std::isfinite(v)) return fail(GATEAU_EINVAL, "opacity must be finite and >= 0 (row %d, point %zu)", j, k);
-            padded[j * Kp + k] = static_cast<float>(v);
+            tau[j * nf + k] = v;
+        }
+    std::vector<float> padded(static_cast<size_t>(2 * n_pwv) * Kp, 0.f);
+    for (int j = 0; j < n_pwv; ++j)
+        for (size_t k = 0; k < nf; ++k) {
+            const float t0f = static_cast<float>(tau[j * nf + k]);
+            padded[(2 * j) * Kp + k] = t0f;
+            if (j + 1 < n_pwv) padded[(2 * j + 1) * Kp + k] = static_cast<float>(tau[(j + 1) * nf + k]) - t0f;
         }
     GATEAU_CUDA(p->d_tau.ensure(padded.size() * sizeof(float)));
     GATEAU_CUDA(cudaMemcpy(p->d_tau.p, padded.data(), padded.size() * sizeof(float), cudaMemcpyHostToDevice));

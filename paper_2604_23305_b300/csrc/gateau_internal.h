@@ -56,11 +56,12 @@ struct DevTables {
     const float* screen;
     int nx, ny;
     double pitch;
-    // opacity table [n_pwv][Kp]
+    // opacity table [n_pwv][2][Kp]: row 2j = tau_j(nu), row 2j+1 = tau_{j+1} - tau_j
     const float* tau;
     int n_pwv;
     double pwv_min, dpwv;
-    // source cube [n_az][n_el][Kp] in W/Hz (as given; c2 carries the 1/k_B)
+    // source cube [n_az][n_el][Kp], pre-multiplied by c2(nu)/k_B: the source term of the
+    // collapsed cascade in kelvin (the caller's cube is kept unscaled beside it)
     const float* cube;
     int n_az, n_el;
     double az0, daz, el0, del;
@@ -68,7 +69,7 @@ struct DevTables {
     int n_freq, Kp;
     const float* c0;                   // [Kp] kelvin
     const float* c1;                   // [Kp] kelvin
-    const float* c2;                   // [Kp] kelvin per (W/Hz)
+    const float* c2;                   // [Kp] kelvin per (W/Hz), folded into cube
     // contraction operands, fp32 [n_ch_pad][Kp] (plain path)
     int n_ch, n_ch_pad;
     const float* H;                    // eta_filt * w_GHz
@@ -96,7 +97,7 @@ struct FusedOperands {
     int n_kstage;                      // K stages of fused_kstage() points
     size_t stage_elems;                // bf16 elements per (group, kstage) block
     int tma_inputs;                    // 1: opacity rows and cube texels are staged by tensor copies
-    const float* c_tiled;              // [Kp/16][3][16] c0, c1, c2 per stage (kelvin)
+    const float* c_tiled;              // [Kp/16][2][16] c0 + c1 and c1 per stage (kelvin)
 };
 
 // Opaque 128-byte tensor-map descriptors (CUtensorMap) for the staged inputs.
@@ -107,6 +108,8 @@ struct __align__(64) TensorMapBytes {
 // ---- kernel launchers (each enqueues on `stream`, returns cudaGetLastError) ----
 cudaError_t launch_row_setup(const DevTables& T, long long t0, long long nt, RowParams* rows,
                              TileInfo* tiles, cudaStream_t stream);
+cudaError_t launch_scale_cube(const float* raw, const float* c2, long long n_texels, int Kp, float* out,
+                              cudaStream_t stream);
 cudaError_t launch_psd_fp32(const DevTables& T, const RowParams* rows, long long r0, long long nrows,
                             float* X, cudaStream_t stream);
 cudaError_t launch_contract_fp32(const DevTables& T, const float* X, long long r0, long long nrows,

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kTileRows) row_setup_kernel(DevTables T, long 
             ti.ia0 = s_nsrc ? s_amin : 0;
             ti.ie0 = s_nsrc ? s_emin : 0;
             int f = 0;
-            if (s_jmax + 1 - s_jmin <= kTauBoxRows - 1) f |= TILE_TAU_FITS;
+            if (s_jmax - s_jmin <= kTauBoxRows - 1) f |= TILE_TAU_FITS;
             if (s_nsrc) {
                 f |= TILE_HAS_SOURCE;
                 if (s_amax + 1 - s_amin <= kCubeBoxAz - 1 && s_emax + 1 - s_emin <= kCubeBoxEl - 1) f |= TILE_CUBE_FITS;
@@ -175,8 +175,8 @@ __global__ void psd_fp32_kernel(DevTables T, const RowParams* __restrict__ rows,
                                 float* __restrict__ X) {
     const long long row = blockIdx.x;
     const RowParams rp = rows[r0 + row];
-    const float* tA = T.tau + static_cast<long long>(rp.tau_j) * T.Kp;
-    const float* tB = tA + T.Kp;
+    const float* tA = T.tau + static_cast<long long>(2 * rp.tau_j) * T.Kp;   // tau_j
+    const float* tD = tA + T.Kp;                                             // tau_{j+1} - tau_j
     const bool has_src = rp.src_idx >= 0;
     const float fa = rp.src_fa, fe = rp.src_fe;
     const float w00 = (1.f - fa) * (1.f - fe), w10 = fa * (1.f - fe), w01 = (1.f - fa) * fe, w11 = fa * fe;
@@ -187,10 +187,9 @@ __global__ void psd_fp32_kernel(DevTables T, const RowParams* __restrict__ rows,
     float* xr = X + row * T.Kp;
     for (int k = threadIdx.x * 4; k < T.Kp; k += blockDim.x * 4) {
         const float4 a4 = *reinterpret_cast<const float4*>(tA + k);
-        const float4 b4 = *reinterpret_cast<const float4*>(tB + k);
+        const float4 d4 = *reinterpret_cast<const float4*>(tD + k);
         const float4 c04 = *reinterpret_cast<const float4*>(T.c0 + k);
         const float4 c14 = *reinterpret_cast<const float4*>(T.c1 + k);
-        const float4 c24 = *reinterpret_cast<const float4*>(T.c2 + k);
         float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
         if (has_src) {
             const float4 q00 = *reinterpret_cast<const float4*>(s00 + k);
@@ -205,16 +204,37 @@ __global__ void psd_fp32_kernel(DevTables T, const RowParams* __restrict__ rows,
         float4 o;
 #define GATEAU_PSD(c)                                                  \
     {                                                                  \
-        const float tau = a4.c + rp.tau_f * (b4.c - a4.c);             \
+        const float tau = fmaf(rp.tau_f, d4.c, a4.c);                  \
         const float arg = rp.csc * tau;                                \
         const float e = expf(-arg);                                    \
         const float ome = -expm1f(-arg);                               \
-        o.c = c04.c + c14.c * ome + c24.c * e * p.c;                   \
+        o.c = c04.c + c14.c * ome + e * p.c;                           \
     }
         GATEAU_PSD(x) GATEAU_PSD(y) GATEAU_PSD(z) GATEAU_PSD(w)
 #undef GATEAU_PSD
         *reinterpret_cast<float4*>(xr + k) = o;
     }
+}
+
+// cube[t][k] = raw[t][k] * c2[k]: the source term of the collapsed cascade in kelvin.
+__global__ void scale_cube_kernel(const float4* __restrict__ raw, const float4* __restrict__ c2, long long n4,
+                                  int Kp4, float4* __restrict__ out) {
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n4;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const float4 a = raw[i], c = c2[i % Kp4];
+        out[i] = make_float4(a.x * c.x, a.y * c.y, a.z * c.z, a.w * c.w);
+    }
+}
+
+cudaError_t launch_scale_cube(const float* raw, const float* c2, long long n_texels, int Kp, float* out,
+                              cudaStream_t stream) {
+    const long long n4 = n_texels * Kp / 4;
+    long long grid = (n4 + 255) / 256;
+    if (grid > 148LL * 16) grid = 148LL * 16;
+    scale_cube_kernel<<<static_cast<unsigned>(grid), 256, 0, stream>>>(
+        reinterpret_cast<const float4*>(raw), reinterpret_cast<const float4*>(c2), n4, Kp / 4,
+        reinterpret_cast<float4*>(out));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_psd_fp32(const DevTables& T, const RowParams* rows, long long r0, long long nrows,
