@@ -52,6 +52,29 @@ __device__ __forceinline__ float4 white_normals4(long long n, int i, int q, uint
     return make_float4(a.x, a.y, b.x, b.y);
 }
 
+// The same four normals with the hardware approximations of log, sin and cos
+// (absolute errors of order 1e-6 in z), used where sigma itself is only known to
+// ~1e-3 (the split-BF16 path's noise contractions).
+__device__ __forceinline__ float2 box_muller_fast(uint32_t xa, uint32_t xb) {
+    const float ua = fmaf(static_cast<float>(xa), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    const float r = sqrtf(-2.0f * __logf(ua));
+    // 2 pi u_b - pi in [-pi, pi), where the approximations are accurate; cos and sin of
+    // 2 pi u_b are then the negated values.
+    const float ang = fmaf(static_cast<float>(xb), 1.4629180792671596e-09f, 7.314590396335798e-10f - 3.14159265358979f);
+    float sn, cs;
+    __sincosf(ang, &sn, &cs);
+    return make_float2(-r * cs, -r * sn);
+}
+
+__device__ __forceinline__ float4 white_normals4_fast(long long n, int i, int q, uint32_t k0, uint32_t k1) {
+    const uint4 x = philox4x32_10(make_uint4(static_cast<uint32_t>(n), static_cast<uint32_t>(n >> 32),
+                                             static_cast<uint32_t>(i), static_cast<uint32_t>(q)),
+                                  k0, k1);
+    const float2 a = box_muller_fast(x.x, x.y);
+    const float2 b = box_muller_fast(x.z, x.w);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
 // Four pink-noise normals for samples 4m..4m+3 of sequence (i, ch).
 __device__ __forceinline__ float4 pink_normals4(long long m, int i, int ch, uint32_t k0, uint32_t k1) {
     const uint4 x = philox4x32_10(make_uint4(static_cast<uint32_t>(m), static_cast<uint32_t>(m >> 32),

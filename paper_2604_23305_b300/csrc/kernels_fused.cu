@@ -15,11 +15,16 @@
 // white noise (Eq. 19) from Philox and writes out[n][i][ch].
 //
 // Warp roles (448 threads, one CTA per SM, persistent over work items):
-//   warp 0 lane 0 : bulk copies of the pre-tiled filter operands (TMA engine), A/B ring
-//   warp 0 lane 1 : tensor copies of the tile's opacity rows and cube texel box, input ring
+//   warp 0        : one thread issuing bulk copies of the pre-tiled filter operands (A/B ring)
 //   warp 1        : TMEM allocator + single-thread tcgen05.mma issuer
-//   warps 2..9    : spectrum producers, one thread per (tile row, half of the 16-point slice)
-//   warps 10..13  : epilogue, one thread per TMEM lane (= tile row)
+//   warp 2        : one thread issuing tensor copies of the tile's opacity rows and cube texel
+//                   box (input ring); each spinning role has a warp of its own
+//   warp 3        : shared tiles only: one thread copying this CTA's finished rows of each
+//                   stage into the peer CTA's shared memory
+//   warps 4..11   : spectrum producers (each warp signals its own rows, no CTA-wide barrier); with 347 channels the two channel groups of a tile run
+//                   on the two CTAs of a cluster, each building half of the tile's rows and
+//                   copying them into the peer's shared memory (one build per row)
+//   warps 12..15  : epilogue, one thread per TMEM lane (= tile row)
 // The input ring runs ahead of the producers, the A/B ring behind them, so the
 // producers read their gathers from shared memory.  Tiles whose opacity rows or
 // cube texels do not fit the staged boxes fall back to global loads.
@@ -40,7 +45,8 @@ constexpr int kAMats = 3;            // X_hi, X_lo, bf16(X^2)
 constexpr int kBMats = 4;            // H_hi, H_lo, G, Q
 constexpr int kProdWarps = 8;
 constexpr int kProdThreads = kProdWarps * 32;
-constexpr int kEpiWarp0 = 2 + kProdWarps;
+constexpr int kProdWarp0 = 4;               // warps 0..3: operand TMA, MMA, input TMA, peer copier
+constexpr int kEpiWarp0 = kProdWarp0 + kProdWarps;
 constexpr int kThreads = (kEpiWarp0 + 4) * 32;
 constexpr int kMaxSmem = 227 * 1024;
 constexpr int kInSlots = 5;          // input-ring depth (stages of staged gathers)
@@ -266,6 +272,33 @@ __device__ __forceinline__ void tensor3d_g2s(uint32_t dst, const void* tmap, int
         : "memory");
 }
 
+// Peer CTA's shared::cluster address of a local shared::cta address.
+__device__ __forceinline__ uint32_t mapa_peer(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release;\nbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// Local shared memory -> peer CTA's shared memory, completing on the peer's mbarrier.
+__device__ __forceinline__ void bulk_s2peer(uint32_t dst_cluster, uint32_t src_cta, uint32_t bytes,
+                                            uint32_t bar_cluster) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst_cluster),
+        "r"(src_cta), "r"(bytes), "r"(bar_cluster)
+        : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -276,6 +309,15 @@ __device__ __forceinline__ void tc_fence_after() {
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
+}
+
+// Commit arriving on the barrier at the same offset in both CTAs of a 2-CTA cluster.
+__device__ __forceinline__ void tc_commit_pair(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            bar),
+        "h"(static_cast<uint16_t>(3))
+        : "memory");
 }
 
 // D[tmem] (+)= A[smem] * B[smem]^T, M=128, N from idesc, K=16, bf16 in, f32 accumulate.
@@ -337,8 +379,11 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 // ---- work decomposition ------------------------------------------------------
+// share = 1: the two channel groups of a tile run on the two CTAs of a cluster,
+// each building half of the tile's spectrum rows and copying it to the peer.
 struct Work {
     long long tiles_per_pix, n_items;
+    int share;
 };
 
 // Item it = tile * n_groups + group; tile = pix * tiles_per_pix + tile-in-pixel.
@@ -370,7 +415,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto empty_bar = [&](int s) { return bar_base + 8u * (2 * NS + s); };
     auto full_in = [&](int s) { return bar_base + 8u * (3 * NS + s); };
     auto empty_in = [&](int s) { return bar_base + 8u * (3 * NS + kInSlots + s); };
-    const int nb = 3 * NS + 2 * kInSlots;
+    auto rows_ready = [&](int s) { return bar_base + 8u * (3 * NS + 2 * kInSlots + s); };
+    const int nb = 4 * NS + 2 * kInSlots;
     const uint32_t acc_full = bar_base + 8u * nb;
     const uint32_t acc_empty = bar_base + 8u * (nb + 1);
     const uint32_t drain_bar = bar_base + 8u * (nb + 2);
@@ -378,15 +424,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + sp.bar_off + 8 * (nb + 3) + 8);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int share = work.share;
+    const uint32_t rank = share ? cluster_rank() : 0u;
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
-            mbar_init(full_a(s), kProdThreads);
+            // shared tile: the copier's arrival + the peer's bytes; otherwise one arrival per producer warp
+            mbar_init(full_a(s), share ? 1 : kProdWarps);
             mbar_init(full_b(s), 1);
-            mbar_init(empty_bar(s), 1);
+            mbar_init(empty_bar(s), share ? 2 : 1);  // both CTAs' MMAs when the tile is shared
+            mbar_init(rows_ready(s), kProdWarps);
         }
         for (int s = 0; s < kInSlots; ++s) {
             mbar_init(full_in(s), 1);
-            mbar_init(empty_in(s), kProdThreads);
+            mbar_init(empty_in(s), kProdWarps);
         }
         mbar_init(acc_full, 1);
         mbar_init(acc_empty, 128);
@@ -401,15 +451,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
+    if (share) cluster_sync_all();              // the peer's barriers exist before any remote arrival
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     const uint32_t d_sig = tmem_base;            // columns [0, NH)
     const uint32_t d_noi = tmem_base + 256;      // columns [256, 256 + NH)
 
     const int n_ks = T.Kp / kKStage;
-    const long long my_items = work.n_items > blockIdx.x
-                                   ? (work.n_items - blockIdx.x + gridDim.x - 1) / gridDim.x
-                                   : 0;
+    // Work units: tiles shared by a cluster, or (tile, group) items for independent CTAs.
+    const long long n_units = share ? work.n_items / 2 : work.n_items;
+    const long long ubase = share ? blockIdx.x / 2 : blockIdx.x;
+    const long long ustride = share ? gridDim.x / 2 : gridDim.x;
+    const long long my_items = n_units > ubase ? (n_units - ubase + ustride - 1) / ustride : 0;
+    auto item_of = [&](long long j) {
+        const long long u = ubase + j * ustride;
+        return share ? u * 2 + rank : u;
+    };
 
     if (warp == 0) {
         if (lane == 0) {
@@ -419,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t ph = 0;           // parity of the current pass over the ring
             const uint32_t bytes = static_cast<uint32_t>(sp.b_bytes);
             for (long long j = 0; j < my_items && !*abort_flag; ++j) {
-                const long long it = blockIdx.x + j * gridDim.x;
+                const long long it = item_of(j);
                 const int grp = static_cast<int>(it % F.n_groups);
                 const uint16_t* src = F.B + static_cast<size_t>(grp) * n_ks * F.stage_elems;
                 bool ok = true;
@@ -438,13 +495,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             for (long long q = (g > NS ? g - NS : 0); q < g; ++q)    // no copy in flight at exit
                 mbar_drain(full_b(static_cast<int>(q % NS)), static_cast<uint32_t>((q / NS) & 1));
-        } else if (lane == 1) {
+        }
+    } else if (warp == 2) {
+        if (lane == 0) {
             // ---------------- staged gathers: opacity rows + cube box per stage (input ring) ----------------
             long long g = 0;
             int s = 0;
             uint32_t ph = 0;
             for (long long j = 0; j < my_items && !*abort_flag; ++j) {
-                const long long it = blockIdx.x + j * gridDim.x;
+                const long long it = item_of(j);
                 long long tile, row0;
                 int pix, nrows, grp;
                 item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
@@ -472,6 +531,33 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             for (long long q = (g > kInSlots ? g - kInSlots : 0); q < g; ++q)
                 mbar_drain(full_in(static_cast<int>(q % kInSlots)), static_cast<uint32_t>((q / kInSlots) & 1));
+        }
+    } else if (warp == 3) {
+        // ---------------- shared tiles: our rows of each stage -> the peer's shared memory ----------------
+        if (share && lane == 0) {
+            constexpr uint32_t amat = kTileM * kKStage * 2;
+            const uint32_t peer = rank ^ 1u;
+            int s = 0;
+            uint32_t par = 0;
+            for (long long j = 0; j < my_items; ++j) {
+                bool ok = true;
+                for (int ks = 0; ks < n_ks; ++ks) {
+                    if (!mbar_wait(rows_ready(s), par, abort_flag, T.status)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t a0 = smem_u32(smem + s * sp.stage_bytes);
+                    const uint32_t bar_peer = mapa_peer(full_a(s), peer);
+#pragma unroll
+                    for (int m = 0; m < kAMats; ++m) {
+                        const uint32_t src = a0 + m * amat + rank * (amat / 2);
+                        bulk_s2peer(mapa_peer(src, peer), src, amat / 2, bar_peer);
+                    }
+                    mbar_arrive_expect_tx(full_a(s), kAMats * (amat / 2));   // the peer's rows into us
+                    if (++s == NS) { s = 0; par ^= 1u; }
+                }
+                if (!ok) break;
+            }
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
@@ -510,7 +596,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_mma(d_sig, xhi, hlo, idesc, 1u);
                     tc_mma(d_noi, xhi, gmat, idesc, acc);
                     tc_mma(d_noi, xsq, qmat, idesc, 1u);
-                    tc_commit(empty_bar(s));          // stage s free once these MMAs finish
+                    if (share) tc_commit_pair(empty_bar(s));   // stage s free in both CTAs
+                    else tc_commit(empty_bar(s));              // stage s free once these MMAs finish
                     if (++s == NS) { s = 0; par ^= 1u; }
                 }
                 if (!ok) break;
@@ -520,16 +607,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_drain(drain_bar, 0);
         }
     } else if (warp < kEpiWarp0) {
-        // ---------------- spectrum producers: thread = (tile row, 8-point half) ----------------
-        const int pw = warp - 2;
-        const int r = (pw & 3) * 32 + lane;
-        const int kh = (pw >> 2) * 8;               // point offset of this thread within the stage
+        // ---------------- spectrum producers ----------------
+        // Independent CTA: thread = (row 0..127, 8 points).  Shared tile: this CTA builds rows
+        // [64 rank, 64 rank + 64), thread = (row, 4 points), and ships them to the peer.
+        const int pw = warp - kProdWarp0;
+        const int r = share ? static_cast<int>(rank) * 64 + (pw & 1) * 32 + lane : (pw & 3) * 32 + lane;
+        const int kh = share ? (pw >> 1) * 4 : (pw >> 2) * 8;   // first point of this thread in the stage
+        const int nq = share ? 1 : 2;                            // float4 quads per thread
         long long g = 0;
         int s = 0, si = 0;
         uint32_t ph = 0, phi = 0;
         bool ok = true;
         for (long long j = 0; j < my_items && ok; ++j) {
-            const long long it = blockIdx.x + j * gridDim.x;
+            const long long it = item_of(j);
             long long tile, row0;
             int pix, nrows, grp;
             item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
@@ -570,75 +660,82 @@ __global__ void __launch_bounds__(kThreads, 1)
             // eta_atm = exp(-csc tau) = 2^(a tau_j + b dtau_j) with a = -csc log2(e), b = a f
             const float ea = -rp.csc * 1.4426950408889634f, eb = ea * rp.tau_f;
             for (int ks = 0; ks < n_ks; ++ks) {
-                if ((g >= NS && !mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, T.status)) ||
-                    !mbar_wait(full_in(si), phi, abort_flag, T.status)) {
+                bool okw = (g < NS || mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, T.status)) &&
+                           mbar_wait(full_in(si), phi, abort_flag, T.status);
+                okw = __all_sync(0xffffffffu, okw);  // the warp signals as one
+                if (!okw) {
                     ok = false;
                     break;
                 }
-                const float* slot = reinterpret_cast<const float*>(smem + sp.in_off + static_cast<size_t>(si) * kInSlotBytes);
-                const float* stau = slot + kTauOff / 4;
-                const float* scon = slot + kConstOff / 4 + kh;     // [c0 + c1][16], [c1][16]
-                const int k = ks * kKStage + kh;
-                float x[8];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int kq = k + 4 * h;
-                    float4 ta, td;
-                    if (tau_box) {
-                        ta = ld4(stau + sA + 4 * h);
-                        td = ld4(stau + sA + kBoxW + 4 * h);
-                    } else {
-                        ta = ld4(gA + kq);
-                        td = ld4(gD + kq);
-                    }
-                    const float4 c01 = ld4(scon + 4 * h);
-                    const float4 c1 = ld4(scon + kKStage + 4 * h);
-                    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (has_src) {
-                        float4 q00, q10, q01, q11;
-                        if (cube_box) {
-                            q00 = ld4(slot + sC00 + 4 * h);
-                            q10 = ld4(slot + sC10 + 4 * h);
-                            q01 = ld4(slot + sC01 + 4 * h);
-                            q11 = ld4(slot + sC11 + 4 * h);
+                uint8_t* a0 = smem + s * sp.stage_bytes;
+                constexpr int amat = kTileM * kKStage * 2;
+                {
+                    const float* slot =
+                        reinterpret_cast<const float*>(smem + sp.in_off + static_cast<size_t>(si) * kInSlotBytes);
+                    const float* stau = slot + kTauOff / 4;
+                    const float* scon = slot + kConstOff / 4 + kh;     // [c0 + c1][16], [c1][16]
+                    const int k = ks * kKStage + kh;
+                    for (int h = 0; h < nq; ++h) {
+                        const int kq = k + 4 * h;
+                        float4 ta, td;
+                        if (tau_box) {
+                            ta = ld4(stau + sA + 4 * h);
+                            td = ld4(stau + sA + kBoxW + 4 * h);
                         } else {
-                            q00 = ld4(g00 + kq);
-                            q10 = ld4(g10 + kq);
-                            q01 = ld4(g01 + kq);
-                            q11 = ld4(g11 + kq);
+                            ta = ld4(gA + kq);
+                            td = ld4(gD + kq);
                         }
-                        p.x = w00 * q00.x + w10 * q10.x + w01 * q01.x + w11 * q11.x;
-                        p.y = w00 * q00.y + w10 * q10.y + w01 * q01.y + w11 * q11.y;
-                        p.z = w00 * q00.z + w10 * q10.z + w01 * q01.z + w11 * q11.z;
-                        p.w = w00 * q00.w + w10 * q10.w + w01 * q01.w + w11 * q11.w;
-                    }
+                        const float4 c01 = ld4(scon + 4 * h);
+                        const float4 c1 = ld4(scon + kKStage + 4 * h);
+                        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (has_src) {
+                            float4 q00, q10, q01, q11;
+                            if (cube_box) {
+                                q00 = ld4(slot + sC00 + 4 * h);
+                                q10 = ld4(slot + sC10 + 4 * h);
+                                q01 = ld4(slot + sC01 + 4 * h);
+                                q11 = ld4(slot + sC11 + 4 * h);
+                            } else {
+                                q00 = ld4(g00 + kq);
+                                q10 = ld4(g10 + kq);
+                                q01 = ld4(g01 + kq);
+                                q11 = ld4(g11 + kq);
+                            }
+                            p.x = w00 * q00.x + w10 * q10.x + w01 * q01.x + w11 * q11.x;
+                            p.y = w00 * q00.y + w10 * q10.y + w01 * q01.y + w11 * q11.y;
+                            p.z = w00 * q00.z + w10 * q10.z + w01 * q01.z + w11 * q11.z;
+                            p.w = w00 * q00.w + w10 * q10.w + w01 * q01.w + w11 * q11.w;
+                        }
+                        float x[4];
 #define GATEAU_FX(i, c)                                          \
     {                                                            \
         const float e = ex2_approx(fmaf(eb, td.c, ea * ta.c));   \
-        x[4 * h + i] = fmaf(e, p.c - c1.c, c01.c);               \
+        x[i] = fmaf(e, p.c - c1.c, c01.c);                       \
     }
-                    GATEAU_FX(0, x) GATEAU_FX(1, y) GATEAU_FX(2, z) GATEAU_FX(3, w)
+                        GATEAU_FX(0, x) GATEAU_FX(1, y) GATEAU_FX(2, z) GATEAU_FX(3, w)
 #undef GATEAU_FX
-                }
-                uint32_t hi[4], lo[4], sq[4];
+                        uint32_t hi[2], lo[2], sq[2];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float xa = x[2 * q], xb = x[2 * q + 1];
-                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(xa, xb);
-                    hi[q] = *reinterpret_cast<const uint32_t*>(&h2);
-                    lo[q] = pack_bf16(xa - __low2float(h2), xb - __high2float(h2));
-                    const __nv_bfloat162 s2 = __hmul2(h2, h2);        // bf16(X_hi^2) for the noise term
-                    sq[q] = *reinterpret_cast<const uint32_t*>(&s2);
+                        for (int q = 0; q < 2; ++q) {
+                            const float xa = x[2 * q], xb = x[2 * q + 1];
+                            const __nv_bfloat162 h2 = __floats2bfloat162_rn(xa, xb);
+                            hi[q] = *reinterpret_cast<const uint32_t*>(&h2);
+                            lo[q] = pack_bf16(xa - __low2float(h2), xb - __high2float(h2));
+                            const __nv_bfloat162 s2 = __hmul2(h2, h2);        // bf16(X_hi^2) for the noise term
+                            sq[q] = *reinterpret_cast<const uint32_t*>(&s2);
+                        }
+                        const size_t off = core_offset(r, kh + 4 * h, kTileM);
+                        *reinterpret_cast<uint2*>(a0 + 0 * amat + off) = make_uint2(hi[0], hi[1]);
+                        *reinterpret_cast<uint2*>(a0 + 1 * amat + off) = make_uint2(lo[0], lo[1]);
+                        *reinterpret_cast<uint2*>(a0 + 2 * amat + off) = make_uint2(sq[0], sq[1]);
+                    }
                 }
-                uint8_t* a0 = smem + s * sp.stage_bytes;
-                const size_t off = core_offset(r, kh, kTileM);
-                constexpr int amat = kTileM * kKStage * 2;
-                *reinterpret_cast<uint4*>(a0 + 0 * amat + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                *reinterpret_cast<uint4*>(a0 + 1 * amat + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-                *reinterpret_cast<uint4*>(a0 + 2 * amat + off) = make_uint4(sq[0], sq[1], sq[2], sq[3]);
-                fence_proxy_async();
-                mbar_arrive(full_a(s));
-                mbar_arrive(empty_in(si));
+                fence_proxy_async();                 // our generic stores -> the tensor-core (async) proxy
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(share ? rows_ready(s) : full_a(s));
+                    mbar_arrive(empty_in(si));
+                }
                 ++g;
                 if (++s == NS) { s = 0; ph ^= 1u; }
                 if (++si == kInSlots) { si = 0; phi ^= 1u; }
@@ -654,7 +751,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const bool ok = mbar_wait(acc_full, static_cast<uint32_t>(j & 1), abort_flag, T.status);
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
-            const long long it = blockIdx.x + j * gridDim.x;
+            const long long it = item_of(j);
             long long tile, row0;
             int pix, nrows, grp;
             item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
@@ -673,7 +770,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int ch0 = ch_base + c + 4 * q;
                         if (ch0 >= T.n_ch) break;
                         float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (white) z = white_normals4(n, pix, ch0 >> 2, T.key0, T.key1);
+                        if (white) z = white_normals4_fast(n, pix, ch0 >> 2, T.key0, T.key1);
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const int ch = ch0 + e;
@@ -693,6 +790,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     tc_fence_before();
     __syncthreads();
+    if (share) cluster_sync_all();              // no copy into or out of our shared memory in flight
     tc_fence_after();
     if (warp == 1) {
         __syncwarp();
@@ -708,6 +806,7 @@ cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, cons
     Work w;
     w.tiles_per_pix = (nt + kTileM - 1) / kTileM;
     w.n_items = w.tiles_per_pix * T.n_pix * F.n_groups;
+    w.share = F.n_groups == 2 ? 1 : 0;
     if (w.n_items == 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(fused_bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(sp.total));
@@ -715,9 +814,34 @@ cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, cons
     CUtensorMap mt, mc;
     memcpy(&mt, &tm_tau, sizeof(mt));
     memcpy(&mc, &tm_cube, sizeof(mc));
-    long long grid = w.n_items < n_sm ? w.n_items : n_sm;
-    fused_bf16x3_kernel<<<static_cast<unsigned>(grid), kThreads, sp.total, stream>>>(mt, mc, T, F, rows, tiles, t0,
-                                                                                     nt, w, out);
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = sp.total;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    long long grid;
+    if (w.share) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3(static_cast<unsigned>(n_sm / 2 * 2));
+        int max_clusters = 0;
+        e = cudaOccupancyMaxActiveClusters(&max_clusters, fused_bf16x3_kernel, &cfg);
+        if (e != cudaSuccess) return e;
+        if (max_clusters < 1) return cudaErrorInvalidConfiguration;
+        const long long tiles = w.n_items / 2;
+        grid = 2 * (tiles < max_clusters ? tiles : max_clusters);
+    } else {
+        cfg.attrs = nullptr;
+        cfg.numAttrs = 0;
+        grid = w.n_items < n_sm ? w.n_items : n_sm;
+    }
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    e = cudaLaunchKernelEx(&cfg, fused_bf16x3_kernel, mt, mc, T, F, rows, tiles, t0, nt, w, out);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
