@@ -32,14 +32,21 @@ __device__ __forceinline__ float log_unit(uint32_t x) {
     return log1pf(-v);
 }
 
+// cos and sin of 2 pi u_b, u_b = (x_b + 1/2) 2^-32: the angle is shifted by -pi into
+// [-pi, pi), where the hardware sin/cos approximations are accurate (absolute error
+// ~5e-7), and the results are negated back.
+__device__ __forceinline__ float2 cos_sin_2pi_u(uint32_t xb) {
+    const float ang = fmaf(static_cast<float>(xb), 1.4629180792671596e-09f, 7.314590396335798e-10f - 3.14159265358979f);
+    float sn, cs;
+    __sincosf(ang, &sn, &cs);
+    return make_float2(-cs, -sn);
+}
+
 // Box-Muller pair from two words: r = sqrt(-2 ln u_a), angle 2 pi u_b.
 __device__ __forceinline__ float2 box_muller(uint32_t xa, uint32_t xb) {
     const float r = sqrtf(-2.0f * log_unit(xa));
-    // 2 u_b = (x_b + 1/2) 2^-31, so sincospi gives sin/cos(2 pi u_b)
-    const float s2 = fmaf(static_cast<float>(xb), 4.656612873077393e-10f, 2.3283064365386963e-10f);
-    float sn, cs;
-    sincospif(s2, &sn, &cs);
-    return make_float2(r * cs, r * sn);
+    const float2 cs = cos_sin_2pi_u(xb);
+    return make_float2(r * cs.x, r * cs.y);
 }
 
 // Four white-noise normals for channels 4q..4q+3 of row (n, i).
@@ -58,12 +65,8 @@ __device__ __forceinline__ float4 white_normals4(long long n, int i, int q, uint
 __device__ __forceinline__ float2 box_muller_fast(uint32_t xa, uint32_t xb) {
     const float ua = fmaf(static_cast<float>(xa), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
     const float r = sqrtf(-2.0f * __logf(ua));
-    // 2 pi u_b - pi in [-pi, pi), where the approximations are accurate; cos and sin of
-    // 2 pi u_b are then the negated values.
-    const float ang = fmaf(static_cast<float>(xb), 1.4629180792671596e-09f, 7.314590396335798e-10f - 3.14159265358979f);
-    float sn, cs;
-    __sincosf(ang, &sn, &cs);
-    return make_float2(-r * cs, -r * sn);
+    const float2 cs = cos_sin_2pi_u(xb);
+    return make_float2(r * cs.x, r * cs.y);
 }
 
 __device__ __forceinline__ float4 white_normals4_fast(long long n, int i, int q, uint32_t k0, uint32_t k1) {

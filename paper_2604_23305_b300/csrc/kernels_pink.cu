@@ -16,6 +16,7 @@
 
 namespace gateau {
 
+// Samples are visited in groups of the 4 that one Philox call serves (m = n >> 2).
 template <int NP>
 __global__ __launch_bounds__(256) void pink_phase1_kernel(DevTables T, PinkWork W, long long t0,
                                                           long long nt) {
@@ -34,12 +35,17 @@ __global__ __launch_bounds__(256) void pink_phase1_kernel(DevTables T, PinkWork 
             av[j] = (j < np) ? T.pink_a[ch * np + j] : 0.f;
             st[j] = 0.f;
         }
-        float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (long long n = a0; n < b0; ++n) {
-            if (n == a0 || (n & 3) == 0) z4 = pink_normals4(n >> 2, i, ch, T.key0, T.key1);
-            const float z = f4_get(z4, static_cast<int>(n & 3));
+        for (long long n = a0; n < b0;) {
+            const long long m = n >> 2;
+            const int q0 = static_cast<int>(n & 3);
+            const int q1 = static_cast<int>(min(b0 - (m << 2), 4LL));
+            const float4 z4 = pink_normals4(m, i, ch, T.key0, T.key1);
+            for (int q = q0; q < q1; ++q) {
+                const float z = f4_get(z4, q);
 #pragma unroll
-            for (int j = 0; j < NP; ++j) st[j] = fmaf(av[j], st[j], z);
+                for (int j = 0; j < NP; ++j) st[j] = fmaf(av[j], st[j], z);
+            }
+            n = (m << 2) + q1;
         }
         float* ag = W.agg + (c * S + s) * np;
 #pragma unroll
@@ -70,11 +76,14 @@ __global__ void pink_phase2_kernel(DevTables T, float* state, PinkWork W, long l
     }
 }
 
+// Phase 3 reads, updates and writes out one group of up to 4 samples at a time,
+// with the next group's loads issued before the current group's recurrence.
 template <int NP>
 __global__ __launch_bounds__(256) void pink_phase3_kernel(DevTables T, PinkWork W, long long t0,
                                                           long long nt, float* __restrict__ out) {
     const long long S = static_cast<long long>(T.n_pix) * T.n_ch;
     const int np = T.n_pole;
+    const long long stride = static_cast<long long>(T.n_pix) * T.n_ch;
     for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < W.C * S;
          idx += static_cast<long long>(gridDim.x) * blockDim.x) {
         const int c = static_cast<int>(idx / S);
@@ -92,18 +101,42 @@ __global__ __launch_bounds__(256) void pink_phase3_kernel(DevTables T, PinkWork 
         }
         const float d = T.pink_d[ch];
         float* o = out + ((a0 - t0) * T.n_pix + i) * static_cast<long long>(T.n_ch) + ch;
-        const long long stride = static_cast<long long>(T.n_pix) * T.n_ch;
-        float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (long long n = a0; n < b0; ++n, o += stride) {
-            if (n == a0 || (n & 3) == 0) z4 = pink_normals4(n >> 2, i, ch, T.key0, T.key1);
-            const float z = f4_get(z4, static_cast<int>(n & 3));
-            float y = d * z;
+        long long n = a0;
+        // current group [n, n + cnt) and its loaded outputs
+        int q0 = static_cast<int>(n & 3);
+        int q1 = static_cast<int>(min(b0 - ((n >> 2) << 2), 4LL));
+        float cur[4];
 #pragma unroll
-            for (int j = 0; j < NP; ++j) {
-                st[j] = fmaf(av[j], st[j], z);
-                y = fmaf(rv[j], st[j], y);
+        for (int q = 0; q < 4; ++q) cur[q] = (q >= q0 && q < q1) ? o[(q - q0) * stride] : 0.f;
+        while (n < b0) {
+            const long long m = n >> 2;
+            const int cnt = q1 - q0;
+            float* on = o + cnt * stride;
+            const long long nn = (m << 2) + q1;          // first sample of the next group
+            const int r1 = static_cast<int>(min(b0 - nn, 4LL));
+            float nxt[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) nxt[q] = (q < r1) ? on[q * stride] : 0.f;
+            const float4 z4 = pink_normals4(m, i, ch, T.key0, T.key1);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q >= q0 && q < q1) {
+                    const float z = f4_get(z4, q);
+                    float y = d * z;
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        st[j] = fmaf(av[j], st[j], z);
+                        y = fmaf(rv[j], st[j], y);
+                    }
+                    o[(q - q0) * stride] = cur[q] + y;
+                }
             }
-            *o += y;
+            n = nn;
+            o = on;
+            q0 = 0;
+            q1 = r1 > 0 ? r1 : 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cur[q] = nxt[q];
         }
     }
 }
