@@ -19,11 +19,12 @@
 //   warp 1        : TMEM allocator + single-thread tcgen05.mma issuer
 //   warp 2        : one thread issuing tensor copies of the tile's opacity rows and cube texel
 //                   box (input ring); each spinning role has a warp of its own
-//   warp 3        : shared tiles only: one thread copying this CTA's finished rows of each
-//                   stage into the peer CTA's shared memory
-//   warps 4..11   : spectrum producers (each warp signals its own rows, no CTA-wide barrier); with 347 channels the two channel groups of a tile run
-//                   on the two CTAs of a cluster, each building half of the tile's rows and
-//                   copying them into the peer's shared memory (one build per row)
+//   warp 3        : idle
+//   warps 4..11   : spectrum producers; each warp signals its own rows (no CTA-wide barrier).
+//                   With 347 channels the two channel groups of a tile run on the two CTAs of
+//                   a cluster: each CTA builds half of the tile's rows, one 8-row core-matrix
+//                   group per warp, and each warp bulk-copies its finished 256-byte blocks
+//                   straight into the peer's shared memory (one build per row, no relay)
 //   warps 12..15  : epilogue, one thread per TMEM lane (= tile row)
 // The input ring runs ahead of the producers, the A/B ring behind them, so the
 // producers read their gathers from shared memory.  Tiles whose opacity rows or
@@ -45,7 +46,7 @@ constexpr int kAMats = 3;            // X_hi, X_lo, bf16(X^2)
 constexpr int kBMats = 4;            // H_hi, H_lo, G, Q
 constexpr int kProdWarps = 8;
 constexpr int kProdThreads = kProdWarps * 32;
-constexpr int kProdWarp0 = 4;               // warps 0..3: operand TMA, MMA, input TMA, peer copier
+constexpr int kProdWarp0 = 4;               // warps 0..3: operand TMA, MMA, input TMA, idle
 constexpr int kEpiWarp0 = kProdWarp0 + kProdWarps;
 constexpr int kThreads = (kEpiWarp0 + 4) * 32;
 constexpr int kMaxSmem = 227 * 1024;
@@ -410,13 +411,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int NS = sp.n_stages;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + sp.bar_off);
     const uint32_t bar_base = smem_u32(bars);
+    // One "stage full" barrier per ring slot: the operand copy's arrival (+ its bytes) and the
+    // spectrum rows' arrival(s) (+ the peer's bytes for a shared tile), so the MMA issuer waits once.
     auto full_a = [&](int s) { return bar_base + 8u * s; };
-    auto full_b = [&](int s) { return bar_base + 8u * (NS + s); };
+    auto full_b = full_a;
     auto empty_bar = [&](int s) { return bar_base + 8u * (2 * NS + s); };
     auto full_in = [&](int s) { return bar_base + 8u * (3 * NS + s); };
     auto empty_in = [&](int s) { return bar_base + 8u * (3 * NS + kInSlots + s); };
-    auto rows_ready = [&](int s) { return bar_base + 8u * (3 * NS + 2 * kInSlots + s); };
-    const int nb = 4 * NS + 2 * kInSlots;
+    const int nb = 3 * NS + 2 * kInSlots;
     const uint32_t acc_full = bar_base + 8u * nb;
     const uint32_t acc_empty = bar_base + 8u * (nb + 1);
     const uint32_t drain_bar = bar_base + 8u * (nb + 2);
@@ -428,15 +430,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t rank = share ? cluster_rank() : 0u;
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
-            // shared tile: the copier's arrival + the peer's bytes; otherwise one arrival per producer warp
-            mbar_init(full_a(s), share ? 1 : kProdWarps);
-            mbar_init(full_b(s), 1);
+            // one arrival per warp of the producer group that builds the stage + the operand copy's
+            // (its bytes and, for a shared tile, the peer's rows)
+            mbar_init(full_a(s), kProdWarps / 2 + 1);   // one producer group builds a stage
             mbar_init(empty_bar(s), share ? 2 : 1);  // both CTAs' MMAs when the tile is shared
-            mbar_init(rows_ready(s), kProdWarps);
         }
         for (int s = 0; s < kInSlots; ++s) {
             mbar_init(full_in(s), 1);
-            mbar_init(empty_in(s), kProdWarps);
+            mbar_init(empty_in(s), kProdWarps / 2);
         }
         mbar_init(acc_full, 1);
         mbar_init(acc_empty, 128);
@@ -475,6 +476,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             int s = 0;
             uint32_t ph = 0;           // parity of the current pass over the ring
             const uint32_t bytes = static_cast<uint32_t>(sp.b_bytes);
+            // a shared tile also receives the peer's half of the rows (3 matrices x 64 rows x 16 points)
+            const uint32_t expect = bytes + (share ? static_cast<uint32_t>(kAMats * kTileM * kKStage) : 0u);
             for (long long j = 0; j < my_items && !*abort_flag; ++j) {
                 const long long it = item_of(j);
                 const int grp = static_cast<int>(it % F.n_groups);
@@ -485,7 +488,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(full_b(s), bytes);
+                    mbar_arrive_expect_tx(full_b(s), expect);
                     bulk_g2s(smem_u32(smem + s * sp.stage_bytes + sp.a_bytes), src + ks * F.stage_elems, bytes,
                              full_b(s));
                     ++g;
@@ -532,33 +535,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (long long q = (g > kInSlots ? g - kInSlots : 0); q < g; ++q)
                 mbar_drain(full_in(static_cast<int>(q % kInSlots)), static_cast<uint32_t>((q / kInSlots) & 1));
         }
-    } else if (warp == 3) {
-        // ---------------- shared tiles: our rows of each stage -> the peer's shared memory ----------------
-        if (share && lane == 0) {
-            constexpr uint32_t amat = kTileM * kKStage * 2;
-            const uint32_t peer = rank ^ 1u;
-            int s = 0;
-            uint32_t par = 0;
-            for (long long j = 0; j < my_items; ++j) {
-                bool ok = true;
-                for (int ks = 0; ks < n_ks; ++ks) {
-                    if (!mbar_wait(rows_ready(s), par, abort_flag, T.status)) {
-                        ok = false;
-                        break;
-                    }
-                    const uint32_t a0 = smem_u32(smem + s * sp.stage_bytes);
-                    const uint32_t bar_peer = mapa_peer(full_a(s), peer);
-#pragma unroll
-                    for (int m = 0; m < kAMats; ++m) {
-                        const uint32_t src = a0 + m * amat + rank * (amat / 2);
-                        bulk_s2peer(mapa_peer(src, peer), src, amat / 2, bar_peer);
-                    }
-                    mbar_arrive_expect_tx(full_a(s), kAMats * (amat / 2));   // the peer's rows into us
-                    if (++s == NS) { s = 0; par ^= 1u; }
-                }
-                if (!ok) break;
-            }
-        }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
@@ -573,8 +549,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_after();
                 }
                 for (int ks = 0; ks < n_ks; ++ks) {
-                    if (!mbar_wait(full_b(s), par, abort_flag, T.status) ||
-                        !mbar_wait(full_a(s), par, abort_flag, T.status)) {
+                    if (!mbar_wait(full_a(s), par, abort_flag, T.status)) {
                         ok = false;
                         break;
                     }
@@ -596,8 +571,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_mma(d_sig, xhi, hlo, idesc, 1u);
                     tc_mma(d_noi, xhi, gmat, idesc, acc);
                     tc_mma(d_noi, xsq, qmat, idesc, 1u);
-                    if (share) tc_commit_pair(empty_bar(s));   // stage s free in both CTAs
-                    else tc_commit(empty_bar(s));              // stage s free once these MMAs finish
+                    if (share) tc_commit_pair(empty_bar(s));   // slot s free in both CTAs
+                    else tc_commit(empty_bar(s));              // slot s free once these MMAs finish
                     if (++s == NS) { s = 0; par ^= 1u; }
                 }
                 if (!ok) break;
@@ -606,76 +581,101 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_commit(drain_bar);                     // no MMA in flight at exit (bounded)
             mbar_drain(drain_bar, 0);
         }
-    } else if (warp < kEpiWarp0) {
+    } else if (warp >= kProdWarp0 && warp < kEpiWarp0) {
         // ---------------- spectrum producers ----------------
-        // Independent CTA: thread = (row 0..127, 8 points).  Shared tile: this CTA builds rows
-        // [64 rank, 64 rank + 64), thread = (row, 4 points), and ships them to the peer.
+        // Two groups of four warps build alternate stages (global stage g = item * n_ks + ks,
+        // group = g mod 2), so each warp has two stage periods for one stage's rows.
+        // Independent CTA: warp = 32 rows, thread = (row, 16 points).
+        // Shared tile: this CTA builds rows [64 rank, 64 rank + 64); warp = 16 rows (two 8-row
+        // core-matrix groups), thread = (row, 8 points), so the warp's rows of each matrix form
+        // one contiguous 512-byte block, copied to the peer as it is.
+        // Each thread stores 8 consecutive points (16 bytes) per matrix: a warp's store covers
+        // whole 128-byte core-matrix rows, without bank conflicts.
         const int pw = warp - kProdWarp0;
-        const int r = share ? static_cast<int>(rank) * 64 + (pw & 1) * 32 + lane : (pw & 3) * 32 + lane;
-        const int kh = share ? (pw >> 1) * 4 : (pw >> 2) * 8;   // first point of this thread in the stage
-        const int nq = share ? 1 : 2;                            // float4 quads per thread
-        long long g = 0;
-        int s = 0, si = 0;
+        const int pgrp = pw >> 2;                    // stage parity built by this warp
+        const int wq = pw & 3;                       // warp within its group
+        const int r = share ? static_cast<int>(rank) * 64 + 16 * wq + (lane >> 1) : 32 * wq + lane;
+        const int kh = share ? 8 * (lane & 1) : 0;   // first point of this thread in the stage
+        const int nq = share ? 2 : 4;                // float4 quads per thread
+        // The peer's rank (our own rank for an independent CTA, so that an address mapping the
+        // compiler may evaluate ahead of the share test never names a CTA outside the cluster).
+        const uint32_t peer = share ? (rank ^ 1u) : rank;
+        constexpr int amat = kTileM * kKStage * 2;
+        long long g = pgrp;                          // global stage index
+        long long j = 0;                             // item index
+        int ks = pgrp;
+        while (ks >= n_ks) { ks -= n_ks; ++j; }
+        int s = pgrp % NS, si = pgrp % kInSlots;
         uint32_t ph = 0, phi = 0;
+        long long j_rows = -1;                       // item whose row constants are loaded
         bool ok = true;
-        for (long long j = 0; j < my_items && ok; ++j) {
-            const long long it = item_of(j);
-            long long tile, row0;
-            int pix, nrows, grp;
-            item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
-            const TileInfo ti = tiles[tile];
-            const bool valid = r < nrows;
-            RowParams rp;
-            if (valid) {
-                rp = rows[static_cast<long long>(pix) * nt + row0 + r];
-            } else {
-                rp.csc = 1.f; rp.tau_j = ti.j0; rp.tau_f = 0.f; rp.src_idx = -1; rp.src_fa = 0.f; rp.src_fe = 0.f;
-                rp.src_cell = -1;
-            }
-            if (rp.tau_j < 0 || rp.tau_j > T.n_pwv - 2) {
-                atomicOr(T.status, GATEAU_STATUS_BAD_INDEX);
-                rp.tau_j = 0;
-            }
-            const bool has_src = valid && rp.src_idx >= 0;
-            // staged boxes, with a range check that sends a row to the global path otherwise
-            const int dj = rp.tau_j - ti.j0;
-            const bool tau_box = F.tma_inputs && (ti.flags & TILE_TAU_FITS) && dj >= 0 && dj <= kTauBoxRows - 1;
-            const int da = has_src ? (rp.src_cell >> 16) - ti.ia0 : 0;
-            const int de = has_src ? (rp.src_cell & 0xffff) - ti.ie0 : 0;
-            const bool cube_box = has_src && F.tma_inputs && (ti.flags & TILE_CUBE_FITS) && da >= 0 &&
-                                  da <= kCubeBoxAz - 2 && de >= 0 && de <= kCubeBoxEl - 2;
-            const float* gA = T.tau + static_cast<long long>(2 * rp.tau_j) * T.Kp;    // tau_j
-            const float* gD = gA + T.Kp;                                               // tau_{j+1} - tau_j
-            const float fa = rp.src_fa, fe = rp.src_fe;
-            const float w00 = (1.f - fa) * (1.f - fe), w10 = fa * (1.f - fe), w01 = (1.f - fa) * fe, w11 = fa * fe;
-            const float* g00 = T.cube + (has_src ? rp.src_idx : 0);
-            const float* g10 = g00 + static_cast<long long>(T.n_el) * T.Kp;
-            const float* g01 = g00 + T.Kp;
-            const float* g11 = g10 + T.Kp;
-            const int sA = 2 * dj * kBoxW + kh;                                  // float offsets inside a slot
-            const int sC00 = (da * kCubeBoxEl + de) * kBoxW + kh;
-            const int sC10 = sC00 + kCubeBoxEl * kBoxW;
-            const int sC01 = sC00 + kBoxW;
-            const int sC11 = sC10 + kBoxW;
-            // eta_atm = exp(-csc tau) = 2^(a tau_j + b dtau_j) with a = -csc log2(e), b = a f
-            const float ea = -rp.csc * 1.4426950408889634f, eb = ea * rp.tau_f;
-            for (int ks = 0; ks < n_ks; ++ks) {
-                bool okw = (g < NS || mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, T.status)) &&
-                           mbar_wait(full_in(si), phi, abort_flag, T.status);
-                okw = __all_sync(0xffffffffu, okw);  // the warp signals as one
-                if (!okw) {
-                    ok = false;
-                    break;
+        // row constants of the current item
+        bool tau_box = false, cube_box = false, has_src = false;
+        const float* gA = T.tau;
+        const float* gD = T.tau;
+        const float *g00 = T.cube, *g10 = T.cube, *g01 = T.cube, *g11 = T.cube;
+        float w00 = 0.f, w10 = 0.f, w01 = 0.f, w11 = 0.f, ea = 0.f, eb = 0.f;
+        int sA = 0, sC00 = 0;
+        while (ok && j < my_items) {
+            if (j != j_rows) {
+                j_rows = j;
+                const long long it = item_of(j);
+                long long tile, row0;
+                int pix, nrows, grp;
+                item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
+                const TileInfo ti = tiles[tile];
+                const bool valid = r < nrows;
+                RowParams rp;
+                if (valid) {
+                    rp = rows[static_cast<long long>(pix) * nt + row0 + r];
+                } else {
+                    rp.csc = 1.f; rp.tau_j = ti.j0; rp.tau_f = 0.f; rp.src_idx = -1; rp.src_fa = 0.f;
+                    rp.src_fe = 0.f; rp.src_cell = -1;
                 }
-                uint8_t* a0 = smem + s * sp.stage_bytes;
-                constexpr int amat = kTileM * kKStage * 2;
-                {
-                    const float* slot =
-                        reinterpret_cast<const float*>(smem + sp.in_off + static_cast<size_t>(si) * kInSlotBytes);
-                    const float* stau = slot + kTauOff / 4;
-                    const float* scon = slot + kConstOff / 4 + kh;     // [c0 + c1][16], [c1][16]
-                    const int k = ks * kKStage + kh;
-                    for (int h = 0; h < nq; ++h) {
+                if (rp.tau_j < 0 || rp.tau_j > T.n_pwv - 2) {
+                    atomicOr(T.status, GATEAU_STATUS_BAD_INDEX);
+                    rp.tau_j = 0;
+                }
+                has_src = valid && rp.src_idx >= 0;
+                // staged boxes, with a range check that sends a row to the global path otherwise
+                const int dj = rp.tau_j - ti.j0;
+                tau_box = F.tma_inputs && (ti.flags & TILE_TAU_FITS) && dj >= 0 && dj <= kTauBoxRows - 1;
+                const int da = has_src ? (rp.src_cell >> 16) - ti.ia0 : 0;
+                const int de = has_src ? (rp.src_cell & 0xffff) - ti.ie0 : 0;
+                cube_box = has_src && F.tma_inputs && (ti.flags & TILE_CUBE_FITS) && da >= 0 &&
+                           da <= kCubeBoxAz - 2 && de >= 0 && de <= kCubeBoxEl - 2;
+                gA = T.tau + static_cast<long long>(2 * rp.tau_j) * T.Kp;    // tau_j
+                gD = gA + T.Kp;                                               // tau_{j+1} - tau_j
+                const float fa = rp.src_fa, fe = rp.src_fe;
+                w00 = (1.f - fa) * (1.f - fe); w10 = fa * (1.f - fe); w01 = (1.f - fa) * fe; w11 = fa * fe;
+                g00 = T.cube + (has_src ? rp.src_idx : 0);
+                g10 = g00 + static_cast<long long>(T.n_el) * T.Kp;
+                g01 = g00 + T.Kp;
+                g11 = g10 + T.Kp;
+                sA = 2 * dj * kBoxW + kh;                                     // float offsets inside a slot
+                sC00 = (da * kCubeBoxEl + de) * kBoxW + kh;
+                // eta_atm = exp(-csc tau) = 2^(a tau_j + b dtau_j) with a = -csc log2(e), b = a f
+                ea = -rp.csc * 1.4426950408889634f;
+                eb = ea * rp.tau_f;
+            }
+            bool okw = (g < NS || mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, T.status)) &&
+                       mbar_wait(full_in(si), phi, abort_flag, T.status);
+            okw = __all_sync(0xffffffffu, okw);      // the warp signals as one
+            if (!okw) {
+                ok = false;
+                break;
+            }
+            uint8_t* a0 = smem + s * sp.stage_bytes;
+            {
+                const float* slot =
+                    reinterpret_cast<const float*>(smem + sp.in_off + static_cast<size_t>(si) * kInSlotBytes);
+                const float* stau = slot + kTauOff / 4;
+                const float* scon = slot + kConstOff / 4 + kh;     // [c0 + c1][16], [c1][16]
+                const int k = ks * kKStage + kh;
+                uint32_t hi[8], lo[8], sq[8];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    if (h < nq) {
                         const int kq = k + 4 * h;
                         float4 ta, td;
                         if (tau_box) {
@@ -692,9 +692,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                             float4 q00, q10, q01, q11;
                             if (cube_box) {
                                 q00 = ld4(slot + sC00 + 4 * h);
-                                q10 = ld4(slot + sC10 + 4 * h);
-                                q01 = ld4(slot + sC01 + 4 * h);
-                                q11 = ld4(slot + sC11 + 4 * h);
+                                q10 = ld4(slot + sC00 + kCubeBoxEl * kBoxW + 4 * h);
+                                q01 = ld4(slot + sC00 + kBoxW + 4 * h);
+                                q11 = ld4(slot + sC00 + kCubeBoxEl * kBoxW + kBoxW + 4 * h);
                             } else {
                                 q00 = ld4(g00 + kq);
                                 q10 = ld4(g10 + kq);
@@ -714,34 +714,49 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
                         GATEAU_FX(0, x) GATEAU_FX(1, y) GATEAU_FX(2, z) GATEAU_FX(3, w)
 #undef GATEAU_FX
-                        uint32_t hi[2], lo[2], sq[2];
 #pragma unroll
                         for (int q = 0; q < 2; ++q) {
                             const float xa = x[2 * q], xb = x[2 * q + 1];
                             const __nv_bfloat162 h2 = __floats2bfloat162_rn(xa, xb);
-                            hi[q] = *reinterpret_cast<const uint32_t*>(&h2);
-                            lo[q] = pack_bf16(xa - __low2float(h2), xb - __high2float(h2));
-                            const __nv_bfloat162 s2 = __hmul2(h2, h2);        // bf16(X_hi^2) for the noise term
-                            sq[q] = *reinterpret_cast<const uint32_t*>(&s2);
+                            hi[2 * h + q] = *reinterpret_cast<const uint32_t*>(&h2);
+                            lo[2 * h + q] = pack_bf16(xa - __low2float(h2), xb - __high2float(h2));
+                            const __nv_bfloat162 s2 = __hmul2(h2, h2);    // bf16(X_hi^2) for the noise term
+                            sq[2 * h + q] = *reinterpret_cast<const uint32_t*>(&s2);
                         }
-                        const size_t off = core_offset(r, kh + 4 * h, kTileM);
-                        *reinterpret_cast<uint2*>(a0 + 0 * amat + off) = make_uint2(hi[0], hi[1]);
-                        *reinterpret_cast<uint2*>(a0 + 1 * amat + off) = make_uint2(lo[0], lo[1]);
-                        *reinterpret_cast<uint2*>(a0 + 2 * amat + off) = make_uint2(sq[0], sq[1]);
                     }
                 }
-                fence_proxy_async();                 // our generic stores -> the tensor-core (async) proxy
-                __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(share ? rows_ready(s) : full_a(s));
-                    mbar_arrive(empty_in(si));
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    if (2 * hh < nq) {
+                        const size_t off = core_offset(r, kh + 8 * hh, kTileM);   // 16-byte aligned
+                        *reinterpret_cast<uint4*>(a0 + 0 * amat + off) =
+                            make_uint4(hi[4 * hh], hi[4 * hh + 1], hi[4 * hh + 2], hi[4 * hh + 3]);
+                        *reinterpret_cast<uint4*>(a0 + 1 * amat + off) =
+                            make_uint4(lo[4 * hh], lo[4 * hh + 1], lo[4 * hh + 2], lo[4 * hh + 3]);
+                        *reinterpret_cast<uint4*>(a0 + 2 * amat + off) =
+                            make_uint4(sq[4 * hh], sq[4 * hh + 1], sq[4 * hh + 2], sq[4 * hh + 3]);
+                    }
                 }
-                ++g;
-                if (++s == NS) { s = 0; ph ^= 1u; }
-                if (++si == kInSlots) { si = 0; phi ^= 1u; }
             }
+            fence_proxy_async();                     // our generic stores -> the tensor-core (async) proxy
+            __syncwarp();
+            if (share && lane < kAMats) {
+                // lane m: this warp's 16-row block of matrix m -> the same place in the peer CTA
+                const uint32_t blk = smem_u32(a0) + static_cast<uint32_t>(lane * amat) +
+                                     static_cast<uint32_t>((static_cast<int>(rank) * 64 + 16 * wq) / 8) * 256u;
+                bulk_s2peer(mapa_peer(blk, peer), blk, 512u, mapa_peer(full_a(s), peer));
+            }
+            if (lane < 2) mbar_arrive(lane == 0 ? full_a(s) : empty_in(si));
+            // next stage of this parity
+            g += 2;
+            s += 2;
+            while (s >= NS) { s -= NS; ph ^= 1u; }
+            si += 2;
+            while (si >= kInSlots) { si -= kInSlots; phi ^= 1u; }
+            ks += 2;
+            while (ks >= n_ks) { ks -= n_ks; ++j; }
         }
-    } else {
+    } else if (warp >= kEpiWarp0) {
         // ---------------- epilogue: thread = TMEM lane = tile row ----------------
         const int quad = warp & 3;                   // TMEM lane quadrant this warp may access
         const int r = quad * 32 + lane;
