@@ -239,6 +239,24 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
+// Bounded wait for a long-pending phase (the epilogue's wait for a finished item): between
+// polls the thread sleeps, so idle waiters do not take shared-memory issue slots from the
+// roles on the critical path.
+__device__ __forceinline__ bool mbar_wait_idle(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                               unsigned int* status) {
+    const long long t_start = clock64();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t_start > kWaitCycles) {
+            *abort_flag = 1;
+            atomicOr(status, GATEAU_STATUS_WAIT_TIMEOUT);
+            return false;
+        }
+        __nanosleep(256);
+    }
+}
+
 // Bounded wait used on the exit path (no abort check).
 __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
     const long long t_start = clock64();
@@ -399,6 +417,7 @@ __device__ __forceinline__ void item_coords(const Work& w, int n_groups, long lo
     nrows = rem < kTileM ? static_cast<int>(rem) : kTileM;
 }
 
+template <int kShare>
 __global__ void __launch_bounds__(kThreads, 1)
     fused_bf16x3_kernel(const __grid_constant__ CUtensorMap tm_tau, const __grid_constant__ CUtensorMap tm_cube,
                         DevTables T, FusedOperands F, const RowParams* __restrict__ rows,
@@ -426,7 +445,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + sp.bar_off + 8 * (nb + 3) + 8);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int share = work.share;
+    constexpr int share = kShare;
     const uint32_t rank = share ? cluster_rank() : 0u;
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -596,7 +615,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int wq = pw & 3;                       // warp within its group
         const int r = share ? static_cast<int>(rank) * 64 + 16 * wq + (lane >> 1) : 32 * wq + lane;
         const int kh = share ? 8 * (lane & 1) : 0;   // first point of this thread in the stage
-        const int nq = share ? 2 : 4;                // float4 quads per thread
+        constexpr int nq = share ? 2 : 4;            // float4 quads per thread
         // The peer's rank (our own rank for an independent CTA, so that an address mapping the
         // compiler may evaluate ahead of the share test never names a CTA outside the cluster).
         const uint32_t peer = share ? (rank ^ 1u) : rank;
@@ -672,70 +691,74 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const float* stau = slot + kTauOff / 4;
                 const float* scon = slot + kConstOff / 4 + kh;     // [c0 + c1][16], [c1][16]
                 const int k = ks * kKStage + kh;
-                uint32_t hi[8], lo[8], sq[8];
+                // Read everything this stage needs from the input slot, then release the slot so
+                // the next gathers land while this warp computes.
+                float4 arg[nq], src[nq], c01[nq], c1[nq];
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    if (h < nq) {
-                        const int kq = k + 4 * h;
-                        float4 ta, td;
-                        if (tau_box) {
-                            ta = ld4(stau + sA + 4 * h);
-                            td = ld4(stau + sA + kBoxW + 4 * h);
+                for (int h = 0; h < nq; ++h) {
+                    const int kq = k + 4 * h;
+                    float4 ta, td;
+                    if (tau_box) {
+                        ta = ld4(stau + sA + 4 * h);
+                        td = ld4(stau + sA + kBoxW + 4 * h);
+                    } else {
+                        ta = ld4(gA + kq);
+                        td = ld4(gD + kq);
+                    }
+                    c01[h] = ld4(scon + 4 * h);
+                    c1[h] = ld4(scon + kKStage + 4 * h);
+                    // eta_atm = exp(-csc tau) = 2^(a tau_j + b dtau_j)
+                    arg[h] = make_float4(fmaf(eb, td.x, ea * ta.x), fmaf(eb, td.y, ea * ta.y),
+                                         fmaf(eb, td.z, ea * ta.z), fmaf(eb, td.w, ea * ta.w));
+                    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (has_src) {
+                        float4 q00, q10, q01, q11;
+                        if (cube_box) {
+                            q00 = ld4(slot + sC00 + 4 * h);
+                            q10 = ld4(slot + sC00 + kCubeBoxEl * kBoxW + 4 * h);
+                            q01 = ld4(slot + sC00 + kBoxW + 4 * h);
+                            q11 = ld4(slot + sC00 + kCubeBoxEl * kBoxW + kBoxW + 4 * h);
                         } else {
-                            ta = ld4(gA + kq);
-                            td = ld4(gD + kq);
+                            q00 = ld4(g00 + kq);
+                            q10 = ld4(g10 + kq);
+                            q01 = ld4(g01 + kq);
+                            q11 = ld4(g11 + kq);
                         }
-                        const float4 c01 = ld4(scon + 4 * h);
-                        const float4 c1 = ld4(scon + kKStage + 4 * h);
-                        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (has_src) {
-                            float4 q00, q10, q01, q11;
-                            if (cube_box) {
-                                q00 = ld4(slot + sC00 + 4 * h);
-                                q10 = ld4(slot + sC00 + kCubeBoxEl * kBoxW + 4 * h);
-                                q01 = ld4(slot + sC00 + kBoxW + 4 * h);
-                                q11 = ld4(slot + sC00 + kCubeBoxEl * kBoxW + kBoxW + 4 * h);
-                            } else {
-                                q00 = ld4(g00 + kq);
-                                q10 = ld4(g10 + kq);
-                                q01 = ld4(g01 + kq);
-                                q11 = ld4(g11 + kq);
-                            }
-                            p.x = w00 * q00.x + w10 * q10.x + w01 * q01.x + w11 * q11.x;
-                            p.y = w00 * q00.y + w10 * q10.y + w01 * q01.y + w11 * q11.y;
-                            p.z = w00 * q00.z + w10 * q10.z + w01 * q01.z + w11 * q11.z;
-                            p.w = w00 * q00.w + w10 * q10.w + w01 * q01.w + w11 * q11.w;
-                        }
-                        float x[4];
-#define GATEAU_FX(i, c)                                          \
-    {                                                            \
-        const float e = ex2_approx(fmaf(eb, td.c, ea * ta.c));   \
-        x[i] = fmaf(e, p.c - c1.c, c01.c);                       \
-    }
-                        GATEAU_FX(0, x) GATEAU_FX(1, y) GATEAU_FX(2, z) GATEAU_FX(3, w)
+                        p.x = w00 * q00.x + w10 * q10.x + w01 * q01.x + w11 * q11.x;
+                        p.y = w00 * q00.y + w10 * q10.y + w01 * q01.y + w11 * q11.y;
+                        p.z = w00 * q00.z + w10 * q10.z + w01 * q01.z + w11 * q11.z;
+                        p.w = w00 * q00.w + w10 * q10.w + w01 * q01.w + w11 * q11.w;
+                    }
+                    src[h] = p;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty_in(si));
+                uint32_t hi[2 * nq], lo[2 * nq], sq[2 * nq];
+#pragma unroll
+                for (int h = 0; h < nq; ++h) {
+                    float x[4];
+#define GATEAU_FX(i, c) x[i] = fmaf(ex2_approx(arg[h].c), src[h].c - c1[h].c, c01[h].c);
+                    GATEAU_FX(0, x) GATEAU_FX(1, y) GATEAU_FX(2, z) GATEAU_FX(3, w)
 #undef GATEAU_FX
 #pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            const float xa = x[2 * q], xb = x[2 * q + 1];
-                            const __nv_bfloat162 h2 = __floats2bfloat162_rn(xa, xb);
-                            hi[2 * h + q] = *reinterpret_cast<const uint32_t*>(&h2);
-                            lo[2 * h + q] = pack_bf16(xa - __low2float(h2), xb - __high2float(h2));
-                            const __nv_bfloat162 s2 = __hmul2(h2, h2);    // bf16(X_hi^2) for the noise term
-                            sq[2 * h + q] = *reinterpret_cast<const uint32_t*>(&s2);
-                        }
+                    for (int q = 0; q < 2; ++q) {
+                        const float xa = x[2 * q], xb = x[2 * q + 1];
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(xa, xb);
+                        hi[2 * h + q] = *reinterpret_cast<const uint32_t*>(&h2);
+                        lo[2 * h + q] = pack_bf16(xa - __low2float(h2), xb - __high2float(h2));
+                        const __nv_bfloat162 s2 = __hmul2(h2, h2);        // bf16(X_hi^2) for the noise term
+                        sq[2 * h + q] = *reinterpret_cast<const uint32_t*>(&s2);
                     }
                 }
 #pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    if (2 * hh < nq) {
-                        const size_t off = core_offset(r, kh + 8 * hh, kTileM);   // 16-byte aligned
-                        *reinterpret_cast<uint4*>(a0 + 0 * amat + off) =
-                            make_uint4(hi[4 * hh], hi[4 * hh + 1], hi[4 * hh + 2], hi[4 * hh + 3]);
-                        *reinterpret_cast<uint4*>(a0 + 1 * amat + off) =
-                            make_uint4(lo[4 * hh], lo[4 * hh + 1], lo[4 * hh + 2], lo[4 * hh + 3]);
-                        *reinterpret_cast<uint4*>(a0 + 2 * amat + off) =
-                            make_uint4(sq[4 * hh], sq[4 * hh + 1], sq[4 * hh + 2], sq[4 * hh + 3]);
-                    }
+                for (int hh = 0; hh < nq / 2; ++hh) {
+                    const size_t off = core_offset(r, kh + 8 * hh, kTileM);   // 16-byte aligned
+                    *reinterpret_cast<uint4*>(a0 + 0 * amat + off) =
+                        make_uint4(hi[4 * hh], hi[4 * hh + 1], hi[4 * hh + 2], hi[4 * hh + 3]);
+                    *reinterpret_cast<uint4*>(a0 + 1 * amat + off) =
+                        make_uint4(lo[4 * hh], lo[4 * hh + 1], lo[4 * hh + 2], lo[4 * hh + 3]);
+                    *reinterpret_cast<uint4*>(a0 + 2 * amat + off) =
+                        make_uint4(sq[4 * hh], sq[4 * hh + 1], sq[4 * hh + 2], sq[4 * hh + 3]);
                 }
             }
             fence_proxy_async();                     // our generic stores -> the tensor-core (async) proxy
@@ -746,7 +769,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                      static_cast<uint32_t>((static_cast<int>(rank) * 64 + 16 * wq) / 8) * 256u;
                 bulk_s2peer(mapa_peer(blk, peer), blk, 512u, mapa_peer(full_a(s), peer));
             }
-            if (lane < 2) mbar_arrive(lane == 0 ? full_a(s) : empty_in(si));
+            if (lane == 0) mbar_arrive(full_a(s));
             // next stage of this parity
             g += 2;
             s += 2;
@@ -763,7 +786,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool white = (T.noise_flags & GATEAU_NOISE_WHITE) != 0;
         for (long long j = 0; j < my_items; ++j) {
             // tcgen05.ld is warp-collective: take the wait's outcome warp-uniformly.
-            const bool ok = mbar_wait(acc_full, static_cast<uint32_t>(j & 1), abort_flag, T.status);
+            const bool ok = mbar_wait_idle(acc_full, static_cast<uint32_t>(j & 1), abort_flag, T.status);
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
             const long long it = item_of(j);
@@ -823,7 +846,8 @@ cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, cons
     w.n_items = w.tiles_per_pix * T.n_pix * F.n_groups;
     w.share = F.n_groups == 2 ? 1 : 0;
     if (w.n_items == 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(fused_bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    auto kernel = w.share ? fused_bf16x3_kernel<1> : fused_bf16x3_kernel<0>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(sp.total));
     if (e != cudaSuccess) return e;
     CUtensorMap mt, mc;
@@ -844,7 +868,7 @@ cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, cons
         cfg.numAttrs = 1;
         cfg.gridDim = dim3(static_cast<unsigned>(n_sm / 2 * 2));
         int max_clusters = 0;
-        e = cudaOccupancyMaxActiveClusters(&max_clusters, fused_bf16x3_kernel, &cfg);
+        e = cudaOccupancyMaxActiveClusters(&max_clusters, kernel, &cfg);
         if (e != cudaSuccess) return e;
         if (max_clusters < 1) return cudaErrorInvalidConfiguration;
         const long long tiles = w.n_items / 2;
@@ -855,7 +879,7 @@ cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, cons
         grid = w.n_items < n_sm ? w.n_items : n_sm;
     }
     cfg.gridDim = dim3(static_cast<unsigned>(grid));
-    e = cudaLaunchKernelEx(&cfg, fused_bf16x3_kernel, mt, mc, T, F, rows, tiles, t0, nt, w, out);
+    e = cudaLaunchKernelEx(&cfg, kernel, mt, mc, T, F, rows, tiles, t0, nt, w, out);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
