@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(empty_in(s), kProdWarps / 2);
         }
         mbar_init(acc_full, 1);
-        mbar_init(acc_empty, 128);
+        mbar_init(acc_empty, 4 + kProdWarps);   // the epilogue warps and the producer warps
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -486,6 +486,61 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto item_of = [&](long long j) {
         const long long u = ubase + j * ustride;
         return share ? u * 2 + rank : u;
+    };
+
+    // ---------------- epilogue of one item: this warp's share of the channel chunks ----------------
+    // A warp reads the TMEM lanes of its quadrant (warp mod 4) = tile rows [32 quad, 32 quad + 32).
+    // Each quadrant's chunks of 16 channels are split over three warps: the epilogue warp and one
+    // warp of each producer group, which are idle while the accumulators drain.
+    const int n_chunks = NH / 16;
+    const int epi_role = warp >= kEpiWarp0 ? 0 : (warp < kProdWarp0 + 4 ? 1 : 2);
+    const int cut1 = (n_chunks + 2) / 3, cut2 = cut1 + (n_chunks - cut1 + 1) / 2;
+    const int chunk_lo = epi_role == 0 ? 0 : (epi_role == 1 ? cut1 : cut2);
+    const int chunk_hi = epi_role == 0 ? cut1 : (epi_role == 1 ? cut2 : n_chunks);
+    const bool white = (T.noise_flags & GATEAU_NOISE_WHITE) != 0;
+    auto epilogue_item = [&](long long j) -> bool {
+        // tcgen05.ld is warp-collective: take the wait's outcome warp-uniformly.
+        const bool okw = mbar_wait(acc_full, static_cast<uint32_t>(j & 1), abort_flag, T.status);
+        if (!__all_sync(0xffffffffu, okw)) return false;
+        tc_fence_after();
+        const int quad = warp & 3;
+        const int r = quad * 32 + lane;
+        const long long it = item_of(j);
+        long long tile, row0;
+        int pix, nrows, grp;
+        item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
+        const long long n = t0 + row0 + r;
+        float* orow = out + ((row0 + r) * T.n_pix + pix) * static_cast<long long>(T.n_ch);
+        const int ch_base = grp * NH;
+        const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
+        for (int c = 16 * chunk_lo; c < 16 * chunk_hi; c += 16) {
+            float sv[16], nv[16];
+            tmem_ld16(d_sig + lane_off + c, sv);
+            tmem_ld16(d_noi + lane_off + c, nv);
+            tmem_wait_ld();
+            if (r < nrows) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int ch0 = ch_base + c + 4 * q;
+                    if (ch0 >= T.n_ch) break;
+                    float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (white) z = white_normals4_fast(n, pix, ch0 >> 2, T.key0, T.key1);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int ch = ch0 + e;
+                        if (ch < T.n_ch) {
+                            const float pk = T.kb1e9 * sv[4 * q + e];
+                            const float sigma = T.kB * sqrtf(T.noise_scale * fmaxf(nv[4 * q + e], 0.f));
+                            orow[ch] = fmaf(sigma, f4_get(z, e), pk);
+                        }
+                    }
+                }
+            }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty);   // one arrival per epilogue-sharing warp
+        return true;
     };
 
     if (warp == 0) {
@@ -620,24 +675,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         // compiler may evaluate ahead of the share test never names a CTA outside the cluster).
         const uint32_t peer = share ? (rank ^ 1u) : rank;
         constexpr int amat = kTileM * kKStage * 2;
-        long long g = pgrp;                          // global stage index
-        long long j = 0;                             // item index
-        int ks = pgrp;
-        while (ks >= n_ks) { ks -= n_ks; ++j; }
+        long long g = pgrp;                          // global stage index = item * n_ks + ks
         int s = pgrp % NS, si = pgrp % kInSlots;
         uint32_t ph = 0, phi = 0;
-        long long j_rows = -1;                       // item whose row constants are loaded
         bool ok = true;
-        // row constants of the current item
-        bool tau_box = false, cube_box = false, has_src = false;
-        const float* gA = T.tau;
-        const float* gD = T.tau;
-        const float *g00 = T.cube, *g10 = T.cube, *g01 = T.cube, *g11 = T.cube;
-        float w00 = 0.f, w10 = 0.f, w01 = 0.f, w11 = 0.f, ea = 0.f, eb = 0.f;
-        int sA = 0, sC00 = 0;
-        while (ok && j < my_items) {
-            if (j != j_rows) {
-                j_rows = j;
+        for (long long j = 0; j < my_items && ok; ++j) {
+            // row constants of item j
+            bool tau_box, cube_box, has_src;
+            const float *gA, *gD, *g00, *g10, *g01, *g11;
+            float w00, w10, w01, w11, ea, eb;
+            int sA, sC00;
+            {
                 const long long it = item_of(j);
                 long long tile, row0;
                 int pix, nrows, grp;
@@ -677,153 +725,115 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ea = -rp.csc * 1.4426950408889634f;
                 eb = ea * rp.tau_f;
             }
-            bool okw = (g < NS || mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, T.status)) &&
-                       mbar_wait(full_in(si), phi, abort_flag, T.status);
-            okw = __all_sync(0xffffffffu, okw);      // the warp signals as one
-            if (!okw) {
-                ok = false;
-                break;
-            }
-            uint8_t* a0 = smem + s * sp.stage_bytes;
-            {
-                const float* slot =
-                    reinterpret_cast<const float*>(smem + sp.in_off + static_cast<size_t>(si) * kInSlotBytes);
-                const float* stau = slot + kTauOff / 4;
-                const float* scon = slot + kConstOff / 4 + kh;     // [c0 + c1][16], [c1][16]
-                const int k = ks * kKStage + kh;
-                // Read everything this stage needs from the input slot, then release the slot so
-                // the next gathers land while this warp computes.
-                float4 arg[nq], src[nq], c01[nq], c1[nq];
-#pragma unroll
-                for (int h = 0; h < nq; ++h) {
-                    const int kq = k + 4 * h;
-                    float4 ta, td;
-                    if (tau_box) {
-                        ta = ld4(stau + sA + 4 * h);
-                        td = ld4(stau + sA + kBoxW + 4 * h);
-                    } else {
-                        ta = ld4(gA + kq);
-                        td = ld4(gD + kq);
-                    }
-                    c01[h] = ld4(scon + 4 * h);
-                    c1[h] = ld4(scon + kKStage + 4 * h);
-                    // eta_atm = exp(-csc tau) = 2^(a tau_j + b dtau_j)
-                    arg[h] = make_float4(fmaf(eb, td.x, ea * ta.x), fmaf(eb, td.y, ea * ta.y),
-                                         fmaf(eb, td.z, ea * ta.z), fmaf(eb, td.w, ea * ta.w));
-                    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (has_src) {
-                        float4 q00, q10, q01, q11;
-                        if (cube_box) {
-                            q00 = ld4(slot + sC00 + 4 * h);
-                            q10 = ld4(slot + sC00 + kCubeBoxEl * kBoxW + 4 * h);
-                            q01 = ld4(slot + sC00 + kBoxW + 4 * h);
-                            q11 = ld4(slot + sC00 + kCubeBoxEl * kBoxW + kBoxW + 4 * h);
-                        } else {
-                            q00 = ld4(g00 + kq);
-                            q10 = ld4(g10 + kq);
-                            q01 = ld4(g01 + kq);
-                            q11 = ld4(g11 + kq);
-                        }
-                        p.x = w00 * q00.x + w10 * q10.x + w01 * q01.x + w11 * q11.x;
-                        p.y = w00 * q00.y + w10 * q10.y + w01 * q01.y + w11 * q11.y;
-                        p.z = w00 * q00.z + w10 * q10.z + w01 * q01.z + w11 * q11.z;
-                        p.w = w00 * q00.w + w10 * q10.w + w01 * q01.w + w11 * q11.w;
-                    }
-                    src[h] = p;
+            // the stages of item j with this warp's parity (g advances by 2, across items too)
+            for (int ks = static_cast<int>((pgrp + j * n_ks) & 1); ks < n_ks; ks += 2) {
+                bool okw = (g < NS || mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, T.status)) &&
+                           mbar_wait(full_in(si), phi, abort_flag, T.status);
+                okw = __all_sync(0xffffffffu, okw);      // the warp signals as one
+                if (!okw) {
+                    ok = false;
+                    break;
                 }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(empty_in(si));
-                uint32_t hi[2 * nq], lo[2 * nq], sq[2 * nq];
+                uint8_t* a0 = smem + s * sp.stage_bytes;
+                {
+                    const float* slot =
+                        reinterpret_cast<const float*>(smem + sp.in_off + static_cast<size_t>(si) * kInSlotBytes);
+                    const float* stau = slot + kTauOff / 4;
+                    const float* scon = slot + kConstOff / 4 + kh;     // [c0 + c1][16], [c1][16]
+                    const int k = ks * kKStage + kh;
+                    // Read everything this stage needs from the input slot, then release the slot so
+                    // the next gathers land while this warp computes.
+                    float4 arg[nq], src[nq], c01[nq], c1[nq];
 #pragma unroll
-                for (int h = 0; h < nq; ++h) {
-                    float x[4];
+                    for (int h = 0; h < nq; ++h) {
+                        const int kq = k + 4 * h;
+                        float4 ta, td;
+                        if (tau_box) {
+                            ta = ld4(stau + sA + 4 * h);
+                            td = ld4(stau + sA + kBoxW + 4 * h);
+                        } else {
+                            ta = ld4(gA + kq);
+                            td = ld4(gD + kq);
+                        }
+                        c01[h] = ld4(scon + 4 * h);
+                        c1[h] = ld4(scon + kKStage + 4 * h);
+                        // eta_atm = exp(-csc tau) = 2^(a tau_j + b dtau_j)
+                        arg[h] = make_float4(fmaf(eb, td.x, ea * ta.x), fmaf(eb, td.y, ea * ta.y),
+                                             fmaf(eb, td.z, ea * ta.z), fmaf(eb, td.w, ea * ta.w));
+                        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (has_src) {
+                            float4 q00, q10, q01, q11;
+                            if (cube_box) {
+                                q00 = ld4(slot + sC00 + 4 * h);
+                                q10 = ld4(slot + sC00 + kCubeBoxEl * kBoxW + 4 * h);
+                                q01 = ld4(slot + sC00 + kBoxW + 4 * h);
+                                q11 = ld4(slot + sC00 + kCubeBoxEl * kBoxW + kBoxW + 4 * h);
+                            } else {
+                                q00 = ld4(g00 + kq);
+                                q10 = ld4(g10 + kq);
+                                q01 = ld4(g01 + kq);
+                                q11 = ld4(g11 + kq);
+                            }
+                            p.x = w00 * q00.x + w10 * q10.x + w01 * q01.x + w11 * q11.x;
+                            p.y = w00 * q00.y + w10 * q10.y + w01 * q01.y + w11 * q11.y;
+                            p.z = w00 * q00.z + w10 * q10.z + w01 * q01.z + w11 * q11.z;
+                            p.w = w00 * q00.w + w10 * q10.w + w01 * q01.w + w11 * q11.w;
+                        }
+                        src[h] = p;
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(empty_in(si));
+                    uint32_t hi[2 * nq], lo[2 * nq], sq[2 * nq];
+#pragma unroll
+                    for (int h = 0; h < nq; ++h) {
+                        float x[4];
 #define GATEAU_FX(i, c) x[i] = fmaf(ex2_approx(arg[h].c), src[h].c - c1[h].c, c01[h].c);
-                    GATEAU_FX(0, x) GATEAU_FX(1, y) GATEAU_FX(2, z) GATEAU_FX(3, w)
+                        GATEAU_FX(0, x) GATEAU_FX(1, y) GATEAU_FX(2, z) GATEAU_FX(3, w)
 #undef GATEAU_FX
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const float xa = x[2 * q], xb = x[2 * q + 1];
-                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(xa, xb);
-                        hi[2 * h + q] = *reinterpret_cast<const uint32_t*>(&h2);
-                        lo[2 * h + q] = pack_bf16(xa - __low2float(h2), xb - __high2float(h2));
-                        const __nv_bfloat162 s2 = __hmul2(h2, h2);        // bf16(X_hi^2) for the noise term
-                        sq[2 * h + q] = *reinterpret_cast<const uint32_t*>(&s2);
-                    }
-                }
-#pragma unroll
-                for (int hh = 0; hh < nq / 2; ++hh) {
-                    const size_t off = core_offset(r, kh + 8 * hh, kTileM);   // 16-byte aligned
-                    *reinterpret_cast<uint4*>(a0 + 0 * amat + off) =
-                        make_uint4(hi[4 * hh], hi[4 * hh + 1], hi[4 * hh + 2], hi[4 * hh + 3]);
-                    *reinterpret_cast<uint4*>(a0 + 1 * amat + off) =
-                        make_uint4(lo[4 * hh], lo[4 * hh + 1], lo[4 * hh + 2], lo[4 * hh + 3]);
-                    *reinterpret_cast<uint4*>(a0 + 2 * amat + off) =
-                        make_uint4(sq[4 * hh], sq[4 * hh + 1], sq[4 * hh + 2], sq[4 * hh + 3]);
-                }
-            }
-            fence_proxy_async();                     // our generic stores -> the tensor-core (async) proxy
-            __syncwarp();
-            if (share && lane < kAMats) {
-                // lane m: this warp's 16-row block of matrix m -> the same place in the peer CTA
-                const uint32_t blk = smem_u32(a0) + static_cast<uint32_t>(lane * amat) +
-                                     static_cast<uint32_t>((static_cast<int>(rank) * 64 + 16 * wq) / 8) * 256u;
-                bulk_s2peer(mapa_peer(blk, peer), blk, 512u, mapa_peer(full_a(s), peer));
-            }
-            if (lane == 0) mbar_arrive(full_a(s));
-            // next stage of this parity
-            g += 2;
-            s += 2;
-            while (s >= NS) { s -= NS; ph ^= 1u; }
-            si += 2;
-            while (si >= kInSlots) { si -= kInSlots; phi ^= 1u; }
-            ks += 2;
-            while (ks >= n_ks) { ks -= n_ks; ++j; }
-        }
-    } else if (warp >= kEpiWarp0) {
-        // ---------------- epilogue: thread = TMEM lane = tile row ----------------
-        const int quad = warp & 3;                   // TMEM lane quadrant this warp may access
-        const int r = quad * 32 + lane;
-        const bool white = (T.noise_flags & GATEAU_NOISE_WHITE) != 0;
-        for (long long j = 0; j < my_items; ++j) {
-            // tcgen05.ld is warp-collective: take the wait's outcome warp-uniformly.
-            const bool ok = mbar_wait_idle(acc_full, static_cast<uint32_t>(j & 1), abort_flag, T.status);
-            if (!__all_sync(0xffffffffu, ok)) break;
-            tc_fence_after();
-            const long long it = item_of(j);
-            long long tile, row0;
-            int pix, nrows, grp;
-            item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
-            const long long n = t0 + row0 + r;
-            float* orow = out + ((row0 + r) * T.n_pix + pix) * static_cast<long long>(T.n_ch);
-            const int ch_base = grp * NH;
-            for (int c = 0; c < NH; c += 16) {
-                float sv[16], nv[16];
-                const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
-                tmem_ld16(d_sig + lane_off + c, sv);
-                tmem_ld16(d_noi + lane_off + c, nv);
-                tmem_wait_ld();
-                if (r < nrows) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int ch0 = ch_base + c + 4 * q;
-                        if (ch0 >= T.n_ch) break;
-                        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (white) z = white_normals4_fast(n, pix, ch0 >> 2, T.key0, T.key1);
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int ch = ch0 + e;
-                            if (ch < T.n_ch) {
-                                const float pk = T.kb1e9 * sv[4 * q + e];
-                                const float sigma = T.kB * sqrtf(T.noise_scale * fmaxf(nv[4 * q + e], 0.f));
-                                orow[ch] = fmaf(sigma, f4_get(z, e), pk);
-                            }
+                        for (int q = 0; q < 2; ++q) {
+                            const float xa = x[2 * q], xb = x[2 * q + 1];
+                            const __nv_bfloat162 h2 = __floats2bfloat162_rn(xa, xb);
+                            hi[2 * h + q] = *reinterpret_cast<const uint32_t*>(&h2);
+                            lo[2 * h + q] = pack_bf16(xa - __low2float(h2), xb - __high2float(h2));
+                            const __nv_bfloat162 s2 = __hmul2(h2, h2);        // bf16(X_hi^2) for the noise term
+                            sq[2 * h + q] = *reinterpret_cast<const uint32_t*>(&s2);
                         }
                     }
+#pragma unroll
+                    for (int hh = 0; hh < nq / 2; ++hh) {
+                        const size_t off = core_offset(r, kh + 8 * hh, kTileM);   // 16-byte aligned
+                        *reinterpret_cast<uint4*>(a0 + 0 * amat + off) =
+                            make_uint4(hi[4 * hh], hi[4 * hh + 1], hi[4 * hh + 2], hi[4 * hh + 3]);
+                        *reinterpret_cast<uint4*>(a0 + 1 * amat + off) =
+                            make_uint4(lo[4 * hh], lo[4 * hh + 1], lo[4 * hh + 2], lo[4 * hh + 3]);
+                        *reinterpret_cast<uint4*>(a0 + 2 * amat + off) =
+                            make_uint4(sq[4 * hh], sq[4 * hh + 1], sq[4 * hh + 2], sq[4 * hh + 3]);
+                    }
                 }
+                fence_proxy_async();                     // our generic stores -> the tensor-core (async) proxy
+                __syncwarp();
+                if (share && lane < kAMats) {
+                    // lane m: this warp's 16-row block of matrix m -> the same place in the peer CTA
+                    const uint32_t blk = smem_u32(a0) + static_cast<uint32_t>(lane * amat) +
+                                         static_cast<uint32_t>((static_cast<int>(rank) * 64 + 16 * wq) / 8) * 256u;
+                    bulk_s2peer(mapa_peer(blk, peer), blk, 512u, mapa_peer(full_a(s), peer));
+                }
+                if (lane == 0) mbar_arrive(full_a(s));
+                // next stage of this parity
+                g += 2;
+                s += 2;
+                while (s >= NS) { s -= NS; ph ^= 1u; }
+                si += 2;
+                while (si >= kInSlots) { si -= kInSlots; phi ^= 1u; }
             }
-            tc_fence_before();
-            mbar_arrive(acc_empty);
+            if (!ok) break;
+            ok = epilogue_item(j);                 // this warp's share of item j's epilogue
         }
+    } else if (warp >= kEpiWarp0) {
+        // ---------------- epilogue warps ----------------
+        for (long long j = 0; j < my_items; ++j)
+            if (!epilogue_item(j)) break;
     }
 
     tc_fence_before();
