@@ -170,22 +170,35 @@ bool fused_encode_input_maps(const float* tau, int n_pwv, const float* cube, int
 }
 
 // ---- shared-memory plan -------------------------------------------------------
+// The spectrum rows (A: X_hi, X_lo, bf16(X^2)) and the filter operands (B: H_hi, H_lo, G, Q)
+// of a stage live in two rings of their own.  A slot is reused only after the rows have been
+// built again (and, for a shared tile, copied from the peer), a long round trip, so the A ring
+// is the deeper one; a B slot only waits for its copy from L2.
 struct SmemPlan {
-    int n_stages;
-    size_t a_bytes, b_bytes, stage_bytes, in_off, bar_off, total;
+    int nsa, nsb;                       // A-ring and B-ring depths (nsb <= nsa)
+    size_t a_bytes, b_bytes, b_off, in_off, bar_off, total;
 };
 
 __host__ __device__ inline SmemPlan smem_plan(int n_half) {
     SmemPlan p;
     p.a_bytes = static_cast<size_t>(kAMats) * kTileM * kKStage * 2;
     p.b_bytes = static_cast<size_t>(kBMats) * n_half * kKStage * 2;
-    p.stage_bytes = p.a_bytes + p.b_bytes;
     const size_t bar_reserve = 512;
     const size_t in_bytes = static_cast<size_t>(kInSlots) * kInSlotBytes;
-    int ns = static_cast<int>((kMaxSmem - 1024 - bar_reserve - in_bytes) / p.stage_bytes);
-    if (ns > 6) ns = 6;
-    p.n_stages = ns;
-    p.in_off = p.stage_bytes * ns;
+    const long long avail = static_cast<long long>(kMaxSmem) - 1024 - bar_reserve - in_bytes;
+    p.nsa = 0;
+    p.nsb = 0;
+    for (int nsb = 4; nsb >= 2; --nsb) {
+        long long nsa = (avail - static_cast<long long>(nsb) * p.b_bytes) / static_cast<long long>(p.a_bytes);
+        if (nsa > 8) nsa = 8;
+        if (nsa >= nsb) {
+            p.nsa = static_cast<int>(nsa);
+            p.nsb = nsb;
+            break;
+        }
+    }
+    p.b_off = p.a_bytes * p.nsa;
+    p.in_off = p.b_off + p.b_bytes * p.nsb;
     p.bar_off = p.in_off + in_bytes;
     p.total = p.bar_off + bar_reserve + 1024;   // + alignment slack
     return p;
@@ -427,17 +440,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int NH = F.n_half;
     const SmemPlan sp = smem_plan(NH);
-    const int NS = sp.n_stages;
+    const int NS = sp.nsa;                       // A-ring depth
+    const int NSB = sp.nsb;                      // B-ring depth
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + sp.bar_off);
     const uint32_t bar_base = smem_u32(bars);
     // One "stage full" barrier per ring slot: the operand copy's arrival (+ its bytes) and the
     // spectrum rows' arrival(s) (+ the peer's bytes for a shared tile), so the MMA issuer waits once.
-    auto full_a = [&](int s) { return bar_base + 8u * s; };
-    auto full_b = full_a;
-    auto empty_bar = [&](int s) { return bar_base + 8u * (2 * NS + s); };
-    auto full_in = [&](int s) { return bar_base + 8u * (3 * NS + s); };
-    auto empty_in = [&](int s) { return bar_base + 8u * (3 * NS + kInSlots + s); };
-    const int nb = 3 * NS + 2 * kInSlots;
+    auto full_a = [&](int s) { return bar_base + 8u * s; };                        // per A slot
+    auto empty_bar = [&](int s) { return bar_base + 8u * (NS + s); };              // per A slot
+    auto empty_b = [&](int s) { return bar_base + 8u * (2 * NS + s); };            // per B slot
+    auto full_in = [&](int s) { return bar_base + 8u * (2 * NS + NSB + s); };
+    auto empty_in = [&](int s) { return bar_base + 8u * (2 * NS + NSB + kInSlots + s); };
+    const int nb = 2 * NS + NSB + 2 * kInSlots;
     const uint32_t acc_full = bar_base + 8u * nb;
     const uint32_t acc_empty = bar_base + 8u * (nb + 1);
     const uint32_t drain_bar = bar_base + 8u * (nb + 2);
@@ -454,6 +468,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(full_a(s), kProdWarps / 2 + 1);   // one producer group builds a stage
             mbar_init(empty_bar(s), share ? 2 : 1);  // both CTAs' MMAs when the tile is shared
         }
+        for (int s = 0; s < NSB; ++s) mbar_init(empty_b(s), 1);
         for (int s = 0; s < kInSlots; ++s) {
             mbar_init(full_in(s), 1);
             mbar_init(empty_in(s), kProdWarps / 2);
@@ -545,10 +560,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- filter operands: one bulk copy per stage (A/B ring) ----------------
+            // ---------------- filter operands: one bulk copy per stage (B ring) ----------------
+            // Stage g's operands go to B slot g mod NSB and complete on the stage-full barrier of
+            // A slot g mod NS.  NSB <= NS: the copy for stage g starts after the MMAs of stage
+            // g - NSB, so that barrier is already in stage g's phase.
             long long g = 0;
-            int s = 0;
-            uint32_t ph = 0;           // parity of the current pass over the ring
+            int s = 0, sa = 0;
+            uint32_t ph = 0;           // parity of the current pass over the B ring
             const uint32_t bytes = static_cast<uint32_t>(sp.b_bytes);
             // a shared tile also receives the peer's half of the rows (3 matrices x 64 rows x 16 points)
             const uint32_t expect = bytes + (share ? static_cast<uint32_t>(kAMats * kTileM * kKStage) : 0u);
@@ -558,20 +576,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint16_t* src = F.B + static_cast<size_t>(grp) * n_ks * F.stage_elems;
                 bool ok = true;
                 for (int ks = 0; ks < n_ks; ++ks) {
-                    if (g >= NS && !mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, T.status)) {
+                    if (g >= NSB && !mbar_wait(empty_b(s), ph ^ 1u, abort_flag, T.status)) {
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(full_b(s), expect);
-                    bulk_g2s(smem_u32(smem + s * sp.stage_bytes + sp.a_bytes), src + ks * F.stage_elems, bytes,
-                             full_b(s));
+                    mbar_arrive_expect_tx(full_a(sa), expect);
+                    bulk_g2s(smem_u32(smem + sp.b_off + s * sp.b_bytes), src + ks * F.stage_elems, bytes,
+                             full_a(sa));
                     ++g;
-                    if (++s == NS) { s = 0; ph ^= 1u; }
+                    if (++s == NSB) { s = 0; ph ^= 1u; }
+                    if (++sa == NS) sa = 0;
                 }
                 if (!ok) break;
             }
-            for (long long q = (g > NS ? g - NS : 0); q < g; ++q)    // no copy in flight at exit
-                mbar_drain(full_b(static_cast<int>(q % NS)), static_cast<uint32_t>((q / NS) & 1));
+            for (long long q = (g > NSB ? g - NSB : 0); q < g; ++q)  // no copy in flight at exit
+                mbar_drain(full_a(static_cast<int>(q % NS)), static_cast<uint32_t>((q / NS) & 1));
         }
     } else if (warp == 2) {
         if (lane == 0) {
@@ -613,7 +632,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             const uint32_t idesc = make_idesc(NH);
-            int s = 0;
+            int s = 0, sb = 0;
             uint32_t par = 0;
             bool ok = true;
             for (long long j = 0; j < my_items && ok; ++j) {
@@ -628,8 +647,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(smem + s * sp.stage_bytes);
-                    const uint32_t b0 = a0 + static_cast<uint32_t>(sp.a_bytes);
+                    const uint32_t a0 = smem_u32(smem + s * sp.a_bytes);
+                    const uint32_t b0 = smem_u32(smem + sp.b_off + sb * sp.b_bytes);
                     const uint32_t a_mat = kTileM * kKStage * 2;            // bytes per A matrix
                     const uint32_t b_mat = static_cast<uint32_t>(NH) * kKStage * 2;
                     const uint64_t xhi = smem_desc(a0 + 0 * a_mat, 128, 256);
@@ -645,9 +664,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_mma(d_sig, xhi, hlo, idesc, 1u);
                     tc_mma(d_noi, xhi, gmat, idesc, acc);
                     tc_mma(d_noi, xsq, qmat, idesc, 1u);
-                    if (share) tc_commit_pair(empty_bar(s));   // slot s free in both CTAs
-                    else tc_commit(empty_bar(s));              // slot s free once these MMAs finish
+                    if (share) tc_commit_pair(empty_bar(s));   // A slot s free in both CTAs
+                    else tc_commit(empty_bar(s));              // A slot s free once these MMAs finish
+                    tc_commit(empty_b(sb));                    // B slot sb free (read by our MMAs only)
                     if (++s == NS) { s = 0; par ^= 1u; }
+                    if (++sb == NSB) sb = 0;
                 }
                 if (!ok) break;
                 tc_commit(acc_full);                  // accumulators of item j complete
@@ -734,7 +755,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ok = false;
                     break;
                 }
-                uint8_t* a0 = smem + s * sp.stage_bytes;
+                uint8_t* a0 = smem + s * sp.a_bytes;
                 {
                     const float* slot =
                         reinterpret_cast<const float*>(smem + sp.in_off + static_cast<size_t>(si) * kInSlotBytes);
@@ -850,7 +871,7 @@ cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, cons
                                 const TensorMapBytes& tm_cube, const RowParams* rows, const TileInfo* tiles,
                                 long long t0, long long nt, float* out, int n_sm, cudaStream_t stream) {
     const SmemPlan sp = smem_plan(F.n_half);
-    if (sp.n_stages < 2) return cudaErrorInvalidConfiguration;
+    if (sp.nsb < 2) return cudaErrorInvalidConfiguration;
     Work w;
     w.tiles_per_pix = (nt + kTileM - 1) / kTileM;
     w.n_items = w.tiles_per_pix * T.n_pix * F.n_groups;
