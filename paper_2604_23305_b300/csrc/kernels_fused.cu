@@ -448,10 +448,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     // spectrum rows' arrival(s) (+ the peer's bytes for a shared tile), so the MMA issuer waits once.
     auto full_a = [&](int s) { return bar_base + 8u * s; };                        // per A slot
     auto empty_bar = [&](int s) { return bar_base + 8u * (NS + s); };              // per A slot
-    auto empty_b = [&](int s) { return bar_base + 8u * (2 * NS + s); };            // per B slot
-    auto full_in = [&](int s) { return bar_base + 8u * (2 * NS + NSB + s); };
-    auto empty_in = [&](int s) { return bar_base + 8u * (2 * NS + NSB + kInSlots + s); };
-    const int nb = 2 * NS + NSB + 2 * kInSlots;
+    auto full_in = [&](int s) { return bar_base + 8u * (2 * NS + s); };
+    auto empty_in = [&](int s) { return bar_base + 8u * (2 * NS + kInSlots + s); };
+    const int nb = 2 * NS + 2 * kInSlots;
     const uint32_t acc_full = bar_base + 8u * nb;
     const uint32_t acc_empty = bar_base + 8u * (nb + 1);
     const uint32_t drain_bar = bar_base + 8u * (nb + 2);
@@ -468,7 +467,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(full_a(s), kProdWarps / 2 + 1);   // one producer group builds a stage
             mbar_init(empty_bar(s), share ? 2 : 1);  // both CTAs' MMAs when the tile is shared
         }
-        for (int s = 0; s < NSB; ++s) mbar_init(empty_b(s), 1);
         for (int s = 0; s < kInSlots; ++s) {
             mbar_init(full_in(s), 1);
             mbar_init(empty_in(s), kProdWarps / 2);
@@ -562,11 +560,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             // ---------------- filter operands: one bulk copy per stage (B ring) ----------------
             // Stage g's operands go to B slot g mod NSB and complete on the stage-full barrier of
-            // A slot g mod NS.  NSB <= NS: the copy for stage g starts after the MMAs of stage
-            // g - NSB, so that barrier is already in stage g's phase.
+            // A slot g mod NS.  B slot g mod NSB is free once the MMAs of stage g - NSB are done,
+            // which the commit to that stage's A-slot barrier reports (one commit per stage).
+            // NSB <= NS: the copy for stage g starts after the MMAs of stage g - NSB, so the
+            // stage-full barrier is already in stage g's phase.
             long long g = 0;
             int s = 0, sa = 0;
-            uint32_t ph = 0;           // parity of the current pass over the B ring
+            int sf = 0;                // A slot of stage g - NSB
+            uint32_t pf = 0;           // its pass parity over the A ring
             const uint32_t bytes = static_cast<uint32_t>(sp.b_bytes);
             // a shared tile also receives the peer's half of the rows (3 matrices x 64 rows x 16 points)
             const uint32_t expect = bytes + (share ? static_cast<uint32_t>(kAMats * kTileM * kKStage) : 0u);
@@ -576,15 +577,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint16_t* src = F.B + static_cast<size_t>(grp) * n_ks * F.stage_elems;
                 bool ok = true;
                 for (int ks = 0; ks < n_ks; ++ks) {
-                    if (g >= NSB && !mbar_wait(empty_b(s), ph ^ 1u, abort_flag, T.status)) {
-                        ok = false;
-                        break;
+                    if (g >= NSB) {
+                        if (!mbar_wait(empty_bar(sf), pf, abort_flag, T.status)) {
+                            ok = false;
+                            break;
+                        }
+                        if (++sf == NS) { sf = 0; pf ^= 1u; }
                     }
                     mbar_arrive_expect_tx(full_a(sa), expect);
                     bulk_g2s(smem_u32(smem + sp.b_off + s * sp.b_bytes), src + ks * F.stage_elems, bytes,
                              full_a(sa));
                     ++g;
-                    if (++s == NSB) { s = 0; ph ^= 1u; }
+                    if (++s == NSB) s = 0;
                     if (++sa == NS) sa = 0;
                 }
                 if (!ok) break;
@@ -666,7 +670,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_mma(d_noi, xsq, qmat, idesc, 1u);
                     if (share) tc_commit_pair(empty_bar(s));   // A slot s free in both CTAs
                     else tc_commit(empty_bar(s));              // A slot s free once these MMAs finish
-                    tc_commit(empty_b(sb));                    // B slot sb free (read by our MMAs only)
                     if (++s == NS) { s = 0; par ^= 1u; }
                     if (++sb == NSB) sb = 0;
                 }
