@@ -283,13 +283,105 @@ gateau_status gateau_plan_get_timing(gateau_plan* plan, double* ms, long long* r
  * too small; *n_out receives the spaxel count. */
 gateau_status gateau_hex_offsets(int R_hex, double spacing_rad, double* out, int count, int* n_out);
 
-/* Serving: simulate several plans' chunks on one stream.  plans[k] runs samples
- * t0s[k] .. t0s[k]+nts[k]-1 into outs[k] (device) exactly as gateau_run would,
- * with the same chunk-order rules and bit-identical results; the row-setup
- * kernels of all k are batched into one launch.  0 < n <= 256; the whole batch
- * is validated before anything is enqueued. */
+/* Several plans' chunks on one stream.  plans[k] runs samples t0s[k] ..
+ * t0s[k]+nts[k]-1 into outs[k] (device) exactly as gateau_run would, with the
+ * same chunk-order rules and bit-identical results, enqueued in k order.
+ * 0 < n <= 256; the whole batch is validated before anything is enqueued. */
 gateau_status gateau_run_batch(gateau_plan* const* plans, const long long* t0s, const long long* nts,
                                float* const* outs, int n, void* stream);
+
+/* Upper bound of the device memory a plan holds (bytes), from the shapes its
+ * setters will receive and the longest chunk it will run: desc as for
+ * gateau_plan_create, n_ch channels, an n_az x n_el source cube, an nx x ny
+ * screen, an n_pwv-row table, chunks of at most chunk_samples samples, and
+ * n_custom_pointing custom-scan samples (0 for built-in scans).  Used by
+ * servers to admit a request before its plan exists.  EINVAL on bad sizes. */
+gateau_status gateau_plan_estimate_bytes(const gateau_plan_desc* desc, int n_ch, int n_az, int n_el, int nx, int ny,
+                                         int n_pwv, long long chunk_samples, long long n_custom_pointing,
+                                         size_t* bytes);
+
+/* ---- Serving: many simulations sharing one GPU (continuous batching) -----
+ * The paper runs one simulation per call (Sect. 3).  A server runs a stream of
+ * them -- requests, each a whole simulation (a plan and a scan length) that
+ * arrives at some time -- the way a shared simulation service would: it admits
+ * a request as soon as one of its max_active slots and enough of its device
+ * memory budget are free (first come, first served), creates the request's
+ * plan at that moment through the caller's factory, runs the scan in chunks of
+ * time samples on one of its streams, copies every chunk's TOD to the host,
+ * and destroys the plan (release callback) when the last chunk has arrived,
+ * which frees the slot and the memory for the next arrivals.  Requests admitted
+ * while others run are on the GPU at the same time: each active request keeps
+ * two chunks in flight on its own stream, so their kernels and copies overlap.
+ * A request's TOD is bit-identical to gateau_run of the same plan over the
+ * same chunks, alone or in any mix. */
+typedef struct gateau_server gateau_server;
+
+typedef struct {
+    size_t budget_bytes;        /* device memory for admitted requests: their plans (as
+                                   requested) plus two chunk buffers each */
+    int max_active;             /* requests admitted at once (slots), 1..256 */
+    long long chunk_samples;    /* time samples per chunk, >= 1 ... */
+    size_t max_chunk_bytes;     /* ... reduced so that one chunk's TOD stays within this many
+                                   bytes (>= 4096; also sizes the pinned host staging) */
+    int n_streams;              /* CUDA streams, 1..256; admitted request k (in admission
+                                   order) runs on stream k mod n_streams */
+    int dry_run;                /* 1: scheduling only, no CUDA call and no plan use: a chunk of D
+                                   detector samples occupies its stream for
+                                   D * dry_seconds_per_sample on a virtual clock (host tests) */
+    double dry_seconds_per_sample;
+} gateau_server_desc;
+
+typedef struct {
+    double arrival_s;           /* seconds after gateau_server_run starts; non-decreasing */
+    long long nt;               /* scan length in samples, >= 1 */
+    int n_pix, n_ch;            /* TOD row shape: the plan's spaxels and channels */
+    size_t device_bytes;        /* the plan's device memory (gateau_plan_estimate_bytes) */
+    float* host_out;            /* NULL, or host [nt][n_pix][n_ch] that receives the TOD */
+} gateau_request;
+
+/* Factory: create the plan of request `request` (index into the array given to
+ * gateau_server_run), ready to run from t0 = 0; NULL marks the request failed.
+ * Release: the server is done with the plan (all chunks on the host); the
+ * caller destroys it.  Both are called on the thread running the server. */
+typedef gateau_plan* (*gateau_plan_factory)(void* user, int request);
+typedef void (*gateau_plan_release)(void* user, int request, gateau_plan* plan);
+
+typedef struct {
+    int n_requests, n_done, n_failed;
+    double p50_latency_s, p99_latency_s;   /* arrival -> last chunk on the host, over done requests
+                                              (linear interpolation between order statistics) */
+    double mean_latency_s, max_latency_s;
+    double makespan_s;                     /* run start -> last completion */
+    double detector_samples;               /* sum of nt * n_pix * n_ch over done requests */
+    double throughput;                     /* detector_samples / makespan_s */
+    size_t peak_bytes;                     /* most budget held at once */
+    int peak_active;                       /* most requests admitted at once */
+    double overlap;                        /* mean number of requests with chunks in flight,
+                                              sampled at every chunk launch */
+} gateau_server_stats;
+
+/* Create / destroy a server.  Create allocates the pinned host staging
+ * (2 x max_active x max_chunk_bytes) and the device chunk buffers lazily per
+ * admitted request.  EINVAL on out-of-range fields. */
+gateau_status gateau_server_create(const gateau_server_desc* desc, gateau_server** out);
+void gateau_server_destroy(gateau_server* server);
+
+/* Run requests[0..n-1] to completion in real time (dry_run: virtual time):
+ * requests become visible at their arrival_s.  A request whose device_bytes plus
+ * chunk buffers exceed the whole budget, or whose plan the factory cannot make,
+ * or whose run fails, is marked failed and the others go on.  Returns after the
+ * last request finished; stats may be NULL.  ECUDA aborts the run (every admitted
+ * plan is released first).  n <= 1000000. */
+gateau_status gateau_server_run(gateau_server* server, const gateau_request* requests, int n,
+                                gateau_plan_factory create, gateau_plan_release release, void* user,
+                                gateau_server_stats* stats);
+
+/* Outcome of request `request` of the last run: state (0 pending, 2 done,
+ * 3 failed), latency (arrival -> done, s), admission time (s after the start)
+ * and the TOD checksum {sum, sum of squares} (float64, accumulated on the GPU
+ * per chunk in a fixed order, so equal TODs give equal checksums). */
+gateau_status gateau_server_request_result(gateau_server* server, int request, int* state, double* latency_s,
+                                           double* admitted_s, double* checksum2);
 
 /* Allocation-free pink-noise scan.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory while they run

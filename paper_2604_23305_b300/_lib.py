@@ -49,7 +49,29 @@ class PlanInfo(C.Structure):
                 ("staged_inputs", C.c_int)]
 
 
+class ServerDesc(C.Structure):
+    _fields_ = [("budget_bytes", C.c_size_t), ("max_active", C.c_int), ("chunk_samples", C.c_longlong),
+                ("max_chunk_bytes", C.c_size_t), ("n_streams", C.c_int), ("dry_run", C.c_int),
+                ("dry_seconds_per_sample", C.c_double)]
+
+
+class Request(C.Structure):
+    _fields_ = [("arrival_s", C.c_double), ("nt", C.c_longlong), ("n_pix", C.c_int), ("n_ch", C.c_int),
+                ("device_bytes", C.c_size_t), ("host_out", C.c_void_p)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("n_requests", C.c_int), ("n_done", C.c_int), ("n_failed", C.c_int),
+                ("p50_latency_s", C.c_double), ("p99_latency_s", C.c_double), ("mean_latency_s", C.c_double),
+                ("max_latency_s", C.c_double), ("makespan_s", C.c_double), ("detector_samples", C.c_double),
+                ("throughput", C.c_double), ("peak_bytes", C.c_size_t), ("peak_active", C.c_int),
+                ("overlap", C.c_double)]
+
+
 PlanP = C.c_void_p
+ServerP = C.c_void_p
+PLAN_FACTORY = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_int)
+PLAN_RELEASE = C.CFUNCTYPE(None, C.c_void_p, C.c_int, C.c_void_p)
 
 # name -> (restype, argtypes); mirrors include/gateau.h one to one.
 SIGNATURES = {
@@ -81,6 +103,13 @@ SIGNATURES = {
     "gateau_hex_offsets": (C.c_int, [C.c_int, C.c_double, dp, C.c_int, C.POINTER(C.c_int)]),
     "gateau_plan_set_timing": (C.c_int, [PlanP, C.c_int]),
     "gateau_plan_get_timing": (C.c_int, [PlanP, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+    "gateau_plan_estimate_bytes": (C.c_int, [C.POINTER(PlanDesc), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                             C.c_int, C.c_longlong, C.c_longlong, C.POINTER(C.c_size_t)]),
+    "gateau_server_create": (C.c_int, [C.POINTER(ServerDesc), C.POINTER(ServerP)]),
+    "gateau_server_destroy": (None, [ServerP]),
+    "gateau_server_run": (C.c_int, [ServerP, C.POINTER(Request), C.c_int, PLAN_FACTORY, PLAN_RELEASE, C.c_void_p,
+                                    C.POINTER(ServerStats)]),
+    "gateau_server_request_result": (C.c_int, [ServerP, C.c_int, C.POINTER(C.c_int), dp, dp, dp]),
     "gateau_pink_noise_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                             C.c_ulonglong, C.c_longlong, C.c_longlong, C.c_void_p, C.c_void_p,
                                             C.c_void_p]),

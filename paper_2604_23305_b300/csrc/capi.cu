@@ -8,6 +8,7 @@
 #include <cmath>
 #include <memory>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "gateau_internal.h"
@@ -36,21 +37,64 @@ gateau_status fail(gateau_status st, const char* fmt, ...) {
                         #call, cudaGetErrorString(e_), __FILE__, __LINE__);                       \
     } while (0)
 
-// Grow-only device buffer.
+// Grow-only device buffer in the stream-ordered allocator.  Allocation and release run on the
+// owning plan's memory stream, which first waits for the work the plan enqueued, so freeing a
+// plan's memory never synchronises the device (a server destroys finished requests' plans while
+// others run).
+struct MemOrder {
+    cudaStream_t mem = nullptr;        // allocation / release stream (non-blocking)
+    cudaStream_t after[2] = {nullptr, nullptr};   // streams whose enqueued work must finish first
+    bool after_used[2] = {false, false};
+    cudaError_t ready() {
+        if (mem) return cudaSuccess;
+        static std::once_flag pool_once;
+        std::call_once(pool_once, [] {
+            // Keep freed blocks in this process's default pool instead of returning them to the
+            // driver at every synchronisation (a process-local setting of the pool).
+            int dev = 0;
+            cudaMemPool_t pool;
+            if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+                unsigned long long keep = ~0ull;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            }
+        });
+        return cudaStreamCreateWithFlags(&mem, cudaStreamNonBlocking);
+    }
+    // Order the memory stream after everything enqueued so far on the plan's run streams.
+    cudaError_t fence() {
+        for (int i = 0; i < 2; ++i) {
+            if (!after_used[i]) continue;
+            cudaEvent_t e = nullptr;
+            cudaError_t err = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+            if (err != cudaSuccess) return err;
+            err = cudaEventRecord(e, after[i]);
+            if (err == cudaSuccess) err = cudaStreamWaitEvent(mem, e, 0);
+            cudaEventDestroy(e);                      // released once the wait is resolved
+            if (err != cudaSuccess) return err;
+        }
+        return cudaSuccess;
+    }
+};
+
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
-    cudaError_t ensure(size_t n) {
+    cudaError_t ensure(size_t n, MemOrder& mo) {
         if (n <= bytes) return cudaSuccess;
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-        cudaError_t e = cudaMalloc(&p, n);
-        if (e == cudaSuccess) bytes = n;
+        cudaError_t e = mo.ready();
+        if (e != cudaSuccess) return e;
+        release(mo);
+        e = cudaMallocAsync(&p, n, mo.mem);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(mo.mem);   // usable on any stream from here
+        if (e == cudaSuccess) {
+            bytes = n;
+        } else {
+            p = nullptr;
+        }
         return e;
     }
-    void release() {
-        if (p) cudaFree(p);
+    void release(MemOrder& mo) {
+        if (p && mo.ready() == cudaSuccess && mo.fence() == cudaSuccess) cudaFreeAsync(p, mo.mem);
         p = nullptr;
         bytes = 0;
     }
@@ -117,10 +161,23 @@ struct gateau_plan {
     std::vector<cudaEvent_t> ev_pool;
     long long runs = 0, launches = 0;
 
+    MemOrder mo;                     // stream order of this plan's device allocations
+    bool ran = false;                // a run was enqueued (on last_stream)
+
+    // Point the memory order at the streams this plan enqueued work on.
+    void track_streams() {
+        mo.after[0] = last_stream;
+        mo.after_used[0] = ran;
+        mo.after[1] = copy_stream;
+        mo.after_used[1] = copy_stream != nullptr;
+    }
+
     ~gateau_plan() {
+        track_streams();
         DevBuf* bufs[] = {&d_pix, &d_cube, &d_cube_raw, &d_screen, &d_tau, &d_custom, &d_c, &d_HGQ, &d_fusedB, &d_pink,
                           &d_state, &d_status, &d_rows, &d_tiles, &d_X, &d_agg, &d_stage[0], &d_stage[1]};
-        for (DevBuf* b : bufs) b->release();
+        for (DevBuf* b : bufs) b->release(mo);
+        if (mo.mem) cudaStreamDestroy(mo.mem);       // its pending frees still complete
         for (int i = 0; i < 2; ++i) {
             if (ev_done[i]) cudaEventDestroy(ev_done[i]);
             if (ev_copied[i]) cudaEventDestroy(ev_copied[i]);
@@ -137,6 +194,12 @@ struct gateau_plan {
 };
 
 namespace {
+
+// Grow a plan buffer; the old contents are released after the plan's enqueued work.
+cudaError_t grow(gateau_plan* p, DevBuf& b, size_t n) {
+    p->track_streams();
+    return b.ensure(n, p->mo);
+}
 
 size_t device_bytes(const gateau_plan* p) {
     const DevBuf* bufs[] = {&p->d_pix, &p->d_cube, &p->d_cube_raw, &p->d_screen, &p->d_tau, &p->d_custom, &p->d_c,
@@ -191,7 +254,7 @@ gateau_status finalize(gateau_plan* p) {
         }
         for (int k = 0; k < ks; ++k) cv.push_back(cv[static_cast<size_t>(Kp) + b * ks + k]);
     }
-    GATEAU_CUDA(p->d_c.ensure(cv.size() * sizeof(float)));
+    GATEAU_CUDA(grow(p, p->d_c, cv.size() * sizeof(float)));
     GATEAU_CUDA(cudaMemcpy(p->d_c.p, cv.data(), cv.size() * sizeof(float), cudaMemcpyHostToDevice));
     p->fused.c_tiled = p->d_c.as<float>() + 3 * static_cast<size_t>(Kp);
     p->cube_scale_dirty = true;
@@ -221,7 +284,7 @@ gateau_status finalize(gateau_plan* p) {
             hgq[mat + i] = static_cast<float>(G[i]);
             hgq[2 * mat + i] = static_cast<float>(Q[i]);
         }
-        GATEAU_CUDA(p->d_HGQ.ensure(hgq.size() * sizeof(float)));
+        GATEAU_CUDA(grow(p, p->d_HGQ, hgq.size() * sizeof(float)));
         GATEAU_CUDA(cudaMemcpy(p->d_HGQ.p, hgq.data(), hgq.size() * sizeof(float), cudaMemcpyHostToDevice));
     } else {
         const int n_groups = (n_ch + 255) / 256;
@@ -229,7 +292,7 @@ gateau_status finalize(gateau_plan* p) {
         std::vector<uint16_t> tiled;
         size_t stage_elems = 0;
         fused_tile_operands(H.data(), G.data(), Q.data(), n_ch, Kp, n_half, n_groups, tiled, stage_elems);
-        GATEAU_CUDA(p->d_fusedB.ensure(tiled.size() * sizeof(uint16_t)));
+        GATEAU_CUDA(grow(p, p->d_fusedB, tiled.size() * sizeof(uint16_t)));
         GATEAU_CUDA(cudaMemcpy(p->d_fusedB.p, tiled.data(), tiled.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
         p->fused.B = p->d_fusedB.as<uint16_t>();
         p->fused.n_half = n_half;
@@ -256,11 +319,11 @@ gateau_status finalize(gateau_plan* p) {
         pk[p->pink_a.size() + i] = static_cast<float>(p->pink_r[i]);
     }
     for (int c = 0; c < n_ch; ++c) pk[2 * p->pink_a.size() + c] = static_cast<float>(p->pink_d[c]);
-    GATEAU_CUDA(p->d_pink.ensure(pk.size() * sizeof(float)));
+    GATEAU_CUDA(grow(p, p->d_pink, pk.size() * sizeof(float)));
     GATEAU_CUDA(cudaMemcpy(p->d_pink.p, pk.data(), pk.size() * sizeof(float), cudaMemcpyHostToDevice));
     const size_t state_bytes = static_cast<size_t>(d.n_pix) * n_ch * np * sizeof(float);
     if (p->d_state.bytes < state_bytes) {
-        GATEAU_CUDA(p->d_state.ensure(state_bytes));
+        GATEAU_CUDA(grow(p, p->d_state, state_bytes));
         GATEAU_CUDA(cudaMemset(p->d_state.p, 0, state_bytes));
     }
     p->dirty = false;
@@ -381,7 +444,7 @@ gateau_status enqueue_run(gateau_plan* p, long long t0, long long nt, float* out
     if (st != GATEAU_OK) return st;
     const gateau_plan_desc& d = p->desc;
     const long long rows = nt * d.n_pix;
-    GATEAU_CUDA(p->d_rows.ensure(static_cast<size_t>(rows) * sizeof(RowParams)));
+    GATEAU_CUDA(grow(p, p->d_rows, static_cast<size_t>(rows) * sizeof(RowParams)));
     const DevTables T = make_tables(p);
     RowParams* R = p->d_rows.as<RowParams>();
     if (p->timing) {
@@ -402,7 +465,7 @@ gateau_status enqueue_run(gateau_plan* p, long long t0, long long nt, float* out
     TileInfo* tiles = nullptr;
     if (d.precision == GATEAU_PREC_BF16X3) {
         const long long n_tiles = (nt + kTileRows - 1) / kTileRows * d.n_pix;
-        GATEAU_CUDA(p->d_tiles.ensure(static_cast<size_t>(n_tiles) * sizeof(TileInfo)));
+        GATEAU_CUDA(grow(p, p->d_tiles, static_cast<size_t>(n_tiles) * sizeof(TileInfo)));
         tiles = p->d_tiles.as<TileInfo>();
         if (p->maps_dirty) {
             std::string err;
@@ -420,7 +483,7 @@ gateau_status enqueue_run(gateau_plan* p, long long t0, long long nt, float* out
     if (d.precision == GATEAU_PREC_FP32) {
         // Unfused baseline: spectra in HBM chunk by chunk, then the SIMT contraction.
         const long long chunk = std::min<long long>(rows, 131072);
-        GATEAU_CUDA(p->d_X.ensure(static_cast<size_t>(chunk) * p->Kp * sizeof(float)));
+        GATEAU_CUDA(grow(p, p->d_X, static_cast<size_t>(chunk) * p->Kp * sizeof(float)));
         // Timing covers the whole chunk loop: SPECTRUM and CONTRACT alternate, so the
         // loop is reported under CONTRACT and SPECTRUM stays zero for this path.
         GATEAU_CUDA(tm.begin(GATEAU_PHASE_CONTRACT));
@@ -440,7 +503,7 @@ gateau_status enqueue_run(gateau_plan* p, long long t0, long long nt, float* out
     if (d.noise_flags & GATEAU_NOISE_PINK) {
         PinkWork W;
         pink_choose_chunks(nt, static_cast<long long>(d.n_pix) * p->n_ch, W.C, W.L);
-        GATEAU_CUDA(p->d_agg.ensure(static_cast<size_t>(W.C) * d.n_pix * p->n_ch * p->n_pole * sizeof(float)));
+        GATEAU_CUDA(grow(p, p->d_agg, static_cast<size_t>(W.C) * d.n_pix * p->n_ch * p->n_pole * sizeof(float)));
         W.agg = p->d_agg.as<float>();
         GATEAU_CUDA(tm.begin(GATEAU_PHASE_PINK));
         GATEAU_CUDA(launch_pink(T, p->d_state.as<float>(), W, t0, nt, out, stream));
@@ -450,6 +513,7 @@ gateau_status enqueue_run(gateau_plan* p, long long t0, long long nt, float* out
     p->runs += 1;
     p->next_t0 = t0 + nt;
     p->last_stream = stream;
+    p->ran = true;
     return GATEAU_OK;
 }
 
@@ -504,9 +568,9 @@ void gateau_plan_destroy(gateau_plan* plan) { delete plan; }
 // Device-side plan buffers that every run needs (pixel offsets, status word).
 static gateau_status ensure_base(gateau_plan* p) {
     if (!p->d_pix.p) {
-        GATEAU_CUDA(p->d_pix.ensure(p->pix_off.size() * sizeof(double)));
+        GATEAU_CUDA(grow(p, p->d_pix, p->pix_off.size() * sizeof(double)));
         GATEAU_CUDA(cudaMemcpy(p->d_pix.p, p->pix_off.data(), p->pix_off.size() * sizeof(double), cudaMemcpyHostToDevice));
-        GATEAU_CUDA(p->d_status.ensure(sizeof(unsigned int)));
+        GATEAU_CUDA(grow(p, p->d_status, sizeof(unsigned int)));
         GATEAU_CUDA(cudaMemset(p->d_status.p, 0, sizeof(unsigned int)));
         int dev = 0;
         GATEAU_CUDA(cudaGetDevice(&dev));
@@ -527,8 +591,8 @@ gateau_status gateau_set_source_cube(gateau_plan* p, const float* cube, int n_az
     const size_t nf = p->desc.n_freq, Kp = p->Kp;
     const size_t cube_bytes = static_cast<size_t>(n_az) * n_el * Kp * sizeof(float);
     if (p->d_cube.bytes < cube_bytes || p->n_az != n_az || p->n_el != n_el) p->maps_dirty = true;
-    GATEAU_CUDA(p->d_cube.ensure(cube_bytes));
-    GATEAU_CUDA(p->d_cube_raw.ensure(cube_bytes));
+    GATEAU_CUDA(grow(p, p->d_cube, cube_bytes));
+    GATEAU_CUDA(grow(p, p->d_cube_raw, cube_bytes));
     if (Kp != nf) GATEAU_CUDA(cudaMemset(p->d_cube_raw.p, 0, cube_bytes));
     GATEAU_CUDA(cudaMemcpy2D(p->d_cube_raw.p, Kp * sizeof(float), cube, nf * sizeof(float), nf * sizeof(float),
                              static_cast<size_t>(n_az) * n_el, kind_of(mem)));
@@ -551,7 +615,7 @@ gateau_status gateau_set_atmosphere_screen(gateau_plan* p, const float* screen, 
     gateau_status st = ensure_base(p);
     if (st != GATEAU_OK) return st;
     const size_t n = static_cast<size_t>(nx) * ny;
-    GATEAU_CUDA(p->d_screen.ensure(n * sizeof(float)));
+    GATEAU_CUDA(grow(p, p->d_screen, n * sizeof(float)));
     if (is_epl) {
         std::vector<float> h;
         st = fetch_floats(screen, n, mem, h);
@@ -595,7 +659,7 @@ gateau_status gateau_set_atmosphere_table(gateau_plan* p, const float* table, in
             padded[(2 * j) * Kp + k] = t0f;
             if (j + 1 < n_pwv) padded[(2 * j + 1) * Kp + k] = static_cast<float>(tau[(j + 1) * nf + k]) - t0f;
         }
-    GATEAU_CUDA(p->d_tau.ensure(padded.size() * sizeof(float)));
+    GATEAU_CUDA(grow(p, p->d_tau, padded.size() * sizeof(float)));
     GATEAU_CUDA(cudaMemcpy(p->d_tau.p, padded.data(), padded.size() * sizeof(float), cudaMemcpyHostToDevice));
     p->n_pwv = n_pwv;
     p->pwv_min = pwv_min_mm;
@@ -644,7 +708,8 @@ gateau_status gateau_set_dispersive_element(gateau_plan* p, int kind, int n_ch, 
         return fail(GATEAU_EINVAL, "%s", err.c_str());
     if (p->has_disp && n_ch != p->n_ch) {
         p->has_pink = false;
-        p->d_state.release();
+        p->track_streams();
+        p->d_state.release(p->mo);
     }
     p->eta_filt = std::move(eta);
     p->disp_kind = kind;
@@ -681,7 +746,7 @@ gateau_status gateau_set_scan(gateau_plan* p, int kind, const double* params, in
         if (check_mem(mem) != GATEAU_OK) return GATEAU_EINVAL;
         gateau_status st = ensure_base(p);
         if (st != GATEAU_OK) return st;
-        GATEAU_CUDA(p->d_custom.ensure(static_cast<size_t>(n_custom) * 2 * sizeof(double)));
+        GATEAU_CUDA(grow(p, p->d_custom, static_cast<size_t>(n_custom) * 2 * sizeof(double)));
         GATEAU_CUDA(cudaMemcpy(p->d_custom.p, custom, static_cast<size_t>(n_custom) * 2 * sizeof(double), kind_of(mem)));
     }
     p->scan_kind = kind;
@@ -721,7 +786,7 @@ gateau_status gateau_run_host(gateau_plan* p, long long t0, long long nt, float*
     const long long per_sample = static_cast<long long>(p->desc.n_pix) * std::max(p->n_ch, 1);
     const long long chunk = std::max<long long>(128, std::min<long long>(nt, (256LL << 20) / (4 * per_sample)) / 128 * 128);
     const size_t chunk_bytes = static_cast<size_t>(std::min(chunk, nt)) * per_sample * sizeof(float);
-    for (int i = 0; i < 2; ++i) GATEAU_CUDA(p->d_stage[i].ensure(chunk_bytes));
+    for (int i = 0; i < 2; ++i) GATEAU_CUDA(grow(p, p->d_stage[i], chunk_bytes));
     int c = 0;
     for (long long a = 0; a < nt; a += chunk, ++c) {
         const int b = c & 1;
@@ -757,6 +822,44 @@ gateau_status gateau_run_batch(gateau_plan* const* plans, const long long* t0s, 
         gateau_status st = enqueue_run(plans[k], t0s[k], nts[k], outs[k], static_cast<cudaStream_t>(stream));
         if (st != GATEAU_OK) return st;
     }
+    return GATEAU_OK;
+}
+
+gateau_status gateau_plan_estimate_bytes(const gateau_plan_desc* d, int n_ch, int n_az, int n_el, int nx, int ny,
+                                         int n_pwv, long long chunk, long long n_custom, size_t* bytes) {
+    if (!d || !bytes) return fail(GATEAU_EINVAL, "desc and bytes must be non-NULL");
+    *bytes = 0;
+    if (d->n_freq < 2 || d->n_pix < 1 || n_ch < 1 || n_az < 2 || n_el < 2 || nx < 1 || ny < 1 || n_pwv < 2 ||
+        chunk < 1 || n_custom < 0)
+        return fail(GATEAU_EINVAL, "need n_freq >= 2, n_pix, n_ch, nx, ny, chunk >= 1, cube and table >= 2");
+    if (!(d->pink_f_min_hz > 0.0) || !(d->f_sample_hz > 2.0 * d->pink_f_min_hz))
+        return fail(GATEAU_EINVAL, "need 0 < pink_f_min < f_sample/2");
+    const double Kp = static_cast<double>((d->n_freq + 31) / 32 * 32);
+    const int np = pink_pole_count(d->pink_f_min_hz, d->f_sample_hz);
+    const double n_pix = d->n_pix, nc = n_ch;
+    double b = n_pix * 2 * 8 + 64;                                   // spaxel offsets, status word
+    b += 2.0 * n_az * n_el * Kp * 4;                                 // source cube as set + scaled copy
+    b += static_cast<double>(nx) * ny * 4;                           // screen
+    b += 2.0 * n_pwv * Kp * 4;                                       // interleaved opacity table
+    b += 5.0 * Kp * 4;                                               // c0, c1, c2 + per-stage tiling
+    if (d->precision == GATEAU_PREC_FP32) {
+        b += 3.0 * ((n_ch + 63) / 64 * 64) * Kp * 4;                 // FP32 H, G, Q
+        b += std::min(static_cast<double>(chunk) * n_pix, 131072.0) * Kp * 4;   // spectrum chunk
+    } else {
+        const int n_groups = (n_ch + 255) / 256;
+        const int n_half = ((n_ch + n_groups - 1) / n_groups + 15) / 16 * 16;
+        b += static_cast<double>(n_groups) * n_half * 4 * Kp * 2;    // BF16 operands
+        b += std::ceil(static_cast<double>(chunk) / kTileRows) * n_pix * sizeof(TileInfo);
+    }
+    b += nc * (2 * np + 1) * 4 + n_pix * nc * np * 4;                // pink tables + state
+    b += static_cast<double>(chunk) * n_pix * sizeof(RowParams);     // row parameters
+    int C = 1;
+    long long L = chunk;
+    pink_choose_chunks(chunk, static_cast<long long>(d->n_pix) * n_ch, C, L);
+    b += static_cast<double>(C) * n_pix * nc * np * 4;               // pink chunk states
+    b += static_cast<double>(n_custom) * 2 * 8;                      // custom pointing
+    b += 24 * 4096;                                                  // allocation granularity
+    *bytes = static_cast<size_t>(b);
     return GATEAU_OK;
 }
 

@@ -58,6 +58,44 @@ def _stage_structs(stages, n_freq):
     return arr, keep
 
 
+def _plan_desc(sc: dict, pix: np.ndarray, precision: str, white: bool, pink: bool) -> L.PlanDesc:
+    """gateau_plan_desc of a scenario (pix must stay alive while the struct is used)."""
+    noise = sc.get("noise", {})
+    d = L.PlanDesc()
+    d.n_freq = int(sc["n_freq"])
+    d.f_lo_hz, d.f_hi_hz, d.f_sample_hz = sc["f_lo"], sc["f_hi"], sc["f_sample"]
+    d.n_pix = pix.shape[0]
+    d.pix_offsets_rad = _dptr(pix)
+    atm = sc["atmosphere"]
+    d.T_atm_K, d.T_cmb_K = atm["T_atm"], sc["T_cmb"]
+    d.h_column_m, d.wind_mps = atm["h_column"], atm["wind"]
+    d.eta_taper, d.rho_surf_m, d.eta_pol = sc["eta_taper"], sc["rho_surf"], sc["eta_pol"]
+    d.delta_al_J, d.eta_pb = sc["delta_al"], sc["eta_pb"]
+    d.seed = int(noise.get("seed", 0))
+    d.precision = _PREC[precision]
+    d.noise_flags = (L.NOISE_WHITE if white else 0) | (L.NOISE_PINK if pink else 0)
+    d.pink_f_min_hz = float(noise.get("pink_f_min", 1e-3))
+    return d
+
+
+def estimate_bytes(sc: dict, chunk_samples: int, precision: str = "bf16x3", white: bool = True,
+                   pink: bool = True) -> int:
+    """gateau_plan_estimate_bytes for a scenario: device memory its plan holds, upper bound."""
+    pix = _f64(sc["pix_offsets"]).reshape(-1, 2)
+    d = _plan_desc(sc, pix, precision, white, pink)
+    atm, src = sc["atmosphere"], sc["source"]
+    cube = np.asarray(src["cube"])
+    scr = np.asarray(atm["screen"])
+    custom = sc["scan"].get("custom")
+    out = C.c_size_t(0)
+    L.check(L.lib().gateau_plan_estimate_bytes(C.byref(d), int(np.asarray(sc["dispersive"]["f_c"]).size),
+                                               cube.shape[0], cube.shape[1], scr.shape[1], scr.shape[0],
+                                               np.asarray(atm["table"]).shape[0], int(chunk_samples),
+                                               0 if custom is None else int(np.asarray(custom).shape[0]),
+                                               C.byref(out)))
+    return int(out.value)
+
+
 class Plan:
     """A configured simulation (one instrument, one sky, one scan)."""
 
@@ -69,20 +107,8 @@ class Plan:
         self.pix = _f64(sc["pix_offsets"]).reshape(-1, 2)
         self.n_pix = self.pix.shape[0]
         noise = sc.get("noise", {})
-        d = L.PlanDesc()
-        d.n_freq = self.n_freq
-        d.f_lo_hz, d.f_hi_hz, d.f_sample_hz = sc["f_lo"], sc["f_hi"], sc["f_sample"]
-        d.n_pix = self.n_pix
-        d.pix_offsets_rad = _dptr(self.pix)
         atm = sc["atmosphere"]
-        d.T_atm_K, d.T_cmb_K = atm["T_atm"], sc["T_cmb"]
-        d.h_column_m, d.wind_mps = atm["h_column"], atm["wind"]
-        d.eta_taper, d.rho_surf_m, d.eta_pol = sc["eta_taper"], sc["rho_surf"], sc["eta_pol"]
-        d.delta_al_J, d.eta_pb = sc["delta_al"], sc["eta_pb"]
-        d.seed = int(noise.get("seed", 0))
-        d.precision = _PREC[precision]
-        d.noise_flags = (L.NOISE_WHITE if white else 0) | (L.NOISE_PINK if pink else 0)
-        d.pink_f_min_hz = float(noise.get("pink_f_min", 1e-3))
+        d = _plan_desc(sc, self.pix, precision, white, pink)
         self.precision = precision
         self._h = L.PlanP()
         L.check(self._lib.gateau_plan_create(C.byref(d), C.byref(self._h)))
