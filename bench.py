@@ -292,7 +292,7 @@ def main():
     contract_ms = phase_ms[2] / max(runs, 1)
     alg_flops = 6.0 * n_freq * per_step                      # 3 contractions x 2 N_f per detector sample
     info = plan.info()
-    n_groups = (n_ch + 255) // 256
+    n_groups = (n_ch + 175) // 176
     n_half = ((n_ch + n_groups - 1) // n_groups + 15) // 16 * 16
     tiles = math.ceil(nt / 128) * plan.n_pix
     exec_flops = 5 * 2.0 * 128 * n_half * n_groups * info.n_freq_padded * tiles

@@ -287,7 +287,7 @@ gateau_status finalize(gateau_plan* p) {
         GATEAU_CUDA(grow(p, p->d_HGQ, hgq.size() * sizeof(float)));
         GATEAU_CUDA(cudaMemcpy(p->d_HGQ.p, hgq.data(), hgq.size() * sizeof(float), cudaMemcpyHostToDevice));
     } else {
-        const int n_groups = (n_ch + 255) / 256;
+        const int n_groups = (n_ch + 175) / 176;   // groups of <= 176 channels: B stages fit the rings
         const int n_half = ((n_ch + n_groups - 1) / n_groups + 15) / 16 * 16;
         std::vector<uint16_t> tiled;
         size_t stage_elems = 0;
@@ -846,7 +846,7 @@ gateau_status gateau_plan_estimate_bytes(const gateau_plan_desc* d, int n_ch, in
         b += 3.0 * ((n_ch + 63) / 64 * 64) * Kp * 4;                 // FP32 H, G, Q
         b += std::min(static_cast<double>(chunk) * n_pix, 131072.0) * Kp * 4;   // spectrum chunk
     } else {
-        const int n_groups = (n_ch + 255) / 256;
+        const int n_groups = (n_ch + 175) / 176;   // groups of <= 176 channels: B stages fit the rings
         const int n_half = ((n_ch + n_groups - 1) / n_groups + 15) / 16 * 16;
         b += static_cast<double>(n_groups) * n_half * 4 * Kp * 2;    // BF16 operands
         b += std::ceil(static_cast<double>(chunk) / kTileRows) * n_pix * sizeof(TileInfo);

@@ -33,7 +33,7 @@ struct __align__(16) RowParams {
 // that both can be staged in shared memory by tensor copies.
 constexpr int kTileRows = 128;
 constexpr int kTauBoxRows = 8;                // opacity rows per staged box
-constexpr int kCubeBoxAz = 16, kCubeBoxEl = 8; // cube texels per staged box
+constexpr int kCubeBoxAz = 12, kCubeBoxEl = 4; // cube texels per staged box (a 128-sample tile of a 30"/s raster spans ~8 x 2 cells)
 enum { TILE_TAU_FITS = 1, TILE_CUBE_FITS = 2, TILE_HAS_SOURCE = 4 };
 struct __align__(16) TileInfo {
     int j0;           // lowest opacity row of the tile

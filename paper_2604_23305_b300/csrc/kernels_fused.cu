@@ -49,14 +49,14 @@ constexpr int kProdThreads = kProdWarps * 32;
 constexpr int kProdWarp0 = 4;               // warps 0..3: operand TMA, MMA, input TMA, idle
 constexpr int kEpiWarp0 = kProdWarp0 + kProdWarps;
 constexpr int kThreads = (kEpiWarp0 + 4) * 32;
-constexpr int kMaxSmem = 227 * 1024;
-constexpr int kInSlots = 5;          // input-ring depth (stages of staged gathers)
+constexpr int kMaxSmem = 218 * 1024;   // a 2-CTA cluster launch with 223 KB per CTA was refused; stay below
+constexpr int kInSlots = 6;          // input-ring depth (stages of staged gathers)
 // Staged rows are 20 points wide (80 B): the 16 points of the stage plus 4 that
 // are never read.  With a 20-word row stride, successive texels start on
 // different shared-memory banks, so lanes reading different texels at the same
 // point do not conflict.
 constexpr int kBoxW = 20;
-constexpr int kCubeBoxBytes = kCubeBoxAz * kCubeBoxEl * kBoxW * 4;    // 10240
+constexpr int kCubeBoxBytes = kCubeBoxAz * kCubeBoxEl * kBoxW * 4;    // 3840
 constexpr int kTauBoxBytes = 2 * kTauBoxRows * kBoxW * 4;             // (tau_j, dtau_j) rows: 1280
 constexpr int kConstBytes = 2 * kKStage * 4;                          // c0 + c1 and c1 of the stage
 constexpr int kTauOff = kCubeBoxBytes;
