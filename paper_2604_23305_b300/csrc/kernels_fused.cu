@@ -21,10 +21,10 @@
 //                   box (input ring); each spinning role has a warp of its own
 //   warp 3        : idle
 //   warps 4..11   : spectrum producers; each warp signals its own rows (no CTA-wide barrier).
-//                   With 347 channels the two channel groups of a tile run on the two CTAs of
-//                   a cluster: each CTA builds half of the tile's rows, one 8-row core-matrix
-//                   group per warp, and each warp bulk-copies its finished 256-byte blocks
-//                   straight into the peer's shared memory (one build per row, no relay)
+//                   With 177-352 channels the two channel groups of a tile run on the two CTAs
+//                   of a cluster: each CTA builds half of the tile's rows, 16 rows per warp,
+//                   and each warp bulk-copies its finished 512-byte blocks straight into the
+//                   peer's shared memory (one build per row, no relay)
 //   warps 12..15  : epilogue, one thread per TMEM lane (= tile row)
 // The input ring runs ahead of the producers, the A/B ring behind them, so the
 // producers read their gathers from shared memory.  Tiles whose opacity rows or
@@ -45,7 +45,6 @@ constexpr int kKStage = 16;          // spectral points per pipeline stage (one 
 constexpr int kAMats = 3;            // X_hi, X_lo, bf16(X^2)
 constexpr int kBMats = 4;            // H_hi, H_lo, G, Q
 constexpr int kProdWarps = 8;
-constexpr int kProdThreads = kProdWarps * 32;
 constexpr int kProdWarp0 = 4;               // warps 0..3: operand TMA, MMA, input TMA, idle
 constexpr int kEpiWarp0 = kProdWarp0 + kProdWarps;
 constexpr int kThreads = (kEpiWarp0 + 4) * 32;
@@ -462,14 +461,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t rank = share ? cluster_rank() : 0u;
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
-            // one arrival per warp of the producer group that builds the stage + the operand copy's
-            // (its bytes and, for a shared tile, the peer's rows)
-            mbar_init(full_a(s), kProdWarps / 2 + 1);   // one producer group builds a stage
+            // one arrival per producer warp that builds the stage (a group of four for a shared
+            // tile, all eight otherwise) + the operand copy's (its bytes and, for a shared tile,
+            // the peer's rows)
+            mbar_init(full_a(s), (share ? kProdWarps / 2 : kProdWarps) + 1);
             mbar_init(empty_bar(s), share ? 2 : 1);  // both CTAs' MMAs when the tile is shared
         }
         for (int s = 0; s < kInSlots; ++s) {
             mbar_init(full_in(s), 1);
-            mbar_init(empty_in(s), kProdWarps / 2);
+            mbar_init(empty_in(s), share ? kProdWarps / 2 : kProdWarps);
         }
         mbar_init(acc_full, 1);
         mbar_init(acc_empty, 4 + kProdWarps);   // the epilogue warps and the producer warps
@@ -681,76 +681,86 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp >= kProdWarp0 && warp < kEpiWarp0) {
         // ---------------- spectrum producers ----------------
-        // Two groups of four warps build alternate stages (global stage g = item * n_ks + ks,
-        // group = g mod 2), so each warp has two stage periods for one stage's rows.
-        // Independent CTA: warp = 32 rows, thread = (row, 16 points).
-        // Shared tile: this CTA builds rows [64 rank, 64 rank + 64); warp = 16 rows (two 8-row
-        // core-matrix groups), thread = (row, 8 points), so the warp's rows of each matrix form
-        // one contiguous 512-byte block, copied to the peer as it is.
-        // Each thread stores 8 consecutive points (16 bytes) per matrix: a warp's store covers
-        // whole 128-byte core-matrix rows, without bank conflicts.
+        // Warp = 16 rows x the 16 points of a stage; thread = two rows (r, r + 8: the same place
+        // in the warp's two 8-row core-matrix groups) x one quad of 4 points.  Lanes 8q..8q+7 are
+        // the 8 rows of quad q, so a quarter-warp phase of a 16-byte shared load reads one quad of
+        // (mostly) one table row or texel and broadcasts it.  When the two rows of a thread use the
+        // same table row and cube cell (the usual case: samples 50 ms apart) the gathers are read
+        // once for both.  A warp's 8-byte stores of one (row, matrix) cover whole core-matrix rows
+        // (two wavefronts per 256 bytes).
+        // Shared tile: this CTA builds rows [64 rank, 64 rank + 64); two groups of four warps take
+        // alternate stages (global stage g = item * n_ks + ks, group = g mod 2), so a warp has two
+        // stage periods for one stage; each warp bulk-copies its finished 512-byte row blocks into
+        // the peer.  Independent CTA: all eight warps build every stage, 16 rows each.
         const int pw = warp - kProdWarp0;
-        const int pgrp = pw >> 2;                    // stage parity built by this warp
-        const int wq = pw & 3;                       // warp within its group
-        const int r = share ? static_cast<int>(rank) * 64 + 16 * wq + (lane >> 1) : 32 * wq + lane;
-        const int kh = share ? 8 * (lane & 1) : 0;   // first point of this thread in the stage
-        constexpr int nq = share ? 2 : 4;            // float4 quads per thread
+        const int pgrp = share ? pw >> 2 : 0;        // stage parity built by this warp (shared tile)
+        constexpr int kStep = share ? 2 : 1;         // stages from one of this warp's stages to the next
+        const int row_lo = share ? static_cast<int>(rank) * 64 + 16 * (pw & 3) : 16 * pw;
+        const int quad = lane >> 3;                  // points 4 quad .. 4 quad + 3 of the stage
+        const int rr[2] = {row_lo + (lane & 7), row_lo + (lane & 7) + 8};
         // The peer's rank (our own rank for an independent CTA, so that an address mapping the
         // compiler may evaluate ahead of the share test never names a CTA outside the cluster).
         const uint32_t peer = share ? (rank ^ 1u) : rank;
         constexpr int amat = kTileM * kKStage * 2;
+        enum { kHasSrc = 1, kTauBox = 2, kCubeBox = 4 };
+        struct RowC {
+            int flags, tau_j, src_idx, sA, sC00;     // staged offsets in floats, without the quad
+            float w00, w10, w01, w11, ea, eb;
+        };
         long long g = pgrp;                          // global stage index = item * n_ks + ks
         int s = pgrp % NS, si = pgrp % kInSlots;
         uint32_t ph = 0, phi = 0;
         bool ok = true;
         for (long long j = 0; j < my_items && ok; ++j) {
             // row constants of item j
-            bool tau_box, cube_box, has_src;
-            const float *gA, *gD, *g00, *g10, *g01, *g11;
-            float w00, w10, w01, w11, ea, eb;
-            int sA, sC00;
+            RowC rc[2];
             {
                 const long long it = item_of(j);
                 long long tile, row0;
                 int pix, nrows, grp;
                 item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
                 const TileInfo ti = tiles[tile];
-                const bool valid = r < nrows;
-                RowParams rp;
-                if (valid) {
-                    rp = rows[static_cast<long long>(pix) * nt + row0 + r];
-                } else {
-                    rp.csc = 1.f; rp.tau_j = ti.j0; rp.tau_f = 0.f; rp.src_idx = -1; rp.src_fa = 0.f;
-                    rp.src_fe = 0.f; rp.src_cell = -1;
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int r = rr[i];
+                    const bool valid = r < nrows;
+                    RowParams rp;
+                    if (valid) {
+                        rp = rows[static_cast<long long>(pix) * nt + row0 + r];
+                    } else {
+                        rp.csc = 1.f; rp.tau_j = ti.j0; rp.tau_f = 0.f; rp.src_idx = -1; rp.src_fa = 0.f;
+                        rp.src_fe = 0.f; rp.src_cell = -1;
+                    }
+                    if (rp.tau_j < 0 || rp.tau_j > T.n_pwv - 2) {
+                        atomicOr(T.status, GATEAU_STATUS_BAD_INDEX);
+                        rp.tau_j = 0;
+                    }
+                    const bool has_src = valid && rp.src_idx >= 0;
+                    // staged boxes, with a range check that sends a row to the global path otherwise
+                    const int dj = rp.tau_j - ti.j0;
+                    const bool tau_box = F.tma_inputs && (ti.flags & TILE_TAU_FITS) && dj >= 0 && dj <= kTauBoxRows - 1;
+                    const int da = has_src ? (rp.src_cell >> 16) - ti.ia0 : 0;
+                    const int de = has_src ? (rp.src_cell & 0xffff) - ti.ie0 : 0;
+                    const bool cube_box = has_src && F.tma_inputs && (ti.flags & TILE_CUBE_FITS) && da >= 0 &&
+                                          da <= kCubeBoxAz - 2 && de >= 0 && de <= kCubeBoxEl - 2;
+                    RowC& c = rc[i];
+                    c.flags = (has_src ? kHasSrc : 0) | (tau_box ? kTauBox : 0) | (cube_box ? kCubeBox : 0);
+                    c.tau_j = rp.tau_j;
+                    c.src_idx = has_src ? rp.src_idx : 0;
+                    c.sA = 2 * dj * kBoxW;
+                    c.sC00 = (da * kCubeBoxEl + de) * kBoxW;
+                    const float fa = rp.src_fa, fe = rp.src_fe;
+                    c.w00 = (1.f - fa) * (1.f - fe); c.w10 = fa * (1.f - fe); c.w01 = (1.f - fa) * fe; c.w11 = fa * fe;
+                    // eta_atm = exp(-csc tau) = 2^(a tau_j + b dtau_j) with a = -csc log2(e), b = a f
+                    c.ea = -rp.csc * 1.4426950408889634f;
+                    c.eb = c.ea * rp.tau_f;
                 }
-                if (rp.tau_j < 0 || rp.tau_j > T.n_pwv - 2) {
-                    atomicOr(T.status, GATEAU_STATUS_BAD_INDEX);
-                    rp.tau_j = 0;
-                }
-                has_src = valid && rp.src_idx >= 0;
-                // staged boxes, with a range check that sends a row to the global path otherwise
-                const int dj = rp.tau_j - ti.j0;
-                tau_box = F.tma_inputs && (ti.flags & TILE_TAU_FITS) && dj >= 0 && dj <= kTauBoxRows - 1;
-                const int da = has_src ? (rp.src_cell >> 16) - ti.ia0 : 0;
-                const int de = has_src ? (rp.src_cell & 0xffff) - ti.ie0 : 0;
-                cube_box = has_src && F.tma_inputs && (ti.flags & TILE_CUBE_FITS) && da >= 0 &&
-                           da <= kCubeBoxAz - 2 && de >= 0 && de <= kCubeBoxEl - 2;
-                gA = T.tau + static_cast<long long>(2 * rp.tau_j) * T.Kp;    // tau_j
-                gD = gA + T.Kp;                                               // tau_{j+1} - tau_j
-                const float fa = rp.src_fa, fe = rp.src_fe;
-                w00 = (1.f - fa) * (1.f - fe); w10 = fa * (1.f - fe); w01 = (1.f - fa) * fe; w11 = fa * fe;
-                g00 = T.cube + (has_src ? rp.src_idx : 0);
-                g10 = g00 + static_cast<long long>(T.n_el) * T.Kp;
-                g01 = g00 + T.Kp;
-                g11 = g10 + T.Kp;
-                sA = 2 * dj * kBoxW + kh;                                     // float offsets inside a slot
-                sC00 = (da * kCubeBoxEl + de) * kBoxW + kh;
-                // eta_atm = exp(-csc tau) = 2^(a tau_j + b dtau_j) with a = -csc log2(e), b = a f
-                ea = -rp.csc * 1.4426950408889634f;
-                eb = ea * rp.tau_f;
             }
-            // the stages of item j with this warp's parity (g advances by 2, across items too)
-            for (int ks = static_cast<int>((pgrp + j * n_ks) & 1); ks < n_ks; ks += 2) {
+            // the two rows read the same gathers (same table row, same cube cell, same paths)
+            const bool same = rc[0].flags == rc[1].flags && rc[0].tau_j == rc[1].tau_j &&
+                              rc[0].src_idx == rc[1].src_idx && rc[0].sA == rc[1].sA && rc[0].sC00 == rc[1].sC00;
+            // the stages of item j built by this warp (g advances by kStep, across items too)
+            for (int ks = share ? static_cast<int>((pgrp + j * n_ks) & 1) : 0; ks < n_ks; ks += kStep) {
                 bool okw = (g < NS || mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, T.status)) &&
                            mbar_wait(full_in(si), phi, abort_flag, T.status);
                 okw = __all_sync(0xffffffffu, okw);      // the warp signals as one
@@ -759,96 +769,97 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 uint8_t* a0 = smem + s * sp.a_bytes;
+                float x[2][4];
                 {
                     const float* slot =
                         reinterpret_cast<const float*>(smem + sp.in_off + static_cast<size_t>(si) * kInSlotBytes);
                     const float* stau = slot + kTauOff / 4;
-                    const float* scon = slot + kConstOff / 4 + kh;     // [c0 + c1][16], [c1][16]
-                    const int k = ks * kKStage + kh;
-                    // Read everything this stage needs from the input slot, then release the slot so
-                    // the next gathers land while this warp computes.
-                    float4 arg[nq], src[nq], c01[nq], c1[nq];
-#pragma unroll
-                    for (int h = 0; h < nq; ++h) {
-                        const int kq = k + 4 * h;
-                        float4 ta, td;
-                        if (tau_box) {
-                            ta = ld4(stau + sA + 4 * h);
-                            td = ld4(stau + sA + kBoxW + 4 * h);
+                    const float* scon = slot + kConstOff / 4;                // [c0 + c1][16], [c1][16]
+                    const int kq = ks * kKStage + 4 * quad;                  // first point of this thread
+                    const float4 c01 = ld4(scon + 4 * quad);
+                    const float4 c1 = ld4(scon + kKStage + 4 * quad);
+                    float4 ta, td, q00, q10, q01, q11;
+                    auto gather = [&](const RowC& c) {
+                        if (c.flags & kTauBox) {
+                            ta = ld4(stau + c.sA + 4 * quad);
+                            td = ld4(stau + c.sA + kBoxW + 4 * quad);
                         } else {
+                            const float* gA = T.tau + static_cast<long long>(2 * c.tau_j) * T.Kp;
                             ta = ld4(gA + kq);
-                            td = ld4(gD + kq);
+                            td = ld4(gA + T.Kp + kq);
                         }
-                        c01[h] = ld4(scon + 4 * h);
-                        c1[h] = ld4(scon + kKStage + 4 * h);
-                        // eta_atm = exp(-csc tau) = 2^(a tau_j + b dtau_j)
-                        arg[h] = make_float4(fmaf(eb, td.x, ea * ta.x), fmaf(eb, td.y, ea * ta.y),
-                                             fmaf(eb, td.z, ea * ta.z), fmaf(eb, td.w, ea * ta.w));
-                        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (has_src) {
-                            float4 q00, q10, q01, q11;
-                            if (cube_box) {
-                                q00 = ld4(slot + sC00 + 4 * h);
-                                q10 = ld4(slot + sC00 + kCubeBoxEl * kBoxW + 4 * h);
-                                q01 = ld4(slot + sC00 + kBoxW + 4 * h);
-                                q11 = ld4(slot + sC00 + kCubeBoxEl * kBoxW + kBoxW + 4 * h);
-                            } else {
-                                q00 = ld4(g00 + kq);
-                                q10 = ld4(g10 + kq);
-                                q01 = ld4(g01 + kq);
-                                q11 = ld4(g11 + kq);
-                            }
-                            p.x = w00 * q00.x + w10 * q10.x + w01 * q01.x + w11 * q11.x;
-                            p.y = w00 * q00.y + w10 * q10.y + w01 * q01.y + w11 * q11.y;
-                            p.z = w00 * q00.z + w10 * q10.z + w01 * q01.z + w11 * q11.z;
-                            p.w = w00 * q00.w + w10 * q10.w + w01 * q01.w + w11 * q11.w;
+                        if (c.flags & kCubeBox) {
+                            const float* b = slot + c.sC00 + 4 * quad;
+                            q00 = ld4(b);
+                            q10 = ld4(b + kCubeBoxEl * kBoxW);
+                            q01 = ld4(b + kBoxW);
+                            q11 = ld4(b + kCubeBoxEl * kBoxW + kBoxW);
+                        } else if (c.flags & kHasSrc) {
+                            const float* g00 = T.cube + c.src_idx + kq;
+                            const float* g10 = g00 + static_cast<long long>(T.n_el) * T.Kp;
+                            q00 = ld4(g00);
+                            q10 = ld4(g10);
+                            q01 = ld4(g00 + T.Kp);
+                            q11 = ld4(g10 + T.Kp);
+                        } else {
+                            q00 = q10 = q01 = q11 = make_float4(0.f, 0.f, 0.f, 0.f);
                         }
-                        src[h] = p;
+                    };
+                    // Read everything this stage needs from the input slot, then release the slot so
+                    // the next gathers land while this warp computes.  X = (c0 + c1) + e (P'_src - c1).
+                    float4 arg[2], src[2];
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const RowC& c = rc[i];
+                        if (i == 0 || !same) gather(c);
+                        arg[i] = make_float4(fmaf(c.eb, td.x, c.ea * ta.x), fmaf(c.eb, td.y, c.ea * ta.y),
+                                             fmaf(c.eb, td.z, c.ea * ta.z), fmaf(c.eb, td.w, c.ea * ta.w));
+                        src[i].x = c.w00 * q00.x + c.w10 * q10.x + c.w01 * q01.x + c.w11 * q11.x;
+                        src[i].y = c.w00 * q00.y + c.w10 * q10.y + c.w01 * q01.y + c.w11 * q11.y;
+                        src[i].z = c.w00 * q00.z + c.w10 * q10.z + c.w01 * q01.z + c.w11 * q11.z;
+                        src[i].w = c.w00 * q00.w + c.w10 * q10.w + c.w01 * q01.w + c.w11 * q11.w;
                     }
                     __syncwarp();
                     if (lane == 0) mbar_arrive(empty_in(si));
-                    uint32_t hi[2 * nq], lo[2 * nq], sq[2 * nq];
 #pragma unroll
-                    for (int h = 0; h < nq; ++h) {
-                        float x[4];
-#define GATEAU_FX(i, c) x[i] = fmaf(ex2_approx(arg[h].c), src[h].c - c1[h].c, c01[h].c);
-                        GATEAU_FX(0, x) GATEAU_FX(1, y) GATEAU_FX(2, z) GATEAU_FX(3, w)
-#undef GATEAU_FX
-#pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            const float xa = x[2 * q], xb = x[2 * q + 1];
-                            const __nv_bfloat162 h2 = __floats2bfloat162_rn(xa, xb);
-                            hi[2 * h + q] = *reinterpret_cast<const uint32_t*>(&h2);
-                            lo[2 * h + q] = pack_bf16(xa - __low2float(h2), xb - __high2float(h2));
-                            const __nv_bfloat162 s2 = __hmul2(h2, h2);        // bf16(X_hi^2) for the noise term
-                            sq[2 * h + q] = *reinterpret_cast<const uint32_t*>(&s2);
-                        }
+                    for (int i = 0; i < 2; ++i) {
+                        x[i][0] = fmaf(ex2_approx(arg[i].x), src[i].x - c1.x, c01.x);
+                        x[i][1] = fmaf(ex2_approx(arg[i].y), src[i].y - c1.y, c01.y);
+                        x[i][2] = fmaf(ex2_approx(arg[i].z), src[i].z - c1.z, c01.z);
+                        x[i][3] = fmaf(ex2_approx(arg[i].w), src[i].w - c1.w, c01.w);
                     }
+                }
 #pragma unroll
-                    for (int hh = 0; hh < nq / 2; ++hh) {
-                        const size_t off = core_offset(r, kh + 8 * hh, kTileM);   // 16-byte aligned
-                        *reinterpret_cast<uint4*>(a0 + 0 * amat + off) =
-                            make_uint4(hi[4 * hh], hi[4 * hh + 1], hi[4 * hh + 2], hi[4 * hh + 3]);
-                        *reinterpret_cast<uint4*>(a0 + 1 * amat + off) =
-                            make_uint4(lo[4 * hh], lo[4 * hh + 1], lo[4 * hh + 2], lo[4 * hh + 3]);
-                        *reinterpret_cast<uint4*>(a0 + 2 * amat + off) =
-                            make_uint4(sq[4 * hh], sq[4 * hh + 1], sq[4 * hh + 2], sq[4 * hh + 3]);
+                for (int i = 0; i < 2; ++i) {
+                    uint32_t hi[2], lo[2], sq[2];
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const float xa = x[i][2 * q], xb = x[i][2 * q + 1];
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(xa, xb);
+                        hi[q] = *reinterpret_cast<const uint32_t*>(&h2);
+                        lo[q] = pack_bf16(xa - __low2float(h2), xb - __high2float(h2));
+                        const __nv_bfloat162 s2 = __hmul2(h2, h2);            // bf16(X_hi^2) for the noise term
+                        sq[q] = *reinterpret_cast<const uint32_t*>(&s2);
                     }
+                    const size_t off = core_offset(rr[i], 4 * quad, kTileM);  // 8-byte aligned
+                    *reinterpret_cast<uint2*>(a0 + 0 * amat + off) = make_uint2(hi[0], hi[1]);
+                    *reinterpret_cast<uint2*>(a0 + 1 * amat + off) = make_uint2(lo[0], lo[1]);
+                    *reinterpret_cast<uint2*>(a0 + 2 * amat + off) = make_uint2(sq[0], sq[1]);
                 }
                 fence_proxy_async();                     // our generic stores -> the tensor-core (async) proxy
                 __syncwarp();
                 if (share && lane < kAMats) {
                     // lane m: this warp's 16-row block of matrix m -> the same place in the peer CTA
                     const uint32_t blk = smem_u32(a0) + static_cast<uint32_t>(lane * amat) +
-                                         static_cast<uint32_t>((static_cast<int>(rank) * 64 + 16 * wq) / 8) * 256u;
+                                         static_cast<uint32_t>(row_lo / 8) * 256u;
                     bulk_s2peer(mapa_peer(blk, peer), blk, 512u, mapa_peer(full_a(s), peer));
                 }
                 if (lane == 0) mbar_arrive(full_a(s));
-                // next stage of this parity
-                g += 2;
-                s += 2;
+                // this warp's next stage
+                g += kStep;
+                s += kStep;
                 while (s >= NS) { s -= NS; ph ^= 1u; }
-                si += 2;
+                si += kStep;
                 while (si >= kInSlots) { si -= kInSlots; phi ^= 1u; }
             }
             if (!ok) break;
