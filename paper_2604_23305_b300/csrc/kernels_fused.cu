@@ -19,12 +19,12 @@
 //   warp 1        : TMEM allocator + single-thread tcgen05.mma issuer
 //   warp 2        : one thread issuing tensor copies of the tile's opacity rows and cube texel
 //                   box (input ring); each spinning role has a warp of its own
-//   warp 3        : idle
+//   warp 3        : shared tiles only: one thread copying this CTA's finished rows of each
+//                   stage into the peer CTA's shared memory
 //   warps 4..11   : spectrum producers; each warp signals its own rows (no CTA-wide barrier).
 //                   With 177-352 channels the two channel groups of a tile run on the two CTAs
 //                   of a cluster: each CTA builds half of the tile's rows, 16 rows per warp,
-//                   and each warp bulk-copies its finished 512-byte blocks straight into the
-//                   peer's shared memory (one build per row, no relay)
+//                   and warp 3 ships them into the peer's shared memory (one build per row)
 //   warps 12..15  : epilogue, one thread per TMEM lane (= tile row)
 // The input ring runs ahead of the producers, the A/B ring behind them, so the
 // producers read their gathers from shared memory.  Tiles whose opacity rows or
@@ -45,7 +45,7 @@ constexpr int kKStage = 16;          // spectral points per pipeline stage (one 
 constexpr int kAMats = 3;            // X_hi, X_lo, bf16(X^2)
 constexpr int kBMats = 4;            // H_hi, H_lo, G, Q
 constexpr int kProdWarps = 8;
-constexpr int kProdWarp0 = 4;               // warps 0..3: operand TMA, MMA, input TMA, idle
+constexpr int kProdWarp0 = 4;               // warps 0..3: operand TMA, MMA, input TMA, peer copier
 constexpr int kEpiWarp0 = kProdWarp0 + kProdWarps;
 constexpr int kThreads = (kEpiWarp0 + 4) * 32;
 constexpr int kMaxSmem = 218 * 1024;   // a 2-CTA cluster launch with 223 KB per CTA was refused; stay below
@@ -449,7 +449,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto empty_bar = [&](int s) { return bar_base + 8u * (NS + s); };              // per A slot
     auto full_in = [&](int s) { return bar_base + 8u * (2 * NS + s); };
     auto empty_in = [&](int s) { return bar_base + 8u * (2 * NS + kInSlots + s); };
-    const int nb = 2 * NS + 2 * kInSlots;
+    auto rows_ready = [&](int s) { return bar_base + 8u * (2 * NS + 2 * kInSlots + s); };   // per A slot
+    const int nb = 3 * NS + 2 * kInSlots;
     const uint32_t acc_full = bar_base + 8u * nb;
     const uint32_t acc_empty = bar_base + 8u * (nb + 1);
     const uint32_t drain_bar = bar_base + 8u * (nb + 2);
@@ -461,10 +462,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t rank = share ? cluster_rank() : 0u;
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
-            // one arrival per producer warp that builds the stage (a group of four for a shared
-            // tile, all eight otherwise) + the operand copy's (its bytes and, for a shared tile,
-            // the peer's rows)
-            mbar_init(full_a(s), (share ? kProdWarps / 2 : kProdWarps) + 1);
+            // the operand copy's arrival (its bytes and, for a shared tile, the peer's rows) + one
+            // per producer warp (independent CTA) or the copier's (shared tile, after the rows of
+            // the stage are ready and on their way to the peer)
+            mbar_init(full_a(s), (share ? 1 : kProdWarps) + 1);
+            mbar_init(rows_ready(s), kProdWarps / 2);   // shared tile: the group of four that builds it
             mbar_init(empty_bar(s), share ? 2 : 1);  // both CTAs' MMAs when the tile is shared
         }
         for (int s = 0; s < kInSlots; ++s) {
@@ -632,6 +634,35 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (long long q = (g > kInSlots ? g - kInSlots : 0); q < g; ++q)
                 mbar_drain(full_in(static_cast<int>(q % kInSlots)), static_cast<uint32_t>((q / kInSlots) & 1));
         }
+    } else if (warp == 3) {
+        // ---------------- shared tiles: this CTA's rows of each stage -> the peer ----------------
+        // Off the producers' critical path: they signal rows_ready and go on; this thread issues
+        // the three 2 KB bulk copies (its 64 rows of X_hi, X_lo, bf16(X^2)) into the peer's
+        // shared memory, completing on the peer's stage-full barrier, then arrives on ours.
+        if (share && lane == 0) {
+            constexpr uint32_t amat = kTileM * kKStage * 2;
+            const uint32_t peer = rank ^ 1u;
+            int s = 0;
+            uint32_t par = 0;
+            bool ok = true;
+            for (long long j = 0; j < my_items && ok; ++j) {
+                for (int ks = 0; ks < n_ks; ++ks) {
+                    if (!mbar_wait(rows_ready(s), par, abort_flag, T.status)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t a0 = smem_u32(smem + s * sp.a_bytes);
+                    const uint32_t bar_peer = mapa_peer(full_a(s), peer);
+#pragma unroll
+                    for (int m = 0; m < kAMats; ++m) {
+                        const uint32_t src = a0 + m * amat + rank * (amat / 2);
+                        bulk_s2peer(mapa_peer(src, peer), src, amat / 2, bar_peer);
+                    }
+                    mbar_arrive(full_a(s));
+                    if (++s == NS) { s = 0; par ^= 1u; }
+                }
+            }
+        }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
@@ -690,17 +721,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         // (two wavefronts per 256 bytes).
         // Shared tile: this CTA builds rows [64 rank, 64 rank + 64); two groups of four warps take
         // alternate stages (global stage g = item * n_ks + ks, group = g mod 2), so a warp has two
-        // stage periods for one stage; each warp bulk-copies its finished 512-byte row blocks into
-        // the peer.  Independent CTA: all eight warps build every stage, 16 rows each.
+        // stage periods for one stage; the copier warp ships the stage's rows to the peer once the
+        // group has built them.  Independent CTA: all eight warps build every stage, 16 rows each.
         const int pw = warp - kProdWarp0;
         const int pgrp = share ? pw >> 2 : 0;        // stage parity built by this warp (shared tile)
         constexpr int kStep = share ? 2 : 1;         // stages from one of this warp's stages to the next
         const int row_lo = share ? static_cast<int>(rank) * 64 + 16 * (pw & 3) : 16 * pw;
         const int quad = lane >> 3;                  // points 4 quad .. 4 quad + 3 of the stage
         const int rr[2] = {row_lo + (lane & 7), row_lo + (lane & 7) + 8};
-        // The peer's rank (our own rank for an independent CTA, so that an address mapping the
-        // compiler may evaluate ahead of the share test never names a CTA outside the cluster).
-        const uint32_t peer = share ? (rank ^ 1u) : rank;
         constexpr int amat = kTileM * kKStage * 2;
         enum { kHasSrc = 1, kTauBox = 2, kCubeBox = 4 };
         struct RowC {
@@ -848,13 +876,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 fence_proxy_async();                     // our generic stores -> the tensor-core (async) proxy
                 __syncwarp();
-                if (share && lane < kAMats) {
-                    // lane m: this warp's 16-row block of matrix m -> the same place in the peer CTA
-                    const uint32_t blk = smem_u32(a0) + static_cast<uint32_t>(lane * amat) +
-                                         static_cast<uint32_t>(row_lo / 8) * 256u;
-                    bulk_s2peer(mapa_peer(blk, peer), blk, 512u, mapa_peer(full_a(s), peer));
-                }
-                if (lane == 0) mbar_arrive(full_a(s));
+                if (lane == 0) mbar_arrive(share ? rows_ready(s) : full_a(s));
                 // this warp's next stage
                 g += kStep;
                 s += kStep;
