@@ -190,6 +190,7 @@ __host__ __device__ inline SmemPlan smem_plan(int n_half) {
     for (int nsb = 4; nsb >= 2; --nsb) {
         long long nsa = (avail - static_cast<long long>(nsb) * p.b_bytes) / static_cast<long long>(p.a_bytes);
         if (nsa > 8) nsa = 8;
+        nsa &= ~1LL;                               // whole stage pairs
         if (nsa >= nsb) {
             p.nsa = static_cast<int>(nsa);
             p.nsb = nsb;
@@ -445,8 +446,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t bar_base = smem_u32(bars);
     // One "stage full" barrier per ring slot: the operand copy's arrival (+ its bytes) and the
     // spectrum rows' arrival(s) (+ the peer's bytes for a shared tile), so the MMA issuer waits once.
-    auto full_a = [&](int s) { return bar_base + 8u * s; };                        // per A slot
-    auto empty_bar = [&](int s) { return bar_base + 8u * (NS + s); };              // per A slot
+    // The MMA issuer takes two 16-point stages per handshake (10 MMAs per wait and commit):
+    // the stage-full and stage-free barriers belong to pairs of A slots (2p, 2p + 1).
+    auto full_a = [&](int s) { return bar_base + 8u * (s >> 1); };                 // per A-slot pair
+    auto empty_bar = [&](int s) { return bar_base + 8u * (NS + (s >> 1)); };       // per A-slot pair
     auto full_in = [&](int s) { return bar_base + 8u * (2 * NS + s); };
     auto empty_in = [&](int s) { return bar_base + 8u * (2 * NS + kInSlots + s); };
     auto rows_ready = [&](int s) { return bar_base + 8u * (2 * NS + 2 * kInSlots + s); };   // per A slot
@@ -461,14 +464,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int share = kShare;
     const uint32_t rank = share ? cluster_rank() : 0u;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NS; ++s) {
-            // the operand copy's arrival (its bytes and, for a shared tile, the peer's rows) + one
-            // per producer warp (independent CTA) or the copier's (shared tile, after the rows of
-            // the stage are ready and on their way to the peer)
-            mbar_init(full_a(s), (share ? 1 : kProdWarps) + 1);
-            mbar_init(rows_ready(s), kProdWarps / 2);   // shared tile: the group of four that builds it
+        for (int s = 0; s < NS; s += 2) {
+            // per stage of the pair: the operand copy's arrival (its bytes and, for a shared tile,
+            // the peer's rows) + one per producer warp (independent CTA) or the copier's (shared
+            // tile, after the rows of the stage are ready and on their way to the peer)
+            mbar_init(full_a(s), 2 * ((share ? 1 : kProdWarps) + 1));
             mbar_init(empty_bar(s), share ? 2 : 1);  // both CTAs' MMAs when the tile is shared
         }
+        for (int s = 0; s < NS; ++s) mbar_init(rows_ready(s), kProdWarps / 2);   // the group that builds it
         for (int s = 0; s < kInSlots; ++s) {
             mbar_init(full_in(s), 1);
             mbar_init(empty_in(s), share ? kProdWarps / 2 : kProdWarps);
@@ -676,33 +679,37 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!ok) break;
                     tc_fence_after();
                 }
-                for (int ks = 0; ks < n_ks; ++ks) {
+                for (int ks = 0; ks < n_ks; ks += 2) {               // n_ks is even (Kp % 32 == 0)
                     if (!mbar_wait(full_a(s), par, abort_flag, T.status)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(smem + s * sp.a_bytes);
-                    const uint32_t b0 = smem_u32(smem + sp.b_off + sb * sp.b_bytes);
                     const uint32_t a_mat = kTileM * kKStage * 2;            // bytes per A matrix
                     const uint32_t b_mat = static_cast<uint32_t>(NH) * kKStage * 2;
-                    const uint64_t xhi = smem_desc(a0 + 0 * a_mat, 128, 256);
-                    const uint64_t xlo = smem_desc(a0 + 1 * a_mat, 128, 256);
-                    const uint64_t xsq = smem_desc(a0 + 2 * a_mat, 128, 256);
-                    const uint64_t hhi = smem_desc(b0 + 0 * b_mat, 128, 256);
-                    const uint64_t hlo = smem_desc(b0 + 1 * b_mat, 128, 256);
-                    const uint64_t gmat = smem_desc(b0 + 2 * b_mat, 128, 256);
-                    const uint64_t qmat = smem_desc(b0 + 3 * b_mat, 128, 256);
-                    const uint32_t acc = ks > 0 ? 1u : 0u;
-                    tc_mma(d_sig, xhi, hhi, idesc, acc);
-                    tc_mma(d_sig, xlo, hhi, idesc, 1u);
-                    tc_mma(d_sig, xhi, hlo, idesc, 1u);
-                    tc_mma(d_noi, xhi, gmat, idesc, acc);
-                    tc_mma(d_noi, xsq, qmat, idesc, 1u);
-                    if (share) tc_commit_pair(empty_bar(s));   // A slot s free in both CTAs
-                    else tc_commit(empty_bar(s));              // A slot s free once these MMAs finish
-                    if (++s == NS) { s = 0; par ^= 1u; }
-                    if (++sb == NSB) sb = 0;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t a0 = smem_u32(smem + (s + h) * sp.a_bytes);
+                        const uint32_t b0 = smem_u32(smem + sp.b_off + sb * sp.b_bytes);
+                        const uint64_t xhi = smem_desc(a0 + 0 * a_mat, 128, 256);
+                        const uint64_t xlo = smem_desc(a0 + 1 * a_mat, 128, 256);
+                        const uint64_t xsq = smem_desc(a0 + 2 * a_mat, 128, 256);
+                        const uint64_t hhi = smem_desc(b0 + 0 * b_mat, 128, 256);
+                        const uint64_t hlo = smem_desc(b0 + 1 * b_mat, 128, 256);
+                        const uint64_t gmat = smem_desc(b0 + 2 * b_mat, 128, 256);
+                        const uint64_t qmat = smem_desc(b0 + 3 * b_mat, 128, 256);
+                        const uint32_t acc = (ks > 0 || h > 0) ? 1u : 0u;
+                        tc_mma(d_sig, xhi, hhi, idesc, acc);
+                        tc_mma(d_sig, xlo, hhi, idesc, 1u);
+                        tc_mma(d_sig, xhi, hlo, idesc, 1u);
+                        tc_mma(d_noi, xhi, gmat, idesc, acc);
+                        tc_mma(d_noi, xsq, qmat, idesc, 1u);
+                        if (++sb == NSB) sb = 0;
+                    }
+                    if (share) tc_commit_pair(empty_bar(s));   // A slots s, s+1 free in both CTAs
+                    else tc_commit(empty_bar(s));              // A slots s, s+1 free once these MMAs finish
+                    s += 2;
+                    if (s == NS) { s = 0; par ^= 1u; }
                 }
                 if (!ok) break;
                 tc_commit(acc_full);                  // accumulators of item j complete
