@@ -25,7 +25,8 @@
 //                   With 177-352 channels the two channel groups of a tile run on the two CTAs
 //                   of a cluster: each CTA builds half of the tile's rows, 16 rows per warp,
 //                   and warp 3 ships them into the peer's shared memory (one build per row)
-//   warps 12..15  : epilogue, one thread per TMEM lane (= tile row)
+//   warps 12..15  : shared tiles: a third producer group; independent CTAs: epilogue only.
+//                   The epilogue of each item is shared by warps 4..15 (three per TMEM quadrant)
 // The input ring runs ahead of the producers, the A/B ring behind them, so the
 // producers read their gathers from shared memory.  Tiles whose opacity rows or
 // cube texels do not fit the staged boxes fall back to global loads.
@@ -717,7 +718,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_commit(drain_bar);                     // no MMA in flight at exit (bounded)
             mbar_drain(drain_bar, 0);
         }
-    } else if (warp >= kProdWarp0 && warp < kEpiWarp0) {
+    } else if (warp >= kProdWarp0 && (share || warp < kEpiWarp0)) {
         // ---------------- spectrum producers ----------------
         // Warp = 16 rows x the 16 points of a stage; thread = two rows (r, r + 8: the same place
         // in the warp's two 8-row core-matrix groups) x one quad of 4 points.  Lanes 8q..8q+7 are
@@ -726,14 +727,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         // same table row and cube cell (the usual case: samples 50 ms apart) the gathers are read
         // once for both.  A warp's 8-byte stores of one (row, matrix) cover whole core-matrix rows
         // (two wavefronts per 256 bytes).
-        // Shared tile: this CTA builds rows [64 rank, 64 rank + 64); two groups of four warps take
-        // alternate stages (global stage g = item * n_ks + ks, group = g mod 2), so a warp has two
-        // stage periods for one stage; the copier warp ships the stage's rows to the peer once the
-        // group has built them.  Independent CTA: all eight warps build every stage, 16 rows each.
+        // Shared tile: this CTA builds rows [64 rank, 64 rank + 64); three groups of four warps
+        // (warps 4-15: the epilogue warps build too) take stages in turn (global stage
+        // g = item * n_ks + ks, group = g mod 3), so a warp has three stage periods for one stage;
+        // the copier warp ships the stage's rows to the peer once the group has built them.
+        // Independent CTA: warps 4-11 build every stage, 16 rows each.
         const int pw = warp - kProdWarp0;
-        const int pgrp = share ? pw >> 2 : 0;        // stage parity built by this warp (shared tile)
-        constexpr int kStep = share ? 2 : 1;         // stages from one of this warp's stages to the next
-        const int row_lo = share ? static_cast<int>(rank) * 64 + 16 * (pw & 3) : 16 * pw;
+        const int pgrp = share ? pw >> 2 : 0;        // stage residue mod kStep built by this warp
+        constexpr int kStep = share ? 3 : 1;         // stages from one of this warp's stages to the next
+        const int row_lo = share ? static_cast<int>(rank) * 64 + 16 * (pw & 3) : 16 * pw;   // pw & 3: warp in group
         const int quad = lane >> 3;                  // points 4 quad .. 4 quad + 3 of the stage
         const int rr[2] = {row_lo + (lane & 7), row_lo + (lane & 7) + 8};
         constexpr int amat = kTileM * kKStage * 2;
@@ -794,8 +796,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             // the two rows read the same gathers (same table row, same cube cell, same paths)
             const bool same = rc[0].flags == rc[1].flags && rc[0].tau_j == rc[1].tau_j &&
                               rc[0].src_idx == rc[1].src_idx && rc[0].sA == rc[1].sA && rc[0].sC00 == rc[1].sC00;
-            // the stages of item j built by this warp (g advances by kStep, across items too)
-            for (int ks = share ? static_cast<int>((pgrp + j * n_ks) & 1) : 0; ks < n_ks; ks += kStep) {
+            // the stages of item j built by this warp (g advances by kStep, across items too:
+            // ks = first ks >= 0 with (j n_ks + ks) mod kStep == pgrp)
+            for (int ks = share ? static_cast<int>(((pgrp - j * n_ks) % kStep + kStep) % kStep) : 0; ks < n_ks;
+                 ks += kStep) {
                 bool okw = (g < NS || mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, T.status)) &&
                            mbar_wait(full_in(si), phi, abort_flag, T.status);
                 okw = __all_sync(0xffffffffu, okw);      // the warp signals as one
@@ -895,7 +899,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = epilogue_item(j);                 // this warp's share of item j's epilogue
         }
     } else if (warp >= kEpiWarp0) {
-        // ---------------- epilogue warps ----------------
+        // ---------------- epilogue warps (independent CTAs; shared tiles use them as producers) ----
         for (long long j = 0; j < my_items; ++j)
             if (!epilogue_item(j)) break;
     }
