@@ -35,7 +35,21 @@ __global__ __launch_bounds__(256) void pink_phase1_kernel(DevTables T, PinkWork 
             av[j] = (j < np) ? T.pink_a[ch * np + j] : 0.f;
             st[j] = 0.f;
         }
-        for (long long n = a0; n < b0;) {
+        long long n = a0;
+        // whole groups of 4 (the usual case: chunk starts are multiples of 4 when t0 is)
+        if ((n & 3) == 0) {
+            for (; n + 4 <= b0; n += 4) {
+                const float4 z4 = pink_normals4(n >> 2, i, ch, T.key0, T.key1);
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    float v = fmaf(av[j], st[j], z4.x);
+                    v = fmaf(av[j], v, z4.y);
+                    v = fmaf(av[j], v, z4.z);
+                    st[j] = fmaf(av[j], v, z4.w);
+                }
+            }
+        }
+        while (n < b0) {                             // partial groups at either end
             const long long m = n >> 2;
             const int q0 = static_cast<int>(n & 3);
             const int q1 = static_cast<int>(min(b0 - (m << 2), 4LL));
@@ -102,7 +116,37 @@ __global__ __launch_bounds__(256) void pink_phase3_kernel(DevTables T, PinkWork 
         const float d = T.pink_d[ch];
         float* o = out + ((a0 - t0) * T.n_pix + i) * static_cast<long long>(T.n_ch) + ch;
         long long n = a0;
-        // current group [n, n + cnt) and its loaded outputs
+        // whole groups of 4 (the usual case: chunk starts are multiples of 4 when t0 is), with the
+        // next group's outputs loaded before the current group's recurrence
+        if ((n & 3) == 0 && n + 4 <= b0) {
+            float cur4[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cur4[q] = o[q * stride];
+            while (n + 4 <= b0) {
+                const bool full_next = n + 8 <= b0;
+                float nxt4[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) nxt4[q] = full_next ? o[(4 + q) * stride] : 0.f;
+                const float4 z4 = pink_normals4(n >> 2, i, ch, T.key0, T.key1);
+                const float zq[4] = {z4.x, z4.y, z4.z, z4.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float z = zq[q];
+                    float y = d * z;
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        st[j] = fmaf(av[j], st[j], z);
+                        y = fmaf(rv[j], st[j], y);
+                    }
+                    o[q * stride] = cur4[q] + y;
+                }
+                n += 4;
+                o += 4 * stride;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) cur4[q] = nxt4[q];
+            }
+        }
+        // partial groups at either end: current group [n, n + cnt) and its loaded outputs
         int q0 = static_cast<int>(n & 3);
         int q1 = static_cast<int>(min(b0 - ((n >> 2) << 2), 4LL));
         float cur[4];
