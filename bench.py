@@ -189,6 +189,26 @@ def dist_env():
     return world, rank, local
 
 
+def replica_seeds(rank: int) -> dict:
+    """Each rank simulates an independent copy of the workload: its own screen and noise seeds."""
+    return dict(seed=rank, noise_seed=1 + rank)
+
+
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The slowest rank's time (the job's time); dist is torch.distributed or None."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, per_step: float, steps: int, elapsed_s: float) -> float:
+    """Whole-job throughput: the units all ranks processed / the slowest rank's time."""
+    return world * per_step * steps / elapsed_s
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -250,15 +270,10 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def ranks_max(x: float) -> float:
+        return max_over_ranks(x, dist, "cuda")
 
-    # Each rank simulates an independent copy of the workload (its own screen / noise seeds).
-    sc = W.scenario(args.workload, nt_total=args.nt, seed=rank, noise_seed=1 + rank)
+    sc = W.scenario(args.workload, nt_total=args.nt, **replica_seeds(rank))
     nt = sc["nt_total"]
     per_step = W.detector_samples(sc)
     plan = Plan(sc, precision=args.precision, white=True, pink=True)
@@ -281,11 +296,11 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    elapsed_s = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+    elapsed_s = ranks_max(ev0.elapsed_time(ev1) / 1e3)
     phase_ms, runs, launches = plan.get_timing()
     plan.set_timing(False)
     flags = plan.status()
-    value = world * per_step * args.steps / elapsed_s
+    value = job_value(world, per_step, args.steps, elapsed_s)
 
     bf16_peak, hbm_peak, peak_kind = peaks()
     n_freq, n_ch = sc["n_freq"], plan.n_ch
@@ -334,8 +349,8 @@ def main():
             p32.run(0, nt, o32)
         e1.record(stream)
         torch.cuda.synchronize()
-        t32 = max_over_ranks(e0.elapsed_time(e1) / 1e3)
-        v32 = world * per_step * args.fp32_steps / t32
+        t32 = ranks_max(e0.elapsed_time(e1) / 1e3)
+        v32 = job_value(world, per_step, args.fp32_steps, t32)
         result["fp32_path"] = {"value": v32, "unit": UNIT, "ms_per_step": 1e3 * t32 / args.fp32_steps,
                                "speedup_of_bf16x3": value / v32}
         del o32, p32
@@ -367,8 +382,8 @@ def main():
         t = time.perf_counter()
         for _ in range(args.e2e_steps):
             e2e_step()
-        te = max_over_ranks(time.perf_counter() - t)
-        result["e2e"] = {"value": world * per_step * args.e2e_steps / te, "unit": UNIT,
+        te = ranks_max(time.perf_counter() - t)
+        result["e2e"] = {"value": job_value(world, per_step, args.e2e_steps, te), "unit": UNIT,
                          "h2d_bytes_per_step": int(cube.nbytes + screen.nbytes + table.nbytes),
                          "d2h_bytes_per_step": int(host_out.nbytes), "ms_per_step": 1e3 * te / args.e2e_steps}
         del pe, host_out
