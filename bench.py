@@ -147,7 +147,7 @@ def cpu_baseline(sc, budget_s=12.0):
 
 
 def serving_leg(n_requests: int, seed: int = 2, budget_bytes: float = 120e9, max_active: int = 16,
-                chunk_samples: int = 4096, max_chunk_bytes: int = 32 << 20):
+                chunk_samples: int = 4096, max_chunk_bytes: int = 32 << 20, builders: int = 6):
     """The serving workload: n_requests simulations (hexagonal IFUs of 1-61 spaxels, 100-347
     channels, 1000-6000 spectral points, 10 s - 10 min at 160 Hz) through the native server,
     admitted by a device-memory budget.  First all requests arrive at once (saturated: the
@@ -160,7 +160,7 @@ def serving_leg(n_requests: int, seed: int = 2, budget_bytes: float = 120e9, max
     scs, reqs = build_requests(shapes, ServingInputs(seed), chunk_samples)
     make = lambda i: Plan(scs[i], precision="bf16x3", device_inputs=False)
     srv = Server(int(budget_bytes), max_active=max_active, chunk_samples=chunk_samples,
-                 max_chunk_bytes=max_chunk_bytes, n_streams=max_active)
+                 max_chunk_bytes=max_chunk_bytes, n_streams=max_active, n_builders=builders)
     srv.run(reqs[:4], make)                                       # warm-up (not reported)
     sat = srv.run(reqs, make)
     capacity = sat["n_done"] / sat["makespan_s"]
@@ -172,7 +172,7 @@ def serving_leg(n_requests: int, seed: int = 2, budget_bytes: float = 120e9, max
     keys = ("p50_latency_s", "p99_latency_s", "mean_latency_s", "max_latency_s", "makespan_s", "throughput",
             "detector_samples", "peak_bytes", "peak_active", "overlap", "n_done", "n_failed")
     out = {k: st[k] for k in keys}
-    out.update(requests=n_requests, budget_bytes=int(budget_bytes), max_active=max_active,
+    out.update(requests=n_requests, budget_bytes=int(budget_bytes), max_active=max_active, plan_builders=builders,
                chunk_samples=chunk_samples, capacity_req_per_s=capacity, arrival_rate_req_per_s=rate,
                saturated={k: sat[k] for k in ("makespan_s", "throughput", "p50_latency_s", "p99_latency_s",
                                               "overlap")},

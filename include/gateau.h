@@ -283,6 +283,14 @@ gateau_status gateau_plan_get_timing(gateau_plan* plan, double* ms, long long* r
  * too small; *n_out receives the spaxel count. */
 gateau_status gateau_hex_offsets(int R_hex, double spacing_rad, double* out, int count, int* n_out);
 
+/* Build everything a plan derives from its setters' inputs -- the collapsed
+ * cascade, the filter operands, the pink-noise filters -- and upload it, so
+ * that the first gateau_run only enqueues work.  Optional: gateau_run does it
+ * when needed.  ESTATE if a setter is missing.  Blocks the calling thread
+ * (host work and synchronous uploads); plans of different threads are
+ * independent, so a service can prepare plans on worker threads. */
+gateau_status gateau_plan_prepare(gateau_plan* plan);
+
 /* Several plans' chunks on one stream.  plans[k] runs samples t0s[k] ..
  * t0s[k]+nts[k]-1 into outs[k] (device) exactly as gateau_run would, with the
  * same chunk-order rules and bit-identical results, enqueued in k order.
@@ -329,6 +337,10 @@ typedef struct {
                                    detector samples occupies its stream for
                                    D * dry_seconds_per_sample on a virtual clock (host tests) */
     double dry_seconds_per_sample;
+    int n_builders;             /* 0..64 threads that create (factory) and prepare
+                                   (gateau_plan_prepare) admitted requests' plans while the
+                                   running requests' chunks are launched; 0 builds on the thread
+                                   running the server (always so in a dry run) */
 } gateau_server_desc;
 
 typedef struct {
@@ -341,8 +353,10 @@ typedef struct {
 
 /* Factory: create the plan of request `request` (index into the array given to
  * gateau_server_run), ready to run from t0 = 0; NULL marks the request failed.
+ * With n_builders > 0 it is called on builder threads (several at once, each
+ * for a different request); otherwise on the thread running the server.
  * Release: the server is done with the plan (all chunks on the host); the
- * caller destroys it.  Both are called on the thread running the server. */
+ * caller destroys it.  Release is called on the thread running the server. */
 typedef gateau_plan* (*gateau_plan_factory)(void* user, int request);
 typedef void (*gateau_plan_release)(void* user, int request, gateau_plan* plan);
 

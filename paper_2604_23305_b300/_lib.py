@@ -52,7 +52,7 @@ class PlanInfo(C.Structure):
 class ServerDesc(C.Structure):
     _fields_ = [("budget_bytes", C.c_size_t), ("max_active", C.c_int), ("chunk_samples", C.c_longlong),
                 ("max_chunk_bytes", C.c_size_t), ("n_streams", C.c_int), ("dry_run", C.c_int),
-                ("dry_seconds_per_sample", C.c_double)]
+                ("dry_seconds_per_sample", C.c_double), ("n_builders", C.c_int)]
 
 
 class Request(C.Structure):
@@ -91,6 +91,7 @@ SIGNATURES = {
     "gateau_set_pink_noise": (C.c_int, [PlanP, dp, dp]),
     "gateau_set_scan": (C.c_int, [PlanP, C.c_int, dp, C.c_int, C.c_double, C.c_double, C.c_void_p,
                                   C.c_longlong, C.c_int]),
+    "gateau_plan_prepare": (C.c_int, [PlanP]),
     "gateau_run": (C.c_int, [PlanP, C.c_longlong, C.c_longlong, C.c_void_p, C.c_void_p]),
     "gateau_run_host": (C.c_int, [PlanP, C.c_longlong, C.c_longlong, C.c_void_p, C.c_void_p]),
     "gateau_run_batch": (C.c_int, [C.POINTER(PlanP), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),

@@ -758,6 +758,15 @@ gateau_status gateau_set_scan(gateau_plan* p, int kind, const double* params, in
     return GATEAU_OK;
 }
 
+gateau_status gateau_plan_prepare(gateau_plan* p) {
+    if (!p) return fail(GATEAU_EINVAL, "plan is NULL");
+    gateau_status st = check_complete(p);
+    if (st != GATEAU_OK) return st;
+    st = ensure_base(p);
+    if (st != GATEAU_OK) return st;
+    return finalize(p);
+}
+
 gateau_status gateau_run(gateau_plan* p, long long t0, long long nt, float* dev_out, void* stream) {
     if (!p) return fail(GATEAU_EINVAL, "plan is NULL");
     gateau_status st = validate_run(p, t0, nt, dev_out);

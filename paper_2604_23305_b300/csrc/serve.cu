@@ -13,13 +13,18 @@
 //
 // A dry-run mode replays the same scheduling decisions on a virtual clock with
 // no CUDA call, so the admission, slot and budget logic is testable on a host
-// without a GPU.
+// without a GPU.  Plans can be built (factory + gateau_plan_prepare: filter
+// design, operand tiling, uploads) on builder threads, so an admission does not
+// hold up the launches of the requests already running.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -76,7 +81,17 @@ __global__ void tod_sum_parts(const double* __restrict__ part, double* __restric
     }
 }
 
-enum { kPending = 0, kActive = 1, kDone = 2, kFailed = 3 };
+enum { kPending = 0, kActive = 1, kDone = 2, kFailed = 3, kBuilding = 4 };
+
+// Builder threads: create (factory) and prepare the plans of admitted requests.
+struct Builders {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<int> todo;
+    std::vector<std::pair<int, gateau_plan*>> done;   // plan NULL: the factory or prepare failed
+    bool stop = false;
+    std::vector<std::thread> threads;
+};
 
 struct Slot {
     float* d_out = nullptr;          // chunk TOD (device)
@@ -259,9 +274,77 @@ gateau_status gateau_server_run(gateau_server* srv, const gateau_request* reques
         ++n_finished;
     };
 
+    // An admitted request whose plan exists: a stream, pinned staging and chunk buffers.
+    auto activate = [&](Req& q, int idx, gateau_plan* plan) {
+        q.plan = plan;
+        if (!plan) {                                  // the factory or the preparation failed
+            finish(q, idx, kFailed);
+            return;
+        }
+        q.stream = admitted_count % d.n_streams;
+        ++admitted_count;
+        q.state = kActive;
+        if (dry) return;
+        q.pin = srv->free_pins.back();
+        srv->free_pins.pop_back();
+        cudaStream_t st = srv->streams[q.stream];
+        cudaError_t e = cudaSuccess;
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaMallocAsync(reinterpret_cast<void**>(&q.slot[b].d_out), q.chunk_bytes, st);
+            if (e == cudaSuccess)
+                e = cudaMallocAsync(reinterpret_cast<void**>(&q.slot[b].d_part), (2 * kSumBlocks + 2) * sizeof(double), st);
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            finish(q, idx, kFailed);
+        }
+    };
+
+    Builders B;
+    std::vector<std::pair<int, gateau_plan*>> failed_builds;   // guarded by B.mu
+    int n_building = 0;
+    const bool use_builders = !dry && d.n_builders > 0;
+    if (use_builders) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        for (int w = 0; w < d.n_builders; ++w)
+            B.threads.emplace_back([&, dev]() {
+                cudaSetDevice(dev);
+                while (true) {
+                    int idx = -1;
+                    {
+                        std::unique_lock<std::mutex> lk(B.mu);
+                        B.cv.wait(lk, [&] { return B.stop || !B.todo.empty(); });
+                        if (B.todo.empty()) return;           // stop requested and nothing left
+                        idx = B.todo.front();
+                        B.todo.pop_front();
+                    }
+                    gateau_plan* plan = create(user, idx);
+                    if (plan && gateau_plan_prepare(plan) != GATEAU_OK) {
+                        std::lock_guard<std::mutex> lk(B.mu);
+                        B.done.emplace_back(idx, plan);      // released by the server thread
+                        B.done.back().second = nullptr;
+                        failed_builds.push_back(std::make_pair(idx, plan));
+                        continue;
+                    }
+                    std::lock_guard<std::mutex> lk(B.mu);
+                    B.done.emplace_back(idx, plan);
+                }
+            });
+    }
+
     while (n_finished < n) {
         bool progress = false;
         const double t = now();
+        // plans whose preparation failed on a builder: hand them back to the caller
+        if (use_builders) {
+            std::vector<std::pair<int, gateau_plan*>> bad;
+            {
+                std::lock_guard<std::mutex> lk(B.mu);
+                bad.swap(failed_builds);
+            }
+            for (auto& pr : bad) release(user, pr.first, pr.second);
+        }
 
         // 1. retire chunks whose TOD reached the host (in order per request)
         for (int i = 0; i < n && run_status == GATEAU_OK; ++i) {
@@ -319,44 +402,43 @@ gateau_status gateau_server_run(gateau_server* srv, const gateau_request* reques
             }
             if (n_active >= d.max_active || held + need > d.budget_bytes) break;   // wait for room
             q.t_admit = now();
-            q.plan = create(user, next);
-            if (!q.plan) {
-                q.state = kFailed;
-                q.t_done = now();
-                ++n_finished;
-                ++next;
-                progress = true;
-                continue;
-            }
             q.held = need;
             held += need;
             peak_bytes = std::max(peak_bytes, held);
-            q.stream = admitted_count % d.n_streams;
-            ++admitted_count;
-            q.state = kActive;
             ++n_active;
             peak_active = std::max(peak_active, n_active);
-            if (!dry) {
-                q.pin = srv->free_pins.back();
-                srv->free_pins.pop_back();
-                cudaStream_t st = srv->streams[q.stream];
-                cudaError_t e = cudaSuccess;
-                for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-                    e = cudaMallocAsync(reinterpret_cast<void**>(&q.slot[b].d_out), q.chunk_bytes, st);
-                    if (e == cudaSuccess)
-                        e = cudaMallocAsync(reinterpret_cast<void**>(&q.slot[b].d_part),
-                                            (2 * kSumBlocks + 2) * sizeof(double), st);
+            if (use_builders) {
+                q.state = kBuilding;
+                ++n_building;
+                {
+                    std::lock_guard<std::mutex> lk(B.mu);
+                    B.todo.push_back(next);
                 }
-                if (e != cudaSuccess) {
-                    cudaGetLastError();
-                    finish(q, next, kFailed);
-                    ++next;
-                    progress = true;
-                    continue;
+                B.cv.notify_one();
+            } else {
+                gateau_plan* plan = create(user, next);
+                if (plan && !dry && gateau_plan_prepare(plan) != GATEAU_OK) {
+                    release(user, next, plan);
+                    plan = nullptr;
                 }
+                activate(q, next, plan);
             }
             ++next;
             progress = true;
+        }
+
+        // 2b. plans finished by the builders
+        if (use_builders && n_building > 0) {
+            std::vector<std::pair<int, gateau_plan*>> ready;
+            {
+                std::lock_guard<std::mutex> lk(B.mu);
+                ready.swap(B.done);
+            }
+            for (auto& pr : ready) {
+                --n_building;
+                activate(R[pr.first], pr.first, pr.second);
+                progress = true;
+            }
         }
 
         // 3. launch chunks: every active request keeps two in flight
@@ -426,9 +508,11 @@ gateau_status gateau_server_run(gateau_server* srv, const gateau_request* reques
             const double t_now = now();
             const bool arrival_ahead = next < n && R[next].state == kPending && requests[next].arrival_s > t_now;
             if (arrival_ahead) t_next = std::min(t_next, requests[next].arrival_s);
-            // Nothing in flight and no arrival still to come: the pending requests cannot be admitted
-            // (cannot happen with the admission rules above; kept as a guard against spinning).
-            if (!busy && !arrival_ahead) break;
+            // Nothing in flight, no plan being built and no arrival still to come: the pending
+            // requests cannot be admitted (cannot happen with the admission rules above; kept as a
+            // guard against spinning).
+            if (!busy && n_building == 0 && !arrival_ahead) break;
+            if (n_building > 0) busy = true;
             if (dry) {
                 vclock = std::max(vclock, t_next);
             } else {
@@ -438,6 +522,20 @@ gateau_status gateau_server_run(gateau_server* srv, const gateau_request* reques
         }
     }
 
+    if (use_builders) {                            // no build left in flight
+        {
+            std::lock_guard<std::mutex> lk(B.mu);
+            B.stop = true;
+            B.todo.clear();
+        }
+        B.cv.notify_all();
+        for (std::thread& th : B.threads) th.join();
+        for (auto& pr : B.done)
+            if (pr.second) release(user, pr.first, pr.second);
+        for (auto& pr : failed_builds) release(user, pr.first, pr.second);
+        for (Req& q : R)
+            if (q.state == kBuilding) q.state = kFailed;
+    }
     if (run_status != GATEAU_OK) {                 // release whatever is still admitted
         for (cudaStream_t st : srv->streams) cudaStreamSynchronize(st);
         for (int i = 0; i < n; ++i)

@@ -28,7 +28,7 @@ class Server:
 
     def __init__(self, budget_bytes: int, max_active: int = 16, chunk_samples: int = 4096,
                  max_chunk_bytes: int = 32 << 20, n_streams: int | None = None, dry_run: bool = False,
-                 dry_seconds_per_sample: float = 0.0):
+                 dry_seconds_per_sample: float = 0.0, n_builders: int = 0):
         self._lib = L.lib()
         d = L.ServerDesc()
         d.budget_bytes = int(budget_bytes)
@@ -38,6 +38,7 @@ class Server:
         d.n_streams = int(n_streams if n_streams is not None else max_active)
         d.dry_run = 1 if dry_run else 0
         d.dry_seconds_per_sample = float(dry_seconds_per_sample)
+        d.n_builders = int(n_builders)
         self._h = L.ServerP()
         L.check(self._lib.gateau_server_create(C.byref(d), C.byref(self._h)))
         self.n = 0

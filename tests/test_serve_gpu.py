@@ -45,17 +45,23 @@ def test_request_results_are_the_same_alone_and_in_the_mix():
         alone.append((out, srv.result(0)["checksum"]))
         srv.close()
 
-    srv = Server(budget_bytes=8 << 30, max_active=4, chunk_samples=CHUNK, max_chunk_bytes=16 << 20, n_streams=4)
-    outs = outputs(reqs)
-    st = srv.run([dict(r, host_out=o) for r, o in zip(reqs, outs)], make)
-    assert st["n_done"] == 4 and st["n_failed"] == 0
-    assert st["peak_active"] == 4
-    assert st["overlap"] > 1.0                       # requests had chunks in flight together
-    assert 0 < st["p50_latency_s"] <= st["p99_latency_s"] <= st["max_latency_s"]
-    for i in range(4):
-        assert np.array_equal(outs[i], alone[i][0]), f"request {i} differs in the mix"
-        assert srv.result(i)["checksum"] == alone[i][1]
-        assert np.isfinite(outs[i]).all() and np.abs(outs[i]).max() > 0
+    # the mix: four requests at once, plans built on the server thread (all four then have chunks
+    # in flight together) and on three builder threads (they start as their plans are ready)
+    for builders in (0, 3):
+        srv = Server(budget_bytes=8 << 30, max_active=4, chunk_samples=CHUNK, max_chunk_bytes=16 << 20,
+                     n_streams=4, n_builders=builders)
+        outs = outputs(reqs)
+        st = srv.run([dict(r, host_out=o) for r, o in zip(reqs, outs)], make)
+        assert st["n_done"] == 4 and st["n_failed"] == 0
+        assert st["peak_active"] == 4
+        if builders == 0:
+            assert st["overlap"] > 1.0                   # requests had chunks in flight together
+        assert 0 < st["p50_latency_s"] <= st["p99_latency_s"] <= st["max_latency_s"]
+        for i in range(4):
+            assert np.array_equal(outs[i], alone[i][0]), f"request {i} differs in the mix ({builders} builders)"
+            assert srv.result(i)["checksum"] == alone[i][1]
+            assert np.isfinite(outs[i]).all() and np.abs(outs[i]).max() > 0
+        srv.close()
 
 
 def test_server_tod_equals_plan_runs_over_the_same_chunks():
