@@ -671,6 +671,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             const uint32_t idesc = make_idesc(NH);
+            // slot-0 descriptors and the per-slot steps of the start-address field
+            const uint32_t a_mat = kTileM * kKStage * 2;                // bytes per A matrix
+            const uint32_t b_mat = static_cast<uint32_t>(NH) * kKStage * 2;
+            const uint32_t a_base = smem_u32(smem), b_base = smem_u32(smem + sp.b_off);
+            const uint64_t dx0 = smem_desc(a_base + 0 * a_mat, 128, 256), dx1 = smem_desc(a_base + 1 * a_mat, 128, 256),
+                           dx2 = smem_desc(a_base + 2 * a_mat, 128, 256);
+            const uint64_t dh0 = smem_desc(b_base + 0 * b_mat, 128, 256), dh1 = smem_desc(b_base + 1 * b_mat, 128, 256),
+                           dh2 = smem_desc(b_base + 2 * b_mat, 128, 256), dh3 = smem_desc(b_base + 3 * b_mat, 128, 256);
+            const uint32_t a_step = static_cast<uint32_t>(sp.a_bytes >> 4), b_step = static_cast<uint32_t>(sp.b_bytes >> 4);
             int s = 0, sb = 0;
             uint32_t par = 0;
             bool ok = true;
@@ -686,19 +695,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a_mat = kTileM * kKStage * 2;            // bytes per A matrix
-                    const uint32_t b_mat = static_cast<uint32_t>(NH) * kKStage * 2;
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const uint32_t a0 = smem_u32(smem + (s + h) * sp.a_bytes);
-                        const uint32_t b0 = smem_u32(smem + sp.b_off + sb * sp.b_bytes);
-                        const uint64_t xhi = smem_desc(a0 + 0 * a_mat, 128, 256);
-                        const uint64_t xlo = smem_desc(a0 + 1 * a_mat, 128, 256);
-                        const uint64_t xsq = smem_desc(a0 + 2 * a_mat, 128, 256);
-                        const uint64_t hhi = smem_desc(b0 + 0 * b_mat, 128, 256);
-                        const uint64_t hlo = smem_desc(b0 + 1 * b_mat, 128, 256);
-                        const uint64_t gmat = smem_desc(b0 + 2 * b_mat, 128, 256);
-                        const uint64_t qmat = smem_desc(b0 + 3 * b_mat, 128, 256);
+                        // descriptors of A slot s + h and B slot sb: the slot-0 descriptors plus the
+                        // slot offset in 16-byte units (start-address field, bits 0-13; no carry:
+                        // shared addresses stay below 256 KB)
+                        const uint64_t da = static_cast<uint64_t>((s + h) * a_step);
+                        const uint64_t db = static_cast<uint64_t>(sb * b_step);
+                        const uint64_t xhi = dx0 + da, xlo = dx1 + da, xsq = dx2 + da;
+                        const uint64_t hhi = dh0 + db, hlo = dh1 + db, gmat = dh2 + db, qmat = dh3 + db;
                         const uint32_t acc = (ks > 0 || h > 0) ? 1u : 0u;
                         tc_mma(d_sig, xhi, hhi, idesc, acc);
                         tc_mma(d_sig, xlo, hhi, idesc, 1u);
