@@ -304,3 +304,22 @@ def test_full_size_ifu_sampled_rows():
     again = p.run(0, nt)
     torch.cuda.synchronize()
     assert torch.equal(out, again)                    # deterministic
+
+
+@pytest.mark.parametrize("n_ch", [150, 200, 400])
+def test_signal_parity_across_channel_groupings(n_ch):
+    """The fused kernel's channel grouping: <= 176 channels run on independent CTAs, 177-352 on
+    2-CTA clusters sharing the spectrum rows, more than 352 on independent CTAs per group of
+    <= 176 (each building the rows again)."""
+    def mutate(sc):
+        f_c = W.geometric_channels(sc["f_lo"], sc["f_hi"], n_ch)
+        sc["dispersive"] = dict(kind="filterbank", f_c=f_c, R=np.full(n_ch, 300.0), eta_peak=np.full(n_ch, 0.16))
+        A, alpha = W.pink_levels(n_ch, 11)
+        sc["noise"] = dict(sc["noise"], pink_A=A, pink_alpha=alpha)
+
+    sc, ref = oracle("single_pixel_small", 0, 260, mutate=mutate)
+    got, flags, _ = gpu_run(sc, "bf16x3", 0, 260)
+    err = rel_err(got, ref["p_kid"])
+    print(f"bf16x3 {n_ch} channels: max rel err {err:.3e}")
+    assert err < SIGNAL_TOL["bf16x3"]
+    assert flags & ~L.STATUS_PWV_CLAMPED == 0
