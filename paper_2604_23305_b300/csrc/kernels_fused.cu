@@ -682,6 +682,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t a_step = static_cast<uint32_t>(sp.a_bytes >> 4), b_step = static_cast<uint32_t>(sp.b_bytes >> 4);
             int s = 0, sb = 0;
             uint32_t par = 0;
+            long long n_pairs = 0;                                     // stage pairs committed
             bool ok = true;
             for (long long j = 0; j < my_items && ok; ++j) {
                 if (j > 0) {
@@ -715,6 +716,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (share) tc_commit_pair(empty_bar(s));   // A slots s, s+1 free in both CTAs
                     else tc_commit(empty_bar(s));              // A slots s, s+1 free once these MMAs finish
                     s += 2;
+                    ++n_pairs;
                     if (s == NS) { s = 0; par ^= 1u; }
                 }
                 if (!ok) break;
@@ -722,6 +724,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_commit(drain_bar);                     // no MMA in flight at exit (bounded)
             mbar_drain(drain_bar, 0);
+            // A shared tile's stage-free barriers also take the peer's commits, which travel over
+            // the cluster; nothing else waits for those of the last pairs.  Waiting here for each
+            // of the last pairs to complete (both commits in) leaves no arrival addressed to this
+            // CTA in flight when the cluster leaves.
+            if (share)
+                for (long long q = (n_pairs > NS / 2 ? n_pairs - NS / 2 : 0); q < n_pairs; ++q)
+                    mbar_drain(empty_bar(static_cast<int>((2 * q) % NS)), static_cast<uint32_t>(((2 * q) / NS) & 1));
         }
     } else if (warp >= kProdWarp0 && (share || warp < kEpiWarp0)) {
         // ---------------- spectrum producers ----------------
