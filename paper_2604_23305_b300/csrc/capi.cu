@@ -291,11 +291,7 @@ gateau_status finalize(gateau_plan* p) {
         const int n_half = ((n_ch + n_groups - 1) / n_groups + 15) / 16 * 16;
         std::vector<uint16_t> tiled;
         size_t stage_elems = 0;
-        // two groups run as MMA pairs, each CTA holding half of its group's filter columns:
-        // tile the operands in half-groups (half-group 2 g + t = columns [n_half/2 t, ...) of group g)
-        const int tile_split = n_groups == 2 ? 2 : 1;
-        fused_tile_operands(H.data(), G.data(), Q.data(), n_ch, Kp, n_half / tile_split, n_groups * tile_split,
-                            tiled, stage_elems);
+        fused_tile_operands(H.data(), G.data(), Q.data(), n_ch, Kp, n_half, n_groups, tiled, stage_elems);
         GATEAU_CUDA(grow(p, p->d_fusedB, tiled.size() * sizeof(uint16_t)));
         GATEAU_CUDA(cudaMemcpy(p->d_fusedB.p, tiled.data(), tiled.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
         p->fused.B = p->d_fusedB.as<uint16_t>();

@@ -179,18 +179,16 @@ struct SmemPlan {
     size_t a_bytes, b_bytes, b_off, in_off, bar_off, total;
 };
 
-// n_b: filter columns held per CTA (the channel group, or half of it when two CTAs share one MMA);
-// nsb_max: deepest B ring wanted.
-__host__ __device__ inline SmemPlan smem_plan(int n_b, int nsb_max) {
+__host__ __device__ inline SmemPlan smem_plan(int n_half) {
     SmemPlan p;
     p.a_bytes = static_cast<size_t>(kAMats) * kTileM * kKStage * 2;
-    p.b_bytes = static_cast<size_t>(kBMats) * n_b * kKStage * 2;
+    p.b_bytes = static_cast<size_t>(kBMats) * n_half * kKStage * 2;
     const size_t bar_reserve = 512;
     const size_t in_bytes = static_cast<size_t>(kInSlots) * kInSlotBytes;
     const long long avail = static_cast<long long>(kMaxSmem) - 1024 - bar_reserve - in_bytes;
     p.nsa = 0;
     p.nsb = 0;
-    for (int nsb = nsb_max; nsb >= 2; --nsb) {
+    for (int nsb = 4; nsb >= 2; --nsb) {
         long long nsa = (avail - static_cast<long long>(nsb) * p.b_bytes) / static_cast<long long>(p.a_bytes);
         if (nsa > 8) nsa = 8;
         nsa &= ~1LL;                               // whole stage pairs
@@ -207,7 +205,7 @@ __host__ __device__ inline SmemPlan smem_plan(int n_b, int nsb_max) {
     return p;
 }
 
-size_t fused_smem_bytes() { return smem_plan(176, 4).total; }
+size_t fused_smem_bytes() { return smem_plan(176).total; }
 
 // ---- PTX wrappers ------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -334,70 +332,6 @@ __device__ __forceinline__ void bulk_s2peer(uint32_t dst_cluster, uint32_t src_c
         : "memory");
 }
 
-// Arrival on a barrier of another CTA of the cluster (shared::cluster address).
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
-}
-
-// ---- tcgen05 with one CTA (CG = 1) or a CTA pair (CG = 2) per MMA ----
-// All tcgen05 instructions of one kernel use the same CTA group.  With CG = 2 the two CTAs of a
-// pair (cluster ranks 2p, 2p + 1) allocate tensor memory together, the even one issues the MMAs
-// (M = 256: rows 0-127 from its shared memory, 128-255 from its peer's, each holding half of the
-// B columns) and each CTA's tensor memory receives its 128 rows of D.
-template <int CG>
-__device__ __forceinline__ void tcg_alloc512(uint32_t slot) {
-    if constexpr (CG == 2)
-        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(slot) : "memory");
-    else
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(slot) : "memory");
-}
-template <int CG>
-__device__ __forceinline__ void tcg_relinquish() {
-    if constexpr (CG == 2)
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
-    else
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-template <int CG>
-__device__ __forceinline__ void tcg_dealloc512(uint32_t taddr) {
-    if constexpr (CG == 2)
-        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;" ::"r"(taddr) : "memory");
-    else
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(taddr) : "memory");
-}
-// Commit arriving on the barrier at the same offset in each CTA of `mask` (cluster ranks).
-template <int CG>
-__device__ __forceinline__ void tcg_commit_mc(uint32_t bar, uint16_t mask) {
-    if constexpr (CG == 2)
-        asm volatile(
-            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                bar),
-            "h"(mask)
-            : "memory");
-    else
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                bar),
-            "h"(mask)
-            : "memory");
-}
-template <int CG>
-__device__ __forceinline__ void tcg_mma(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                        uint32_t accumulate) {
-    if constexpr (CG == 2)
-        asm volatile(
-            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-            "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-            : "memory");
-    else
-        asm volatile(
-            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-            "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-            : "memory");
-}
-
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -439,13 +373,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     return d;                           // base offset 0, swizzle mode 0 (none)
 }
 
-// Instruction descriptor: kind::f16, A = B = bf16, D = f32, both K-major, M = 128 or 256.
-__host__ __device__ constexpr uint32_t make_idesc(int n, int m) {
+// Instruction descriptor: kind::f16, A = B = bf16, D = f32, both K-major, M = 128.
+__host__ __device__ constexpr uint32_t make_idesc(int n) {
     return (1u << 4)                                  // D format f32
            | (1u << 7)                                // A format bf16
            | (1u << 10)                               // B format bf16
            | (static_cast<uint32_t>(n >> 3) << 17)    // N / 8
-           | (static_cast<uint32_t>(m >> 4) << 24);   // M / 16
+           | (static_cast<uint32_t>(kTileM >> 4) << 24);  // M / 16
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
@@ -480,9 +414,6 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // ---- work decomposition ------------------------------------------------------
 // share = 1: the two channel groups of a tile run on the two CTAs of a cluster,
 // each building half of the tile's spectrum rows and copying it to the peer.
-// share = 2: 4-CTA clusters, cluster rank = 2 group + t, over two consecutive tiles (t = 0, 1).
-// The two CTAs of a channel group form an MMA pair (M = 256: both tiles' rows, half of the
-// group's filter columns in each CTA); the two CTAs of a tile share its rows as with share = 1.
 struct Work {
     long long tiles_per_pix, n_items;
     int share;
@@ -508,10 +439,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         float* __restrict__ out) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    constexpr bool mma2 = kShare == 2;           // MMA pairs (cta_group::2) in 4-CTA clusters
-    constexpr int CG = mma2 ? 2 : 1;
     const int NH = F.n_half;
-    const SmemPlan sp = mma2 ? smem_plan(NH / 2, 8) : smem_plan(NH, 4);
+    const SmemPlan sp = smem_plan(NH);
     const int NS = sp.nsa;                       // A-ring depth
     const int NSB = sp.nsb;                      // B-ring depth
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + sp.bar_off);
@@ -531,23 +460,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t drain_bar = bar_base + 8u * (nb + 2);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + sp.bar_off + 8 * (nb + 3));
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + sp.bar_off + 8 * (nb + 3) + 8);
-    // MMA pairs: the leader's "both CTAs' operands of this stage pair are in place" barrier, one
-    // arrival from the peer's relay thread per stage pair
-    auto pair_full = [&](int s) { return bar_base + 8u * (nb + 5 + (s >> 1)); };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int share = kShare >= 1 ? 1 : 0;   // the rows of a tile are built by two CTAs
-    const uint32_t crank = share ? cluster_rank() : 0u;
-    // rank: which half of the tile's rows this CTA builds (and its channel group)
-    const uint32_t rank = mma2 ? (crank >> 1) : crank;
-    const uint32_t row_peer = mma2 ? (crank ^ 2u) : (crank ^ 1u);   // the CTA with the other half of the rows
-    const uint32_t mma_peer = crank ^ 1u;                            // mma2: the other CTA of the MMA pair
-    const bool leader = !mma2 || (crank & 1u) == 0;                  // issues the MMAs
-    // commit targets: stage-pair slots free in every CTA that reads or writes them; accumulators
-    // ready in the MMA pair; a local-only signal
-    const uint16_t mask_all = mma2 ? 0xF : 0x3;
-    const uint16_t mask_pair = static_cast<uint16_t>(mma2 ? (0x3u << (crank & ~1u)) : (1u << crank));
-    const uint16_t mask_self = static_cast<uint16_t>(1u << crank);
+    constexpr int share = kShare;
+    const uint32_t rank = share ? cluster_rank() : 0u;
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; s += 2) {
             // per stage of the pair: the operand copy's arrival (its bytes and, for a shared tile,
@@ -562,17 +478,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(empty_in(s), share ? kProdWarps / 2 : kProdWarps);
         }
         mbar_init(acc_full, 1);
-        // the epilogue warps and the producer warps (of both CTAs of an MMA pair, at its leader)
-        mbar_init(acc_empty, (mma2 ? 2 : 1) * (4 + kProdWarps));
+        mbar_init(acc_empty, 4 + kProdWarps);   // the epilogue warps and the producer warps
         mbar_init(drain_bar, 1);
-        if (mma2)
-            for (int s = 0; s < NS; s += 2) mbar_init(pair_full(s), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {   // CG = 2: both CTAs of the MMA pair allocate together
-        tcg_alloc512<CG>(smem_u32(tmem_slot));
-        tcg_relinquish<CG>();
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
@@ -583,28 +497,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t d_noi = tmem_base + 256;      // columns [256, 256 + NH)
 
     const int n_ks = T.Kp / kKStage;
-    // Work units: tiles shared by a cluster, pairs of tiles for 4-CTA clusters, or (tile, group)
-    // items for independent CTAs.
-    const long long n_tiles = work.n_items / (share ? 2 : 1);
-    const int csize = mma2 ? 4 : (share ? 2 : 1);
-    const long long n_units = mma2 ? (n_tiles + 1) / 2 : (share ? n_tiles : work.n_items);
-    const long long ubase = blockIdx.x / csize;
-    const long long ustride = gridDim.x / csize;
+    // Work units: tiles shared by a cluster, or (tile, group) items for independent CTAs.
+    const long long n_units = share ? work.n_items / 2 : work.n_items;
+    const long long ubase = share ? blockIdx.x / 2 : blockIdx.x;
+    const long long ustride = share ? gridDim.x / 2 : gridDim.x;
     const long long my_items = n_units > ubase ? (n_units - ubase + ustride - 1) / ustride : 0;
-    // This CTA's item j: its tile (pixel, first sample, rows) and channel group.  With 4-CTA
-    // clusters an odd tile count leaves the last unit's second tile empty: it takes the previous
-    // tile's coordinates with no rows, so every role runs the same stages and writes nothing.
-    auto coords = [&](long long j, long long& tile, int& pix, long long& row0, int& nrows, int& grp) {
+    auto item_of = [&](long long j) {
         const long long u = ubase + j * ustride;
-        if (mma2) {
-            long long tl = 2 * u + (crank & 1u);
-            const bool empty = tl >= n_tiles;
-            if (empty) tl = n_tiles - 1;
-            item_coords(work, F.n_groups, tl * 2 + rank, tile, pix, row0, nrows, grp, nt);
-            if (empty) nrows = 0;
-        } else {
-            item_coords(work, F.n_groups, share ? u * 2 + rank : u, tile, pix, row0, nrows, grp, nt);
-        }
+        return share ? u * 2 + rank : u;
     };
 
     // ---------------- epilogue of one item: this warp's share of the channel chunks ----------------
@@ -624,9 +524,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const int quad = warp & 3;
         const int r = quad * 32 + lane;
+        const long long it = item_of(j);
         long long tile, row0;
         int pix, nrows, grp;
-        coords(j, tile, pix, row0, nrows, grp);
+        item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
         const long long n = t0 + row0 + r;
         float* orow = out + ((row0 + r) * T.n_pix + pix) * static_cast<long long>(T.n_ch);
         const int ch_base = grp * NH;
@@ -657,10 +558,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) {   // one arrival per epilogue-sharing warp, at the CTA that issues the MMAs
-            if (leader) mbar_arrive(acc_empty);
-            else mbar_arrive_cluster(mapa_peer(acc_empty, mma_peer));
-        }
+        if (lane == 0) mbar_arrive(acc_empty);   // one arrival per epilogue-sharing warp
         return true;
     };
 
@@ -680,13 +578,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             // a shared tile also receives the peer's half of the rows (3 matrices x 64 rows x 16 points)
             const uint32_t expect = bytes + (share ? static_cast<uint32_t>(kAMats * kTileM * kKStage) : 0u);
             for (long long j = 0; j < my_items && !*abort_flag; ++j) {
-                long long tile, row0;
-                int pix, nrows, grp;
-                coords(j, tile, pix, row0, nrows, grp);
-                // MMA pairs: this CTA holds filter columns [NH/2 t, NH/2 t + NH/2) of its group,
-                // tiled on the host as half-groups 2 grp + t
-                const int bgrp = mma2 ? 2 * grp + static_cast<int>(crank & 1u) : grp;
-                const uint16_t* src = F.B + static_cast<size_t>(bgrp) * n_ks * F.stage_elems;
+                const long long it = item_of(j);
+                const int grp = static_cast<int>(it % F.n_groups);
+                const uint16_t* src = F.B + static_cast<size_t>(grp) * n_ks * F.stage_elems;
                 bool ok = true;
                 for (int ks = 0; ks < n_ks; ++ks) {
                     if (g >= NSB) {
@@ -715,9 +609,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             int s = 0;
             uint32_t ph = 0;
             for (long long j = 0; j < my_items && !*abort_flag; ++j) {
+                const long long it = item_of(j);
                 long long tile, row0;
                 int pix, nrows, grp;
-                coords(j, tile, pix, row0, nrows, grp);
+                item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
                 const TileInfo ti = tiles[tile];
                 const bool tau_box = F.tma_inputs && (ti.flags & TILE_TAU_FITS);
                 const bool cube_box = F.tma_inputs && (ti.flags & TILE_CUBE_FITS);
@@ -750,7 +645,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // shared memory, completing on the peer's stage-full barrier, then arrives on ours.
         if (share && lane == 0) {
             constexpr uint32_t amat = kTileM * kKStage * 2;
-            const uint32_t peer = row_peer;
+            const uint32_t peer = rank ^ 1u;
             int s = 0;
             uint32_t par = 0;
             bool ok = true;
@@ -773,36 +668,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else if (warp == 1) {
-        if (lane == 0 && !leader) {
-            // ---------------- MMA pair, odd CTA: relay ----------------
-            // The leader cannot wait on this CTA's barriers: once a stage pair's operands are in
-            // place here (B half, own rows, the row peer's rows), tell it.
-            int s = 0;
-            uint32_t par = 0;
-            long long n_pairs = 0;
-            bool ok = true;
-            for (long long j = 0; j < my_items && ok; ++j)
-                for (int ks = 0; ks < n_ks; ks += 2) {
-                    if (!mbar_wait(full_a(s), par, abort_flag, T.status)) {
-                        ok = false;
-                        break;
-                    }
-                    mbar_arrive_cluster(mapa_peer(pair_full(s), mma_peer));
-                    s += 2;
-                    ++n_pairs;
-                    if (s == NS) { s = 0; par ^= 1u; }
-                }
-            // both leaders' commits of the last stage pairs land here before the cluster leaves
-            for (long long q = (n_pairs > NS / 2 ? n_pairs - NS / 2 : 0); q < n_pairs; ++q)
-                mbar_drain(empty_bar(static_cast<int>((2 * q) % NS)), static_cast<uint32_t>(((2 * q) / NS) & 1));
-        } else if (lane == 0) {
-            // ---------------- MMA issuer ----------------
-            // MMA pairs: M = 256 (this CTA's tile rows, then the peer's), N = NH with NH/2 filter
-            // columns in each CTA's B slot.
-            const uint32_t idesc = make_idesc(NH, mma2 ? 2 * kTileM : kTileM);
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = make_idesc(NH);
             // slot-0 descriptors and the per-slot steps of the start-address field
             const uint32_t a_mat = kTileM * kKStage * 2;                // bytes per A matrix
-            const uint32_t b_mat = static_cast<uint32_t>(mma2 ? NH / 2 : NH) * kKStage * 2;
+            const uint32_t b_mat = static_cast<uint32_t>(NH) * kKStage * 2;
             const uint32_t a_base = smem_u32(smem), b_base = smem_u32(smem + sp.b_off);
             const uint64_t dx0 = smem_desc(a_base + 0 * a_mat, 128, 256), dx1 = smem_desc(a_base + 1 * a_mat, 128, 256),
                            dx2 = smem_desc(a_base + 2 * a_mat, 128, 256);
@@ -820,8 +691,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_after();
                 }
                 for (int ks = 0; ks < n_ks; ks += 2) {               // n_ks is even (Kp % 32 == 0)
-                    if (!mbar_wait(full_a(s), par, abort_flag, T.status) ||
-                        (mma2 && !mbar_wait(pair_full(s), par, abort_flag, T.status))) {
+                    if (!mbar_wait(full_a(s), par, abort_flag, T.status)) {
                         ok = false;
                         break;
                     }
@@ -836,31 +706,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const uint64_t xhi = dx0 + da, xlo = dx1 + da, xsq = dx2 + da;
                         const uint64_t hhi = dh0 + db, hlo = dh1 + db, gmat = dh2 + db, qmat = dh3 + db;
                         const uint32_t acc = (ks > 0 || h > 0) ? 1u : 0u;
-                        tcg_mma<CG>(d_sig, xhi, hhi, idesc, acc);
-                        tcg_mma<CG>(d_sig, xlo, hhi, idesc, 1u);
-                        tcg_mma<CG>(d_sig, xhi, hlo, idesc, 1u);
-                        tcg_mma<CG>(d_noi, xhi, gmat, idesc, acc);
-                        tcg_mma<CG>(d_noi, xsq, qmat, idesc, 1u);
+                        tc_mma(d_sig, xhi, hhi, idesc, acc);
+                        tc_mma(d_sig, xlo, hhi, idesc, 1u);
+                        tc_mma(d_sig, xhi, hlo, idesc, 1u);
+                        tc_mma(d_noi, xhi, gmat, idesc, acc);
+                        tc_mma(d_noi, xsq, qmat, idesc, 1u);
                         if (++sb == NSB) sb = 0;
                     }
-                    // A slots s, s+1 free: in both CTAs of a shared tile, in all four CTAs of an
-                    // MMA-pair cluster (the row peers write into each other's slots)
-                    if (share) tcg_commit_mc<CG>(empty_bar(s), mask_all);
+                    if (share) tc_commit_pair(empty_bar(s));   // A slots s, s+1 free in both CTAs
                     else tc_commit(empty_bar(s));              // A slots s, s+1 free once these MMAs finish
                     s += 2;
                     ++n_pairs;
                     if (s == NS) { s = 0; par ^= 1u; }
                 }
                 if (!ok) break;
-                // accumulators of item j complete (in both CTAs of an MMA pair)
-                if (mma2) tcg_commit_mc<CG>(acc_full, mask_pair);
-                else tc_commit(acc_full);
+                tc_commit(acc_full);                  // accumulators of item j complete
             }
-            if (mma2) tcg_commit_mc<CG>(drain_bar, mask_self);   // no MMA in flight at exit (bounded)
-            else tc_commit(drain_bar);
+            tc_commit(drain_bar);                     // no MMA in flight at exit (bounded)
             mbar_drain(drain_bar, 0);
-            // MMA pairs: the peer's epilogue arrivals of the last item land here before we leave
-            if (mma2 && my_items > 0) mbar_drain(acc_empty, static_cast<uint32_t>((my_items - 1) & 1));
             // A shared tile's stage-free barriers also take the peer's commits, which travel over
             // the cluster; nothing else waits for those of the last pairs.  Waiting here for each
             // of the last pairs to complete (both commits in) leaves no arrival addressed to this
@@ -903,9 +766,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             // row constants of item j
             RowC rc[2];
             {
+                const long long it = item_of(j);
                 long long tile, row0;
                 int pix, nrows, grp;
-                coords(j, tile, pix, row0, nrows, grp);
+                item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
                 const TileInfo ti = tiles[tile];
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
@@ -1060,24 +924,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     if (warp == 1) {
         __syncwarp();
-        tcg_dealloc512<CG>(tmem_base);
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
     }
 }
 
 cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, const TensorMapBytes& tm_tau,
                                 const TensorMapBytes& tm_cube, const RowParams* rows, const TileInfo* tiles,
                                 long long t0, long long nt, float* out, int n_sm, cudaStream_t stream) {
-    // Two channel groups: 4-CTA clusters of two MMA pairs (the filter operands are tiled in
-    // half-groups on the host); otherwise one CTA per (tile, group) item.
-    const bool mma2 = F.n_groups == 2;
-    const SmemPlan sp = mma2 ? smem_plan(F.n_half / 2, 8) : smem_plan(F.n_half, 4);
+    const SmemPlan sp = smem_plan(F.n_half);
     if (sp.nsb < 2) return cudaErrorInvalidConfiguration;
     Work w;
     w.tiles_per_pix = (nt + kTileM - 1) / kTileM;
     w.n_items = w.tiles_per_pix * T.n_pix * F.n_groups;
-    w.share = mma2 ? 2 : 0;
+    w.share = F.n_groups == 2 ? 1 : 0;
     if (w.n_items == 0) return cudaSuccess;
-    auto kernel = mma2 ? fused_bf16x3_kernel<2> : fused_bf16x3_kernel<0>;
+    auto kernel = w.share ? fused_bf16x3_kernel<1> : fused_bf16x3_kernel<0>;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(sp.total));
     if (e != cudaSuccess) return e;
@@ -1090,20 +951,20 @@ cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, cons
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     long long grid;
-    if (mma2) {
+    if (w.share) {
         attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 4;
+        attr[0].val.clusterDim.x = 2;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cfg.gridDim = dim3(static_cast<unsigned>(n_sm / 4 * 4));
+        cfg.gridDim = dim3(static_cast<unsigned>(n_sm / 2 * 2));
         int max_clusters = 0;
         e = cudaOccupancyMaxActiveClusters(&max_clusters, kernel, &cfg);
         if (e != cudaSuccess) return e;
         if (max_clusters < 1) return cudaErrorInvalidConfiguration;
-        const long long units = (w.n_items / 2 + 1) / 2;     // pairs of tiles
-        grid = 4 * (units < max_clusters ? units : max_clusters);
+        const long long tiles = w.n_items / 2;
+        grid = 2 * (tiles < max_clusters ? tiles : max_clusters);
     } else {
         cfg.attrs = nullptr;
         cfg.numAttrs = 0;

@@ -309,9 +309,8 @@ def test_full_size_ifu_sampled_rows():
 @pytest.mark.parametrize("n_ch", [150, 200, 400])
 def test_signal_parity_across_channel_groupings(n_ch):
     """The fused kernel's channel grouping: <= 176 channels run on independent CTAs, 177-352 on
-    4-CTA clusters (two MMA pairs over two tiles, the rows of a tile shared by its two channel
-    groups; 260 samples = 3 tiles leave the second pair tile empty), more than 352 on independent
-    CTAs per group of <= 176 (each building the rows again)."""
+    2-CTA clusters sharing the spectrum rows, more than 352 on independent CTAs per group of
+    <= 176 (each building the rows again)."""
     def mutate(sc):
         f_c = W.geometric_channels(sc["f_lo"], sc["f_hi"], n_ch)
         sc["dispersive"] = dict(kind="filterbank", f_c=f_c, R=np.full(n_ch, 300.0), eta_peak=np.full(n_ch, 0.16))
