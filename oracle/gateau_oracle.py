@@ -21,6 +21,7 @@ float64, stage by stage, with no algebraic collapse, blocking or fusion:
   * photon noise                   -- Sect. 2.6, Eqs. 17-19
   * pink noise                     -- Sect. 2.6, Eq. 20 (pole-zero IIR reading)
   * total                          -- Sect. 2.7, Eq. 21
+  * brightness-temperature output  -- Sect. 2.7 (simulated skydip, linear P -> T_b map)
 
 Readings of points the paper leaves silent or garbled (each also listed in the
 design notes of the repository):
@@ -49,6 +50,14 @@ design notes of the repository):
     f_min*10^(j/3) (3 per decade, up to f_s/2), zeros a factor 10^(alpha/6)
     above each pole, matched-z mapping, gain set so that the one-sided PSD at
     1 Hz equals A, zero state at the first sample of the scan (n = 0).
+  * Skydip (Sect. 2.7): the PWV is varied over n uniformly spaced zenith values
+    pwv_lo .. pwv_hi at the scan's base elevation theta_0, with no source and
+    no noise (the recorded power is the noise-free P_KID, the mean of
+    P_tot).  T_b of a channel is the line-of-sight brightness temperature of
+    the isothermal atmosphere, T_atm (1 - eta_atm), averaged over the band
+    with the channel's weights eta_filt * w.  The map T_b = a P + b is the
+    ordinary least-squares line through the n points, and it is applied to
+    the total power P_tot of every sample.
 """
 from __future__ import annotations
 
@@ -614,11 +623,44 @@ def row_geometry(sc: dict, n: np.ndarray, pix: np.ndarray):
     return t, az, el, pwv
 
 
+def skydip_calibration(sc: dict, inst: Instrument | None = None, pwv_lo: float = 0.5, pwv_hi: float = 2.0,
+                       n_pwv: int = 16):
+    """Per-channel brightness-temperature scale from a simulated skydip (Sect. 2.7).
+
+    The zenith PWV takes n_pwv uniformly spaced values pwv_lo .. pwv_hi (mm) at the base
+    elevation theta_0 of the scan, with no source; for each value the cascade gives P_nu,
+    the channel powers P_KID (Eq. 16) and the band-averaged sky brightness temperature
+    T_b = T_atm sum_nu eta_filt w (1 - eta_atm) / sum_nu eta_filt w.  Returns
+    dict(a, b, pwv, p_kid, t_b) with the least-squares line T_b = a P_KID + b per channel.
+    """
+    if inst is None:
+        inst = build_instrument(sc)
+    atm = sc["atmosphere"]
+    pwv = np.linspace(pwv_lo, pwv_hi, n_pwv, dtype=F64)
+    el = np.full(n_pwv, sc["scan"]["theta0"], dtype=F64)
+    tau_z = zenith_opacity(opacity_table(sc), atm["pwv_min"], atm["dpwv"], pwv)
+    eta_atm = atmospheric_transmission(tau_z, el)                        # [n_pwv, nu]
+    P_src = np.zeros_like(eta_atm)
+    P = cascade(P_src, eta_atm, inst.nu, inst.prim, atm["T_atm"], sc["T_cmb"],
+                sc["eta_taper"], inst.eta_surf, sc["eta_pol"])
+    p_kid = kid_power(inst.eta_filt, inst.w, P)                          # [n_pwv, ch]
+    hw = inst.eta_filt * inst.w                                           # [ch, nu]
+    t_b = atm["T_atm"] * ((1.0 - eta_atm) @ hw.T) / hw.sum(axis=1)       # [n_pwv, ch]
+    # ordinary least squares per channel: a = cov(P, T) / var(P), b = mean(T) - a mean(P)
+    dp = p_kid - p_kid.mean(axis=0)
+    dt = t_b - t_b.mean(axis=0)
+    a = (dp * dt).sum(axis=0) / (dp * dp).sum(axis=0)
+    b = t_b.mean(axis=0) - a * p_kid.mean(axis=0)
+    return dict(a=a, b=b, pwv=pwv, p_kid=p_kid, t_b=t_b)
+
+
 def simulate(sc: dict, t0: int, nt: int, inst: Instrument | None = None,
-             white: bool = True, pink: bool = True, pink_state=None, return_parts: bool = False):
+             white: bool = True, pink: bool = True, pink_state=None, return_parts: bool = False,
+             kelvin: dict | None = None):
     """TOD out[n - t0, i, ch] in W for samples n in [t0, t0 + nt), all spaxels (Eq. 21).
 
     pink_state [n_pix, n_ch, n_pole] is the filter state before sample t0 (zeros at t0 = 0).
+    kelvin: the result of skydip_calibration; the TOD is then a P_tot + b in K (Sect. 2.7).
     """
     if inst is None:
         inst = build_instrument(sc)
@@ -666,6 +708,8 @@ def simulate(sc: dict, t0: int, nt: int, inst: Instrument | None = None,
             p_pn[:, :, ch] = y
             new_state[:, ch, :] = s
     total = p_kid + p_wn + p_pn                                           # Eq. 21
+    if kelvin is not None:
+        total = kelvin["a"] * total + kelvin["b"]                        # brightness scale (Sect. 2.7)
     if return_parts:
         return dict(total=total, p_kid=p_kid, p_wn=p_wn, p_pn=p_pn, sigma=sigma,
                     pwv=pwv.reshape(nt, n_pix), el=el.reshape(nt, n_pix), pink_state=new_state)

@@ -451,3 +451,79 @@ def test_hex_layout_geometry():
         key = lambda a: set(map(tuple, np.round(a, 9)))
         assert key(off) == key(-off)
     assert O.hex_offsets(3, 1.0).shape[0] == 37
+
+
+# ---------------------------------------------------------------- skydip / brightness temperature (Sect. 2.7)
+
+def _planck_mode(T, nu):
+    """Single-mode thermal power spectral density h nu / (exp(h nu / k T) - 1), written out."""
+    return np.array([H * v / math.expm1(H * v / (KB * T)) for v in np.atleast_1d(nu)])
+
+
+def test_skydip_single_point_channel_closed_form():
+    """A channel that sees one grid frequency nu_0 (weight H w) behind the atmosphere alone:
+    P = H w [B_cmb + (1 - eta)(B_atm - B_cmb)] and T_b = T_atm (1 - eta), so the skydip line is
+    exactly T_b = a P + b with a = T_atm / (H w (B_atm - B_cmb)), b = -T_atm B_cmb / (B_atm - B_cmb)."""
+    sc = W.scenario("single_pixel_small", nt_total=16)
+    sc["cascade"] = []
+    inst = O.build_instrument(sc)
+    k0 = inst.nu.size // 3
+    Hk = 0.37
+    eta = np.zeros((1, inst.nu.size))
+    eta[0, k0] = Hk
+    inst.eta_filt = eta
+    cal = O.skydip_calibration(sc, inst, 0.2, 3.0, 12)
+    T_atm = sc["atmosphere"]["T_atm"]
+    b_atm = _planck_mode(T_atm, inst.nu[k0])[0]
+    b_cmb = _planck_mode(sc["T_cmb"], inst.nu[k0])[0]
+    a_want = T_atm / (Hk * inst.w[k0] * (b_atm - b_cmb))
+    b_want = -T_atm * b_cmb / (b_atm - b_cmb)
+    np.testing.assert_allclose(cal["a"], [a_want], rtol=1e-10)
+    np.testing.assert_allclose(cal["b"], [b_want], rtol=1e-8, atol=1e-12)
+    # the brightness temperatures are those of the swept PWVs at the base elevation
+    tau = O.zenith_opacity(np.asarray(sc["atmosphere"]["table"], dtype=float), sc["atmosphere"]["pwv_min"],
+                           sc["atmosphere"]["dpwv"], cal["pwv"])[:, k0]
+    eta_atm = np.exp(-tau / math.sin(sc["scan"]["theta0"]))
+    np.testing.assert_allclose(cal["t_b"][:, 0], T_atm * (1 - eta_atm), rtol=1e-12)
+
+
+def test_skydip_rayleigh_jeans_band_limit():
+    """At h nu << k T the sky-coupled power of any band is k_B T_b sum(eta_filt w): with the
+    atmosphere alone and no CMB, the skydip gives a = 1 / (k_B sum eta_filt w), b = 0, to the
+    Rayleigh-Jeans accuracy h nu / 2 k T (~2e-4 at 1-2 GHz and 273 K)."""
+    sc = W.scenario("single_pixel_small", nt_total=16)
+    n_f = 256
+    sc.update(f_lo=1.0e9, f_hi=2.0e9, n_freq=n_f, delta_al=0.0, T_cmb=0.0, cascade=[])
+    f_c = np.linspace(1.2e9, 1.8e9, 5)
+    sc["dispersive"] = dict(kind="filterbank", f_c=f_c, R=np.full(5, 40.0), eta_peak=np.full(5, 0.5))
+    pw = np.arange(501) * 0.01
+    sc["atmosphere"].update(table=(0.05 + 0.3 * pw)[:, None] * np.linspace(0.8, 1.2, n_f)[None, :],
+                            table_is_opacity=True, pwv_min=0.0, dpwv=0.01)
+    inst = O.build_instrument(sc)
+    cal = O.skydip_calibration(sc, inst, 0.2, 3.0, 10)
+    hw = (inst.eta_filt * inst.w).sum(axis=1)
+    np.testing.assert_allclose(cal["a"], 1.0 / (KB * hw), rtol=5e-4)
+    assert np.all(np.abs(cal["b"]) < 5e-4 * cal["t_b"].max())
+
+
+def test_skydip_fit_is_the_least_squares_line():
+    """The fitted (a, b) per channel equal numpy's degree-1 polynomial fit of T_b on P_KID, and
+    the standard cascade's response is affine in T_b to well under a millikelvin per kelvin."""
+    sc = W.scenario("single_pixel_small", nt_total=16)
+    cal = O.skydip_calibration(sc, None, 0.4, 2.4, 16)
+    for ch in range(0, cal["a"].size, 7):
+        x = cal["p_kid"][:, ch] / cal["p_kid"][:, ch].mean()           # scaled for a well-posed fit
+        slope, icpt = np.polyfit(x, cal["t_b"][:, ch], 1)
+        np.testing.assert_allclose(cal["a"][ch], slope / cal["p_kid"][:, ch].mean(), rtol=1e-9)
+        np.testing.assert_allclose(cal["b"][ch], icpt, rtol=1e-9, atol=1e-9)
+    resid = cal["t_b"] - (cal["a"] * cal["p_kid"] + cal["b"])
+    span = cal["t_b"].max(axis=0) - cal["t_b"].min(axis=0)
+    assert np.all(np.abs(resid).max(axis=0) < 1e-3 * np.maximum(span, 1.0))
+
+
+def test_kelvin_output_is_the_affine_map_of_the_total_power():
+    sc = W.scenario("single_pixel_small", nt_total=40)
+    cal = O.skydip_calibration(sc)
+    w = O.simulate(sc, 0, 40)
+    k = O.simulate(sc, 0, 40, kelvin=cal)
+    np.testing.assert_allclose(k, cal["a"] * w + cal["b"], rtol=1e-14)
