@@ -153,7 +153,9 @@ enum {
     GATEAU_VEC_C2 = 5,             /* [n_freq] coefficient of eta_atm * P_src                   */
     GATEAU_VEC_PINK_A = 6,         /* [n_ch][n_pole] discrete poles a_j                         */
     GATEAU_VEC_PINK_R = 7,         /* [n_ch][n_pole] residues r_j (gain folded in)              */
-    GATEAU_VEC_PINK_D = 8          /* [n_ch] direct term d (gain folded in)                     */
+    GATEAU_VEC_PINK_D = 8,         /* [n_ch] direct term d (gain folded in)                     */
+    GATEAU_VEC_TB_A = 9,           /* [n_ch] skydip scale a (K/W), see gateau_set_output_kelvin  */
+    GATEAU_VEC_TB_B = 10           /* [n_ch] skydip offset b (K)                                */
 };
 
 /* Library version string and the calling thread's last error message. */
@@ -226,8 +228,22 @@ gateau_status gateau_set_scan(gateau_plan* plan, int kind, const double* params,
                               double phi0_rad, double theta0_rad, const double* custom,
                               long long n_custom, int mem);
 
+/* Output units (Sect. 2.7).  enable = 0 (the default): detected power P_tot in W.
+ * enable != 0: brightness temperature in K by a simulated skydip.  When the plan
+ * is prepared, the device sweeps the zenith PWV over n_pwv uniformly spaced
+ * values pwv_lo_mm .. pwv_hi_mm (both included) at the scan's base elevation
+ * theta0 with no source and no noise, and for every channel records P_KID
+ * (Eq. 16) and the band-averaged line-of-sight brightness temperature of the
+ * isothermal atmosphere, T_b = T_atm sum eta_filt w (1 - eta_atm) / sum
+ * eta_filt w; the least-squares line T_b = a P_KID + b (FP64) then maps every
+ * output sample: out = a P_tot + b (gateau_plan_get_vector GATEAU_VEC_TB_A/B
+ * after gateau_plan_prepare).  A channel whose power does not change over the
+ * sweep gets a = 0.  Needs the table and scan before the plan is prepared.
+ * EINVAL unless 0 <= pwv_lo < pwv_hi and 2 <= n_pwv <= 64. */
+gateau_status gateau_set_output_kelvin(gateau_plan* plan, int enable, double pwv_lo_mm, double pwv_hi_mm, int n_pwv);
+
 /* Simulate samples n = t0 .. t0+nt-1 for all spaxels into dev_out
- * [nt][n_pix][n_ch] float32 (W), device memory owned by the caller.  Enqueued
+ * [nt][n_pix][n_ch] float32 (W, or K with gateau_set_output_kelvin), device memory owned by the caller.  Enqueued
  * on `stream` (a cudaStream_t, NULL = legacy default stream); returns without
  * synchronising.  t0 must be 0 (restarts the pink-noise state) or the end of
  * the previous chunk (EORDER otherwise), so a scan may be produced in chunks

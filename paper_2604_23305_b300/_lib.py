@@ -16,7 +16,7 @@ STAGE_REFLECTIVE, STAGE_OHMIC, STAGE_REFRACTIVE = 0, 1, 2
 T_SKY = -1.0
 NOISE_WHITE, NOISE_PINK = 1, 2
 STATUS_PWV_CLAMPED, STATUS_WAIT_TIMEOUT, STATUS_BAD_INDEX = 1, 2, 4
-VEC_NU, VEC_WEIGHT, VEC_ETA_FILT, VEC_C0, VEC_C1, VEC_C2, VEC_PINK_A, VEC_PINK_R, VEC_PINK_D = range(9)
+VEC_NU, VEC_WEIGHT, VEC_ETA_FILT, VEC_C0, VEC_C1, VEC_C2, VEC_PINK_A, VEC_PINK_R, VEC_PINK_D, VEC_TB_A, VEC_TB_B = range(11)
 PHASE_ROWS, PHASE_SPECTRUM, PHASE_CONTRACT, PHASE_PINK, PHASE_COUNT = 0, 1, 2, 3, 4
 
 _STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EORDER: "EORDER",
@@ -92,6 +92,7 @@ SIGNATURES = {
     "gateau_set_scan": (C.c_int, [PlanP, C.c_int, dp, C.c_int, C.c_double, C.c_double, C.c_void_p,
                                   C.c_longlong, C.c_int]),
     "gateau_plan_prepare": (C.c_int, [PlanP]),
+    "gateau_set_output_kelvin": (C.c_int, [PlanP, C.c_int, C.c_double, C.c_double, C.c_int]),
     "gateau_run": (C.c_int, [PlanP, C.c_longlong, C.c_longlong, C.c_void_p, C.c_void_p]),
     "gateau_run_host": (C.c_int, [PlanP, C.c_longlong, C.c_longlong, C.c_void_p, C.c_void_p]),
     "gateau_run_batch": (C.c_int, [C.POINTER(PlanP), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),

@@ -135,6 +135,12 @@ struct gateau_plan {
     double phi0 = 0, theta0 = 0;
     long long n_custom = 0;
 
+    // brightness-temperature output (gateau_set_output_kelvin)
+    bool kelvin = false;
+    double dip_lo = 0, dip_hi = 0;
+    int dip_n = 0;
+    std::vector<double> tb_a, tb_b;  // the skydip fit, read back from the device
+
     // derived host tables
     std::vector<double> c0, c1, c2;
     int n_pole = 0;
@@ -143,6 +149,7 @@ struct gateau_plan {
 
     // device memory
     DevBuf d_pix, d_cube, d_cube_raw, d_screen, d_tau, d_custom, d_c, d_HGQ, d_fusedB, d_pink, d_state, d_status;
+    DevBuf d_tb, d_dip;              // skydip fit [2][n_ch] float for the epilogues; FP64 scratch of the fit
     bool cube_scale_dirty = true;    // d_cube = d_cube_raw * c2 / k_B must be recomputed
     DevBuf d_rows, d_tiles, d_X, d_agg, d_stage[2];
     FusedOperands fused{};
@@ -175,7 +182,8 @@ struct gateau_plan {
     ~gateau_plan() {
         track_streams();
         DevBuf* bufs[] = {&d_pix, &d_cube, &d_cube_raw, &d_screen, &d_tau, &d_custom, &d_c, &d_HGQ, &d_fusedB, &d_pink,
-                          &d_state, &d_status, &d_rows, &d_tiles, &d_X, &d_agg, &d_stage[0], &d_stage[1]};
+                          &d_state, &d_status, &d_rows, &d_tiles, &d_X, &d_agg, &d_stage[0], &d_stage[1],
+                          &d_tb, &d_dip};
         for (DevBuf* b : bufs) b->release(mo);
         if (mo.mem) cudaStreamDestroy(mo.mem);       // its pending frees still complete
         for (int i = 0; i < 2; ++i) {
@@ -204,7 +212,7 @@ cudaError_t grow(gateau_plan* p, DevBuf& b, size_t n) {
 size_t device_bytes(const gateau_plan* p) {
     const DevBuf* bufs[] = {&p->d_pix, &p->d_cube, &p->d_cube_raw, &p->d_screen, &p->d_tau, &p->d_custom, &p->d_c,
                             &p->d_HGQ, &p->d_fusedB, &p->d_pink, &p->d_state, &p->d_status, &p->d_rows,
-                            &p->d_tiles, &p->d_X, &p->d_agg, &p->d_stage[0], &p->d_stage[1]};
+                            &p->d_tiles, &p->d_X, &p->d_agg, &p->d_stage[0], &p->d_stage[1], &p->d_tb, &p->d_dip};
     size_t s = 0;
     for (const DevBuf* b : bufs) s += b->bytes;
     return s;
@@ -301,6 +309,35 @@ gateau_status finalize(gateau_plan* p) {
         p->fused.stage_elems = stage_elems;
     }
 
+    // brightness-temperature scale (Sect. 2.7): the skydip runs on the device (FP64), its fit
+    // comes back for gateau_plan_get_vector and for the pink coefficients below
+    if (p->kelvin) {
+        const size_t hw_n = static_cast<size_t>(n_ch) * nf;
+        std::vector<double> dip(hw_n + 2 * static_cast<size_t>(nf) + 2 * static_cast<size_t>(n_ch), 0.0);
+        for (int c = 0; c < n_ch; ++c)
+            for (int k = 0; k < nf; ++k) dip[static_cast<size_t>(c) * nf + k] = p->eta_filt[static_cast<size_t>(c) * nf + k] * p->w[k];
+        for (int k = 0; k < nf; ++k) {
+            dip[hw_n + k] = p->c0[k];
+            dip[hw_n + nf + k] = p->c1[k];
+        }
+        GATEAU_CUDA(grow(p, p->d_dip, dip.size() * sizeof(double)));
+        GATEAU_CUDA(grow(p, p->d_tb, 2 * static_cast<size_t>(n_ch) * sizeof(float)));
+        GATEAU_CUDA(cudaMemcpy(p->d_dip.p, dip.data(), (hw_n + 2 * static_cast<size_t>(nf)) * sizeof(double),
+                               cudaMemcpyHostToDevice));
+        double* ab = p->d_dip.as<double>() + hw_n + 2 * static_cast<size_t>(nf);
+        GATEAU_CUDA(launch_skydip_fit(p->d_dip.as<double>(), p->d_dip.as<double>() + hw_n, p->d_tau.as<float>(), nf, Kp,
+                                      p->n_pwv, p->pwv_min, p->dpwv, 1.0 / sin(p->theta0), d.T_atm_K, p->dip_lo,
+                                      p->dip_hi, p->dip_n, n_ch, ab, p->d_tb.as<float>(), nullptr));
+        std::vector<double> abh(2 * static_cast<size_t>(n_ch));
+        GATEAU_CUDA(cudaMemcpy(abh.data(), ab, abh.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        p->tb_a.assign(abh.begin(), abh.begin() + n_ch);
+        p->tb_b.assign(abh.begin() + n_ch, abh.end());
+        p->d_dip.release(p->mo);
+    } else {
+        p->tb_a.clear();
+        p->tb_b.clear();
+    }
+
     // pink filters (Sect. 2.6, Eq. 20)
     p->n_pole = pink_pole_count(d.pink_f_min_hz, d.f_sample_hz);
     const int np = p->n_pole;
@@ -314,11 +351,15 @@ gateau_status finalize(gateau_plan* p) {
                             &p->pink_r[static_cast<size_t>(c) * np], &p->pink_d[c]);
     }
     std::vector<float> pk(static_cast<size_t>(n_ch) * (2 * np + 1));
+    // kelvin output: the pink term enters as tb_a P_pn, i.e. residues and direct term times tb_a
+    // (the filter states do not depend on them)
     for (size_t i = 0; i < p->pink_a.size(); ++i) {
+        const double sc = p->kelvin ? p->tb_a[i / np] : 1.0;
         pk[i] = static_cast<float>(p->pink_a[i]);
-        pk[p->pink_a.size() + i] = static_cast<float>(p->pink_r[i]);
+        pk[p->pink_a.size() + i] = static_cast<float>(sc * p->pink_r[i]);
     }
-    for (int c = 0; c < n_ch; ++c) pk[2 * p->pink_a.size() + c] = static_cast<float>(p->pink_d[c]);
+    for (int c = 0; c < n_ch; ++c)
+        pk[2 * p->pink_a.size() + c] = static_cast<float>((p->kelvin ? p->tb_a[c] : 1.0) * p->pink_d[c]);
     GATEAU_CUDA(grow(p, p->d_pink, pk.size() * sizeof(float)));
     GATEAU_CUDA(cudaMemcpy(p->d_pink.p, pk.data(), pk.size() * sizeof(float), cudaMemcpyHostToDevice));
     const size_t state_bytes = static_cast<size_t>(d.n_pix) * n_ch * np * sizeof(float);
@@ -381,6 +422,8 @@ DevTables make_tables(const gateau_plan* p) {
     T.pink_a = p->d_pink.as<float>();
     T.pink_r = T.pink_a + pa;
     T.pink_d = T.pink_a + 2 * pa;
+    T.tb_a = p->kelvin ? p->d_tb.as<float>() : nullptr;
+    T.tb_b = p->kelvin ? T.tb_a + p->n_ch : nullptr;
     T.status = p->d_status.as<unsigned int>();
     return T;
 }
@@ -666,6 +709,7 @@ gateau_status gateau_set_atmosphere_table(gateau_plan* p, const float* table, in
     p->dpwv = dpwv_mm;
     p->has_table = true;
     p->maps_dirty = true;
+    if (p->kelvin) p->dirty = true;    // the skydip reads the table
     return GATEAU_OK;
 }
 
@@ -754,7 +798,23 @@ gateau_status gateau_set_scan(gateau_plan* p, int kind, const double* params, in
     p->phi0 = phi0_rad;
     p->theta0 = theta0_rad;
     p->n_custom = kind == GATEAU_SCAN_CUSTOM ? n_custom : 0;
+    if (p->kelvin) p->dirty = true;    // the skydip runs at the base elevation theta0
     p->has_scan = true;
+    return GATEAU_OK;
+}
+
+gateau_status gateau_set_output_kelvin(gateau_plan* p, int enable, double pwv_lo_mm, double pwv_hi_mm, int n_pwv) {
+    if (!p) return fail(GATEAU_EINVAL, "plan must be non-NULL");
+    if (enable) {
+        if (n_pwv < 2 || n_pwv > kMaxSkydip) return fail(GATEAU_EINVAL, "skydip needs 2 <= n_pwv <= %d", kMaxSkydip);
+        if (!std::isfinite(pwv_lo_mm) || !std::isfinite(pwv_hi_mm) || !(pwv_lo_mm < pwv_hi_mm) || pwv_lo_mm < 0.0)
+            return fail(GATEAU_EINVAL, "skydip needs 0 <= pwv_lo < pwv_hi (finite)");
+    }
+    p->kelvin = enable != 0;
+    p->dip_lo = pwv_lo_mm;
+    p->dip_hi = pwv_hi_mm;
+    p->dip_n = n_pwv;
+    p->dirty = true;
     return GATEAU_OK;
 }
 
@@ -902,9 +962,14 @@ gateau_status gateau_plan_get_vector(gateau_plan* p, int which, double* out, siz
     if (!p || !out) return fail(GATEAU_EINVAL, "plan and out must be non-NULL");
     const std::vector<double>* src = nullptr;
     std::vector<double> tmp;
-    const bool needs_tables = which >= GATEAU_VEC_C0;
+    const bool needs_tables = which >= GATEAU_VEC_C0 && which <= GATEAU_VEC_PINK_D;
     if (which == GATEAU_VEC_ETA_FILT && !p->has_disp) return fail(GATEAU_ESTATE, "dispersive element not set");
-    if (needs_tables) {
+    if (which == GATEAU_VEC_TB_A || which == GATEAU_VEC_TB_B) {
+        if (!p->kelvin) return fail(GATEAU_ESTATE, "brightness-temperature output not enabled");
+        if (p->dirty || p->tb_a.size() != static_cast<size_t>(p->n_ch))
+            return fail(GATEAU_ESTATE, "the skydip runs when the plan is prepared (gateau_plan_prepare)");
+        src = which == GATEAU_VEC_TB_A ? &p->tb_a : &p->tb_b;
+    } else if (needs_tables) {
         if (!p->has_cascade || !p->has_disp) return fail(GATEAU_ESTATE, "cascade and dispersive element must be set");
         // Host-only rebuild (no device upload) so the tables are available without a GPU.
         std::vector<PrimStage> prim;

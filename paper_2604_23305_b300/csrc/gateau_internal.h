@@ -86,6 +86,10 @@ struct DevTables {
     const float* pink_a;               // [n_ch][n_pole]
     const float* pink_r;               // [n_ch][n_pole] gain folded in
     const float* pink_d;               // [n_ch] gain folded in
+    // brightness-temperature output (Sect. 2.7): out = tb_a[ch] P_tot + tb_b[ch] (K), or null for W.
+    // The pink residues and direct term are already multiplied by tb_a.
+    const float* tb_a;
+    const float* tb_b;
     unsigned int* status;
 };
 
@@ -133,6 +137,16 @@ struct PinkWork {
     long long L;                       // samples per chunk (multiple of 4)
 };
 void pink_choose_chunks(long long nt, long long S, int& C, long long& L);
+// Skydip (Sect. 2.7): for each channel, P_KID and the band-averaged sky brightness temperature at
+// n_dip zenith PWVs pwv_lo .. pwv_hi at elevation el (csc_el = 1 / sin el), no source, and the
+// least-squares line T_b = a P + b.  hw [n_ch][n_freq] = eta_filt w (Hz), c01 [2][n_freq] = the
+// collapsed cascade's c0, c1 (W/Hz), tau the plan's opacity table.  Writes ab [2][n_ch] (FP64:
+// a then b) and ab_f (the same in FP32).  2 <= n_dip <= kMaxSkydip.
+constexpr int kMaxSkydip = 64;
+cudaError_t launch_skydip_fit(const double* hw, const double* c01, const float* tau, int n_freq, int Kp, int n_pwv,
+                              double pwv_min, double dpwv, double csc_el, double T_atm, double pwv_lo, double pwv_hi,
+                              int n_dip, int n_ch, double* ab, float* ab_f, cudaStream_t stream);
+
 cudaError_t launch_pink(const DevTables& T, float* state, const PinkWork& W, long long t0, long long nt,
                         float* out, cudaStream_t stream);
 

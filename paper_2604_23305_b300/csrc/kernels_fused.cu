@@ -550,7 +550,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (ch < T.n_ch) {
                             const float pk = T.kb1e9 * sv[4 * q + e];
                             const float sigma = T.kB * sqrtf(T.noise_scale * fmaxf(nv[4 * q + e], 0.f));
-                            orow[ch] = fmaf(sigma, f4_get(z, e), pk);
+                            const float v = fmaf(sigma, f4_get(z, e), pk);
+                            orow[ch] = T.tb_a ? fmaf(T.tb_a[ch], v, T.tb_b[ch]) : v;   // K (Sect. 2.7) or W
                         }
                     }
                 }

@@ -354,7 +354,8 @@ __global__ __launch_bounds__(256) void contract_fp32_kernel(DevTables T, const f
             if (ch < T.n_ch) {
                 const float pk = T.kb1e9 * s1[i][j];
                 const float sigma = T.kB * sqrtf(T.noise_scale * fmaxf(sn[i][j], 0.f));
-                orow[ch] = fmaf(sigma, f4_get(z, j), pk);
+                const float v = fmaf(sigma, f4_get(z, j), pk);
+                orow[ch] = T.tb_a ? fmaf(T.tb_a[ch], v, T.tb_b[ch]) : v;   // K (Sect. 2.7) or W
             }
         }
     }

@@ -124,8 +124,16 @@ class Plan:
             self.set_source(sc["source"], device=device_inputs)
             self.set_screen(atm, device=device_inputs)
             self.set_table(atm, device=device_inputs)
+        out = sc.get("output")
+        if out is not None and out.get("units", "W") == "K":
+            self.set_output_kelvin(*out.get("skydip", (0.5, 2.0, 16)))
 
     # ---------------------------------------------------------------- setters
+    def set_output_kelvin(self, pwv_lo: float = 0.5, pwv_hi: float = 2.0, n_pwv: int = 16, enable: bool = True):
+        """Brightness-temperature output by a simulated skydip over n_pwv zenith PWVs (mm)."""
+        L.check(self._lib.gateau_set_output_kelvin(self._h, 1 if enable else 0, float(pwv_lo), float(pwv_hi),
+                                                   int(n_pwv)))
+
     def set_cascade(self, stages):
         arr, keep = _stage_structs(stages, self.n_freq)
         L.check(self._lib.gateau_set_cascade(self._h, len(stages), arr))
@@ -182,6 +190,10 @@ class Plan:
                                           n_custom, mem))
 
     # ---------------------------------------------------------------- running
+    def prepare(self):
+        """Build and upload everything derived from the setters (gateau_plan_prepare)."""
+        L.check(self._lib.gateau_plan_prepare(self._h))
+
     def run(self, t0: int, nt: int, out=None, stream=None):
         """Enqueue samples [t0, t0+nt) into a device tensor [nt, n_pix, n_ch] (float32, W)."""
         import torch
