@@ -252,6 +252,7 @@ def main():
     ap.add_argument("--nt", type=int, default=None, help="shorter scan (profiling runs); default: the whole scan")
     ap.add_argument("--serving-requests", type=int, default=256)
     ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--skip-kelvin", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -356,6 +357,39 @@ def main():
         del o32, p32
         torch.cuda.empty_cache()
         out = None
+
+    # brightness-temperature output (Sect. 2.7): the skydip fit runs once when the plan is prepared
+    # (timed against preparing the same plan in W), then every step writes K instead of W
+    if not args.skip_kelvin:
+        torch.cuda.empty_cache()
+        dip = (0.4, 2.4, 16)
+        pw = Plan(sc, precision=args.precision, white=True, pink=True)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        pw.prepare()
+        prep_w = time.perf_counter() - t
+        del pw
+        pk = Plan(dict(sc, output=dict(units="K", skydip=dip)), precision=args.precision, white=True, pink=True)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        pk.prepare()
+        prep_k = time.perf_counter() - t
+        ok = torch.empty((nt, pk.n_pix, pk.n_ch), dtype=torch.float32, device="cuda")
+        pk.run(0, nt, ok)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pk.run(0, nt, ok)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tk = e0.elapsed_time(e1)
+        result["kelvin"] = {"skydip": {"pwv_mm": [dip[0], dip[1]], "n_pwv": dip[2], "elevation_rad": sc["scan"]["theta0"]},
+                            "prepare_ms": 1e3 * prep_k, "prepare_ms_watts": 1e3 * prep_w,
+                            "skydip_ms": 1e3 * (prep_k - prep_w), "ms_per_step": tk,
+                            "step_overhead_vs_watts": tk / (1e3 * elapsed_s / args.steps) - 1.0,
+                            "status_flags": pk.status()}
+        del ok, pk
+        torch.cuda.empty_cache()
 
     # end to end through the C ABI with host buffers: inputs uploaded from pinned host memory by
     # the setters and the TOD copied back by gateau_run_host, both inside the timed region
