@@ -19,7 +19,8 @@ float64, stage by stage, with no algebraic collapse, blocking or fusion:
   * dispersive element             -- Sect. 2.3, Eqs. 6-7 (+ the 2*Delta_Al/h cutoff)
   * KID power                      -- Sect. 2.5, Eq. 16
   * photon noise                   -- Sect. 2.6, Eqs. 17-19
-  * pink noise                     -- Sect. 2.6, Eq. 20 (pole-zero IIR reading)
+  * pink noise                     -- Sect. 2.6, Eq. 20 (pole-zero IIR reading, or the
+                                      exact Timmer & Koenig realisation over the whole scan)
   * total                          -- Sect. 2.7, Eq. 21
   * brightness-temperature output  -- Sect. 2.7 (simulated skydip, linear P -> T_b map)
 
@@ -50,6 +51,14 @@ design notes of the repository):
     f_min*10^(j/3) (3 per decade, up to f_s/2), zeros a factor 10^(alpha/6)
     above each pole, matched-z mapping, gain set so that the one-sided PSD at
     1 Hz equals A, zero state at the first sample of the scan (n = 0).
+    The exact Timmer & Koenig realisation is also provided for a scan of known
+    length N: Fourier coefficients of a real series of length M = 2^ceil(log2 N)
+    (the first N samples are used) with Gaussian real and imaginary parts of
+    variance M f_s S(f_j) / 4 at f_j = j f_s / M, 0 < j < M/2, a real Nyquist
+    coefficient of variance M f_s S / 2, no DC term, S(f) = A f^-alpha the
+    one-sided PSD, and x_n = (1/M) sum_j X_j e^{2 pi i j n / M}.  Its normals
+    come from Philox with counter (q lo, q hi, i, 2^30 | ch), q = j >> 1; bin j
+    takes Box-Muller pair j & 1 as (re, im).
   * Skydip (Sect. 2.7): the PWV is varied over n uniformly spaced zenith values
     pwv_lo .. pwv_hi at the scan's base elevation theta_0, with no source and
     no noise (the recorded power is the noise-free P_KID, the mean of
@@ -497,6 +506,48 @@ def pink_normals(seed: int, n, pix, ch):
     return np.choose(n & 3, [za, zb, zc, zd])
 
 
+def tk_normals(seed: int, j, pix, ch):
+    """(re, im) normals of Fourier bin j of the Timmer-Koenig series of (i, ch): counter
+    (q lo, q hi, i, 2^30 | ch) with q = j >> 1; bin j takes Box-Muller pair j & 1."""
+    j = np.asarray(j, dtype=np.int64)
+    pix = np.asarray(pix, dtype=np.int64)
+    ch = np.asarray(ch, dtype=np.int64)
+    j, pix, ch = np.broadcast_arrays(j, pix, ch)
+    q = j >> 1
+    k0, k1 = _key(seed)
+    x = philox4x32_10(q & 0xFFFFFFFF, q >> 32, pix, np.int64(0x40000000) | ch, k0, k1)
+    za, zb = box_muller(x[0], x[1])
+    zc, zd = box_muller(x[2], x[3])
+    odd = (j & 1) == 1
+    return np.where(odd, zc, za), np.where(odd, zd, zb)
+
+
+# ---------------------------------------------------------------------------
+# Pink noise, exact: Timmer & Koenig (1995) over the whole scan (Sect. 2.6, Eq. 20)
+# ---------------------------------------------------------------------------
+
+def tk_length(n_total: int) -> int:
+    """Length M = 2^ceil(log2 N) of the realisation whose first N samples are the scan."""
+    return max(2, 1 << int(math.ceil(math.log2(max(int(n_total), 1)))))
+
+
+def pink_tk_realisation(seed: int, A: float, alpha: float, f_sample_hz: float, n_total: int, pix: int, ch: int):
+    """Whole-scan pink series x_n, n = 0 .. N-1, of spaxel pix and channel ch (W): Fourier
+    coefficients drawn from the one-sided PSD S(f) = A f^-alpha, then the inverse DFT."""
+    M = tk_length(n_total)
+    if A <= 0.0:
+        return np.zeros(int(n_total), dtype=F64)
+    j = np.arange(1, M // 2 + 1, dtype=np.int64)
+    f = j * (f_sample_hz / M)
+    S = A * f ** (-alpha)
+    re, im = tk_normals(seed, j, pix, ch)
+    X = np.zeros(M // 2 + 1, dtype=np.complex128)
+    X[1:M // 2] = np.sqrt(M * f_sample_hz * S[:-1] / 4.0) * (re[:-1] + 1j * im[:-1])
+    X[M // 2] = np.sqrt(M * f_sample_hz * S[-1] / 2.0) * re[-1]           # real Nyquist coefficient
+    x = np.fft.irfft(X, n=M)                                             # (1/M) sum over the Hermitian spectrum
+    return x[:int(n_total)]
+
+
 # ---------------------------------------------------------------------------
 # Pink noise: pole-zero filter with power response ~ A f^-alpha (Sect. 2.6, Eq. 20)
 # ---------------------------------------------------------------------------
@@ -656,11 +707,12 @@ def skydip_calibration(sc: dict, inst: Instrument | None = None, pwv_lo: float =
 
 def simulate(sc: dict, t0: int, nt: int, inst: Instrument | None = None,
              white: bool = True, pink: bool = True, pink_state=None, return_parts: bool = False,
-             kelvin: dict | None = None):
+             kelvin: dict | None = None, pink_tk: int | None = None):
     """TOD out[n - t0, i, ch] in W for samples n in [t0, t0 + nt), all spaxels (Eq. 21).
 
     pink_state [n_pix, n_ch, n_pole] is the filter state before sample t0 (zeros at t0 = 0).
     kelvin: the result of skydip_calibration; the TOD is then a P_tot + b in K (Sect. 2.7).
+    pink_tk: scan length N; the pink term is then the Timmer-Koenig realisation over [0, N).
     """
     if inst is None:
         inst = build_instrument(sc)
@@ -698,7 +750,16 @@ def simulate(sc: dict, t0: int, nt: int, inst: Instrument | None = None,
     sigma = sigma.reshape(nt, n_pix, n_ch)
     p_pn = np.zeros_like(p_kid)
     new_state = None
-    if pink:
+    if pink and pink_tk is not None:
+        assert t0 + nt <= pink_tk
+        noise = sc.get("noise", {})
+        A = np.asarray(noise.get("pink_A", np.zeros(n_ch)), dtype=F64)
+        alpha = np.asarray(noise.get("pink_alpha", np.ones(n_ch)), dtype=F64)
+        for i in range(n_pix):
+            for ch in range(n_ch):
+                x = pink_tk_realisation(seed, float(A[ch]), float(alpha[ch]), sc["f_sample"], pink_tk, i, ch)
+                p_pn[:, i, ch] = x[t0:t0 + nt]
+    elif pink:
         zp = pink_normals(seed, nn[:, None], ii[:, None], chs[None, :]).reshape(nt, n_pix, n_ch)
         n_pole = inst.pink[0].a.size
         new_state = np.zeros((n_pix, n_ch, n_pole), dtype=F64)

@@ -527,3 +527,57 @@ def test_kelvin_output_is_the_affine_map_of_the_total_power():
     w = O.simulate(sc, 0, 40)
     k = O.simulate(sc, 0, 40, kelvin=cal)
     np.testing.assert_allclose(k, cal["a"] * w + cal["b"], rtol=1e-14)
+
+
+# ---------------------------------------------------------------- exact pink noise: Timmer & Koenig (Sect. 2.6)
+
+def test_tk_realisation_is_the_inverse_dft_of_its_spectrum():
+    """Brute-force inverse DFT on a short scan (N = 50 -> M = 64): x_n = (1/M) [X_{M/2} (-1)^n +
+    2 sum_{0<j<M/2} Re(X_j e^{2 pi i j n / M})], with X_j built from the bin normals and the
+    one-sided PSD amplitudes."""
+    seed, A, alpha, fs, N = 7, 2.0e-17, 1.3, 160.0, 50
+    M = O.tk_length(N)
+    assert M == 64
+    x = O.pink_tk_realisation(seed, A, alpha, fs, N, 2, 5)
+    j = np.arange(1, M // 2 + 1)
+    re, im = O.tk_normals(seed, j, 2, 5)
+    S = A * (j * fs / M) ** (-alpha)
+    n = np.arange(N)
+    want = np.zeros(N)
+    for jj in range(1, M // 2):
+        Xj = math.sqrt(M * fs * S[jj - 1] / 4) * (re[jj - 1] + 1j * im[jj - 1])
+        want += 2.0 * np.real(Xj * np.exp(2j * np.pi * jj * n / M))
+    want += math.sqrt(M * fs * S[-1] / 2) * re[-1] * (-1.0) ** n
+    np.testing.assert_allclose(x, want / M, rtol=1e-10, atol=1e-12 * np.abs(want / M).max())
+
+
+def test_tk_white_limit_variance():
+    """alpha = 0 is white noise of one-sided PSD A: variance sum_j S df = A f_s (M - 1) / (2 M)
+    (M - 2 interior bins of weight 1, the Nyquist bin of weight 1/2); checked over 300
+    independent channel series (relative standard error ~0.3 %)."""
+    A, fs, N = 3.0e-18, 100.0, 1024
+    xs = np.stack([O.pink_tk_realisation(11, A, 0.0, fs, N, 0, ch) for ch in range(300)])
+    want = A * fs * (N - 1) / (2 * N)
+    assert abs(xs.var() / want - 1.0) < 0.015
+
+
+def test_tk_psd_follows_power_law():
+    """Welch PSD of a long realisation: level A at 1 Hz and slope -alpha over two decades."""
+    A, alpha, fs, N = 1.0e-18, 1.5, 160.0, 1 << 17
+    x = O.pink_tk_realisation(3, A, alpha, fs, N, 0, 0)
+    f, P = signal.welch(x, fs=fs, nperseg=1 << 13)
+    band = (f > 0.1) & (f < 10.0)
+    slope, icpt = np.polyfit(np.log10(f[band]), np.log10(P[band]), 1)
+    assert abs(slope + alpha) < 0.1
+    assert abs(icpt - math.log10(A)) < 0.1
+
+
+def test_tk_streams_are_disjoint_from_white_and_pink():
+    """The Fourier-bin counters (c3 = 2^30 | ch) never meet the white (c3 = ch >> 2 < 2^30) or the
+    filtered pink (c3 = 2^31 | ch) counters, and the bin normals are standard normal."""
+    re, im = O.tk_normals(5, np.arange(20000), 1, 3)
+    z = np.concatenate([re, im])
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    assert abs(z.mean()) < 0.03 and abs(z.std() - 1.0) < 0.03
+    w = O.white_normals(5, np.arange(2000), 1, 3)
+    assert not np.any(np.isin(re[:2000], w))
