@@ -253,6 +253,7 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=256)
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-kelvin", action="store_true")
+    ap.add_argument("--skip-tk", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -389,6 +390,36 @@ def main():
                             "step_overhead_vs_watts": tk / (1e3 * elapsed_s / args.steps) - 1.0,
                             "status_flags": pk.status()}
         del ok, pk
+        torch.cuda.empty_cache()
+
+    # exact pink noise (Sect. 2.6, Timmer & Koenig): the whole scan's realisation is drawn and
+    # transformed when the plan is prepared (timed against preparing the filter plan); each step
+    # then adds its samples instead of running the pole-zero filter scan
+    if not args.skip_tk:
+        torch.cuda.empty_cache()
+        pt = Plan(dict(sc, noise=dict(sc["noise"], pink_tk=nt)), precision=args.precision, white=True, pink=True)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        pt.prepare()
+        prep_t = time.perf_counter() - t
+        ot = torch.empty((nt, pt.n_pix, pt.n_ch), dtype=torch.float32, device="cuda")
+        pt.run(0, nt, ot)
+        torch.cuda.synchronize()
+        pt.get_timing()
+        pt.set_timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pt.run(0, nt, ot)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ph, _, _ = pt.get_timing()
+        pt.set_timing(False)
+        info_t = pt.info()
+        result["pink_tk"] = {"fft_length": 1 << (nt - 1).bit_length(), "prepare_ms": 1e3 * prep_t,
+                             "ms_per_step": e0.elapsed_time(e1), "pink_phase_ms": ph[3],
+                             "filter_pink_phase_ms": roofline["phase_ms_per_step"]["pink"],
+                             "device_bytes": int(info_t.device_bytes), "status_flags": pt.status()}
+        del ot, pt
         torch.cuda.empty_cache()
 
     # end to end through the C ABI with host buffers: inputs uploaded from pinned host memory by

@@ -220,6 +220,21 @@ gateau_status gateau_set_dispersive_element(gateau_plan* plan, int kind, int n_c
  * Requires gateau_set_dispersive_element first (ESTATE otherwise). */
 gateau_status gateau_set_pink_noise(gateau_plan* plan, const double* A, const double* alpha);
 
+/* Exact pink noise (Sect. 2.6; Timmer & Koenig 1995) instead of the pole-zero
+ * filter, for a scan of n_total samples (0 restores the filter).  When the plan is
+ * prepared, the device draws each (spaxel i, channel ch) series whole: Fourier
+ * coefficients of a real series of length M = 2^ceil(log2 n_total) with real and
+ * imaginary parts N(0, M f_s S(f_j) / 4) at f_j = j f_s / M (0 < j < M/2), a real
+ * Nyquist coefficient N(0, M f_s S / 2), no DC term, S(f) = A f^-alpha from
+ * gateau_set_pink_noise (one-sided, W^2/Hz at 1 Hz), normals from Philox4x32-10 with
+ * counter (j >> 1 lo, j >> 1 hi, i, 2^30 | ch) and Box-Muller pair j & 1; the inverse
+ * DFT's first n_total samples are the pink term.  The plan then holds them as a
+ * device array [n_total][n_pix][n_ch] float32 (and needs twice n_pix ceil(n_ch/2) M
+ * complex64 of scratch while it is prepared); runs add their samples and may not go
+ * past n_total (EINVAL).  Used only with GATEAU_NOISE_PINK.  EINVAL unless
+ * 0 <= n_total <= 2^30. */
+gateau_status gateau_set_pink_timmer_koenig(gateau_plan* plan, long long n_total);
+
 /* Scan pattern (Sect. 2.4, Eq. 8) with scan offset (phi0, theta0).  params has
  * n_params doubles as listed at GATEAU_SCAN_*.  CUSTOM takes custom[n_custom][2]
  * (phi, theta) per sample (host or device per mem); runs may not go past

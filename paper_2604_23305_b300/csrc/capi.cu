@@ -140,6 +140,7 @@ struct gateau_plan {
     double dip_lo = 0, dip_hi = 0;
     int dip_n = 0;
     std::vector<double> tb_a, tb_b;  // the skydip fit, read back from the device
+    long long tk_n = 0;              // > 0: exact (Timmer-Koenig) pink noise over samples [0, tk_n)
 
     // derived host tables
     std::vector<double> c0, c1, c2;
@@ -150,6 +151,7 @@ struct gateau_plan {
     // device memory
     DevBuf d_pix, d_cube, d_cube_raw, d_screen, d_tau, d_custom, d_c, d_HGQ, d_fusedB, d_pink, d_state, d_status;
     DevBuf d_tb, d_dip;              // skydip fit [2][n_ch] float for the epilogues; FP64 scratch of the fit
+    DevBuf d_tk, d_tkz;              // Timmer-Koenig pink TOD [tk_n][n_pix][n_ch]; its FFT scratch
     bool cube_scale_dirty = true;    // d_cube = d_cube_raw * c2 / k_B must be recomputed
     DevBuf d_rows, d_tiles, d_X, d_agg, d_stage[2];
     FusedOperands fused{};
@@ -183,7 +185,7 @@ struct gateau_plan {
         track_streams();
         DevBuf* bufs[] = {&d_pix, &d_cube, &d_cube_raw, &d_screen, &d_tau, &d_custom, &d_c, &d_HGQ, &d_fusedB, &d_pink,
                           &d_state, &d_status, &d_rows, &d_tiles, &d_X, &d_agg, &d_stage[0], &d_stage[1],
-                          &d_tb, &d_dip};
+                          &d_tb, &d_dip, &d_tk, &d_tkz};
         for (DevBuf* b : bufs) b->release(mo);
         if (mo.mem) cudaStreamDestroy(mo.mem);       // its pending frees still complete
         for (int i = 0; i < 2; ++i) {
@@ -212,7 +214,8 @@ cudaError_t grow(gateau_plan* p, DevBuf& b, size_t n) {
 size_t device_bytes(const gateau_plan* p) {
     const DevBuf* bufs[] = {&p->d_pix, &p->d_cube, &p->d_cube_raw, &p->d_screen, &p->d_tau, &p->d_custom, &p->d_c,
                             &p->d_HGQ, &p->d_fusedB, &p->d_pink, &p->d_state, &p->d_status, &p->d_rows,
-                            &p->d_tiles, &p->d_X, &p->d_agg, &p->d_stage[0], &p->d_stage[1], &p->d_tb, &p->d_dip};
+                            &p->d_tiles, &p->d_X, &p->d_agg, &p->d_stage[0], &p->d_stage[1], &p->d_tb, &p->d_dip,
+                            &p->d_tk, &p->d_tkz};
     size_t s = 0;
     for (const DevBuf* b : bufs) s += b->bytes;
     return s;
@@ -362,6 +365,28 @@ gateau_status finalize(gateau_plan* p) {
         pk[2 * p->pink_a.size() + c] = static_cast<float>((p->kelvin ? p->tb_a[c] : 1.0) * p->pink_d[c]);
     GATEAU_CUDA(grow(p, p->d_pink, pk.size() * sizeof(float)));
     GATEAU_CUDA(cudaMemcpy(p->d_pink.p, pk.data(), pk.size() * sizeof(float), cudaMemcpyHostToDevice));
+    // exact pink noise (Sect. 2.6, Timmer & Koenig): the whole scan's realisation, once per plan
+    if (p->tk_n > 0 && (d.noise_flags & GATEAU_NOISE_PINK)) {
+        const long long M = tk_length(p->tk_n);
+        const size_t n_pairs = static_cast<size_t>(d.n_pix) * ((n_ch + 1) / 2);
+        const size_t zbytes = n_pairs * static_cast<size_t>(M) * sizeof(float2);
+        GATEAU_CUDA(grow(p, p->d_tk, static_cast<size_t>(p->tk_n) * d.n_pix * n_ch * sizeof(float)));
+        GATEAU_CUDA(grow(p, p->d_tkz, 2 * zbytes + 2 * static_cast<size_t>(n_ch) * sizeof(double)));
+        std::vector<double> par(2 * static_cast<size_t>(n_ch), 0.0);
+        for (int c = 0; c < n_ch; ++c) {
+            par[c] = p->has_pink ? p->pink_A[c] : 0.0;
+            par[n_ch + c] = p->has_pink ? p->pink_alpha[c] : 1.0;
+        }
+        uint8_t* zb = p->d_tkz.as<uint8_t>();
+        double* dpar = reinterpret_cast<double*>(zb + 2 * zbytes);
+        GATEAU_CUDA(cudaMemcpy(dpar, par.data(), par.size() * sizeof(double), cudaMemcpyHostToDevice));
+        GATEAU_CUDA(launch_tk_realise(dpar, dpar + n_ch, d.f_sample_hz, static_cast<uint32_t>(d.seed & 0xffffffffull),
+                                      static_cast<uint32_t>(d.seed >> 32), d.n_pix, n_ch, p->tk_n,
+                                      p->kelvin ? p->d_tb.as<float>() : nullptr, reinterpret_cast<float2*>(zb),
+                                      reinterpret_cast<float2*>(zb + zbytes), p->d_tk.as<float>(), nullptr));
+        GATEAU_CUDA(cudaStreamSynchronize(nullptr));
+        p->d_tkz.release(p->mo);
+    }
     const size_t state_bytes = static_cast<size_t>(d.n_pix) * n_ch * np * sizeof(float);
     if (p->d_state.bytes < state_bytes) {
         GATEAU_CUDA(grow(p, p->d_state, state_bytes));
@@ -446,6 +471,9 @@ gateau_status validate_run(const gateau_plan* p, long long t0, long long nt, con
     if ((p->desc.noise_flags & GATEAU_NOISE_PINK) && t0 != 0 && t0 != p->next_t0)
         return fail(GATEAU_EORDER, "t0=%lld does not continue the previous chunk (next t0 is %lld, or 0 to restart)", t0,
                     p->next_t0);
+    if ((p->desc.noise_flags & GATEAU_NOISE_PINK) && p->tk_n > 0 && t0 + nt > p->tk_n)
+        return fail(GATEAU_EINVAL, "the exact pink-noise realisation covers %lld samples, run needs %lld", p->tk_n,
+                    t0 + nt);
     if (p->scan_kind == GATEAU_SCAN_CUSTOM && t0 + nt > p->n_custom)
         return fail(GATEAU_EINVAL, "custom scan has %lld samples, run needs %lld", p->n_custom, t0 + nt);
     if (nt * static_cast<long long>(p->desc.n_pix) > (1LL << 31))
@@ -543,7 +571,14 @@ gateau_status enqueue_run(gateau_plan* p, long long t0, long long nt, float* out
         GATEAU_CUDA(tm.end(GATEAU_PHASE_CONTRACT));
         p->launches += 1;
     }
-    if (d.noise_flags & GATEAU_NOISE_PINK) {
+    if ((d.noise_flags & GATEAU_NOISE_PINK) && p->tk_n > 0) {
+        // exact pink noise: the plan's realisation of samples [t0, t0 + nt), added elementwise
+        const long long S = static_cast<long long>(d.n_pix) * p->n_ch;
+        GATEAU_CUDA(tm.begin(GATEAU_PHASE_PINK));
+        GATEAU_CUDA(launch_tk_add(out, p->d_tk.as<float>() + t0 * S, nt * S, stream));
+        GATEAU_CUDA(tm.end(GATEAU_PHASE_PINK));
+        p->launches += 1;
+    } else if (d.noise_flags & GATEAU_NOISE_PINK) {
         PinkWork W;
         pink_choose_chunks(nt, static_cast<long long>(d.n_pix) * p->n_ch, W.C, W.L);
         GATEAU_CUDA(grow(p, p->d_agg, static_cast<size_t>(W.C) * d.n_pix * p->n_ch * p->n_pole * sizeof(float)));
@@ -814,6 +849,14 @@ gateau_status gateau_set_output_kelvin(gateau_plan* p, int enable, double pwv_lo
     p->dip_lo = pwv_lo_mm;
     p->dip_hi = pwv_hi_mm;
     p->dip_n = n_pwv;
+    p->dirty = true;
+    return GATEAU_OK;
+}
+
+gateau_status gateau_set_pink_timmer_koenig(gateau_plan* p, long long n_total) {
+    if (!p) return fail(GATEAU_EINVAL, "plan must be non-NULL");
+    if (n_total < 0 || n_total > (1LL << 30)) return fail(GATEAU_EINVAL, "need 0 <= n_total <= 2^30 (got %lld)", n_total);
+    p->tk_n = n_total;
     p->dirty = true;
     return GATEAU_OK;
 }

@@ -147,6 +147,17 @@ cudaError_t launch_skydip_fit(const double* hw, const double* c01, const float* 
                               double pwv_min, double dpwv, double csc_el, double T_atm, double pwv_lo, double pwv_hi,
                               int n_dip, int n_ch, double* ab, float* ab_f, cudaStream_t stream);
 
+// Exact pink noise (Timmer & Koenig, Sect. 2.6): tk_length(N) = 2^ceil(log2 N) (>= 2);
+// launch_tk_realise writes tk [n_total][n_pix][n_ch] (W, times scale[ch] when scale is not null)
+// from the per-channel PSD A [n_ch] (W^2/Hz at 1 Hz) and alpha [n_ch], key (k0, k1), using the
+// scratch buffers work0, work1 of (n_pix ceil(n_ch/2)) x tk_length(n_total) float2 each;
+// launch_tk_add adds tk[0 .. count) into out.
+long long tk_length(long long n_total);
+cudaError_t launch_tk_realise(const double* A, const double* alpha, double f_sample, uint32_t k0, uint32_t k1, int n_pix,
+                              int n_ch, long long n_total, const float* scale, float2* work0, float2* work1, float* tk,
+                              cudaStream_t stream);
+cudaError_t launch_tk_add(float* out, const float* tk, long long count, cudaStream_t stream);
+
 cudaError_t launch_pink(const DevTables& T, float* state, const PinkWork& W, long long t0, long long nt,
                         float* out, cudaStream_t stream);
 

@@ -1,0 +1,194 @@
+// Exact pink noise by Timmer & Koenig (1995) over the whole scan (Sect. 2.6, Eq. 20).
+//
+// For a scan of N samples the plan draws, per (spaxel i, channel ch), the Fourier coefficients of
+// a real series of length M = 2^ceil(log2 N) from the one-sided PSD S(f) = A f^-alpha (real and
+// imaginary parts of variance M f_s S(f_j) / 4 at f_j = j f_s / M for 0 < j < M/2, a real Nyquist
+// coefficient of variance M f_s S / 2, no DC term), inverts the DFT and keeps the first N samples.
+// Two channels share one complex inverse FFT: with A_j, B_j Hermitian, the inverse transform of
+// A_j + i B_j is a_n + i b_n.  The transform is a Stockham autosort FFT (radix-8 passes and one
+// radix-2 or -4 pass, FP32, out of place between two buffers); a tiled transpose then writes the
+// series into [n][i][ch], the layout of the TOD, and every run adds its samples to the output.
+// All of it runs once, when the plan is prepared; a run costs one elementwise add.
+#include <utility>
+
+#include "device_common.cuh"
+
+namespace gateau {
+namespace {
+
+constexpr int kTkThreads = 256;
+
+// (re, im) normals of Fourier bin j: counter (q lo, q hi, i, 2^30 | ch), q = j >> 1, Box-Muller
+// pair j & 1.
+__device__ __forceinline__ float2 tk_normals(long long j, int i, int ch, uint32_t k0, uint32_t k1) {
+    const long long q = j >> 1;
+    const uint4 x = philox4x32_10(make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32),
+                                             static_cast<uint32_t>(i), 0x40000000u | static_cast<uint32_t>(ch)),
+                                  k0, k1);
+    return (j & 1) ? box_muller(x.z, x.w) : box_muller(x.x, x.y);
+}
+
+// Coefficient X_j / M of one channel (complex; real at the Nyquist bin, zero at DC or for A = 0).
+__device__ __forceinline__ float2 tk_coef(long long j, int M, int i, int ch, int n_ch, const double* A,
+                                          const double* alpha, double f_sample, uint32_t k0, uint32_t k1) {
+    if (ch >= n_ch || j == 0 || !(A[ch] > 0.0)) return make_float2(0.f, 0.f);
+    const double f = static_cast<double>(j) * f_sample / M;
+    const double S = A[ch] * pow(f, -alpha[ch]);
+    const float2 z = tk_normals(j, i, ch, k0, k1);
+    if (2 * j == M) return make_float2(static_cast<float>(sqrt(M * f_sample * S / 2.0) / M) * z.x, 0.f);
+    const float amp = static_cast<float>(sqrt(M * f_sample * S / 4.0) / M);
+    return make_float2(amp * z.x, amp * z.y);
+}
+
+// Z[pair][j] = X^a_j + i X^b_j for the channel pair (2c, 2c + 1) of spaxel i, pair = i P + c.
+__global__ void __launch_bounds__(kTkThreads) tk_spectrum_kernel(float2* __restrict__ Z, int M, int P, int n_pix,
+                                                                 int n_ch, const double* __restrict__ A,
+                                                                 const double* __restrict__ alpha, double f_sample,
+                                                                 uint32_t k0, uint32_t k1) {
+    const long long half = M / 2 + 1;
+    const long long total = static_cast<long long>(n_pix) * P * half;
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long pair = t / half;
+        const long long j = t - pair * half;
+        const int i = static_cast<int>(pair / P), c = static_cast<int>(pair - static_cast<long long>(i) * P);
+        const float2 a = tk_coef(j, M, i, 2 * c, n_ch, A, alpha, f_sample, k0, k1);
+        const float2 b = tk_coef(j, M, i, 2 * c + 1, n_ch, A, alpha, f_sample, k0, k1);
+        float2* z = Z + pair * M;
+        z[j] = make_float2(a.x - b.y, a.y + b.x);
+        if (j > 0 && 2 * j < M) z[M - j] = make_float2(a.x + b.y, b.x - a.y);   // conj(a) + i conj(b)
+    }
+}
+
+// One Stockham pass of the inverse transform: sub-transforms of length Ns become length R Ns.
+template <int R>
+__global__ void __launch_bounds__(kTkThreads) tk_stockham_kernel(const float2* __restrict__ in, float2* __restrict__ out,
+                                                                 int M, int Ns, long long n_pairs) {
+    const int MR = M / R;
+    const long long total = n_pairs * MR;
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long pair = t / MR;
+        const int j = static_cast<int>(t - pair * MR);
+        const float2* src = in + pair * M;
+        float2* dst = out + pair * M;
+        const int k = j % Ns;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float2 x = src[j + r * MR];
+            // twiddle e^{+2 pi i r k / (R Ns)}: (r k) mod (R Ns) and the power-of-two divisor are exact
+            float s, c;
+            sincospif(2.0f * static_cast<float>((r * k) % (R * Ns)) / static_cast<float>(R * Ns), &s, &c);
+            v[r] = make_float2(x.x * c - x.y * s, x.x * s + x.y * c);
+        }
+        const int idx = (j / Ns) * Ns * R + k;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float s, c;
+                sincospif(2.0f * static_cast<float>((r * q) % R) / static_cast<float>(R), &s, &c);   // constants
+                acc.x += v[r].x * c - v[r].y * s;
+                acc.y += v[r].x * s + v[r].y * c;
+            }
+            dst[idx + q * Ns] = acc;
+        }
+    }
+}
+
+// tk[n][i][ch] = scale[ch] * (Re or Im of Z[i P + ch/2][n]) for n < N: 32 x 32 tiles through shared memory.
+__global__ void __launch_bounds__(256) tk_scatter_kernel(const float2* __restrict__ Z, int M, int P, int n_pix, int n_ch,
+                                                         long long N, const float* __restrict__ scale,
+                                                         float* __restrict__ tk) {
+    __shared__ float tile[32][33];
+    const long long S = static_cast<long long>(n_pix) * n_ch;
+    const long long n0 = static_cast<long long>(blockIdx.x) * 32;
+    const long long s0 = static_cast<long long>(blockIdx.y) * 32;
+    for (int sl = threadIdx.y; sl < 32; sl += 8) {
+        const long long s = s0 + sl, n = n0 + threadIdx.x;
+        float v = 0.f;
+        if (s < S && n < N) {
+            const int i = static_cast<int>(s / n_ch), ch = static_cast<int>(s - static_cast<long long>(i) * n_ch);
+            const float2 z = Z[(static_cast<long long>(i) * P + (ch >> 1)) * M + n];
+            v = (ch & 1) ? z.y : z.x;
+        }
+        tile[sl][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int nl = threadIdx.y; nl < 32; nl += 8) {
+        const long long n = n0 + nl, s = s0 + threadIdx.x;
+        if (s < S && n < N) {
+            const int ch = static_cast<int>(s % n_ch);
+            tk[n * S + s] = tile[threadIdx.x][nl] * (scale ? scale[ch] : 1.f);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) tk_add_kernel(float* __restrict__ out, const float* __restrict__ tk, long long count) {
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < count;
+         e += static_cast<long long>(gridDim.x) * blockDim.x)
+        out[e] += tk[e];
+}
+
+int grid_for(long long work, int threads) {
+    const long long b = (work + threads - 1) / threads;
+    return static_cast<int>(b < 148LL * 32 ? (b > 0 ? b : 1) : 148LL * 32);
+}
+
+}  // namespace
+
+long long tk_length(long long n_total) {
+    long long M = 2;
+    while (M < n_total) M <<= 1;
+    return M;
+}
+
+cudaError_t launch_tk_realise(const double* A, const double* alpha, double f_sample, uint32_t k0, uint32_t k1, int n_pix,
+                              int n_ch, long long n_total, const float* scale, float2* work0, float2* work1, float* tk,
+                              cudaStream_t stream) {
+    const long long M = tk_length(n_total);
+    if (M > (1LL << 30) || n_ch < 1 || n_pix < 1) return cudaErrorInvalidValue;
+    const int P = (n_ch + 1) / 2;
+    const long long n_pairs = static_cast<long long>(n_pix) * P;
+    tk_spectrum_kernel<<<grid_for(n_pairs * (M / 2 + 1), kTkThreads), kTkThreads, 0, stream>>>(
+        work0, static_cast<int>(M), P, n_pix, n_ch, A, alpha, f_sample, k0, k1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int p = 0;
+    while ((1LL << p) < M) ++p;
+    float2* in = work0;
+    float2* out = work1;
+    int Ns = 1;
+    for (int q = 0; q < p / 3; ++q) {
+        tk_stockham_kernel<8><<<grid_for(n_pairs * (M / 8), kTkThreads), kTkThreads, 0, stream>>>(
+            in, out, static_cast<int>(M), Ns, n_pairs);
+        Ns *= 8;
+        std::swap(in, out);
+    }
+    if (p % 3 == 1) {
+        tk_stockham_kernel<2><<<grid_for(n_pairs * (M / 2), kTkThreads), kTkThreads, 0, stream>>>(
+            in, out, static_cast<int>(M), Ns, n_pairs);
+        std::swap(in, out);
+    } else if (p % 3 == 2) {
+        tk_stockham_kernel<4><<<grid_for(n_pairs * (M / 4), kTkThreads), kTkThreads, 0, stream>>>(
+            in, out, static_cast<int>(M), Ns, n_pairs);
+        std::swap(in, out);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long S = static_cast<long long>(n_pix) * n_ch;
+    const dim3 grid(static_cast<unsigned>((n_total + 31) / 32), static_cast<unsigned>((S + 31) / 32));
+    if (grid.y > 65535u) return cudaErrorInvalidValue;
+    tk_scatter_kernel<<<grid, dim3(32, 8), 0, stream>>>(in, static_cast<int>(M), P, n_pix, n_ch, n_total, scale, tk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tk_add(float* out, const float* tk, long long count, cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    tk_add_kernel<<<grid_for(count, 256), 256, 0, stream>>>(out, tk, count);
+    return cudaGetLastError();
+}
+
+}  // namespace gateau

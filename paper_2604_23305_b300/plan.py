@@ -119,6 +119,8 @@ class Plan:
         if "pink_A" in noise:
             A, al = _f64(noise["pink_A"]), _f64(noise["pink_alpha"])
             L.check(self._lib.gateau_set_pink_noise(self._h, _dptr(A), _dptr(al)))
+        if noise.get("pink_tk"):
+            self.set_pink_timmer_koenig(int(noise["pink_tk"]))
         if upload:
             self.set_scan(sc["scan"], device=device_inputs)
             self.set_source(sc["source"], device=device_inputs)
@@ -133,6 +135,10 @@ class Plan:
         """Brightness-temperature output by a simulated skydip over n_pwv zenith PWVs (mm)."""
         L.check(self._lib.gateau_set_output_kelvin(self._h, 1 if enable else 0, float(pwv_lo), float(pwv_hi),
                                                    int(n_pwv)))
+
+    def set_pink_timmer_koenig(self, n_total: int):
+        """Exact (Timmer-Koenig) pink noise over samples [0, n_total); 0 restores the filter."""
+        L.check(self._lib.gateau_set_pink_timmer_koenig(self._h, int(n_total)))
 
     def set_cascade(self, stages):
         arr, keep = _stage_structs(stages, self.n_freq)
