@@ -23,6 +23,7 @@ float64, stage by stage, with no algebraic collapse, blocking or fusion:
                                       exact Timmer & Koenig realisation over the whole scan)
   * total                          -- Sect. 2.7, Eq. 21
   * brightness-temperature output  -- Sect. 2.7 (simulated skydip, linear P -> T_b map)
+  * common-mode reduction          -- Sect. 4.2, Eqs. 25-26 (downstream of the TOD)
 
 Readings of points the paper leaves silent or garbled (each also listed in the
 design notes of the repository):
@@ -67,6 +68,12 @@ design notes of the repository):
     with the channel's weights eta_filt * w.  The map T_b = a P + b is the
     ordinary least-squares line through the n points, and it is applied to
     the total power P_tot of every sample.
+  * Common-mode reduction (Eqs. 25-26): the zenith PWV averaged over the
+    observation is the mean of the line-of-sight-screen PWV over every row
+    (n, i) of the scan; eta_atm,z of a channel is the zenith transmission at
+    that PWV averaged over the band with the channel's weights eta_filt w (as
+    T_b is); eta_atm,i(t) = eta_atm,z^csc(el_i(t)) with the spaxel's own
+    elevation (Eq. 10); S_j uses the spaxel offsets (dphi_j, dtheta_j).
 """
 from __future__ import annotations
 
@@ -703,6 +710,39 @@ def skydip_calibration(sc: dict, inst: Instrument | None = None, pwv_lo: float =
     a = (dp * dt).sum(axis=0) / (dp * dp).sum(axis=0)
     b = t_b.mean(axis=0) - a * p_kid.mean(axis=0)
     return dict(a=a, b=b, pwv=pwv, p_kid=p_kid, t_b=t_b)
+
+
+def mean_zenith_pwv(sc: dict, n_total: int) -> float:
+    """The zenith PWV averaged over the observation: mean over rows (n, i), n < n_total."""
+    n_pix = np.asarray(sc["pix_offsets"]).shape[0]
+    nn, ii = np.meshgrid(np.arange(n_total, dtype=np.int64), np.arange(n_pix), indexing="ij")
+    _, _, _, pwv = row_geometry(sc, nn.ravel(), ii.ravel())
+    return float(pwv.mean())
+
+
+def common_mode_reduction(sc: dict, t_b: np.ndarray, t0: int, pwv_mean: float, r_out: float,
+                          inst: Instrument | None = None):
+    """T*_a,i(t, ch) from a K TOD t_b [nt, n_pix, n_ch] of samples t0 .. t0+nt-1 (Eqs. 25-26):
+    T_b,i / eta_i - (1 - eta_i) / (eta_i N_out) sum_j S_j T_b,j / (1 - eta_j), S_j = 1 for spaxels
+    farther than r_out (rad) from the IFU centre, N_out = sum_j S_j."""
+    if inst is None:
+        inst = build_instrument(sc)
+    t_b = np.asarray(t_b, dtype=F64)
+    nt, n_pix, n_ch = t_b.shape
+    atm = sc["atmosphere"]
+    tau = zenith_opacity(opacity_table(sc), atm["pwv_min"], atm["dpwv"], np.array([pwv_mean]))[0]
+    hw = inst.eta_filt * inst.w
+    eta_z = (hw @ np.exp(-tau)) / hw.sum(axis=1)                                  # [n_ch]
+    off = np.asarray(sc["pix_offsets"], dtype=F64).reshape(n_pix, 2)
+    S = (np.hypot(off[:, 0], off[:, 1]) > r_out).astype(F64)
+    n_out = S.sum()
+    assert n_out > 0
+    nn, ii = np.meshgrid(np.arange(t0, t0 + nt, dtype=np.int64), np.arange(n_pix), indexing="ij")
+    _, _, el, _ = row_geometry(sc, nn.ravel(), ii.ravel())
+    csc = (1.0 / np.sin(el)).reshape(nt, n_pix)
+    eta = eta_z[None, None, :] ** csc[:, :, None]                                 # Eq. 10
+    common = (S[None, :, None] * t_b / (1.0 - eta)).sum(axis=1) / n_out           # [nt, n_ch]
+    return t_b / eta - (1.0 - eta) / eta * common[:, None, :]
 
 
 def simulate(sc: dict, t0: int, nt: int, inst: Instrument | None = None,

@@ -581,3 +581,50 @@ def test_tk_streams_are_disjoint_from_white_and_pink():
     assert abs(z.mean()) < 0.03 and abs(z.std() - 1.0) < 0.03
     w = O.white_normals(5, np.arange(2000), 1, 3)
     assert not np.any(np.isin(re[:2000], w))
+
+
+# ---------------------------------------------------------------- common-mode reduction (Sect. 4.2, Eqs. 25-26)
+
+def _cm_case(nt=24):
+    sc = W.scenario("single_pixel_small", nt_total=nt)
+    sc["pix_offsets"] = O.hex_offsets(2, 30 * math.pi / (180 * 3600))          # 19 spaxels, 30" apart
+    sc["scan"] = dict(sc["scan"], kind="daisy", params=(20 * math.pi / (180 * 3600), 1.0, 0.1))
+    inst = O.build_instrument(sc)
+    pwv = 1.1
+    atm = sc["atmosphere"]
+    tau = O.zenith_opacity(O.opacity_table(sc), atm["pwv_min"], atm["dpwv"], np.array([pwv]))[0]
+    hw = inst.eta_filt * inst.w
+    eta_z = (hw @ np.exp(-tau)) / hw.sum(axis=1)
+    n_pix = sc["pix_offsets"].shape[0]
+    nn, ii = np.meshgrid(np.arange(nt), np.arange(n_pix), indexing="ij")
+    _, _, el, _ = O.row_geometry(sc, nn.ravel(), ii.ravel())
+    eta = eta_z[None, None, :] ** (1.0 / np.sin(el)).reshape(nt, n_pix)[:, :, None]
+    return sc, inst, pwv, eta
+
+
+def test_common_mode_recovers_the_source_closed_form():
+    """T_b,i = T_sky (1 - eta_i) + eta_i T_src,i with no source on the off-source spaxels: the
+    common mode is exactly T_sky and Eq. 25 returns T_src,i on every spaxel."""
+    sc, inst, pwv, eta = _cm_case()
+    nt, n_pix, n_ch = eta.shape
+    r_out = 45 * math.pi / (180 * 3600)
+    off = sc["pix_offsets"]
+    inner = np.hypot(off[:, 0], off[:, 1]) <= r_out
+    rng = np.random.default_rng(4)
+    T_sky = 20.0 + 5.0 * rng.random((nt, 1, n_ch))
+    T_src = np.where(inner[None, :, None], rng.random((nt, n_pix, n_ch)), 0.0)
+    t_b = T_sky * (1 - eta) + eta * T_src
+    got = O.common_mode_reduction(sc, t_b, 0, pwv, r_out, inst)
+    np.testing.assert_allclose(got, T_src, atol=1e-10 * T_sky.max())
+
+
+def test_common_mode_pure_atmosphere_is_zero_and_mean_pwv():
+    """A pure sky seen by all spaxels gives T*_a = 0 for any off-source radius; the mean zenith PWV of a
+    uniform screen is its value."""
+    sc, inst, pwv, eta = _cm_case()
+    t_b = 31.0 * (1 - eta)
+    for r_out in (0.0, 25 * math.pi / (180 * 3600)):
+        got = O.common_mode_reduction(sc, t_b, 0, pwv, r_out, inst)
+        assert np.abs(got).max() < 1e-10 * 31.0
+    scu = _uniform_stare_scenario()
+    assert abs(O.mean_zenith_pwv(scu, 16) - float(np.float32(1.2))) < 1e-12    # the screen holds float32
