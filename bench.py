@@ -384,6 +384,24 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         tk = e0.elapsed_time(e1)
+        # downstream: common-mode reduction of the K TOD (Sect. 4.2, Eqs. 25-26), in place, off-source
+        # spaxels beyond 25" (the outer ring of the 5 x 5 IFU)
+        t = time.perf_counter()
+        pwv_mean = pk.mean_zenith_pwv(nt)
+        t_pwv = time.perf_counter() - t
+        r_out = 25.0 * math.pi / (180 * 3600)
+        pk.common_mode(0, ok, pwv_mean, r_out, out=ok)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        pk.common_mode(0, ok, pwv_mean, r_out, out=ok)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_cm = e0.elapsed_time(e1)
+        cm_bytes = 2.0 * ok.numel() * 4 + nt * pk.n_pix * 32.0        # TOD in + out, row records
+        result["common_mode"] = {"ms": t_cm, "mean_pwv_ms": 1e3 * t_pwv, "pwv_mean_mm": pwv_mean, "r_out_arcsec": 25.0,
+                                 "algorithmic_bytes": cm_bytes, "achieved_gbs": cm_bytes / (t_cm / 1e3) / 1e9,
+                                 "peak_gbs": hbm_peak, "frac": cm_bytes / (t_cm / 1e3) / 1e9 / hbm_peak,
+                                 "kernels": "row_setup + band_transmission + common_mode", "status_flags": pk.status()}
         result["kelvin"] = {"skydip": {"pwv_mm": [dip[0], dip[1]], "n_pwv": dip[2], "elevation_rad": sc["scan"]["theta0"]},
                             "prepare_ms": 1e3 * prep_k, "prepare_ms_watts": 1e3 * prep_w,
                             "skydip_ms": 1e3 * (prep_k - prep_w), "ms_per_step": tk,

@@ -322,6 +322,24 @@ gateau_status gateau_hex_offsets(int R_hex, double spacing_rad, double* out, int
  * independent, so a service can prepare plans on worker threads. */
 gateau_status gateau_plan_prepare(gateau_plan* plan);
 
+/* ---- Downstream: common-mode reduction (Sect. 4.2, Eqs. 25-26) ----------
+ * gateau_mean_zenith_pwv: the zenith PWV averaged over the observation, i.e. the
+ * mean of the line-of-sight screen PWV over every row (n, i) with n < n_total,
+ * computed on the device (rows by the row-setup kernel, FP64 sum); synchronous.
+ * gateau_common_mode: for a brightness-temperature TOD tb[nt][n_pix][n_ch]
+ * (device, K, samples t0 .. t0+nt-1, e.g. from a run after
+ * gateau_set_output_kelvin), writes out[nt][n_pix][n_ch] (device; may be tb)
+ *   T*_a,i = T_b,i / eta_i - (1 - eta_i) / (eta_i N_out) sum_j S_j T_b,j / (1 - eta_j)
+ * with S_j = 1 for spaxels farther than r_out_rad from the IFU centre (N_out of
+ * them, at least one or EINVAL), eta_i = eta_z^csc(el_i(t)) at spaxel i's own
+ * elevation (Eq. 10), and eta_z of a channel the zenith transmission at
+ * pwv_mean_mm averaged over the band with the channel's weights eta_filt w.
+ * Enqueued on `stream`; uses the plan's row buffer, so it must not overlap a run
+ * of the same plan. */
+gateau_status gateau_mean_zenith_pwv(gateau_plan* plan, long long n_total, double* pwv_mean_mm);
+gateau_status gateau_common_mode(gateau_plan* plan, long long t0, long long nt, const float* tb, float* out,
+                                 double pwv_mean_mm, double r_out_rad, void* stream);
+
 /* Several plans' chunks on one stream.  plans[k] runs samples t0s[k] ..
  * t0s[k]+nts[k]-1 into outs[k] (device) exactly as gateau_run would, with the
  * same chunk-order rules and bit-identical results, enqueued in k order.

@@ -94,6 +94,9 @@ SIGNATURES = {
     "gateau_plan_prepare": (C.c_int, [PlanP]),
     "gateau_set_output_kelvin": (C.c_int, [PlanP, C.c_int, C.c_double, C.c_double, C.c_int]),
     "gateau_set_pink_timmer_koenig": (C.c_int, [PlanP, C.c_longlong]),
+    "gateau_mean_zenith_pwv": (C.c_int, [PlanP, C.c_longlong, C.POINTER(C.c_double)]),
+    "gateau_common_mode": (C.c_int, [PlanP, C.c_longlong, C.c_longlong, C.c_void_p, C.c_void_p, C.c_double,
+                                     C.c_double, C.c_void_p]),
     "gateau_run": (C.c_int, [PlanP, C.c_longlong, C.c_longlong, C.c_void_p, C.c_void_p]),
     "gateau_run_host": (C.c_int, [PlanP, C.c_longlong, C.c_longlong, C.c_void_p, C.c_void_p]),
     "gateau_run_batch": (C.c_int, [C.POINTER(PlanP), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),

@@ -152,6 +152,7 @@ struct gateau_plan {
     DevBuf d_pix, d_cube, d_cube_raw, d_screen, d_tau, d_custom, d_c, d_HGQ, d_fusedB, d_pink, d_state, d_status;
     DevBuf d_tb, d_dip;              // skydip fit [2][n_ch] float for the epilogues; FP64 scratch of the fit
     DevBuf d_tk, d_tkz;              // Timmer-Koenig pink TOD [tk_n][n_pix][n_ch]; its FFT scratch
+    DevBuf d_hw, d_cm;               // common-mode reduction: eta_filt w (FP64); log eta_z, S_j, PWV sum
     bool cube_scale_dirty = true;    // d_cube = d_cube_raw * c2 / k_B must be recomputed
     DevBuf d_rows, d_tiles, d_X, d_agg, d_stage[2];
     FusedOperands fused{};
@@ -185,7 +186,7 @@ struct gateau_plan {
         track_streams();
         DevBuf* bufs[] = {&d_pix, &d_cube, &d_cube_raw, &d_screen, &d_tau, &d_custom, &d_c, &d_HGQ, &d_fusedB, &d_pink,
                           &d_state, &d_status, &d_rows, &d_tiles, &d_X, &d_agg, &d_stage[0], &d_stage[1],
-                          &d_tb, &d_dip, &d_tk, &d_tkz};
+                          &d_tb, &d_dip, &d_tk, &d_tkz, &d_hw, &d_cm};
         for (DevBuf* b : bufs) b->release(mo);
         if (mo.mem) cudaStreamDestroy(mo.mem);       // its pending frees still complete
         for (int i = 0; i < 2; ++i) {
@@ -215,7 +216,7 @@ size_t device_bytes(const gateau_plan* p) {
     const DevBuf* bufs[] = {&p->d_pix, &p->d_cube, &p->d_cube_raw, &p->d_screen, &p->d_tau, &p->d_custom, &p->d_c,
                             &p->d_HGQ, &p->d_fusedB, &p->d_pink, &p->d_state, &p->d_status, &p->d_rows,
                             &p->d_tiles, &p->d_X, &p->d_agg, &p->d_stage[0], &p->d_stage[1], &p->d_tb, &p->d_dip,
-                            &p->d_tk, &p->d_tkz};
+                            &p->d_tk, &p->d_tkz, &p->d_hw, &p->d_cm};
     size_t s = 0;
     for (const DevBuf* b : bufs) s += b->bytes;
     return s;
@@ -858,6 +859,81 @@ gateau_status gateau_set_pink_timmer_koenig(gateau_plan* p, long long n_total) {
     if (n_total < 0 || n_total > (1LL << 30)) return fail(GATEAU_EINVAL, "need 0 <= n_total <= 2^30 (got %lld)", n_total);
     p->tk_n = n_total;
     p->dirty = true;
+    return GATEAU_OK;
+}
+
+gateau_status gateau_mean_zenith_pwv(gateau_plan* p, long long n_total, double* pwv_mean_mm) {
+    if (!p || !pwv_mean_mm) return fail(GATEAU_EINVAL, "plan and pwv_mean_mm must be non-NULL");
+    gateau_status st = check_complete(p);
+    if (st != GATEAU_OK) return st;
+    if (n_total <= 0) return fail(GATEAU_EINVAL, "need n_total > 0");
+    if (p->scan_kind == GATEAU_SCAN_CUSTOM && n_total > p->n_custom)
+        return fail(GATEAU_EINVAL, "custom scan has %lld samples, the mean needs %lld", p->n_custom, n_total);
+    st = finalize(p);
+    if (st != GATEAU_OK) return st;
+    const int n_pix = p->desc.n_pix;
+    const long long chunk = std::max<long long>(1, (1LL << 22) / n_pix);
+    GATEAU_CUDA(grow(p, p->d_rows, static_cast<size_t>(std::min(chunk, n_total)) * n_pix * sizeof(RowParams)));
+    GATEAU_CUDA(grow(p, p->d_cm, 64));
+    double* sum = p->d_cm.as<double>();
+    GATEAU_CUDA(cudaMemset(sum, 0, sizeof(double)));
+    const DevTables T = make_tables(p);
+    for (long long t0 = 0; t0 < n_total; t0 += chunk) {
+        const long long nt = std::min(chunk, n_total - t0);
+        GATEAU_CUDA(launch_row_setup(T, t0, nt, p->d_rows.as<RowParams>(), nullptr, nullptr));
+        GATEAU_CUDA(launch_sum_pwv(p->d_rows.as<RowParams>(), nt * n_pix, sum, nullptr));
+        p->launches += 2;
+    }
+    double h = 0.0;
+    GATEAU_CUDA(cudaMemcpy(&h, sum, sizeof(double), cudaMemcpyDeviceToHost));
+    *pwv_mean_mm = h / (static_cast<double>(n_total) * n_pix);
+    return GATEAU_OK;
+}
+
+gateau_status gateau_common_mode(gateau_plan* p, long long t0, long long nt, const float* tb, float* out,
+                                 double pwv_mean_mm, double r_out_rad, void* stream) {
+    if (!p || !tb || !out) return fail(GATEAU_EINVAL, "plan, tb and out must be non-NULL");
+    gateau_status st = check_complete(p);
+    if (st != GATEAU_OK) return st;
+    if (t0 < 0 || nt <= 0) return fail(GATEAU_EINVAL, "need t0 >= 0 and nt > 0");
+    if (!std::isfinite(pwv_mean_mm) || !std::isfinite(r_out_rad)) return fail(GATEAU_EINVAL, "non-finite argument");
+    if (p->scan_kind == GATEAU_SCAN_CUSTOM && t0 + nt > p->n_custom)
+        return fail(GATEAU_EINVAL, "custom scan has %lld samples, the reduction needs %lld", p->n_custom, t0 + nt);
+    const int n_pix = p->desc.n_pix, n_ch = p->n_ch, nf = p->desc.n_freq;
+    if (nt * static_cast<long long>(n_pix) > (1LL << 31)) return fail(GATEAU_EINVAL, "nt * n_pix must stay below 2^31");
+    // S_j (Eq. 26): spaxels farther than r_out from the IFU centre
+    std::vector<unsigned char> off(n_pix, 0);
+    int n_out = 0;
+    for (int j = 0; j < n_pix; ++j)
+        if (std::hypot(p->pix_off[2 * j], p->pix_off[2 * j + 1]) > r_out_rad) {
+            off[j] = 1;
+            ++n_out;
+        }
+    if (n_out == 0) return fail(GATEAU_EINVAL, "no spaxel lies farther than r_out = %g rad from the centre", r_out_rad);
+    st = finalize(p);
+    if (st != GATEAU_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t hw_n = static_cast<size_t>(n_ch) * nf;
+    if (p->d_hw.bytes < hw_n * sizeof(double)) {
+        std::vector<double> hw(hw_n);
+        for (int c = 0; c < n_ch; ++c)
+            for (int k = 0; k < nf; ++k) hw[static_cast<size_t>(c) * nf + k] = p->eta_filt[static_cast<size_t>(c) * nf + k] * p->w[k];
+        GATEAU_CUDA(grow(p, p->d_hw, hw_n * sizeof(double)));
+        GATEAU_CUDA(cudaMemcpy(p->d_hw.p, hw.data(), hw_n * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    GATEAU_CUDA(grow(p, p->d_cm, 64 + static_cast<size_t>(n_ch) * sizeof(float) + n_pix));
+    float* log_eta = reinterpret_cast<float*>(p->d_cm.as<uint8_t>() + 64);
+    unsigned char* d_off = reinterpret_cast<unsigned char*>(log_eta + n_ch);
+    GATEAU_CUDA(cudaMemcpyAsync(d_off, off.data(), n_pix, cudaMemcpyHostToDevice, s));
+    GATEAU_CUDA(grow(p, p->d_rows, static_cast<size_t>(nt) * n_pix * sizeof(RowParams)));
+    const DevTables T = make_tables(p);
+    GATEAU_CUDA(launch_band_transmission(p->d_hw.as<double>(), p->d_tau.as<float>(), nf, p->Kp, p->n_pwv, p->pwv_min,
+                                         p->dpwv, pwv_mean_mm, n_ch, log_eta, s));
+    GATEAU_CUDA(launch_row_setup(T, t0, nt, p->d_rows.as<RowParams>(), nullptr, s));
+    GATEAU_CUDA(launch_common_mode(tb, out, p->d_rows.as<RowParams>(), nt, n_pix, n_ch, log_eta, d_off, n_out, s));
+    p->launches += 3;
+    p->last_stream = s;
+    p->ran = true;
     return GATEAU_OK;
 }
 

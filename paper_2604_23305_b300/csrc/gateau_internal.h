@@ -158,6 +158,16 @@ cudaError_t launch_tk_realise(const double* A, const double* alpha, double f_sam
                               cudaStream_t stream);
 cudaError_t launch_tk_add(float* out, const float* tk, long long count, cudaStream_t stream);
 
+// Common-mode reduction (Sect. 4.2, Eqs. 25-26): sum of rows[0 .. n).pwv into *sum (atomic, FP64);
+// log of each channel's band transmission at zenith PWV pwv; T*_a of a TOD tb [nt][n_pix][n_ch]
+// (out may be tb) given the run's rows (csc), log_eta_z [n_ch], off_source [n_pix] (S_j) and N_out.
+cudaError_t launch_sum_pwv(const RowParams* rows, long long n, double* sum, cudaStream_t stream);
+cudaError_t launch_band_transmission(const double* hw, const float* tau, int n_freq, int Kp, int n_pwv, double pwv_min,
+                                     double dpwv, double pwv, int n_ch, float* log_eta_z, cudaStream_t stream);
+cudaError_t launch_common_mode(const float* tb, float* out, const RowParams* rows, long long nt, int n_pix, int n_ch,
+                               const float* log_eta_z, const unsigned char* off_source, int n_out,
+                               cudaStream_t stream);
+
 cudaError_t launch_pink(const DevTables& T, float* state, const PinkWork& W, long long t0, long long nt,
                         float* out, cudaStream_t stream);
 

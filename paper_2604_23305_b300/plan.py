@@ -218,6 +218,23 @@ class Plan:
         L.check(self._lib.gateau_run_host(self._h, t0, nt, out.ctypes.data, C.c_void_p(s.cuda_stream)))
         return out
 
+    def mean_zenith_pwv(self, n_total: int) -> float:
+        """Zenith PWV averaged over the observation's first n_total samples (Sect. 4.2)."""
+        v = C.c_double(0.0)
+        L.check(self._lib.gateau_mean_zenith_pwv(self._h, int(n_total), C.byref(v)))
+        return v.value
+
+    def common_mode(self, t0: int, tb, pwv_mean: float, r_out: float, out=None, stream=None):
+        """Common-mode reduction (Eqs. 25-26) of a device TOD tb [nt, n_pix, n_ch] in K."""
+        import torch
+        assert tb.is_cuda and tb.dtype == torch.float32 and tb.is_contiguous()
+        if out is None:
+            out = torch.empty_like(tb)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        L.check(self._lib.gateau_common_mode(self._h, int(t0), int(tb.shape[0]), tb.data_ptr(), out.data_ptr(),
+                                             float(pwv_mean), float(r_out), C.c_void_p(s.cuda_stream)))
+        return out
+
     def status(self) -> int:
         flags = C.c_uint(0)
         L.check(self._lib.gateau_plan_status(self._h, C.byref(flags)))
