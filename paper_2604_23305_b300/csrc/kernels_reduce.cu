@@ -100,6 +100,69 @@ __global__ void __launch_bounds__(kReduceThreads) common_mode_kernel(const float
     }
 }
 
+// e^a on the special-function unit (relative error ~2^-22).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// e^a - 1 for a <= 0 (a = csc ln eta_z): the Taylor series to a^7 where cancellation would cost
+// digits (|a| < 1/4: truncation < 3e-9 relative), 2^(a log2 e) - 1 beyond (|e^a - 1| > 0.22 there).
+__device__ __forceinline__ float expm1_neg(float a) {
+    if (a > -0.25f)
+        return a * (1.f + a * (0.5f + a * (1.f / 6 + a * (1.f / 24 + a * (1.f / 120 + a * (1.f / 720 + a * (1.f / 5040)))))));
+    return ex2_approx(a * 1.4426950408889634f) - 1.f;
+}
+
+// A whole sample (all spaxels and channels, n_pix n_ch floats) per block in shared memory: the TOD
+// is read and written with unit stride, and each channel's column is reduced from shared memory.
+constexpr int kTileMaxFloats = 12 * 1024;          // 48 KB of slab (+ the spaxels' csc)
+__global__ void __launch_bounds__(kReduceThreads) common_mode_tile_kernel(const float* tb, float* out,
+                                                                          const RowParams* __restrict__ rows,
+                                                                          long long nt, int n_pix, int n_ch,
+                                                                          const float* __restrict__ log_eta_z,
+                                                                          const unsigned char* __restrict__ off_source,
+                                                                          float inv_n_out) {
+    extern __shared__ float slab[];                 // [n_pix][n_ch], then csc [n_pix]
+    const int S = n_pix * n_ch;
+    float* csc = slab + S;
+    for (long long t = blockIdx.x; t < nt; t += gridDim.x) {
+        const float* src = tb + t * S;
+        // eight loads in flight per thread before their shared-memory stores
+        for (int e0 = threadIdx.x; e0 < S; e0 += 8 * kReduceThreads) {
+            float r[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * kReduceThreads;
+                r[u] = e < S ? src[e] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * kReduceThreads;
+                if (e < S) slab[e] = r[u];
+            }
+        }
+        for (int j = threadIdx.x; j < n_pix; j += blockDim.x) csc[j] = rows[static_cast<long long>(j) * nt + t].csc;
+        __syncthreads();
+        for (int ch = threadIdx.x; ch < n_ch; ch += blockDim.x) {
+            const float lz = log_eta_z[ch];
+            float common = 0.f;
+            for (int j = 0; j < n_pix; ++j)
+                if (off_source[j]) common += __fdividef(slab[j * n_ch + ch], -expm1_neg(csc[j] * lz));   // T_b,j / (1 - eta_j)
+            common *= inv_n_out;
+            for (int i = 0; i < n_pix; ++i) {
+                const float a = csc[i] * lz;                                            // ln eta_i
+                slab[i * n_ch + ch] = (slab[i * n_ch + ch] + expm1_neg(a) * common) * ex2_approx(-a * 1.4426950408889634f);
+            }
+        }
+        __syncthreads();
+        float* dst = out + t * S;
+        for (int e = threadIdx.x; e < S; e += blockDim.x) dst[e] = slab[e];
+        __syncthreads();
+    }
+}
+
 int grid_for(long long work) {
     const long long b = (work + kReduceThreads - 1) / kReduceThreads;
     return static_cast<int>(b < 148LL * 16 ? (b > 0 ? b : 1) : 148LL * 16);
@@ -123,8 +186,14 @@ cudaError_t launch_common_mode(const float* tb, float* out, const RowParams* row
                                const float* log_eta_z, const unsigned char* off_source, int n_out,
                                cudaStream_t stream) {
     if (n_out < 1) return cudaErrorInvalidValue;
-    common_mode_kernel<<<grid_for(nt * n_ch), kReduceThreads, 0, stream>>>(
-        tb, out, rows, nt, n_pix, n_ch, log_eta_z, off_source, 1.0f / static_cast<float>(n_out));
+    if (static_cast<long long>(n_pix) * n_ch <= kTileMaxFloats) {
+        const size_t smem = (static_cast<size_t>(n_pix) * n_ch + n_pix) * sizeof(float);
+        const long long blocks = nt < 148LL * 6 ? nt : 148LL * 6;
+        common_mode_tile_kernel<<<static_cast<unsigned>(blocks), kReduceThreads, smem, stream>>>(
+            tb, out, rows, nt, n_pix, n_ch, log_eta_z, off_source, 1.0f / static_cast<float>(n_out));
+    } else
+        common_mode_kernel<<<grid_for(nt * n_ch), kReduceThreads, 0, stream>>>(
+            tb, out, rows, nt, n_pix, n_ch, log_eta_z, off_source, 1.0f / static_cast<float>(n_out));
     return cudaGetLastError();
 }
 
