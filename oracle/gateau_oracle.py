@@ -11,6 +11,9 @@ arithmetic.
 Every function evaluates the paper's equations literally, in SI units and
 float64, stage by stage, with no algebraic collapse, blocking or fusion:
 
+  * preprocessing (source, screen) -- Sect. 2.2, Eqs. 1-3: aperture illumination,
+                                      far field |FFT(A)|^2, beam convolution of the
+                                      source cube, footprint smoothing of the screen
   * scan and pointing              -- Sect. 2.4, Eq. 8 (daisy) and the text after it
   * screen coordinates + PWV       -- Sect. 2.4, Eq. 9 (frozen flow) + bilinear lookup
   * zenith transmission + airmass  -- Sect. 2.4, Eq. 10
@@ -60,6 +63,16 @@ design notes of the repository):
     one-sided PSD, and x_n = (1/M) sum_j X_j e^{2 pi i j n / M}.  Its normals
     come from Philox with counter (q lo, q hi, i, 2^30 | ch), q = j >> 1; bin j
     takes Box-Muller pair j & 1 as (re, im).
+  * Aperture illumination (Eq. 2, garbled in print): a Gaussian whose amplitude
+    falls to t_edge dB at the rim, A(r) = 10^((t_edge / 20) (r / R)^2) for
+    r = lambda sqrt(l^2 + m^2) < R, zero outside.  The far field (Eq. 3) is the
+    2-D DFT of A sampled in wavelengths with spacing 1 / (N pitch), so that the
+    pattern comes out on the angular grid of pitch `pitch` (offset q pitch at
+    index q mod N), |.|^2 normalised to a peak of 1.  Eq. 1 is evaluated as the
+    discrete linear convolution on the cube's grid, sum over cells of
+    I cos(theta') F (phi - phi', theta - theta') dphi dtheta, times A_p = pi R^2.
+    The screen is smoothed (periodically) by A(r) on the screen grid in metres,
+    normalised to unit sum.
   * Skydip (Sect. 2.7): the PWV is varied over n uniformly spaced zenith values
     pwv_lo .. pwv_hi at the scan's base elevation theta_0, with no source and
     no noise (the recorded power is the noise-free P_KID, the mean of
@@ -89,6 +102,63 @@ C_LIGHT = 299792458.0          # m / s
 E_CHARGE = 1.602176634e-19     # J / eV
 
 F64 = np.float64
+
+
+# ---------------------------------------------------------------------------
+# Preprocessing: beam far field, source convolution, screen smoothing (Sect. 2.2, Eqs. 1-3)
+# ---------------------------------------------------------------------------
+
+def aperture_illumination(r_m, R_tel_m: float, t_edge_db: float):
+    """Amplitude 10^((t_edge/20) (r/R)^2) inside the rim (r < R), zero outside (Eq. 2 reading)."""
+    r = np.asarray(r_m, dtype=F64)
+    return np.where(r < R_tel_m, 10.0 ** ((t_edge_db / 20.0) * (r / R_tel_m) ** 2), 0.0)
+
+
+def _fft_offsets(n: int) -> np.ndarray:
+    """Index q of an n-point DFT <-> signed offset q for q < n/2, q - n above."""
+    q = np.arange(n)
+    return np.where(q < n // 2, q, q - n).astype(F64)
+
+
+def beam_far_field(nu_hz: float, n_a: int, n_e: int, d_az: float, d_el: float, R_tel_m: float, t_edge_db: float):
+    """F(q d_az, p d_el) at index (q mod n_a, p mod n_e), peak 1 (Eq. 3): |DFT of A(l, m)|^2 with l, m
+    in wavelengths on spacings 1 / (n_a d_az), 1 / (n_e d_el)."""
+    lam = C_LIGHT / nu_hz
+    l = _fft_offsets(n_a) / (n_a * d_az)
+    m = _fft_offsets(n_e) / (n_e * d_el)
+    Lg, Mg = np.meshgrid(l, m, indexing="ij")
+    A = aperture_illumination(lam * np.hypot(Lg, Mg), R_tel_m, t_edge_db)
+    F = np.abs(np.fft.fft2(A)) ** 2
+    return F / F.max()
+
+
+def convolve_source(I_cube: np.ndarray, nu_hz: np.ndarray, el0_rad: float, d_az: float, d_el: float,
+                    R_tel_m: float, t_edge_db: float) -> np.ndarray:
+    """P_src[a][e][nu] = A_p sum_{a', e'} I[a'][e'][nu] cos(el_e') F_nu(a - a', e - e') d_az d_el (Eq. 1),
+    the beam on the grid of offsets from beam_far_field at twice the cube size (linear convolution)."""
+    I_cube = np.asarray(I_cube, dtype=F64)
+    n_az, n_el, n_f = I_cube.shape
+    el = el0_rad + d_el * np.arange(n_el)
+    A_p = math.pi * R_tel_m ** 2
+    out = np.empty_like(I_cube)
+    for k in range(n_f):
+        F = beam_far_field(float(nu_hz[k]), 2 * n_az, 2 * n_el, d_az, d_el, R_tel_m, t_edge_db)
+        src = np.zeros((2 * n_az, 2 * n_el))
+        src[:n_az, :n_el] = I_cube[:, :, k] * np.cos(el)[None, :]
+        conv = np.real(np.fft.ifft2(np.fft.fft2(src) * np.fft.fft2(F)))
+        out[:, :, k] = A_p * d_az * d_el * conv[:n_az, :n_el]
+    return out
+
+
+def smooth_screen(screen: np.ndarray, pitch_m: float, R_tel_m: float, t_edge_db: float) -> np.ndarray:
+    """Periodic convolution of the screen [ny][nx] with the illumination footprint A(r), r in metres on
+    the screen grid, normalised to unit sum (line-of-sight PWV, Sect. 2.2)."""
+    s = np.asarray(screen, dtype=F64)
+    ny, nx = s.shape
+    X, Y = np.meshgrid(_fft_offsets(nx) * pitch_m, _fft_offsets(ny) * pitch_m, indexing="xy")
+    K = aperture_illumination(np.hypot(X, Y), R_tel_m, t_edge_db)
+    K = K / K.sum()
+    return np.real(np.fft.ifft2(np.fft.fft2(s) * np.fft.fft2(K)))
 
 
 # ---------------------------------------------------------------------------

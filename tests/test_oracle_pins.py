@@ -628,3 +628,64 @@ def test_common_mode_pure_atmosphere_is_zero_and_mean_pwv():
         assert np.abs(got).max() < 1e-10 * 31.0
     scu = _uniform_stare_scenario()
     assert abs(O.mean_zenith_pwv(scu, 16) - float(np.float32(1.2))) < 1e-12    # the screen holds float32
+
+
+# ---------------------------------------------------------------- preprocessing (Sect. 2.2, Eqs. 1-3)
+
+ARCSEC_RAD = math.pi / (180 * 3600)
+
+
+def test_far_field_uniform_aperture_is_airy():
+    """t_edge = 0 dB: uniform circular aperture, F(theta) = [2 J1(x) / x]^2, x = 2 pi R theta / lambda
+    (the grid spans 2048" at 2": the aperture radius is ~50 samples)."""
+    from scipy.special import j1
+    nu, R = 300e9, 5.0
+    pitch = 2 * ARCSEC_RAD
+    F = O.beam_far_field(nu, 1024, 1024, pitch, pitch, R, 0.0)
+    lam = O.C_LIGHT / nu
+    q = np.arange(1, 20)
+    x = 2 * math.pi * R * q * pitch / lam
+    airy = (2 * j1(x) / x) ** 2
+    np.testing.assert_allclose(F[q, 0], airy, atol=1e-2)
+    np.testing.assert_allclose(F[0, q], airy, atol=1e-2)
+
+
+def test_far_field_untruncated_gaussian_closed_form():
+    """A taper of -120 dB at the rim (field 1e-6 there) leaves an effectively untruncated Gaussian
+    A = exp(-a r^2), a = (120/20) ln 10 / R^2, whose far field is F(u) = exp(-2 pi^2 u^2 / (a lambda^2))."""
+    nu, R = 220e9, 5.0
+    pitch = 3 * ARCSEC_RAD
+    F = O.beam_far_field(nu, 512, 256, pitch, pitch, R, -120.0)
+    lam = O.C_LIGHT / nu
+    a = 6.0 * math.log(10.0) / R ** 2
+    u = np.arange(0, 40) * pitch
+    want = np.exp(-2 * math.pi ** 2 * u ** 2 / (a * lam ** 2))
+    np.testing.assert_allclose(F[:40, 0], want, atol=2e-4)
+    np.testing.assert_allclose(F[0, :40], want, atol=2e-4)
+
+
+def test_source_convolution_of_a_point_is_the_beam():
+    """I = I0 at one cell: P = A_p I0 cos(el') F(a - a', e - e') d_az d_el with F at twice the grid."""
+    n_az, n_el = 16, 8
+    d = 4 * ARCSEC_RAD
+    nu = np.array([250e9, 400e9])
+    I = np.zeros((n_az, n_el, 2))
+    a0, e0 = 5, 3
+    I[a0, e0, :] = 2.5e-17
+    el0 = 0.8
+    P = O.convolve_source(I, nu, el0, d, d, 5.0, -12.0)
+    for k in range(2):
+        F = O.beam_far_field(float(nu[k]), 2 * n_az, 2 * n_el, d, d, 5.0, -12.0)
+        ia = (np.arange(n_az)[:, None] - a0) % (2 * n_az)
+        ie = (np.arange(n_el)[None, :] - e0) % (2 * n_el)
+        want = math.pi * 25.0 * 2.5e-17 * math.cos(el0 + e0 * d) * F[ia, ie] * d * d
+        np.testing.assert_allclose(P[:, :, k], want, rtol=1e-9, atol=1e-12 * want.max())
+
+
+def test_screen_smoothing_conserves_and_keeps_constants():
+    rng = np.random.default_rng(8)
+    scr = rng.normal(1.0, 0.1, (64, 128))
+    out = O.smooth_screen(scr, 0.5, 5.0, -10.0)
+    assert abs(out.sum() - scr.sum()) < 1e-9 * abs(scr.sum())
+    np.testing.assert_allclose(O.smooth_screen(np.full((32, 32), 0.7), 0.5, 5.0, -10.0), 0.7, rtol=1e-12)
+    assert out.std() < scr.std()
