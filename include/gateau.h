@@ -322,6 +322,33 @@ gateau_status gateau_hex_offsets(int R_hex, double spacing_rad, double* out, int
  * independent, so a service can prepare plans on worker threads. */
 gateau_status gateau_plan_prepare(gateau_plan* plan);
 
+/* ---- Preprocessing (Sect. 2.2, Eqs. 1-3), on the device ---------------------
+ * The telescope far field F from a Gaussian aperture illumination whose amplitude
+ * falls to t_edge_db (dB, e.g. -10) at the rim of radius R_tel_m,
+ * A(r) = 10^((t_edge/20)(r/R)^2) for r < R, 0 outside (Eq. 2), as
+ * F = |2-D DFT of A|^2 normalised to a peak of 1 (Eq. 3).  A is sampled in
+ * wavelengths on spacings 1/(n d) so that F lands on the angular grid of pitch d:
+ * gateau_beam_far_field writes dev_F[n_freq][n_a][n_e] (float32, device) with the
+ * offset (q d_az, p d_el) at index (q mod n_a, p mod n_e).
+ * gateau_convolve_source evaluates Eq. 1 on a specific-intensity cube
+ * dev_I[n_az][n_el][n_freq] (W m^-2 Hz^-1 sr^-1, float32, device; cell (a, e) at
+ * az0 + a d_az, el0 + e d_el): dev_P = A_p sum over cells of I cos(el') F(dphi,
+ * dtheta) d_az d_el (W/Hz, the layout of gateau_set_source_cube), A_p = pi R^2,
+ * the beam taken on the offset grid of twice the cube (a linear convolution).
+ * gateau_smooth_screen convolves a periodic screen dev_screen[ny][nx] (pitch_m)
+ * with the footprint A(r), r in metres, normalised to unit sum (line-of-sight PWV).
+ * Sizes n_a, n_e, n_az, n_el, nx, ny: powers of two.  nu_hz: host [n_freq] (Hz).
+ * Enqueued on `stream` with scratch from its stream-ordered pool; the beam and
+ * convolution calls synchronise the stream before returning.  EINVAL on bad sizes,
+ * pitches or pointers (dev_P may not alias dev_I). */
+gateau_status gateau_beam_far_field(const double* nu_hz, int n_freq, int n_a, int n_e, double d_az_rad, double d_el_rad,
+                                    double R_tel_m, double t_edge_db, float* dev_F, void* stream);
+gateau_status gateau_convolve_source(const float* dev_I, int n_az, int n_el, int n_freq, const double* nu_hz,
+                                     double el0_rad, double d_az_rad, double d_el_rad, double R_tel_m, double t_edge_db,
+                                     float* dev_P, void* stream);
+gateau_status gateau_smooth_screen(const float* dev_screen, int nx, int ny, double pitch_m, double R_tel_m,
+                                   double t_edge_db, float* dev_out, void* stream);
+
 /* ---- Downstream: common-mode reduction (Sect. 4.2, Eqs. 25-26) ----------
  * gateau_mean_zenith_pwv: the zenith PWV averaged over the observation, i.e. the
  * mean of the line-of-sight screen PWV over every row (n, i) with n < n_total,

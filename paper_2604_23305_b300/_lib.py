@@ -95,6 +95,12 @@ SIGNATURES = {
     "gateau_set_output_kelvin": (C.c_int, [PlanP, C.c_int, C.c_double, C.c_double, C.c_int]),
     "gateau_set_pink_timmer_koenig": (C.c_int, [PlanP, C.c_longlong]),
     "gateau_mean_zenith_pwv": (C.c_int, [PlanP, C.c_longlong, C.POINTER(C.c_double)]),
+    "gateau_beam_far_field": (C.c_int, [dp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                                        C.c_void_p, C.c_void_p]),
+    "gateau_convolve_source": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, dp, C.c_double, C.c_double, C.c_double,
+                                         C.c_double, C.c_double, C.c_void_p, C.c_void_p]),
+    "gateau_smooth_screen": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_void_p,
+                                       C.c_void_p]),
     "gateau_common_mode": (C.c_int, [PlanP, C.c_longlong, C.c_longlong, C.c_void_p, C.c_void_p, C.c_double,
                                      C.c_double, C.c_void_p]),
     "gateau_run": (C.c_int, [PlanP, C.c_longlong, C.c_longlong, C.c_void_p, C.c_void_p]),

@@ -937,6 +937,94 @@ gateau_status gateau_common_mode(gateau_plan* p, long long t0, long long nt, con
     return GATEAU_OK;
 }
 
+// ---- preprocessing utilities (Sect. 2.2, Eqs. 1-3): scratch in the stream-ordered pool of `stream` ----
+static bool pow2(int n) { return n >= 2 && (n & (n - 1)) == 0; }
+
+static gateau_status check_beam(double d_az, double d_el, double R, double t_edge) {
+    if (!(d_az > 0.0) || !(d_el > 0.0) || !(R > 0.0) || !std::isfinite(d_az) || !std::isfinite(d_el) ||
+        !std::isfinite(R) || !std::isfinite(t_edge))
+        return fail(GATEAU_EINVAL, "need pitches > 0, R_tel > 0 and a finite edge taper");
+    return GATEAU_OK;
+}
+
+gateau_status gateau_beam_far_field(const double* nu_hz, int n_freq, int n_a, int n_e, double d_az_rad, double d_el_rad,
+                                    double R_tel_m, double t_edge_db, float* dev_F, void* stream) {
+    if (!nu_hz || !dev_F) return fail(GATEAU_EINVAL, "nu_hz and dev_F must be non-NULL");
+    if (n_freq < 1 || !pow2(n_a) || !pow2(n_e)) return fail(GATEAU_EINVAL, "need n_freq >= 1 and n_a, n_e powers of two >= 2");
+    if (check_beam(d_az_rad, d_el_rad, R_tel_m, t_edge_db) != GATEAU_OK) return GATEAU_EINVAL;
+    for (int k = 0; k < n_freq; ++k)
+        if (!(nu_hz[k] > 0.0) || !std::isfinite(nu_hz[k])) return fail(GATEAU_EINVAL, "frequencies must be > 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long plane = static_cast<long long>(n_a) * n_e;
+    // frequencies per batch (also the transposes' grid z extent, <= 65535)
+    const int B = static_cast<int>(std::max<long long>(1, std::min<long long>({n_freq, (1LL << 24) / plane, 4096LL})));
+    void *dnu = nullptr, *buf = nullptr;
+    GATEAU_CUDA(cudaMallocAsync(&dnu, n_freq * sizeof(double), s));
+    GATEAU_CUDA(cudaMallocAsync(&buf, 2 * static_cast<size_t>(B) * plane * sizeof(float2) + B * sizeof(float), s));
+    float2* F = static_cast<float2*>(buf);
+    float2* work = F + static_cast<size_t>(B) * plane;
+    float* peak = reinterpret_cast<float*>(work + static_cast<size_t>(B) * plane);
+    cudaError_t e = cudaMemcpyAsync(dnu, nu_hz, n_freq * sizeof(double), cudaMemcpyHostToDevice, s);
+    for (int f0 = 0; f0 < n_freq && e == cudaSuccess; f0 += B) {
+        const int b = std::min(B, n_freq - f0);
+        e = launch_beam_planes(static_cast<double*>(dnu) + f0, b, n_a, n_e, d_az_rad, d_el_rad, R_tel_m, t_edge_db, F,
+                               work, peak, s);
+        if (e == cudaSuccess) e = launch_real_part(F, dev_F + static_cast<size_t>(f0) * plane, b * plane, s);
+    }
+    cudaStreamSynchronize(s);     // nu_hz is the caller's pageable memory
+    cudaFreeAsync(buf, s);
+    cudaFreeAsync(dnu, s);
+    GATEAU_CUDA(e);
+    return GATEAU_OK;
+}
+
+gateau_status gateau_convolve_source(const float* dev_I, int n_az, int n_el, int n_freq, const double* nu_hz,
+                                     double el0_rad, double d_az_rad, double d_el_rad, double R_tel_m, double t_edge_db,
+                                     float* dev_P, void* stream) {
+    if (!dev_I || !dev_P || !nu_hz) return fail(GATEAU_EINVAL, "dev_I, dev_P and nu_hz must be non-NULL");
+    if (dev_I == dev_P) return fail(GATEAU_EINVAL, "dev_P must not alias dev_I");
+    if (n_freq < 1 || !pow2(n_az) || !pow2(n_el)) return fail(GATEAU_EINVAL, "need n_freq >= 1 and n_az, n_el powers of two >= 2");
+    if (check_beam(d_az_rad, d_el_rad, R_tel_m, t_edge_db) != GATEAU_OK || !std::isfinite(el0_rad)) return GATEAU_EINVAL;
+    for (int k = 0; k < n_freq; ++k)
+        if (!(nu_hz[k] > 0.0) || !std::isfinite(nu_hz[k])) return fail(GATEAU_EINVAL, "frequencies must be > 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long plane = 4LL * n_az * n_el;
+    const int B = static_cast<int>(std::max<long long>(1, std::min<long long>({n_freq, (1LL << 23) / plane, 4096LL})));
+    void *dnu = nullptr, *buf = nullptr;
+    GATEAU_CUDA(cudaMallocAsync(&dnu, n_freq * sizeof(double), s));
+    GATEAU_CUDA(cudaMallocAsync(&buf, 3 * static_cast<size_t>(B) * plane * sizeof(float2) + B * sizeof(float), s));
+    float2* K = static_cast<float2*>(buf);
+    float2* S = K + static_cast<size_t>(B) * plane;
+    float2* work = S + static_cast<size_t>(B) * plane;
+    float* peak = reinterpret_cast<float*>(work + static_cast<size_t>(B) * plane);
+    cudaError_t e = cudaMemcpyAsync(dnu, nu_hz, n_freq * sizeof(double), cudaMemcpyHostToDevice, s);
+    for (int f0 = 0; f0 < n_freq && e == cudaSuccess; f0 += B)
+        e = launch_convolve_source_batch(dev_I, dev_P, static_cast<double*>(dnu), std::min(B, n_freq - f0), f0, n_freq,
+                                         n_az, n_el, el0_rad, d_az_rad, d_el_rad, R_tel_m, t_edge_db, K, S, work, peak, s);
+    cudaStreamSynchronize(s);
+    cudaFreeAsync(buf, s);
+    cudaFreeAsync(dnu, s);
+    GATEAU_CUDA(e);
+    return GATEAU_OK;
+}
+
+gateau_status gateau_smooth_screen(const float* dev_screen, int nx, int ny, double pitch_m, double R_tel_m,
+                                   double t_edge_db, float* dev_out, void* stream) {
+    if (!dev_screen || !dev_out) return fail(GATEAU_EINVAL, "dev_screen and dev_out must be non-NULL");
+    if (!pow2(nx) || !pow2(ny)) return fail(GATEAU_EINVAL, "need nx, ny powers of two >= 2");
+    if (check_beam(pitch_m, pitch_m, R_tel_m, t_edge_db) != GATEAU_OK) return GATEAU_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t n = static_cast<size_t>(nx) * ny;
+    void* buf = nullptr;
+    GATEAU_CUDA(cudaMallocAsync(&buf, 3 * n * sizeof(float2) + sizeof(double), s));
+    float2* K = static_cast<float2*>(buf);
+    cudaError_t e = launch_smooth_screen(dev_screen, dev_out, nx, ny, pitch_m, R_tel_m, t_edge_db, K, K + n, K + 2 * n,
+                                         reinterpret_cast<double*>(K + 3 * n), s);
+    cudaFreeAsync(buf, s);
+    GATEAU_CUDA(e);
+    return GATEAU_OK;
+}
+
 gateau_status gateau_plan_prepare(gateau_plan* p) {
     if (!p) return fail(GATEAU_EINVAL, "plan is NULL");
     gateau_status st = check_complete(p);

@@ -153,6 +153,11 @@ cudaError_t launch_skydip_fit(const double* hw, const double* c01, const float* 
 // scratch buffers work0, work1 of (n_pix ceil(n_ch/2)) x tk_length(n_total) float2 each;
 // launch_tk_add adds tk[0 .. count) into out.
 long long tk_length(long long n_total);
+// Batched complex FFT of `rows` contiguous rows of length M (a power of two) from a, with b as the
+// second buffer (both are overwritten); sign +1: sum e^{+2 pi i jk/M} (unscaled inverse), -1:
+// forward.  *result points at whichever of a, b holds the transform.
+cudaError_t launch_fft_rows(float2* a, float2* b, long long rows, int M, int sign, const float2** result,
+                            cudaStream_t stream);
 cudaError_t launch_tk_realise(const double* A, const double* alpha, double f_sample, uint32_t k0, uint32_t k1, int n_pix,
                               int n_ch, long long n_total, const float* scale, float2* work0, float2* work1, float* tk,
                               cudaStream_t stream);
@@ -167,6 +172,25 @@ cudaError_t launch_band_transmission(const double* hw, const float* tau, int n_f
 cudaError_t launch_common_mode(const float* tb, float* out, const RowParams* rows, long long nt, int n_pix, int n_ch,
                                const float* log_eta_z, const unsigned char* off_source, int n_out,
                                cudaStream_t stream);
+
+// Preprocessing (Sect. 2.2, Eqs. 1-3), kernels_prep.cu.  Planes are complex [B][n0][n1] with n0, n1
+// powers of two.  fft2_planes: 2-D transform in place in a (b scratch).  launch_beam_planes: the far
+// field F of B frequencies nu[0..B) (device FP64) on an na x ne offset grid, peak-normalised, into F.
+// launch_convolve_source_batch: Eq. 1 for frequencies f0 .. f0+B-1 of the cube I [n_az][n_el][n_freq]
+// into P (same layout), with scratch planes K, S, work of B (2 n_az)(2 n_el) each and peak [B].
+// launch_smooth_screen: the screen [ny][nx] smoothed by the normalised footprint, scratch planes of
+// nx ny each and one device double.
+cudaError_t fft2_planes(float2* a, float2* b, int B, int n0, int n1, int sign, cudaStream_t stream);
+cudaError_t launch_real_part(const float2* in, float* out, long long n, cudaStream_t stream);
+cudaError_t launch_beam_planes(const double* nu, int B, int na, int ne, double d_az, double d_el, double R,
+                               double t_edge_db, float2* F, float2* work, float* peak, cudaStream_t stream);
+cudaError_t launch_convolve_source_batch(const float* I, float* P, const double* nu, int B, int f0, int n_freq,
+                                         int n_az, int n_el, double el0, double d_az, double d_el, double R,
+                                         double t_edge_db, float2* K, float2* S, float2* work, float* peak,
+                                         cudaStream_t stream);
+cudaError_t launch_smooth_screen(const float* screen, float* out, int nx, int ny, double pitch, double R,
+                                 double t_edge_db, float2* K, float2* S, float2* work, double* sum,
+                                 cudaStream_t stream);
 
 cudaError_t launch_pink(const DevTables& T, float* state, const PinkWork& W, long long t0, long long nt,
                         float* out, cudaStream_t stream);

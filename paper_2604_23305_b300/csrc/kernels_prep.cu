@@ -1,0 +1,253 @@
+// Preprocessing on the device (Sect. 2.2, Eqs. 1-3): the telescope far field, the beam convolution
+// of the source cube and the footprint smoothing of the PWV screen.
+//
+// Aperture illumination (Eq. 2): a Gaussian whose amplitude falls to t_edge dB at the rim,
+// A(r) = 10^((t_edge/20) (r/R)^2) for r < R, 0 outside, sampled in wavelengths (l, m) with spacings
+// 1/(N_a pitch_az), 1/(N_e pitch_el) so that its 2-D DFT lands on the angular grid of the cube
+// (offset q pitch at index q mod N).  F = |DFT A|^2, normalised to a peak of 1 (Eq. 3).  Eq. 1 is
+// the linear convolution of I cos(el') with F on the cube's grid times A_p dphi dtheta, done as a
+// product of transforms on grids of twice the cube's size.  Every 2-D transform is two passes of
+// the batched row FFT with a tiled transpose after each.  Frequencies go through in batches.
+#include <utility>
+
+#include "gateau_internal.h"
+
+namespace gateau {
+namespace {
+
+constexpr int kPrepThreads = 256;
+constexpr double kC = 299792458.0;
+
+int grid_for(long long work) {
+    const long long b = (work + kPrepThreads - 1) / kPrepThreads;
+    return static_cast<int>(b < 148LL * 32 ? (b > 0 ? b : 1) : 148LL * 32);
+}
+
+__device__ __forceinline__ double fft_offset(int q, int n) { return q < n / 2 ? q : q - n; }
+
+__device__ __forceinline__ double illumination(double r, double R, double t_edge_db) {
+    return r < R ? exp10((t_edge_db / 20.0) * (r / R) * (r / R)) : 0.0;
+}
+
+// A_b(l_q, m_p) for plane b = frequency nu[b].
+__global__ void aperture_kernel(float2* __restrict__ A, const double* __restrict__ nu, int B, int na, int ne,
+                                double d_az, double d_el, double R, double t_edge_db) {
+    const long long total = static_cast<long long>(B) * na * ne;
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int b = static_cast<int>(t / (static_cast<long long>(na) * ne));
+        const int rem = static_cast<int>(t - static_cast<long long>(b) * na * ne);
+        const int q = rem / ne, p = rem - q * ne;
+        const double lam = kC / nu[b];
+        const double l = fft_offset(q, na) / (na * d_az), m = fft_offset(p, ne) / (ne * d_el);
+        A[t] = make_float2(static_cast<float>(illumination(lam * hypot(l, m), R, t_edge_db)), 0.f);
+    }
+}
+
+// [B][n0][n1] -> [B][n1][n0], 32 x 32 tiles.
+__global__ void transpose_kernel(const float2* __restrict__ in, float2* __restrict__ out, int n0, int n1) {
+    __shared__ float2 tile[32][33];
+    const size_t plane = static_cast<size_t>(n0) * n1;
+    const float2* src = in + blockIdx.z * plane;
+    float2* dst = out + blockIdx.z * plane;
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;      // tile of columns (n1) and rows (n0)
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        const int r = r0 + y, c = c0 + threadIdx.x;
+        if (r < n0 && c < n1) tile[y][threadIdx.x] = src[static_cast<size_t>(r) * n1 + c];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        const int c = c0 + y, r = r0 + threadIdx.x;
+        if (r < n0 && c < n1) dst[static_cast<size_t>(c) * n0 + r] = tile[threadIdx.x][y];
+    }
+}
+
+// |E|^2 per plane and its maximum (one block per plane).
+__global__ void power_max_kernel(float2* __restrict__ E, long long plane, float* __restrict__ peak) {
+    __shared__ float red[kPrepThreads / 32];
+    float2* e = E + blockIdx.x * plane;
+    float mx = 0.f;
+    for (long long t = threadIdx.x; t < plane; t += blockDim.x) {
+        const float2 v = e[t];
+        const float pw = v.x * v.x + v.y * v.y;
+        e[t] = make_float2(pw, 0.f);
+        mx = fmaxf(mx, pw);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < kPrepThreads / 32; ++w) m = fmaxf(m, red[w]);
+        peak[blockIdx.x] = m;
+    }
+}
+
+__global__ void scale_planes_kernel(float2* __restrict__ E, long long plane, int B, const float* __restrict__ peak) {
+    const long long total = plane * B;
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const float s = 1.f / peak[t / plane];
+        E[t] = make_float2(E[t].x * s, E[t].y * s);
+    }
+}
+
+// Source planes: S[b][a][e] = I[a][e][f0 + b] cos(el0 + e d_el) inside the cube, 0 in the padding.
+__global__ void source_planes_kernel(const float* __restrict__ I, float2* __restrict__ S, int B, int f0, int n_freq,
+                                     int n_az, int n_el, double el0, double d_el) {
+    const int na = 2 * n_az, ne = 2 * n_el;
+    const long long total = static_cast<long long>(B) * na * ne;
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int b = static_cast<int>(t / (static_cast<long long>(na) * ne));
+        const int rem = static_cast<int>(t - static_cast<long long>(b) * na * ne);
+        const int a = rem / ne, e = rem - a * ne;
+        float v = 0.f;
+        if (a < n_az && e < n_el)
+            v = I[(static_cast<size_t>(a) * n_el + e) * n_freq + f0 + b] * static_cast<float>(cos(el0 + e * d_el));
+        S[t] = make_float2(v, 0.f);
+    }
+}
+
+__global__ void multiply_kernel(float2* __restrict__ S, const float2* __restrict__ K, long long n) {
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < n;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const float2 a = S[t], b = K[t];
+        S[t] = make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    }
+}
+
+// P[a][e][f0 + b] = scale Re S[b][a][e] for the cube's cells.
+__global__ void gather_planes_kernel(const float2* __restrict__ S, float* __restrict__ P, int B, int f0, int n_freq,
+                                     int n_az, int n_el, float scale) {
+    const int ne = 2 * n_el;
+    const long long plane = static_cast<long long>(2 * n_az) * ne;
+    const long long total = static_cast<long long>(B) * n_az * n_el;
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int cell = static_cast<int>(t / B), b = static_cast<int>(t - static_cast<long long>(cell) * B);
+        const int a = cell / n_el, e = cell - a * n_el;
+        P[static_cast<size_t>(cell) * n_freq + f0 + b] = scale * S[b * plane + static_cast<long long>(a) * ne + e].x;
+    }
+}
+
+// Footprint of the screen smoothing: A(r) on the screen grid in metres (offsets in DFT order) and its sum.
+__global__ void footprint_kernel(float2* __restrict__ K, int nx, int ny, double pitch, double R, double t_edge_db,
+                                 double* __restrict__ sum) {
+    __shared__ double red[kPrepThreads / 32];
+    const long long total = static_cast<long long>(nx) * ny;
+    double s = 0.0;
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int y = static_cast<int>(t / nx), x = static_cast<int>(t - static_cast<long long>(y) * nx);
+        const double v = illumination(pitch * hypot(fft_offset(x, nx), fft_offset(y, ny)), R, t_edge_db);
+        K[t] = make_float2(static_cast<float>(v), 0.f);
+        s += v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int w = 0; w < kPrepThreads / 32; ++w) a += red[w];
+        atomicAdd(sum, a);
+    }
+}
+
+__global__ void to_complex_kernel(const float* __restrict__ in, float2* __restrict__ out, long long n) {
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < n;
+         t += static_cast<long long>(gridDim.x) * blockDim.x)
+        out[t] = make_float2(in[t], 0.f);
+}
+
+// out = Re(in) * scale[0 or by the FP64 divisor]: scale_by is null or a device double (1 / (n scale_by)).
+__global__ void real_part_kernel(const float2* __restrict__ in, float* __restrict__ out, long long n, double scale,
+                                 const double* __restrict__ divisor) {
+    const double s = divisor ? scale / divisor[0] : scale;
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < n;
+         t += static_cast<long long>(gridDim.x) * blockDim.x)
+        out[t] = static_cast<float>(in[t].x * s);
+}
+
+}  // namespace
+
+cudaError_t launch_real_part(const float2* in, float* out, long long n, cudaStream_t stream) {
+    real_part_kernel<<<grid_for(n), kPrepThreads, 0, stream>>>(in, out, n, 1.0, nullptr);
+    return cudaGetLastError();
+}
+
+// 2-D transform of B planes [n0][n1] held in a (b is scratch); the result is left in a.
+cudaError_t fft2_planes(float2* a, float2* b, int B, int n0, int n1, int sign, cudaStream_t stream) {
+    const float2* r = nullptr;
+    cudaError_t e = launch_fft_rows(a, b, static_cast<long long>(B) * n0, n1, sign, &r, stream);
+    if (e != cudaSuccess) return e;
+    float2* other = r == a ? b : a;
+    const dim3 blk(32, 8);
+    transpose_kernel<<<dim3((n1 + 31) / 32, (n0 + 31) / 32, B), blk, 0, stream>>>(r, other, n0, n1);   // [n1][n0]
+    e = launch_fft_rows(other, const_cast<float2*>(r), static_cast<long long>(B) * n1, n0, sign, &r, stream);
+    if (e != cudaSuccess) return e;
+    if (r == a) {   // result of the column pass sits in a: move it to b transposed back, then copy into a
+        transpose_kernel<<<dim3((n0 + 31) / 32, (n1 + 31) / 32, B), blk, 0, stream>>>(a, b, n1, n0);
+        return cudaMemcpyAsync(a, b, static_cast<size_t>(B) * n0 * n1 * sizeof(float2), cudaMemcpyDeviceToDevice, stream);
+    }
+    transpose_kernel<<<dim3((n0 + 31) / 32, (n1 + 31) / 32, B), blk, 0, stream>>>(r, a, n1, n0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_beam_planes(const double* nu, int B, int na, int ne, double d_az, double d_el, double R,
+                               double t_edge_db, float2* F, float2* work, float* peak, cudaStream_t stream) {
+    const long long plane = static_cast<long long>(na) * ne;
+    aperture_kernel<<<grid_for(plane * B), kPrepThreads, 0, stream>>>(F, nu, B, na, ne, d_az, d_el, R, t_edge_db);
+    cudaError_t e = fft2_planes(F, work, B, na, ne, -1, stream);
+    if (e != cudaSuccess) return e;
+    power_max_kernel<<<B, kPrepThreads, 0, stream>>>(F, plane, peak);
+    scale_planes_kernel<<<grid_for(plane * B), kPrepThreads, 0, stream>>>(F, plane, B, peak);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convolve_source_batch(const float* I, float* P, const double* nu, int B, int f0, int n_freq,
+                                         int n_az, int n_el, double el0, double d_az, double d_el, double R,
+                                         double t_edge_db, float2* K, float2* S, float2* work, float* peak,
+                                         cudaStream_t stream) {
+    const int na = 2 * n_az, ne = 2 * n_el;
+    const long long n = static_cast<long long>(B) * na * ne;
+    cudaError_t e = launch_beam_planes(nu + f0, B, na, ne, d_az, d_el, R, t_edge_db, K, work, peak, stream);
+    if (e != cudaSuccess) return e;
+    e = fft2_planes(K, work, B, na, ne, -1, stream);                      // transform of the beam kernel
+    if (e != cudaSuccess) return e;
+    source_planes_kernel<<<grid_for(n), kPrepThreads, 0, stream>>>(I, S, B, f0, n_freq, n_az, n_el, el0, d_el);
+    e = fft2_planes(S, work, B, na, ne, -1, stream);
+    if (e != cudaSuccess) return e;
+    multiply_kernel<<<grid_for(n), kPrepThreads, 0, stream>>>(S, K, n);
+    e = fft2_planes(S, work, B, na, ne, +1, stream);
+    if (e != cudaSuccess) return e;
+    const double A_p = 3.141592653589793 * R * R;
+    const float scale = static_cast<float>(A_p * d_az * d_el / (static_cast<double>(na) * ne));   // with 1/(na ne)
+    gather_planes_kernel<<<grid_for(static_cast<long long>(B) * n_az * n_el), kPrepThreads, 0, stream>>>(
+        S, P, B, f0, n_freq, n_az, n_el, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_smooth_screen(const float* screen, float* out, int nx, int ny, double pitch, double R,
+                                 double t_edge_db, float2* K, float2* S, float2* work, double* sum,
+                                 cudaStream_t stream) {
+    const long long n = static_cast<long long>(nx) * ny;
+    cudaError_t e = cudaMemsetAsync(sum, 0, sizeof(double), stream);
+    if (e != cudaSuccess) return e;
+    footprint_kernel<<<grid_for(n), kPrepThreads, 0, stream>>>(K, nx, ny, pitch, R, t_edge_db, sum);
+    to_complex_kernel<<<grid_for(n), kPrepThreads, 0, stream>>>(screen, S, n);
+    e = fft2_planes(K, work, 1, ny, nx, -1, stream);
+    if (e != cudaSuccess) return e;
+    e = fft2_planes(S, work, 1, ny, nx, -1, stream);
+    if (e != cudaSuccess) return e;
+    multiply_kernel<<<grid_for(n), kPrepThreads, 0, stream>>>(S, K, n);
+    e = fft2_planes(S, work, 1, ny, nx, +1, stream);
+    if (e != cudaSuccess) return e;
+    // inverse transform is unscaled (1 / n) and the footprint unnormalised (1 / sum)
+    real_part_kernel<<<grid_for(n), kPrepThreads, 0, stream>>>(S, out, n, 1.0 / static_cast<double>(n), sum);
+    return cudaGetLastError();
+}
+
+}  // namespace gateau

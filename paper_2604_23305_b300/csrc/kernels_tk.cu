@@ -60,10 +60,11 @@ __global__ void __launch_bounds__(kTkThreads) tk_spectrum_kernel(float2* __restr
     }
 }
 
-// One Stockham pass of the inverse transform: sub-transforms of length Ns become length R Ns.
-template <int R>
-__global__ void __launch_bounds__(kTkThreads) tk_stockham_kernel(const float2* __restrict__ in, float2* __restrict__ out,
-                                                                 int M, int Ns, long long n_pairs) {
+// One Stockham pass over rows of length M: sub-transforms of length Ns become length R Ns.
+// SIGN = +1: e^{+2 pi i jk/M} (inverse, unscaled); -1: e^{-2 pi i jk/M} (forward).
+template <int R, int SIGN>
+__global__ void __launch_bounds__(kTkThreads) stockham_kernel(const float2* __restrict__ in, float2* __restrict__ out,
+                                                              int M, int Ns, long long n_pairs) {
     const int MR = M / R;
     const long long total = n_pairs * MR;
     for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(kTkThreads) tk_stockham_kernel(const float2* _
             // twiddle e^{+2 pi i r k / (R Ns)}: (r k) mod (R Ns) and the power-of-two divisor are exact
             float s, c;
             sincospif(2.0f * static_cast<float>((r * k) % (R * Ns)) / static_cast<float>(R * Ns), &s, &c);
+            s *= SIGN;
             v[r] = make_float2(x.x * c - x.y * s, x.x * s + x.y * c);
         }
         const int idx = (j / Ns) * Ns * R + k;
@@ -90,6 +92,7 @@ __global__ void __launch_bounds__(kTkThreads) tk_stockham_kernel(const float2* _
             for (int r = 0; r < R; ++r) {
                 float s, c;
                 sincospif(2.0f * static_cast<float>((r * q) % R) / static_cast<float>(R), &s, &c);   // constants
+                s *= SIGN;
                 acc.x += v[r].x * c - v[r].y * s;
                 acc.y += v[r].x * s + v[r].y * c;
             }
@@ -156,33 +159,43 @@ cudaError_t launch_tk_realise(const double* A, const double* alpha, double f_sam
         work0, static_cast<int>(M), P, n_pix, n_ch, A, alpha, f_sample, k0, k1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    int p = 0;
-    while ((1LL << p) < M) ++p;
-    float2* in = work0;
-    float2* out = work1;
-    int Ns = 1;
-    for (int q = 0; q < p / 3; ++q) {
-        tk_stockham_kernel<8><<<grid_for(n_pairs * (M / 8), kTkThreads), kTkThreads, 0, stream>>>(
-            in, out, static_cast<int>(M), Ns, n_pairs);
-        Ns *= 8;
-        std::swap(in, out);
-    }
-    if (p % 3 == 1) {
-        tk_stockham_kernel<2><<<grid_for(n_pairs * (M / 2), kTkThreads), kTkThreads, 0, stream>>>(
-            in, out, static_cast<int>(M), Ns, n_pairs);
-        std::swap(in, out);
-    } else if (p % 3 == 2) {
-        tk_stockham_kernel<4><<<grid_for(n_pairs * (M / 4), kTkThreads), kTkThreads, 0, stream>>>(
-            in, out, static_cast<int>(M), Ns, n_pairs);
-        std::swap(in, out);
-    }
-    e = cudaGetLastError();
+    const float2* in = nullptr;
+    e = launch_fft_rows(work0, work1, n_pairs, static_cast<int>(M), +1, &in, stream);
     if (e != cudaSuccess) return e;
     const long long S = static_cast<long long>(n_pix) * n_ch;
     const dim3 grid(static_cast<unsigned>((n_total + 31) / 32), static_cast<unsigned>((S + 31) / 32));
     if (grid.y > 65535u) return cudaErrorInvalidValue;
     tk_scatter_kernel<<<grid, dim3(32, 8), 0, stream>>>(in, static_cast<int>(M), P, n_pix, n_ch, n_total, scale, tk);
     return cudaGetLastError();
+}
+
+template <int SIGN>
+cudaError_t fft_rows_dir(float2* a, float2* b, long long rows, int M, const float2** result, cudaStream_t stream) {
+    int p = 0;
+    while ((1 << p) < M) ++p;
+    float2* in = a;
+    float2* out = b;
+    int Ns = 1;
+    for (int q = 0; q < p / 3; ++q) {
+        stockham_kernel<8, SIGN><<<grid_for(rows * (M / 8), kTkThreads), kTkThreads, 0, stream>>>(in, out, M, Ns, rows);
+        Ns *= 8;
+        std::swap(in, out);
+    }
+    if (p % 3 == 1) {
+        stockham_kernel<2, SIGN><<<grid_for(rows * (M / 2), kTkThreads), kTkThreads, 0, stream>>>(in, out, M, Ns, rows);
+        std::swap(in, out);
+    } else if (p % 3 == 2) {
+        stockham_kernel<4, SIGN><<<grid_for(rows * (M / 4), kTkThreads), kTkThreads, 0, stream>>>(in, out, M, Ns, rows);
+        std::swap(in, out);
+    }
+    *result = in;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fft_rows(float2* a, float2* b, long long rows, int M, int sign, const float2** result,
+                            cudaStream_t stream) {
+    if (M < 2 || (M & (M - 1)) != 0 || rows < 1) return cudaErrorInvalidValue;
+    return sign > 0 ? fft_rows_dir<+1>(a, b, rows, M, result, stream) : fft_rows_dir<-1>(a, b, rows, M, result, stream);
 }
 
 cudaError_t launch_tk_add(float* out, const float* tk, long long count, cudaStream_t stream) {
