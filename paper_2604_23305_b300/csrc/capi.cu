@@ -325,13 +325,16 @@ gateau_status finalize(gateau_plan* p) {
             dip[hw_n + nf + k] = p->c1[k];
         }
         GATEAU_CUDA(grow(p, p->d_dip, dip.size() * sizeof(double)));
-        GATEAU_CUDA(grow(p, p->d_tb, 2 * static_cast<size_t>(n_ch) * sizeof(float)));
+        const size_t tb_stride = (static_cast<size_t>(n_ch) + 15) / 16 * 16;
+        GATEAU_CUDA(grow(p, p->d_tb, 2 * tb_stride * sizeof(float)));
+        GATEAU_CUDA(cudaMemset(p->d_tb.p, 0, 2 * tb_stride * sizeof(float)));
         GATEAU_CUDA(cudaMemcpy(p->d_dip.p, dip.data(), (hw_n + 2 * static_cast<size_t>(nf)) * sizeof(double),
                                cudaMemcpyHostToDevice));
         double* ab = p->d_dip.as<double>() + hw_n + 2 * static_cast<size_t>(nf);
         GATEAU_CUDA(launch_skydip_fit(p->d_dip.as<double>(), p->d_dip.as<double>() + hw_n, p->d_tau.as<float>(), nf, Kp,
                                       p->n_pwv, p->pwv_min, p->dpwv, 1.0 / sin(p->theta0), d.T_atm_K, p->dip_lo,
-                                      p->dip_hi, p->dip_n, n_ch, ab, p->d_tb.as<float>(), nullptr));
+                                      p->dip_hi, p->dip_n, n_ch, ab, p->d_tb.as<float>(), static_cast<int>(tb_stride),
+                                      nullptr));
         std::vector<double> abh(2 * static_cast<size_t>(n_ch));
         GATEAU_CUDA(cudaMemcpy(abh.data(), ab, abh.size() * sizeof(double), cudaMemcpyDeviceToHost));
         p->tb_a.assign(abh.begin(), abh.begin() + n_ch);
@@ -449,7 +452,7 @@ DevTables make_tables(const gateau_plan* p) {
     T.pink_r = T.pink_a + pa;
     T.pink_d = T.pink_a + 2 * pa;
     T.tb_a = p->kelvin ? p->d_tb.as<float>() : nullptr;
-    T.tb_b = p->kelvin ? T.tb_a + p->n_ch : nullptr;
+    T.tb_b = p->kelvin ? T.tb_a + (p->n_ch + 15) / 16 * 16 : nullptr;
     T.status = p->d_status.as<unsigned int>();
     return T;
 }

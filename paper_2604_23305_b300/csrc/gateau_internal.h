@@ -87,7 +87,8 @@ struct DevTables {
     const float* pink_r;               // [n_ch][n_pole] gain folded in
     const float* pink_d;               // [n_ch] gain folded in
     // brightness-temperature output (Sect. 2.7): out = tb_a[ch] P_tot + tb_b[ch] (K), or null for W.
-    // The pink residues and direct term are already multiplied by tb_a.
+    // The pink residues and direct term are already multiplied by tb_a.  Both arrays start on
+    // 16-byte boundaries (padded to a multiple of 16 channels), so quads of channels load as float4.
     const float* tb_a;
     const float* tb_b;
     unsigned int* status;
@@ -141,11 +142,11 @@ void pink_choose_chunks(long long nt, long long S, int& C, long long& L);
 // n_dip zenith PWVs pwv_lo .. pwv_hi at elevation el (csc_el = 1 / sin el), no source, and the
 // least-squares line T_b = a P + b.  hw [n_ch][n_freq] = eta_filt w (Hz), c01 [2][n_freq] = the
 // collapsed cascade's c0, c1 (W/Hz), tau the plan's opacity table.  Writes ab [2][n_ch] (FP64:
-// a then b) and ab_f (the same in FP32).  2 <= n_dip <= kMaxSkydip.
+// a then b) and ab_f (the same in FP32, b at ab_f + ab_f_stride).  2 <= n_dip <= kMaxSkydip.
 constexpr int kMaxSkydip = 64;
 cudaError_t launch_skydip_fit(const double* hw, const double* c01, const float* tau, int n_freq, int Kp, int n_pwv,
                               double pwv_min, double dpwv, double csc_el, double T_atm, double pwv_lo, double pwv_hi,
-                              int n_dip, int n_ch, double* ab, float* ab_f, cudaStream_t stream);
+                              int n_dip, int n_ch, double* ab, float* ab_f, int ab_f_stride, cudaStream_t stream);
 
 // Exact pink noise (Timmer & Koenig, Sect. 2.6): tk_length(N) = 2^ceil(log2 N) (>= 2);
 // launch_tk_realise writes tk [n_total][n_pix][n_ch] (W, times scale[ch] when scale is not null)

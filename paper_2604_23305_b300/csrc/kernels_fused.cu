@@ -544,14 +544,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (ch0 >= T.n_ch) break;
                     float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (white) z = white_normals4_fast(n, pix, ch0 >> 2, T.key0, T.key1);
+                    // output scale: brightness temperature a P + b (Sect. 2.7), or W (a = 1, b = 0);
+                    // the arrays are padded, so the quad loads whole
+                    float4 ka = make_float4(1.f, 1.f, 1.f, 1.f), kb = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (T.tb_a) {
+                        ka = ld4(T.tb_a + ch0);
+                        kb = ld4(T.tb_b + ch0);
+                    }
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int ch = ch0 + e;
                         if (ch < T.n_ch) {
                             const float pk = T.kb1e9 * sv[4 * q + e];
                             const float sigma = T.kB * sqrtf(T.noise_scale * fmaxf(nv[4 * q + e], 0.f));
-                            const float v = fmaf(sigma, f4_get(z, e), pk);
-                            orow[ch] = T.tb_a ? fmaf(T.tb_a[ch], v, T.tb_b[ch]) : v;   // K (Sect. 2.7) or W
+                            orow[ch] = fmaf(f4_get(ka, e), fmaf(sigma, f4_get(z, e), pk), f4_get(kb, e));
                         }
                     }
                 }

@@ -33,7 +33,7 @@ __device__ double block_sum(double v, double* red) {
 __global__ void __launch_bounds__(kSkydipThreads) skydip_fit_kernel(
     const double* __restrict__ hw, const double* __restrict__ c01, const float* __restrict__ tau, int n_freq, int Kp,
     int n_pwv, double pwv_min, double dpwv, double csc_el, double T_atm, double pwv_lo, double pwv_hi, int n_dip,
-    int n_ch, double* __restrict__ ab, float* __restrict__ ab_f) {
+    int n_ch, double* __restrict__ ab, float* __restrict__ ab_f, int ab_f_stride) {
     __shared__ double red[kSkydipThreads / 32];
     __shared__ double Pm[kMaxSkydip], Tm[kMaxSkydip];
     const int ch = blockIdx.x;
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kSkydipThreads) skydip_fit_kernel(
         ab[ch] = a;
         ab[n_ch + ch] = b;
         ab_f[ch] = static_cast<float>(a);
-        ab_f[n_ch + ch] = static_cast<float>(b);
+        ab_f[ab_f_stride + ch] = static_cast<float>(b);
     }
 }
 
@@ -90,10 +90,10 @@ __global__ void __launch_bounds__(kSkydipThreads) skydip_fit_kernel(
 
 cudaError_t launch_skydip_fit(const double* hw, const double* c01, const float* tau, int n_freq, int Kp, int n_pwv,
                               double pwv_min, double dpwv, double csc_el, double T_atm, double pwv_lo, double pwv_hi,
-                              int n_dip, int n_ch, double* ab, float* ab_f, cudaStream_t stream) {
+                              int n_dip, int n_ch, double* ab, float* ab_f, int ab_f_stride, cudaStream_t stream) {
     if (n_dip < 2 || n_dip > kMaxSkydip || n_ch < 1 || n_pwv < 2) return cudaErrorInvalidValue;
     skydip_fit_kernel<<<n_ch, kSkydipThreads, 0, stream>>>(hw, c01, tau, n_freq, Kp, n_pwv, pwv_min, dpwv, csc_el,
-                                                           T_atm, pwv_lo, pwv_hi, n_dip, n_ch, ab, ab_f);
+                                                           T_atm, pwv_lo, pwv_hi, n_dip, n_ch, ab, ab_f, ab_f_stride);
     return cudaGetLastError();
 }
 
