@@ -379,7 +379,12 @@ gateau_status gateau_run_batch(gateau_plan* const* plans, const long long* t0s, 
  * gateau_plan_create, n_ch channels, an n_az x n_el source cube, an nx x ny
  * screen, an n_pwv-row table, chunks of at most chunk_samples samples, and
  * n_custom_pointing custom-scan samples (0 for built-in scans).  Used by
- * servers to admit a request before its plan exists.  EINVAL on bad sizes. */
+ * servers to admit a request before its plan exists.  Not included: the exact
+ * pink-noise realisation (gateau_set_pink_timmer_koenig: n_total n_pix n_ch
+ * float32 held, twice n_pix ceil(n_ch/2) 2^ceil(log2 n_total) complex64 while the
+ * plan is prepared) and, with brightness-temperature output or the common-mode
+ * reduction, n_ch n_freq doubles of eta_filt w (transient for the skydip).
+ * EINVAL on bad sizes. */
 gateau_status gateau_plan_estimate_bytes(const gateau_plan_desc* desc, int n_ch, int n_az, int n_el, int nx, int ny,
                                          int n_pwv, long long chunk_samples, long long n_custom_pointing,
                                          size_t* bytes);
