@@ -395,6 +395,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 lanes x 16 columns: thread t gets lane base + t/4 (registers 0, 1, 4, 5) and base + t/4 + 8
+// (registers 2, 3, 6, 7), columns 2 (t % 4) + {0, 1} (registers 0-3) and 8 + 2 (t % 4) + {0, 1} (4-7).
+__device__ __forceinline__ void tmem_ld16x256b_x2(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
@@ -528,36 +539,61 @@ __global__ void __launch_bounds__(kThreads, 1)
         long long tile, row0;
         int pix, nrows, grp;
         item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
-        const long long n = t0 + row0 + r;
-        float* orow = out + ((row0 + r) * T.n_pix + pix) * static_cast<long long>(T.n_ch);
         const int ch_base = grp * NH;
-        const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
+        // Each 16-lane half of the quadrant is read with the 16x256b shape: a thread holds rows R0
+        // and R0 + 8 for channel pairs 2 (lane % 4) + {0, 1} of both 8-channel groups of the chunk,
+        // so one store instruction covers 8 rows x 16 contiguous bytes (the 32x32b shape, one row
+        // per lane, scattered each store over 32 rows).  White noise: a quad's Philox draw (Eq. 19)
+        // serves two lanes (the two channel pairs of the quad); lanes l and l ^ 1 draw it for rows
+        // R0 and R0 + 8 respectively and swap the halves the other needs.
+        (void)r;
+        const int lq = lane & 3, lr = lane >> 2;
+        const bool odd = (lane & 1) != 0;
+        const long long S_row = static_cast<long long>(T.n_pix) * T.n_ch;
+        float* obase = out + (row0 * T.n_pix + pix) * static_cast<long long>(T.n_ch);
         for (int c = 16 * chunk_lo; c < 16 * chunk_hi; c += 16) {
-            float sv[16], nv[16];
-            tmem_ld16(d_sig + lane_off + c, sv);
-            tmem_ld16(d_noi + lane_off + c, nv);
-            tmem_wait_ld();
-            if (r < nrows) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int ch0 = ch_base + c + 4 * q;
-                    if (ch0 >= T.n_ch) break;
-                    float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (white) z = white_normals4_fast(n, pix, ch0 >> 2, T.key0, T.key1);
-                    // output scale: brightness temperature a P + b (Sect. 2.7), or W (a = 1, b = 0);
-                    // the arrays are padded, so the quad loads whole
-                    float4 ka = make_float4(1.f, 1.f, 1.f, 1.f), kb = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (T.tb_a) {
-                        ka = ld4(T.tb_a + ch0);
-                        kb = ld4(T.tb_b + ch0);
+            for (int h = 0; h < 2; ++h) {
+                float sv[8], nv[8];
+                const uint32_t toff = (static_cast<uint32_t>(quad * 32 + 16 * h) << 16) + static_cast<uint32_t>(c);
+                tmem_ld16x256b_x2(d_sig + toff, sv);
+                tmem_ld16x256b_x2(d_noi + toff, nv);
+                tmem_wait_ld();
+                const int R0 = quad * 32 + 16 * h + lr;                  // tile rows R0, R0 + 8
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    const int chq = ch_base + c + 8 * g + 2 * lq;           // this thread's channel pair
+                    float2 z0 = make_float2(0.f, 0.f), z1 = make_float2(0.f, 0.f);   // rows R0, R0 + 8
+                    if (white) {
+                        const float4 z = white_normals4_fast(t0 + row0 + R0 + (odd ? 8 : 0), pix, chq >> 2, T.key0,
+                                                             T.key1);
+                        const float sx = odd ? z.x : z.z, sy = odd ? z.y : z.w;     // what the partner needs
+                        const float rx = __shfl_xor_sync(0xffffffffu, sx, 1);
+                        const float ry = __shfl_xor_sync(0xffffffffu, sy, 1);
+                        z0 = odd ? make_float2(rx, ry) : make_float2(z.x, z.y);
+                        z1 = odd ? make_float2(z.z, z.w) : make_float2(rx, ry);
+                    }
+                    // output scale: brightness temperature a P + b (Sect. 2.7), or W (a = 1, b = 0)
+                    float2 ka = make_float2(1.f, 1.f), kb = make_float2(0.f, 0.f);
+                    if (T.tb_a && chq < T.n_ch) {
+                        ka = *reinterpret_cast<const float2*>(T.tb_a + chq);   // padded arrays, chq even
+                        kb = *reinterpret_cast<const float2*>(T.tb_b + chq);
                     }
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int ch = ch0 + e;
-                        if (ch < T.n_ch) {
-                            const float pk = T.kb1e9 * sv[4 * q + e];
-                            const float sigma = T.kB * sqrtf(T.noise_scale * fmaxf(nv[4 * q + e], 0.f));
-                            orow[ch] = fmaf(f4_get(ka, e), fmaf(sigma, f4_get(z, e), pk), f4_get(kb, e));
+                    for (int rr = 0; rr < 2; ++rr) {
+                        const int R = R0 + 8 * rr;
+                        if (R >= nrows) continue;
+                        float* orow = obase + R * S_row;
+                        const float2 zz = rr ? z1 : z0;
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const int ch = chq + e;
+                            if (ch < T.n_ch) {
+                                const int k = 4 * g + 2 * rr + e;
+                                const float pk = T.kb1e9 * sv[k];
+                                const float sigma = T.kB * sqrtf(T.noise_scale * fmaxf(nv[k], 0.f));
+                                orow[ch] = fmaf(e ? ka.y : ka.x, fmaf(sigma, e ? zz.y : zz.x, pk), e ? kb.y : kb.x);
+                            }
                         }
                     }
                 }
