@@ -415,6 +415,13 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
+// sqrt on the special-function unit (relative error ~2^-22); sigma needs ~1e-2 (Eq. 18).
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // 2^x on the special-function unit (relative error ~2^-22 over the range used here).
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -591,7 +598,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                             if (ch < T.n_ch) {
                                 const int k = 4 * g + 2 * rr + e;
                                 const float pk = T.kb1e9 * sv[k];
-                                const float sigma = T.kB * sqrtf(T.noise_scale * fmaxf(nv[k], 0.f));
+                                // k_B outside the root: k_B^2 times N would leave the normal float range
+                                const float sigma = T.kB * sqrt_approx(T.noise_scale * fmaxf(nv[k], 0.f));
                                 orow[ch] = fmaf(e ? ka.y : ka.x, fmaf(sigma, e ? zz.y : zz.x, pk), e ? kb.y : kb.x);
                             }
                         }
