@@ -963,7 +963,11 @@ gateau_status gateau_beam_far_field(const double* nu_hz, int n_freq, int n_a, in
     const int B = static_cast<int>(std::max<long long>(1, std::min<long long>({n_freq, (1LL << 24) / plane, 4096LL})));
     void *dnu = nullptr, *buf = nullptr;
     GATEAU_CUDA(cudaMallocAsync(&dnu, n_freq * sizeof(double), s));
-    GATEAU_CUDA(cudaMallocAsync(&buf, 2 * static_cast<size_t>(B) * plane * sizeof(float2) + B * sizeof(float), s));
+    if (cudaError_t ea = cudaMallocAsync(&buf, 2 * static_cast<size_t>(B) * plane * sizeof(float2) + B * sizeof(float), s);
+        ea != cudaSuccess) {
+        cudaFreeAsync(dnu, s);
+        GATEAU_CUDA(ea);
+    }
     float2* F = static_cast<float2*>(buf);
     float2* work = F + static_cast<size_t>(B) * plane;
     float* peak = reinterpret_cast<float*>(work + static_cast<size_t>(B) * plane);
@@ -995,7 +999,11 @@ gateau_status gateau_convolve_source(const float* dev_I, int n_az, int n_el, int
     const int B = static_cast<int>(std::max<long long>(1, std::min<long long>({n_freq, (1LL << 23) / plane, 4096LL})));
     void *dnu = nullptr, *buf = nullptr;
     GATEAU_CUDA(cudaMallocAsync(&dnu, n_freq * sizeof(double), s));
-    GATEAU_CUDA(cudaMallocAsync(&buf, 3 * static_cast<size_t>(B) * plane * sizeof(float2) + B * sizeof(float), s));
+    if (cudaError_t ea = cudaMallocAsync(&buf, 3 * static_cast<size_t>(B) * plane * sizeof(float2) + B * sizeof(float), s);
+        ea != cudaSuccess) {
+        cudaFreeAsync(dnu, s);
+        GATEAU_CUDA(ea);
+    }
     float2* K = static_cast<float2*>(buf);
     float2* S = K + static_cast<size_t>(B) * plane;
     float2* work = S + static_cast<size_t>(B) * plane;

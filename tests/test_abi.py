@@ -150,3 +150,43 @@ def test_status_and_info_without_gpu():
     assert p.status() == 0
     t0, st = p.get_state()
     assert t0 == 0 and (st == 0).all()
+
+
+def test_argument_validation_of_the_optional_modes_and_utilities():
+    """The setters and utilities added around the hot path reject bad arguments before any device
+    work (so this runs without a GPU)."""
+    lib = L.lib()
+    sc = W.scenario("single_pixel_small", nt_total=8)
+    p = Plan(sc, upload=False)
+    # brightness temperature: 2 <= n_pwv <= 64, 0 <= lo < hi; disabling always works
+    assert lib.gateau_set_output_kelvin(p._h, 1, 0.5, 2.0, 1) == L.EINVAL
+    assert lib.gateau_set_output_kelvin(p._h, 1, 0.5, 2.0, 65) == L.EINVAL
+    assert lib.gateau_set_output_kelvin(p._h, 1, 2.0, 0.5, 16) == L.EINVAL
+    assert lib.gateau_set_output_kelvin(p._h, 1, -1.0, 0.5, 16) == L.EINVAL
+    assert lib.gateau_set_output_kelvin(p._h, 0, 0.0, 0.0, 0) == L.OK
+    assert lib.gateau_set_output_kelvin(None, 0, 0.0, 0.0, 0) == L.EINVAL
+    # the skydip's scale is only readable once the plan is prepared
+    assert lib.gateau_set_output_kelvin(p._h, 1, 0.5, 2.0, 16) == L.OK
+    buf = np.zeros(64)
+    assert lib.gateau_plan_get_vector(p._h, L.VEC_TB_A, buf.ctypes.data_as(L.dp), 64) == L.ESTATE
+    # exact pink noise: 0 <= n_total <= 2^30
+    assert lib.gateau_set_pink_timmer_koenig(p._h, -1) == L.EINVAL
+    assert lib.gateau_set_pink_timmer_koenig(p._h, (1 << 30) + 1) == L.EINVAL
+    assert lib.gateau_set_pink_timmer_koenig(p._h, 0) == L.OK
+    # common mode and mean PWV need a complete plan
+    v = C.c_double(0.0)
+    assert lib.gateau_mean_zenith_pwv(p._h, 10, C.byref(v)) == L.ESTATE
+    assert lib.gateau_common_mode(p._h, 0, 8, C.c_void_p(1), C.c_void_p(1), 1.0, 0.0, None) == L.ESTATE
+    assert lib.gateau_common_mode(p._h, 0, 8, None, C.c_void_p(1), 1.0, 0.0, None) == L.EINVAL
+    # preprocessing utilities: powers of two, positive pitches / radius, no aliasing
+    nu = np.array([300e9])
+    nup = nu.ctypes.data_as(L.dp)
+    assert lib.gateau_beam_far_field(nup, 1, 100, 64, 1e-5, 1e-5, 5.0, -10.0, C.c_void_p(1), None) == L.EINVAL
+    assert lib.gateau_beam_far_field(nup, 1, 64, 64, 0.0, 1e-5, 5.0, -10.0, C.c_void_p(1), None) == L.EINVAL
+    assert lib.gateau_beam_far_field(nup, 1, 64, 64, 1e-5, 1e-5, -5.0, -10.0, C.c_void_p(1), None) == L.EINVAL
+    assert lib.gateau_convolve_source(C.c_void_p(1), 32, 16, 1, nup, 0.8, 1e-5, 1e-5, 5.0, -10.0, C.c_void_p(1),
+                                      None) == L.EINVAL                     # dev_P aliases dev_I
+    assert lib.gateau_convolve_source(C.c_void_p(1), 30, 16, 1, nup, 0.8, 1e-5, 1e-5, 5.0, -10.0, C.c_void_p(2),
+                                      None) == L.EINVAL
+    assert lib.gateau_smooth_screen(C.c_void_p(1), 48, 64, 0.5, 5.0, -10.0, C.c_void_p(2), None) == L.EINVAL
+    assert lib.gateau_smooth_screen(None, 64, 64, 0.5, 5.0, -10.0, C.c_void_p(2), None) == L.EINVAL
