@@ -61,10 +61,12 @@ __device__ __forceinline__ float4 white_normals4(long long n, int i, int q, uint
 
 // The same four normals with the hardware approximations of log, sin and cos
 // (absolute errors of order 1e-6 in z), used where sigma itself is only known to
-// ~1e-3 (the split-BF16 path's noise contractions).
+// ~1e-3 (the split-BF16 path's noise contractions) and for the pink-noise normals
+// (whose filtered output is compared at 1e-4 of its rms).  ln u is clamped at 0 so
+// that u within an ulp of 1 gives z = 0, never the root of a negative number.
 __device__ __forceinline__ float2 box_muller_fast(uint32_t xa, uint32_t xb) {
     const float ua = fmaf(static_cast<float>(xa), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-    const float r = sqrtf(-2.0f * __logf(ua));
+    const float r = sqrtf(-2.0f * fminf(__logf(ua), 0.f));
     const float2 cs = cos_sin_2pi_u(xb);
     return make_float2(r * cs.x, r * cs.y);
 }
@@ -83,8 +85,8 @@ __device__ __forceinline__ float4 pink_normals4(long long m, int i, int ch, uint
     const uint4 x = philox4x32_10(make_uint4(static_cast<uint32_t>(m), static_cast<uint32_t>(m >> 32),
                                              static_cast<uint32_t>(i), 0x80000000u | static_cast<uint32_t>(ch)),
                                   k0, k1);
-    const float2 a = box_muller(x.x, x.y);
-    const float2 b = box_muller(x.z, x.w);
+    const float2 a = box_muller_fast(x.x, x.y);
+    const float2 b = box_muller_fast(x.z, x.w);
     return make_float4(a.x, a.y, b.x, b.y);
 }
 
