@@ -38,9 +38,12 @@ __global__ void aperture_kernel(float2* __restrict__ A, const double* __restrict
         const int b = static_cast<int>(t / (static_cast<long long>(na) * ne));
         const int rem = static_cast<int>(t - static_cast<long long>(b) * na * ne);
         const int q = rem / ne, p = rem - q * ne;
-        const double lam = kC / nu[b];
-        const double l = fft_offset(q, na) / (na * d_az), m = fft_offset(p, ne) / (ne * d_el);
-        A[t] = make_float2(static_cast<float>(illumination(lam * hypot(l, m), R, t_edge_db)), 0.f);
+        // FP32: the plane is FP32, and l, m stay far below float's range limits
+        const float lam = static_cast<float>(kC / nu[b]);
+        const float l = static_cast<float>(fft_offset(q, na) / (na * d_az));
+        const float m = static_cast<float>(fft_offset(p, ne) / (ne * d_el));
+        const float rr = lam * hypotf(l, m) / static_cast<float>(R);
+        A[t] = make_float2(rr < 1.f ? exp10f(static_cast<float>(t_edge_db / 20.0) * rr * rr) : 0.f, 0.f);
     }
 }
 

@@ -28,15 +28,17 @@ __device__ __forceinline__ float2 tk_normals(long long j, int i, int ch, uint32_
     return (j & 1) ? box_muller(x.z, x.w) : box_muller(x.x, x.y);
 }
 
-// Coefficient X_j / M of one channel (complex; real at the Nyquist bin, zero at DC or for A = 0).
-__device__ __forceinline__ float2 tk_coef(long long j, int M, int i, int ch, int n_ch, const double* A,
-                                          const double* alpha, double f_sample, uint32_t k0, uint32_t k1) {
+// Coefficient X_j / M of one channel (complex; real at the Nyquist bin, zero at DC or for A = 0):
+// sqrt(M f_s A f_j^-alpha / 4) / M = amp_ch f_j^(-alpha/2) with amp_ch = sqrt(M f_s A / 4) / M, the
+// power evaluated as 2^(-alpha/2 log2 f_j) in FP32 (the FFT runs in FP32 too).
+__device__ __forceinline__ float2 tk_coef(long long j, int M, float log2f_j, int i, int ch, int n_ch,
+                                          const double* A, const double* alpha, double f_sample, uint32_t k0,
+                                          uint32_t k1) {
     if (ch >= n_ch || j == 0 || !(A[ch] > 0.0)) return make_float2(0.f, 0.f);
-    const double f = static_cast<double>(j) * f_sample / M;
-    const double S = A[ch] * pow(f, -alpha[ch]);
+    const float amp = static_cast<float>(sqrt(M * f_sample * A[ch] / 4.0) / M) *
+                      exp2f(-0.5f * static_cast<float>(alpha[ch]) * log2f_j);
     const float2 z = tk_normals(j, i, ch, k0, k1);
-    if (2 * j == M) return make_float2(static_cast<float>(sqrt(M * f_sample * S / 2.0) / M) * z.x, 0.f);
-    const float amp = static_cast<float>(sqrt(M * f_sample * S / 4.0) / M);
+    if (2 * j == M) return make_float2(1.41421356237f * amp * z.x, 0.f);       // real Nyquist coefficient
     return make_float2(amp * z.x, amp * z.y);
 }
 
@@ -52,8 +54,9 @@ __global__ void __launch_bounds__(kTkThreads) tk_spectrum_kernel(float2* __restr
         const long long pair = t / half;
         const long long j = t - pair * half;
         const int i = static_cast<int>(pair / P), c = static_cast<int>(pair - static_cast<long long>(i) * P);
-        const float2 a = tk_coef(j, M, i, 2 * c, n_ch, A, alpha, f_sample, k0, k1);
-        const float2 b = tk_coef(j, M, i, 2 * c + 1, n_ch, A, alpha, f_sample, k0, k1);
+        const float lf = j > 0 ? log2f(static_cast<float>(static_cast<double>(j) * f_sample / M)) : 0.f;
+        const float2 a = tk_coef(j, M, lf, i, 2 * c, n_ch, A, alpha, f_sample, k0, k1);
+        const float2 b = tk_coef(j, M, lf, i, 2 * c + 1, n_ch, A, alpha, f_sample, k0, k1);
         float2* z = Z + pair * M;
         z[j] = make_float2(a.x - b.y, a.y + b.x);
         if (j > 0 && 2 * j < M) z[M - j] = make_float2(a.x + b.y, b.x - a.y);   // conj(a) + i conj(b)
