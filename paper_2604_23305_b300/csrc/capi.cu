@@ -405,6 +405,7 @@ DevTables make_tables(const gateau_plan* p) {
     DevTables T{};
     T.n_pix = d.n_pix;
     T.pix_off = p->d_pix.as<double>();
+    T.pix_trig = T.pix_off ? T.pix_off + 2 * static_cast<size_t>(d.n_pix) : nullptr;
     T.f_sample = d.f_sample_hz;
     T.h_column = d.h_column_m;
     T.wind = d.wind_mps;
@@ -650,8 +651,22 @@ void gateau_plan_destroy(gateau_plan* plan) { delete plan; }
 // Device-side plan buffers that every run needs (pixel offsets, status word).
 static gateau_status ensure_base(gateau_plan* p) {
     if (!p->d_pix.p) {
-        GATEAU_CUDA(grow(p, p->d_pix, p->pix_off.size() * sizeof(double)));
-        GATEAU_CUDA(cudaMemcpy(p->d_pix.p, p->pix_off.data(), p->pix_off.size() * sizeof(double), cudaMemcpyHostToDevice));
+        // offsets [n_pix][2], then [n_pix][4]: tan dphi, tan dth, sin dth, cos dth (the row
+        // setup combines them with the scan pointing through the angle-addition identities)
+        const int n = p->desc.n_pix;
+        std::vector<double> tab(6 * static_cast<size_t>(n));
+        for (int i = 0; i < n; ++i) {
+            const double dphi = p->pix_off[2 * i], dth = p->pix_off[2 * i + 1];
+            tab[2 * i] = dphi;
+            tab[2 * i + 1] = dth;
+            double* tr = &tab[2 * static_cast<size_t>(n) + 4 * static_cast<size_t>(i)];
+            tr[0] = std::tan(dphi);
+            tr[1] = std::tan(dth);
+            tr[2] = std::sin(dth);
+            tr[3] = std::cos(dth);
+        }
+        GATEAU_CUDA(grow(p, p->d_pix, tab.size() * sizeof(double)));
+        GATEAU_CUDA(cudaMemcpy(p->d_pix.p, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
         GATEAU_CUDA(grow(p, p->d_status, sizeof(unsigned int)));
         GATEAU_CUDA(cudaMemset(p->d_status.p, 0, sizeof(unsigned int)));
         int dev = 0;
@@ -1124,7 +1139,7 @@ gateau_status gateau_plan_estimate_bytes(const gateau_plan_desc* d, int n_ch, in
     const double Kp = static_cast<double>((d->n_freq + 31) / 32 * 32);
     const int np = pink_pole_count(d->pink_f_min_hz, d->f_sample_hz);
     const double n_pix = d->n_pix, nc = n_ch;
-    double b = n_pix * 2 * 8 + 64;                                   // spaxel offsets, status word
+    double b = n_pix * 6 * 8 + 64;                                   // spaxel offsets and trig, status word
     b += 2.0 * n_az * n_el * Kp * 4;                                 // source cube as set + scaled copy
     b += static_cast<double>(nx) * ny * 4;                           // screen
     b += 2.0 * n_pwv * Kp * 4;                                       // interleaved opacity table

@@ -63,10 +63,17 @@ __device__ __forceinline__ float4 white_normals4(long long n, int i, int q, uint
 // (absolute errors of order 1e-6 in z), used where sigma itself is only known to
 // ~1e-3 (the split-BF16 path's noise contractions) and for the pink-noise normals
 // (whose filtered output is compared at 1e-4 of its rms).  ln u is clamped at 0 so
-// that u within an ulp of 1 gives z = 0, never the root of a negative number.
+// that u within an ulp of 1 gives z = 0, never the root of a negative number; the
+// root is the special-function unit's (argument in [0, 44.4], never subnormal).
+__device__ __forceinline__ float sqrt_approx(float x) {    // special-function unit, rel. error ~2^-22
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float2 box_muller_fast(uint32_t xa, uint32_t xb) {
     const float ua = fmaf(static_cast<float>(xa), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-    const float r = sqrtf(-2.0f * fminf(__logf(ua), 0.f));
+    const float r = sqrt_approx(-2.0f * fminf(__logf(ua), 0.f));
     const float2 cs = cos_sin_2pi_u(xb);
     return make_float2(r * cs.x, r * cs.y);
 }

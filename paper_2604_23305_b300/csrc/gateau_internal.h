@@ -46,6 +46,7 @@ struct DevTables {
     // geometry and scan (Sect. 2.4)
     int n_pix;
     const double* pix_off;             // [n_pix][2]
+    const double* pix_trig;            // [n_pix][4]: tan dphi, tan dth, sin dth, cos dth
     double f_sample, h_column, wind;
     int scan_kind;
     double sp[kMaxScanParams];

@@ -415,13 +415,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
-// sqrt on the special-function unit (relative error ~2^-22); sigma needs ~1e-2 (Eq. 18).
-__device__ __forceinline__ float sqrt_approx(float x) {
-    float y;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 // 2^x on the special-function unit (relative error ~2^-22 over the range used here).
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;

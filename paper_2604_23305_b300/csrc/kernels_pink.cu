@@ -9,12 +9,22 @@
 //            s_in[c+1] = a^len(c) s_in[c] + agg[c], seeded by the carried state;
 //   phase 3: each (chunk, sequence) reruns its chunk from s_in[c] and adds y.
 // Threads of a warp own consecutive channels of one spaxel, so every sample
-// step reads and writes 128 contiguous bytes of out.
+// step reads and writes 128 contiguous bytes of out.  The poles are held in
+// pairs and updated with packed FP32 FMAs (two poles per instruction, each lane
+// rounded exactly like fmaf), which halves the issue slots of the recurrence.
 #include <math.h>
 
 #include "device_common.cuh"
 
 namespace gateau {
+
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Pole pair h of channel ch: (x[2h], x[2h + 1]), zero past the last pole.
+__device__ __forceinline__ float2 pole_pair(const float* x, int ch, int np, int h) {
+    const int j = 2 * h;
+    return make_float2(j < np ? x[ch * np + j] : 0.f, j + 1 < np ? x[ch * np + j + 1] : 0.f);
+}
 
 // Samples are visited in groups of the 4 that one Philox call serves (m = n >> 2).
 template <int NP>
@@ -29,23 +39,24 @@ __global__ __launch_bounds__(256) void pink_phase1_kernel(DevTables T, PinkWork 
         const int i = static_cast<int>(s / T.n_ch), ch = static_cast<int>(s - static_cast<long long>(i) * T.n_ch);
         const long long a0 = t0 + c * W.L;
         const long long b0 = min(a0 + W.L, t0 + nt);
-        float av[NP], st[NP];
+        constexpr int NH = NP / 2;
+        float2 av[NH], st[NH];
 #pragma unroll
-        for (int j = 0; j < NP; ++j) {
-            av[j] = (j < np) ? T.pink_a[ch * np + j] : 0.f;
-            st[j] = 0.f;
+        for (int h = 0; h < NH; ++h) {
+            av[h] = pole_pair(T.pink_a, ch, np, h);
+            st[h] = make_float2(0.f, 0.f);
         }
         long long n = a0;
         // whole groups of 4 (the usual case: chunk starts are multiples of 4 when t0 is)
         if ((n & 3) == 0) {
             for (; n + 4 <= b0; n += 4) {
                 const float4 z4 = pink_normals4(n >> 2, i, ch, T.key0, T.key1);
+                const float zq[4] = {z4.x, z4.y, z4.z, z4.w};
 #pragma unroll
-                for (int j = 0; j < NP; ++j) {
-                    float v = fmaf(av[j], st[j], z4.x);
-                    v = fmaf(av[j], v, z4.y);
-                    v = fmaf(av[j], v, z4.z);
-                    st[j] = fmaf(av[j], v, z4.w);
+                for (int q = 0; q < 4; ++q) {
+                    const float2 zz = make_float2(zq[q], zq[q]);
+#pragma unroll
+                    for (int h = 0; h < NH; ++h) st[h] = fma2(av[h], st[h], zz);
                 }
             }
         }
@@ -56,15 +67,18 @@ __global__ __launch_bounds__(256) void pink_phase1_kernel(DevTables T, PinkWork 
             const float4 z4 = pink_normals4(m, i, ch, T.key0, T.key1);
             for (int q = q0; q < q1; ++q) {
                 const float z = f4_get(z4, q);
+                const float2 zz = make_float2(z, z);
 #pragma unroll
-                for (int j = 0; j < NP; ++j) st[j] = fmaf(av[j], st[j], z);
+                for (int h = 0; h < NH; ++h) st[h] = fma2(av[h], st[h], zz);
             }
             n = (m << 2) + q1;
         }
         float* ag = W.agg + (c * S + s) * np;
 #pragma unroll
-        for (int j = 0; j < NP; ++j)
-            if (j < np) ag[j] = st[j];
+        for (int h = 0; h < NH; ++h) {
+            if (2 * h < np) ag[2 * h] = st[h].x;
+            if (2 * h + 1 < np) ag[2 * h + 1] = st[h].y;
+        }
     }
 }
 
@@ -106,12 +120,13 @@ __global__ __launch_bounds__(256) void pink_phase3_kernel(DevTables T, PinkWork 
         const long long a0 = t0 + c * W.L;
         const long long b0 = min(a0 + W.L, t0 + nt);
         const float* ag = W.agg + (c * S + s) * np;
-        float av[NP], rv[NP], st[NP];
+        constexpr int NH = NP / 2;
+        float2 av[NH], rv[NH], st[NH];
 #pragma unroll
-        for (int j = 0; j < NP; ++j) {
-            av[j] = (j < np) ? T.pink_a[ch * np + j] : 0.f;
-            rv[j] = (j < np) ? T.pink_r[ch * np + j] : 0.f;
-            st[j] = (j < np) ? ag[j] : 0.f;
+        for (int h = 0; h < NH; ++h) {
+            av[h] = pole_pair(T.pink_a, ch, np, h);
+            rv[h] = pole_pair(T.pink_r, ch, np, h);
+            st[h] = make_float2(2 * h < np ? ag[2 * h] : 0.f, 2 * h + 1 < np ? ag[2 * h + 1] : 0.f);
         }
         const float d = T.pink_d[ch];
         float* o = out + ((a0 - t0) * T.n_pix + i) * static_cast<long long>(T.n_ch) + ch;
@@ -132,12 +147,14 @@ __global__ __launch_bounds__(256) void pink_phase3_kernel(DevTables T, PinkWork 
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const float z = zq[q];
-                    float y = d * z;
+                    const float2 zz = make_float2(z, z);
+                    float2 y2 = make_float2(d * z, 0.f);
 #pragma unroll
-                    for (int j = 0; j < NP; ++j) {
-                        st[j] = fmaf(av[j], st[j], z);
-                        y = fmaf(rv[j], st[j], y);
+                    for (int h = 0; h < NH; ++h) {
+                        st[h] = fma2(av[h], st[h], zz);
+                        y2 = fma2(rv[h], st[h], y2);
                     }
+                    const float y = y2.x + y2.y;
                     o[q * stride] = cur4[q] + y;
                 }
                 n += 4;
@@ -166,12 +183,14 @@ __global__ __launch_bounds__(256) void pink_phase3_kernel(DevTables T, PinkWork 
             for (int q = 0; q < 4; ++q) {
                 if (q >= q0 && q < q1) {
                     const float z = f4_get(z4, q);
-                    float y = d * z;
+                    const float2 zz = make_float2(z, z);
+                    float2 y2 = make_float2(d * z, 0.f);
 #pragma unroll
-                    for (int j = 0; j < NP; ++j) {
-                        st[j] = fmaf(av[j], st[j], z);
-                        y = fmaf(rv[j], st[j], y);
+                    for (int h = 0; h < NH; ++h) {
+                        st[h] = fma2(av[h], st[h], zz);
+                        y2 = fma2(rv[h], st[h], y2);
                     }
+                    const float y = y2.x + y2.y;
                     o[(q - q0) * stride] = cur[q] + y;
                 }
             }

@@ -43,54 +43,89 @@ __device__ __forceinline__ void scan_pointing(const DevTables& T, long long n, d
     }
 }
 
-// Python-style floating modulo: result in [0, m) with the sign of m.
-__device__ __forceinline__ double pymod(double a, double m) {
-    double r = fmod(a, m);
-    if (r != 0.0 && ((r < 0.0) != (m < 0.0))) r += m;
+// Python-style floating modulo for m > 0: the result in [0, m).  With q = floor(a / m)
+// the remainder a - q m is exact (one fused multiply-add) whenever q is the true
+// quotient; a quotient rounded across an integer is corrected by one step of m.
+__device__ __forceinline__ double wrap_mod(double a, double m, double inv_m) {
+    const double q = floor(a * inv_m);
+    double r = fma(-q, m, a);
+    if (r < 0.0) r += m;
+    if (r >= m) r -= m;
     return r;
 }
 
-__device__ __forceinline__ RowParams make_row(const DevTables& T, long long n, int i) {
-    const double t = static_cast<double>(n) / T.f_sample;
-    double phs, ths;
-    scan_pointing(T, n, t, phs, ths);
+// What a row needs from its time sample alone (Sect. 2.4): the time, the scan pointing
+// and the trigonometry of it that every spaxel reuses.
+struct SampleGeom {
+    double t, phs, ths, tan_phs, tan_ths, sin_a, cos_a;   // a = ths + theta0
+};
+
+__device__ __forceinline__ SampleGeom sample_geom(const DevTables& T, long long n) {
+    SampleGeom g;
+    g.t = static_cast<double>(n) / T.f_sample;
+    scan_pointing(T, n, g.t, g.phs, g.ths);
+    g.tan_phs = tan(g.phs);
+    g.tan_ths = tan(g.ths);
+    sincos(g.ths + T.theta0, &g.sin_a, &g.cos_a);
+    return g;
+}
+
+// Reciprocals of the per-plan divisors, formed once per thread.
+struct RowScales {
+    double inv_pitch, inv_nx, inv_ny, inv_dpwv, inv_daz, inv_del;
+};
+
+__device__ __forceinline__ RowScales row_scales(const DevTables& T) {
+    RowScales k;
+    k.inv_pitch = 1.0 / T.pitch;
+    k.inv_nx = 1.0 / T.nx;
+    k.inv_ny = 1.0 / T.ny;
+    k.inv_dpwv = 1.0 / T.dpwv;
+    k.inv_daz = 1.0 / T.daz;
+    k.inv_del = 1.0 / T.del;
+    return k;
+}
+
+// Row (sample n, spaxel i).  The spaxel's offsets enter through the angle-addition
+// identities, tan(p + d) = (tan p + tan d) / (1 - tan p tan d) and
+// sin(a + d) = sin a cos d + cos a sin d, with tan d, sin d, cos d tabulated per spaxel.
+__device__ __forceinline__ RowParams make_row(const DevTables& T, const SampleGeom& g, const RowScales& k, int i) {
     const double dphi = T.pix_off[2 * i], dth = T.pix_off[2 * i + 1];
-    const double az = phs + T.phi0 + dphi;                   // spaxel pointing (Sect. 2.4)
-    const double el = ths + T.theta0 + dth;
+    const double* tr = T.pix_trig + 4 * i;
+    const double az = g.phs + T.phi0 + dphi;                 // spaxel pointing (Sect. 2.4)
+    const double el = g.ths + T.theta0 + dth;
     // Frozen-flow screen coordinates (Eq. 9) and periodic bilinear PWV.
-    const double x = T.h_column * tan(phs + dphi) + T.wind * t;
-    const double y = T.h_column * tan(ths + dth);
-    double gx = pymod(x / T.pitch + 0.5 * T.nx, static_cast<double>(T.nx));
-    double gy = pymod(y / T.pitch + 0.5 * T.ny, static_cast<double>(T.ny));
-    if (!(gx >= 0.0 && gx <= T.nx) || !(gy >= 0.0 && gy <= T.ny)) {   // non-finite pointing
+    const double x = T.h_column * ((g.tan_phs + tr[0]) / (1.0 - g.tan_phs * tr[0])) + T.wind * g.t;
+    const double y = T.h_column * ((g.tan_ths + tr[1]) / (1.0 - g.tan_ths * tr[1]));
+    double gx = wrap_mod(x * k.inv_pitch + 0.5 * T.nx, static_cast<double>(T.nx), k.inv_nx);
+    double gy = wrap_mod(y * k.inv_pitch + 0.5 * T.ny, static_cast<double>(T.ny), k.inv_ny);
+    if (!(gx >= 0.0 && gx < T.nx) || !(gy >= 0.0 && gy < T.ny)) {   // non-finite pointing
         atomicOr(T.status, GATEAU_STATUS_BAD_INDEX);
         gx = 0.0;
         gy = 0.0;
     }
-    int ix = static_cast<int>(floor(gx)), iy = static_cast<int>(floor(gy));
+    const int ix = static_cast<int>(floor(gx)), iy = static_cast<int>(floor(gy));
     const double fx = gx - ix, fy = gy - iy;
-    ix %= T.nx;
-    iy %= T.ny;
-    const int ix1 = (ix + 1) % T.nx, iy1 = (iy + 1) % T.ny;
+    const int ix1 = (ix + 1 == T.nx) ? 0 : ix + 1, iy1 = (iy + 1 == T.ny) ? 0 : iy + 1;
     const double s00 = T.screen[static_cast<long long>(iy) * T.nx + ix];
     const double s01 = T.screen[static_cast<long long>(iy) * T.nx + ix1];
     const double s10 = T.screen[static_cast<long long>(iy1) * T.nx + ix];
     const double s11 = T.screen[static_cast<long long>(iy1) * T.nx + ix1];
     const double pwv = (1 - fx) * (1 - fy) * s00 + fx * (1 - fy) * s01 + (1 - fx) * fy * s10 + fx * fy * s11;
     // Opacity-table row (linear in PWV, clamped) and airmass (Eq. 10).
-    double u = (pwv - T.pwv_min) / T.dpwv;
+    double u = (pwv - T.pwv_min) * k.inv_dpwv;
     if (!(u >= 0.0 && u <= T.n_pwv - 1)) {                          // also catches NaN
         u = fmin(fmax(u, 0.0), static_cast<double>(T.n_pwv - 1));
         atomicOr(T.status, GATEAU_STATUS_PWV_CLAMPED);
     }
     const int j = min(static_cast<int>(floor(u)), T.n_pwv - 2);
     RowParams rp;
-    rp.csc = static_cast<float>(1.0 / sin(el));
+    rp.csc = 1.0f / static_cast<float>(g.sin_a * tr[3] + g.cos_a * tr[2]);
     rp.tau_j = j;
     rp.tau_f = static_cast<float>(u - j);
     rp.pwv = static_cast<float>(pwv);
     // Source cell (bilinear, zero outside the grid).
-    const double su = (az - T.az0) / T.daz, sv = (el - T.el0) / T.del;
+    const double su = (az - T.az0) * k.inv_daz, sv = (el - T.el0) * k.inv_del;
     if (su >= 0.0 && su <= T.n_az - 1 && sv >= 0.0 && sv <= T.n_el - 1) {
         const int ia = min(static_cast<int>(floor(su)), T.n_az - 2);
         const int ie = min(static_cast<int>(floor(sv)), T.n_el - 2);
@@ -107,61 +142,85 @@ __device__ __forceinline__ RowParams make_row(const DevTables& T, long long n, i
     return rp;
 }
 
-// One block of kTileRows threads per tile of kTileRows consecutive samples of one
-// spaxel; rows are pixel-major within a run (r = i * nt + (n - t0)).  With a tile
-// buffer, the block also reduces the opacity-row range and the cube box of the tile.
+// One block of kTileRows threads per tile of kTileRows consecutive samples; a thread
+// forms its sample's geometry once and then the rows of every spaxel, stored
+// pixel-major within a run (r = i * nt + (n - t0)), so each spaxel's stores are
+// contiguous across the block.  With a tile buffer, the block also reduces, per
+// spaxel, the tile's opacity-row range and cube box (warp reductions, then the four
+// warps' partial results through a shared-memory buffer that alternates on every
+// spaxel step, so one barrier per step orders each buffer's writes and its read).
 __global__ void __launch_bounds__(kTileRows) row_setup_kernel(DevTables T, long long t0, long long nt,
                                                               RowParams* rows, TileInfo* tiles) {
-    __shared__ int s_jmin, s_jmax, s_amin, s_amax, s_emin, s_emax, s_nsrc;
+    constexpr int kWarps = kTileRows / 32;
+    __shared__ int s_part[2][kWarps][7];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long tpp = (nt + kTileRows - 1) / kTileRows;
-    const long long n_tiles = tpp * T.n_pix;
-    for (long long b = blockIdx.x; b < n_tiles; b += gridDim.x) {
-        const int i = static_cast<int>(b / tpp);
-        const long long r = (b - static_cast<long long>(i) * tpp) * kTileRows + threadIdx.x;
-        if (tiles && threadIdx.x == 0) {
-            s_jmin = s_amin = s_emin = 0x7fffffff;
-            s_jmax = s_amax = s_emax = -1;
-            s_nsrc = 0;
-        }
-        __syncthreads();
-        if (r < nt) {
-            const RowParams rp = make_row(T, t0 + r, i);
-            rows[static_cast<long long>(i) * nt + r] = rp;
-            if (tiles) {
-                atomicMin(&s_jmin, rp.tau_j);
-                atomicMax(&s_jmax, rp.tau_j);
+    const RowScales k = row_scales(T);
+    int use = 0;                                       // alternates the buffer on every spaxel step
+    for (long long b = blockIdx.x; b < tpp; b += gridDim.x) {
+        const long long r = b * kTileRows + threadIdx.x;
+        const bool valid = r < nt;
+        SampleGeom g{};
+        if (valid) g = sample_geom(T, t0 + r);
+        for (int i = 0; i < T.n_pix; ++i) {
+            int jmin = 0x7fffffff, jmax = -1, amin = 0x7fffffff, amax = -1, emin = 0x7fffffff, emax = -1, has = 0;
+            if (valid) {
+                const RowParams rp = make_row(T, g, k, i);
+                rows[static_cast<long long>(i) * nt + r] = rp;
+                jmin = jmax = rp.tau_j;
                 if (rp.src_cell >= 0) {
-                    atomicMin(&s_amin, rp.src_cell >> 16);
-                    atomicMax(&s_amax, rp.src_cell >> 16);
-                    atomicMin(&s_emin, rp.src_cell & 0xffff);
-                    atomicMax(&s_emax, rp.src_cell & 0xffff);
-                    atomicAdd(&s_nsrc, 1);
+                    amin = amax = rp.src_cell >> 16;
+                    emin = emax = rp.src_cell & 0xffff;
+                    has = 1;
                 }
             }
-        }
-        __syncthreads();
-        if (tiles && threadIdx.x == 0) {
-            TileInfo ti;
-            ti.j0 = s_jmin;
-            ti.ia0 = s_nsrc ? s_amin : 0;
-            ti.ie0 = s_nsrc ? s_emin : 0;
-            int f = 0;
-            if (s_jmax - s_jmin <= kTauBoxRows - 1) f |= TILE_TAU_FITS;
-            if (s_nsrc) {
-                f |= TILE_HAS_SOURCE;
-                if (s_amax + 1 - s_amin <= kCubeBoxAz - 1 && s_emax + 1 - s_emin <= kCubeBoxEl - 1) f |= TILE_CUBE_FITS;
+            if (!tiles) continue;
+            const unsigned full = 0xffffffffu;
+            jmin = __reduce_min_sync(full, jmin);
+            jmax = __reduce_max_sync(full, jmax);
+            amin = __reduce_min_sync(full, amin);
+            amax = __reduce_max_sync(full, amax);
+            emin = __reduce_min_sync(full, emin);
+            emax = __reduce_max_sync(full, emax);
+            has = __reduce_add_sync(full, has);
+            const int buf = use;
+            use ^= 1;
+            int* part = s_part[buf][warp];
+            if (lane == 0) {
+                part[0] = jmin; part[1] = jmax; part[2] = amin; part[3] = amax;
+                part[4] = emin; part[5] = emax; part[6] = has;
             }
-            ti.flags = f;
-            tiles[b] = ti;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int v[7] = {0x7fffffff, -1, 0x7fffffff, -1, 0x7fffffff, -1, 0};
+                for (int w = 0; w < kWarps; ++w) {
+                    const int* q = s_part[buf][w];
+                    v[0] = min(v[0], q[0]); v[1] = max(v[1], q[1]);
+                    v[2] = min(v[2], q[2]); v[3] = max(v[3], q[3]);
+                    v[4] = min(v[4], q[4]); v[5] = max(v[5], q[5]);
+                    v[6] += q[6];
+                }
+                TileInfo ti;
+                ti.j0 = v[0];
+                ti.ia0 = v[6] ? v[2] : 0;
+                ti.ie0 = v[6] ? v[4] : 0;
+                int f = 0;
+                if (v[1] - v[0] <= kTauBoxRows - 1) f |= TILE_TAU_FITS;
+                if (v[6]) {
+                    f |= TILE_HAS_SOURCE;
+                    if (v[3] + 1 - v[2] <= kCubeBoxAz - 1 && v[5] + 1 - v[4] <= kCubeBoxEl - 1) f |= TILE_CUBE_FITS;
+                }
+                ti.flags = f;
+                tiles[static_cast<long long>(i) * tpp + b] = ti;
+            }
         }
-        __syncthreads();
     }
 }
 
 cudaError_t launch_row_setup(const DevTables& T, long long t0, long long nt, RowParams* rows, TileInfo* tiles,
                              cudaStream_t stream) {
-    const long long n_tiles = (nt + kTileRows - 1) / kTileRows * T.n_pix;
-    long long grid = n_tiles < 148LL * 16 ? n_tiles : 148LL * 16;
+    const long long tpp = (nt + kTileRows - 1) / kTileRows;        // one block per time tile
+    long long grid = tpp < 148LL * 16 ? tpp : 148LL * 16;
     row_setup_kernel<<<static_cast<unsigned>(grid), kTileRows, 0, stream>>>(T, t0, nt, rows, tiles);
     return cudaGetLastError();
 }
