@@ -395,18 +395,34 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// 16 lanes x 16 columns: thread t gets lane base + t/4 (registers 0, 1, 4, 5) and base + t/4 + 8
-// (registers 2, 3, 6, 7), columns 2 (t % 4) + {0, 1} (registers 0-3) and 8 + 2 (t % 4) + {0, 1} (4-7).
-__device__ __forceinline__ void tmem_ld16x256b_x2(uint32_t taddr, float* v) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+// 16 lanes x 8 columns (the 16x256b shape): thread t gets lane base + t/4 (registers 0, 1) and
+// base + t/4 + 8 (registers 2, 3), columns 2 (t % 4) + {0, 1}.
+__device__ __forceinline__ void tmem_ld16x256b_x1(uint32_t taddr, uint32_t (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                  : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// The wait for this thread's TMEM loads, naming the 12 registers they fill: the compiler sees
+// them written here, so no use of them is scheduled before the data has arrived.
+__device__ __forceinline__ void tmem_wait_ld_regs(uint32_t (&a)[4], uint32_t (&b)[4], uint32_t (&c)[4]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]),
+                   "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3])
+                 :
+                 : "memory");
+}
+
+// The store of the same shape: register i of thread t goes to the cell that tmem_ld16x256b_x1
+// reads into register i of thread t.
+__device__ __forceinline__ void tmem_st16x256b_x1(uint32_t taddr, const float (&v)[4]) {
+    asm volatile("tcgen05.st.sync.aligned.16x256b.x1.b32 [%0], {%1,%2,%3,%4};"
+                 ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                   "r"(__float_as_uint(v[3]))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo_elem, hi_elem);
@@ -518,18 +534,52 @@ __global__ void __launch_bounds__(kThreads, 1)
         return share ? u * 2 + rank : u;
     };
 
-    // ---------------- epilogue of one item: this warp's share of the channel chunks ----------------
+    // ---------------- epilogue of one item: this warp's share of the units ----------------
     // A warp reads the TMEM lanes of its quadrant (warp mod 4) = tile rows [32 quad, 32 quad + 32).
-    // Each quadrant's chunks of 16 channels are split over three warps: the epilogue warp and one
-    // warp of each producer group, which are idle while the accumulators drain.
+    // Unit u = (chunk u / 4 of 16 channels, 16-lane half (u / 2) % 2, 8-channel group u % 2).  Each
+    // quadrant's chunks are split over three warps (the epilogue warp and one warp of each producer
+    // group, idle while the accumulators drain) in runs of whole chunks.  (Runs weighted by the cost
+    // of drawing normals in the epilogue measured slower: the time per unit is not set by the draw.)
     const int n_chunks = NH / 16;
+    const bool white = (T.noise_flags & GATEAU_NOISE_WHITE) != 0;
+    constexpr int kZChunks = 10;
     const int epi_role = warp >= kEpiWarp0 ? 0 : (warp < kProdWarp0 + 4 ? 1 : 2);
     const int cut1 = (n_chunks + 2) / 3, cut2 = cut1 + (n_chunks - cut1 + 1) / 2;
-    const int chunk_lo = epi_role == 0 ? 0 : (epi_role == 1 ? cut1 : cut2);
-    const int chunk_hi = epi_role == 0 ? cut1 : (epi_role == 1 ? cut2 : n_chunks);
-    const bool white = (T.noise_flags & GATEAU_NOISE_WHITE) != 0;
+    const int unit_lo = 4 * (epi_role == 0 ? 0 : (epi_role == 1 ? cut1 : cut2));
+    const int unit_hi = 4 * (epi_role == 0 ? cut1 : (epi_role == 1 ? cut2 : n_chunks));
+    const int zu_all = white ? 4 * min(n_chunks, kZChunks) : 0;       // units with parked normals
+    const int lq = lane & 3, lr = lane >> 2;
+    const bool odd = (lane & 1) != 0;
+    // White normals of Eq. 19 for rows (R0, R0 + 8) x channel pairs (chq, chq + 1) of this thread,
+    // tile row R0 at sample trow0: a quad's Philox draw serves two lanes (the two channel pairs of
+    // the quad); lanes l and l ^ 1 draw it for rows R0 and R0 + 8 respectively and swap the halves
+    // the other needs.  Warp-collective (shuffles).
+    auto white_pair = [&](long long trow0, int pix, int chq, float2& z0, float2& z1) {
+        const float4 z = white_normals4_fast(trow0 + (odd ? 8 : 0), pix, chq >> 2, T.key0, T.key1);
+        const float sx = odd ? z.x : z.z, sy = odd ? z.y : z.w;     // what the partner needs
+        const float rx = __shfl_xor_sync(0xffffffffu, sx, 1);
+        const float ry = __shfl_xor_sync(0xffffffffu, sy, 1);
+        z0 = odd ? make_float2(rx, ry) : make_float2(z.x, z.y);
+        z1 = odd ? make_float2(z.z, z.w) : make_float2(rx, ry);
+    };
+    // The normals depend on (sample, spaxel, channel) only, so the warps that share an item's
+    // epilogue draw them for their own units while the item's MMAs run and park them in the TMEM
+    // columns the accumulators leave free, [176, 256) and [432, 512): chunks 0..9 of a group, 16
+    // columns each (a group's chunk 10 is drawn in the epilogue).  A unit is stored with the shape
+    // the epilogue loads it with.
+    const int zu_hi = white ? min(unit_hi, zu_all) : unit_lo;       // parked units [unit_lo, zu_hi)
+    const int n_zunits = zu_hi > unit_lo ? zu_hi - unit_lo : 0;
+    auto zcol = [](int k) -> uint32_t { return k < 5 ? 176u + 16u * k : 432u + 16u * (k - 5); };
+    auto park_unit = [&](int k, long long row0, int pix, int ch_base) {
+        const int u = unit_lo + k, ck = u >> 2, h = (u >> 1) & 1, g = u & 1, tq = warp & 3;
+        float2 z0, z1;
+        white_pair(t0 + row0 + tq * 32 + 16 * h + lr, pix, ch_base + 16 * ck + 8 * g + 2 * lq, z0, z1);
+        const float zv[4] = {z0.x, z0.y, z1.x, z1.y};
+        tmem_st16x256b_x1(tmem_base + zcol(ck) + 8 * g + (static_cast<uint32_t>(tq * 32 + 16 * h) << 16), zv);
+    };
     auto epilogue_item = [&](long long j) -> bool {
         // tcgen05.ld is warp-collective: take the wait's outcome warp-uniformly.
+        if (n_zunits) tmem_wait_st();            // this warp's parked normals of item j have landed
         const bool okw = mbar_wait(acc_full, static_cast<uint32_t>(j & 1), abort_flag, T.status);
         if (!__all_sync(0xffffffffu, okw)) return false;
         tc_fence_after();
@@ -543,62 +593,71 @@ __global__ void __launch_bounds__(kThreads, 1)
         // Each 16-lane half of the quadrant is read with the 16x256b shape: a thread holds rows R0
         // and R0 + 8 for channel pairs 2 (lane % 4) + {0, 1} of both 8-channel groups of the chunk,
         // so one store instruction covers 8 rows x 16 contiguous bytes (the 32x32b shape, one row
-        // per lane, scattered each store over 32 rows).  White noise: a quad's Philox draw (Eq. 19)
-        // serves two lanes (the two channel pairs of the quad); lanes l and l ^ 1 draw it for rows
-        // R0 and R0 + 8 respectively and swap the halves the other needs.
+        // per lane, scattered each store over 32 rows).
         (void)r;
-        const int lq = lane & 3, lr = lane >> 2;
-        const bool odd = (lane & 1) != 0;
         const long long S_row = static_cast<long long>(T.n_pix) * T.n_ch;
         float* obase = out + (row0 * T.n_pix + pix) * static_cast<long long>(T.n_ch);
-        for (int c = 16 * chunk_lo; c < 16 * chunk_hi; c += 16) {
+        // Unit u = (chunk u / 4, half (u / 2) % 2, 8-channel group u % 2): one 16x256b load of each
+        // of S, N and the parked normals (a thread: rows R0 and R0 + 8 x channels chq, chq + 1).
+        // TMEM reads run one unit ahead: the loads of unit u + 1 are issued before unit u is
+        // computed, and each wait names the registers it completes (no use can move above it).
+        auto issue = [&](int u, uint32_t (&sr)[4], uint32_t (&nr)[4], uint32_t (&zr)[4]) {
+            const int ck = u >> 2;
+            const uint32_t lanes = static_cast<uint32_t>(quad * 32 + 16 * ((u >> 1) & 1)) << 16;
+            const uint32_t col = 16 * ck + 8 * (u & 1);
+            tmem_ld16x256b_x1(d_sig + lanes + col, sr);
+            tmem_ld16x256b_x1(d_noi + lanes + col, nr);
+            if (white && u < zu_all) tmem_ld16x256b_x1(tmem_base + zcol(ck) + 8 * (u & 1) + lanes, zr);   // warp-uniform
+        };
+        auto finish = [&](int u, const uint32_t (&sr)[4], const uint32_t (&nr)[4], const uint32_t (&zr)[4]) {
+            const int ck = u >> 2, h = (u >> 1) & 1, g = u & 1;
+            const int R0 = quad * 32 + 16 * h + lr;                     // tile rows R0, R0 + 8
+            const int chq = ch_base + 16 * ck + 8 * g + 2 * lq;         // this thread's channel pair
+            float2 z0 = make_float2(0.f, 0.f), z1 = make_float2(0.f, 0.f);   // rows R0, R0 + 8
+            if (white && u < zu_all) {
+                z0 = make_float2(__uint_as_float(zr[0]), __uint_as_float(zr[1]));
+                z1 = make_float2(__uint_as_float(zr[2]), __uint_as_float(zr[3]));
+            } else if (white) {
+                white_pair(t0 + row0 + R0, pix, chq, z0, z1);
+            }
+            // output scale: brightness temperature a P + b (Sect. 2.7), or W (a = 1, b = 0)
+            float2 ka = make_float2(1.f, 1.f), kb = make_float2(0.f, 0.f);
+            if (T.tb_a && chq < T.n_ch) {
+                ka = *reinterpret_cast<const float2*>(T.tb_a + chq);   // padded arrays, chq even
+                kb = *reinterpret_cast<const float2*>(T.tb_b + chq);
+            }
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                float sv[8], nv[8];
-                const uint32_t toff = (static_cast<uint32_t>(quad * 32 + 16 * h) << 16) + static_cast<uint32_t>(c);
-                tmem_ld16x256b_x2(d_sig + toff, sv);
-                tmem_ld16x256b_x2(d_noi + toff, nv);
-                tmem_wait_ld();
-                const int R0 = quad * 32 + 16 * h + lr;                  // tile rows R0, R0 + 8
+            for (int rr = 0; rr < 2; ++rr) {
+                const int R = R0 + 8 * rr;
+                if (R >= nrows) continue;
+                float* orow = obase + R * S_row;
+                const float2 zz = rr ? z1 : z0;
 #pragma unroll
-                for (int g = 0; g < 2; ++g) {
-                    const int chq = ch_base + c + 8 * g + 2 * lq;           // this thread's channel pair
-                    float2 z0 = make_float2(0.f, 0.f), z1 = make_float2(0.f, 0.f);   // rows R0, R0 + 8
-                    if (white) {
-                        const float4 z = white_normals4_fast(t0 + row0 + R0 + (odd ? 8 : 0), pix, chq >> 2, T.key0,
-                                                             T.key1);
-                        const float sx = odd ? z.x : z.z, sy = odd ? z.y : z.w;     // what the partner needs
-                        const float rx = __shfl_xor_sync(0xffffffffu, sx, 1);
-                        const float ry = __shfl_xor_sync(0xffffffffu, sy, 1);
-                        z0 = odd ? make_float2(rx, ry) : make_float2(z.x, z.y);
-                        z1 = odd ? make_float2(z.z, z.w) : make_float2(rx, ry);
-                    }
-                    // output scale: brightness temperature a P + b (Sect. 2.7), or W (a = 1, b = 0)
-                    float2 ka = make_float2(1.f, 1.f), kb = make_float2(0.f, 0.f);
-                    if (T.tb_a && chq < T.n_ch) {
-                        ka = *reinterpret_cast<const float2*>(T.tb_a + chq);   // padded arrays, chq even
-                        kb = *reinterpret_cast<const float2*>(T.tb_b + chq);
-                    }
-#pragma unroll
-                    for (int rr = 0; rr < 2; ++rr) {
-                        const int R = R0 + 8 * rr;
-                        if (R >= nrows) continue;
-                        float* orow = obase + R * S_row;
-                        const float2 zz = rr ? z1 : z0;
-#pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            const int ch = chq + e;
-                            if (ch < T.n_ch) {
-                                const int k = 4 * g + 2 * rr + e;
-                                const float pk = T.kb1e9 * sv[k];
-                                // k_B outside the root: k_B^2 times N would leave the normal float range
-                                const float sigma = T.kB * sqrt_approx(T.noise_scale * fmaxf(nv[k], 0.f));
-                                orow[ch] = fmaf(e ? ka.y : ka.x, fmaf(sigma, e ? zz.y : zz.x, pk), e ? kb.y : kb.x);
-                            }
-                        }
+                for (int e = 0; e < 2; ++e) {
+                    const int ch = chq + e;
+                    if (ch < T.n_ch) {
+                        const int k = 2 * rr + e;
+                        const float pk = T.kb1e9 * __uint_as_float(sr[k]);
+                        // k_B outside the root: k_B^2 times N would leave the normal float range
+                        const float sigma = T.kB * sqrt_approx(T.noise_scale * fmaxf(__uint_as_float(nr[k]), 0.f));
+                        orow[ch] = fmaf(e ? ka.y : ka.x, fmaf(sigma, e ? zz.y : zz.x, pk), e ? kb.y : kb.x);
                     }
                 }
             }
+        };
+        uint32_t sa[4], na[4], za[4] = {0u, 0u, 0u, 0u}, sb[4], nb[4], zb[4] = {0u, 0u, 0u, 0u};
+        const int u_end = unit_hi;
+        int u = unit_lo;
+        if (u < u_end) issue(u, sa, na, za);
+        while (u < u_end) {
+            tmem_wait_ld_regs(sa, na, za);
+            if (u + 1 < u_end) issue(u + 1, sb, nb, zb);
+            finish(u, sa, na, za);
+            if (++u >= u_end) break;
+            tmem_wait_ld_regs(sb, nb, zb);
+            if (u + 1 < u_end) issue(u + 1, sa, na, za);
+            finish(u, sb, nb, zb);
+            ++u;
         }
         tc_fence_before();
         __syncwarp();
@@ -806,14 +865,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         int s = pgrp % NS, si = pgrp % kInSlots;
         uint32_t ph = 0, phi = 0;
         bool ok = true;
-        for (long long j = 0; j < my_items && ok; ++j) {
-            // row constants of item j
-            RowC rc[2];
+        // Item j's first kPre stages are built before the epilogue of item j - 1 (their slots are
+        // freed by item j - 1's MMAs alone, kPre <= NS), so the MMAs of item j start as soon as
+        // the accumulators drain.  Parked normals of item j: once the epilogue of item j - 1 has
+        // read its own, one slice every kZEvery stages after kZSkip stages.
+        const int kPre = NS;
+        constexpr int kZSkip = 2, kZEvery = share ? 3 : 8;
+        RowC rc[2];
+        bool same = false;
+        long long z_row0 = 0;
+        int z_pix = 0, z_chb = 0;
+        // row constants of item j (and the coordinates its parked normals need)
+        auto row_consts = [&](long long j) {
             {
                 const long long it = item_of(j);
                 long long tile, row0;
                 int pix, nrows, grp;
                 item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
+                z_row0 = row0;
+                z_pix = pix;
+                z_chb = grp * NH;
                 const TileInfo ti = tiles[tile];
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
@@ -852,19 +923,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             // the two rows read the same gathers (same table row, same cube cell, same paths)
-            const bool same = rc[0].flags == rc[1].flags && rc[0].tau_j == rc[1].tau_j &&
-                              rc[0].src_idx == rc[1].src_idx && rc[0].sA == rc[1].sA && rc[0].sC00 == rc[1].sC00;
-            // the stages of item j built by this warp (g advances by kStep, across items too:
-            // ks = first ks >= 0 with (j n_ks + ks) mod kStep == pgrp)
-            for (int ks = share ? static_cast<int>(((pgrp - j * n_ks) % kStep + kStep) % kStep) : 0; ks < n_ks;
-                 ks += kStep) {
+            same = rc[0].flags == rc[1].flags && rc[0].tau_j == rc[1].tau_j && rc[0].src_idx == rc[1].src_idx &&
+                   rc[0].sA == rc[1].sA && rc[0].sC00 == rc[1].sC00;
+        };
+        // one stage of this warp (ks of the current item): gathers, X, split, stores, arrival
+        auto build_stage = [&](int ks) -> bool {
                 bool okw = (g < NS || mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, T.status)) &&
                            mbar_wait(full_in(si), phi, abort_flag, T.status);
                 okw = __all_sync(0xffffffffu, okw);      // the warp signals as one
-                if (!okw) {
-                    ok = false;
-                    break;
-                }
+                if (!okw) return false;
                 uint8_t* a0 = smem + s * sp.a_bytes;
                 float x[2][4];
                 {
@@ -952,16 +1019,45 @@ __global__ void __launch_bounds__(kThreads, 1)
                 while (s >= NS) { s -= NS; ph ^= 1u; }
                 si += kStep;
                 while (si >= kInSlots) { si -= kInSlots; phi ^= 1u; }
+                return true;
+        };
+        for (long long j = 0; j < my_items && ok; ++j) {
+            // the stages of item j built by this warp (g advances by kStep, across items too:
+            // ks = first ks >= 0 with (j n_ks + ks) mod kStep == pgrp)
+            int ks = share ? static_cast<int>(((pgrp - j * n_ks) % kStep + kStep) % kStep) : 0;
+            int zk = 0, built = 0;
+            row_consts(j);
+            if (j > 0) {
+                for (; ks < n_ks && ks < kPre; ks += kStep)
+                    if (!(ok = build_stage(ks))) break;
+                if (!ok) break;
+                if (!(ok = epilogue_item(j - 1))) break;
+                row_consts(j);                       // formed again: not held across the epilogue
+            }
+            for (; ks < n_ks; ks += kStep) {
+                if (!(ok = build_stage(ks))) break;
+                if (zk < n_zunits && built >= kZSkip && (built - kZSkip) % kZEvery == 0)
+                    park_unit(zk++, z_row0, z_pix, z_chb);
+                ++built;
             }
             if (!ok) break;
-            ok = epilogue_item(j);                 // this warp's share of item j's epilogue
+            while (zk < n_zunits) park_unit(zk++, z_row0, z_pix, z_chb);
         }
+        if (ok && my_items > 0) ok = epilogue_item(my_items - 1);   // this warp's share of the last epilogue
     } else if (warp >= kEpiWarp0) {
         // ---------------- epilogue warps (independent CTAs; shared tiles use them as producers) ----
-        for (long long j = 0; j < my_items; ++j)
+        for (long long j = 0; j < my_items; ++j) {
+            if (n_zunits) {                        // idle while item j's MMAs run: park its normals now
+                long long tile, row0;
+                int pix, nrows, grp;
+                item_coords(work, F.n_groups, item_of(j), tile, pix, row0, nrows, grp, nt);
+                for (int k = 0; k < n_zunits; ++k) park_unit(k, row0, pix, grp * NH);
+            }
             if (!epilogue_item(j)) break;
+        }
     }
 
+    if (warp >= kProdWarp0) tmem_wait_st();     // no parked normals in flight (a role may have stopped early)
     tc_fence_before();
     __syncthreads();
     if (share) cluster_sync_all();              // no copy into or out of our shared memory in flight

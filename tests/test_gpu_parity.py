@@ -317,9 +317,16 @@ def test_signal_parity_across_channel_groupings(n_ch):
         A, alpha = W.pink_levels(n_ch, 11)
         sc["noise"] = dict(sc["noise"], pink_A=A, pink_alpha=alpha)
 
-    sc, ref = oracle("single_pixel_small", 0, 260, mutate=mutate)
+    sc, ref = oracle("single_pixel_small", 0, 260, mutate=mutate, white=True)
     got, flags, _ = gpu_run(sc, "bf16x3", 0, 260)
     err = rel_err(got, ref["p_kid"])
     print(f"bf16x3 {n_ch} channels: max rel err {err:.3e}")
     assert err < SIGNAL_TOL["bf16x3"]
     assert flags & ~L.STATUS_PWV_CLAMPED == 0
+    # white noise through every epilogue role of the grouping (drawn ahead or in the epilogue)
+    got_w, _, _ = gpu_run(sc, "bf16x3", 0, 260, white=True)
+    sigma = ref["sigma"]
+    bound = SIGMA_TOL["bf16x3"] * sigma * (np.abs(ref["p_wn"] / sigma) + 0.1) + 1e-6 * np.abs(ref["p_kid"])
+    worst = np.max(np.abs((got_w - got) - ref["p_wn"]) / bound)
+    print(f"bf16x3 {n_ch} channels: white noise worst error / bound = {worst:.3f}")
+    assert worst <= 1.0
