@@ -487,6 +487,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t drain_bar = bar_base + 8u * (nb + 2);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + sp.bar_off + 8 * (nb + 3));
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + sp.bar_off + 8 * (nb + 3) + 8);
+    // B slot of the first stage of a pair: free once that stage's MMAs are done, which a local
+    // commit between the pair's two stages reports half a pair before the pair's stage-free
+    // barrier (B streaming is latency-bound, so the earlier refill shortens every stage).  The
+    // same early release of the first A slot (a multicast commit) measured slower.
+    auto bfree_first = [&](int s) { return bar_base + 8u * (nb + 5 + (s >> 1)); };   // per A-slot pair
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int share = kShare;
@@ -504,6 +509,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(full_in(s), 1);
             mbar_init(empty_in(s), share ? kProdWarps / 2 : kProdWarps);
         }
+        for (int s = 0; s < NS; s += 2) mbar_init(bfree_first(s), 1);
         mbar_init(acc_full, 1);
         mbar_init(acc_empty, 4 + kProdWarps);   // the epilogue warps and the producer warps
         mbar_init(drain_bar, 1);
@@ -669,8 +675,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             // ---------------- filter operands: one bulk copy per stage (B ring) ----------------
             // Stage g's operands go to B slot g mod NSB and complete on the stage-full barrier of
-            // A slot g mod NS.  B slot g mod NSB is free once the MMAs of stage g - NSB are done,
-            // which the commit to that stage's A-slot barrier reports (one commit per stage).
+            // A slot g mod NS.  B slot g mod NSB is free once the MMAs of stage g - NSB are done:
+            // for the first stage of a pair its own commit reports it, for the second the commit
+            // that frees the pair's A slots.
             // NSB <= NS: the copy for stage g starts after the MMAs of stage g - NSB, so the
             // stage-full barrier is already in stage g's phase.
             long long g = 0;
@@ -687,7 +694,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 bool ok = true;
                 for (int ks = 0; ks < n_ks; ++ks) {
                     if (g >= NSB) {
-                        if (!mbar_wait(empty_bar(sf), pf, abort_flag, T.status)) {
+                        if (!mbar_wait((sf & 1) ? empty_bar(sf) : bfree_first(sf), pf, abort_flag, T.status)) {
                             ok = false;
                             break;
                         }
@@ -814,6 +821,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tc_mma(d_sig, xhi, hlo, idesc, 1u);
                         tc_mma(d_noi, xhi, gmat, idesc, acc);
                         tc_mma(d_noi, xsq, qmat, idesc, 1u);
+                        if (h == 0) tc_commit(bfree_first(s));   // the first stage's B slot
                         if (++sb == NSB) sb = 0;
                     }
                     if (share) tc_commit_pair(empty_bar(s));   // A slots s, s+1 free in both CTAs
@@ -831,9 +839,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             // the cluster; nothing else waits for those of the last pairs.  Waiting here for each
             // of the last pairs to complete (both commits in) leaves no arrival addressed to this
             // CTA in flight when the cluster leaves.
-            if (share)
-                for (long long q = (n_pairs > NS / 2 ? n_pairs - NS / 2 : 0); q < n_pairs; ++q)
-                    mbar_drain(empty_bar(static_cast<int>((2 * q) % NS)), static_cast<uint32_t>(((2 * q) / NS) & 1));
+            // The first-stage B commits of the last pairs likewise: nothing else waits for them.
+            for (long long q = (n_pairs > NS / 2 ? n_pairs - NS / 2 : 0); q < n_pairs; ++q) {
+                const int sq = static_cast<int>((2 * q) % NS);
+                const uint32_t pq = static_cast<uint32_t>(((2 * q) / NS) & 1);
+                if (share) mbar_drain(empty_bar(sq), pq);
+                mbar_drain(bfree_first(sq), pq);
+            }
         }
     } else if (warp >= kProdWarp0 && (share || warp < kEpiWarp0)) {
         // ---------------- spectrum producers ----------------
