@@ -386,7 +386,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         tk = e0.elapsed_time(e1)
-        # downstream: common-mode reduction of the K TOD (Sect. 4.2, Eqs. 25-26), in place, off-source
+        # downstream: common-mode reduction of the K TOD (Sect. 4.3, Eqs. 25-26), in place, off-source
         # spaxels beyond 25" (the outer ring of the 5 x 5 IFU)
         t = time.perf_counter()
         pwv_mean = pk.mean_zenith_pwv(nt)

@@ -349,7 +349,7 @@ gateau_status gateau_convolve_source(const float* dev_I, int n_az, int n_el, int
 gateau_status gateau_smooth_screen(const float* dev_screen, int nx, int ny, double pitch_m, double R_tel_m,
                                    double t_edge_db, float* dev_out, void* stream);
 
-/* ---- Downstream: common-mode reduction (Sect. 4.2, Eqs. 25-26) ----------
+/* ---- Downstream: common-mode reduction (Sect. 4.3, Eqs. 25-26) ----------
  * gateau_mean_zenith_pwv: the zenith PWV averaged over the observation, i.e. the
  * mean of the line-of-sight screen PWV over every row (n, i) with n < n_total,
  * computed on the device (rows by the row-setup kernel, FP64 sum); synchronous.

@@ -26,7 +26,7 @@ float64, stage by stage, with no algebraic collapse, blocking or fusion:
                                       exact Timmer & Koenig realisation over the whole scan)
   * total                          -- Sect. 2.7, Eq. 21
   * brightness-temperature output  -- Sect. 2.7 (simulated skydip, linear P -> T_b map)
-  * common-mode reduction          -- Sect. 4.2, Eqs. 25-26 (downstream of the TOD)
+  * common-mode reduction          -- Sect. 4.3, Eqs. 25-26 (downstream of the TOD)
 
 Readings of points the paper leaves silent or garbled (each also listed in the
 design notes of the repository):

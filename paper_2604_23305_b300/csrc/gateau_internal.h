@@ -165,7 +165,7 @@ cudaError_t launch_tk_realise(const double* A, const double* alpha, double f_sam
                               cudaStream_t stream);
 cudaError_t launch_tk_add(float* out, const float* tk, long long count, cudaStream_t stream);
 
-// Common-mode reduction (Sect. 4.2, Eqs. 25-26): sum of rows[0 .. n).pwv into *sum (atomic, FP64);
+// Common-mode reduction (Sect. 4.3, Eqs. 25-26): sum of rows[0 .. n).pwv into *sum (atomic, FP64);
 // log of each channel's band transmission at zenith PWV pwv; T*_a of a TOD tb [nt][n_pix][n_ch]
 // (out may be tb) given the run's rows (csc), log_eta_z [n_ch], off_source [n_pix] (S_j) and N_out.
 cudaError_t launch_sum_pwv(const RowParams* rows, long long n, double* sum, cudaStream_t stream);

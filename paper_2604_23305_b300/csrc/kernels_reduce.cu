@@ -1,4 +1,4 @@
-// Downstream of the TOD: the common-mode reduction of Sect. 4.2 (Eqs. 25-26).
+// Downstream of the TOD: the common-mode reduction of Sect. 4.3 (Eqs. 25-26).
 //
 // For a brightness-temperature TOD T_b[t][i][ch] each (sample, channel) column is reduced over
 // the spaxels that see no source (S_j = 1, Eq. 26) to the common atmosphere term

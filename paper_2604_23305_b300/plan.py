@@ -219,7 +219,7 @@ class Plan:
         return out
 
     def mean_zenith_pwv(self, n_total: int) -> float:
-        """Zenith PWV averaged over the observation's first n_total samples (Sect. 4.2)."""
+        """Zenith PWV averaged over the observation's first n_total samples (Sect. 4.3)."""
         v = C.c_double(0.0)
         L.check(self._lib.gateau_mean_zenith_pwv(self._h, int(n_total), C.byref(v)))
         return v.value

@@ -1,4 +1,4 @@
-"""Common-mode reduction (Sect. 4.2, Eqs. 25-26) and the observation's mean zenith PWV on the
+"""Common-mode reduction (Sect. 4.3, Eqs. 25-26) and the observation's mean zenith PWV on the
 GPU against the oracle, through the C ABI.  The reduced TOD is a seeded synthetic brightness-
 temperature array given to both sides (no input comes from the CUDA path)."""
 import math

@@ -583,7 +583,7 @@ def test_tk_streams_are_disjoint_from_white_and_pink():
     assert not np.any(np.isin(re[:2000], w))
 
 
-# ---------------------------------------------------------------- common-mode reduction (Sect. 4.2, Eqs. 25-26)
+# ---------------------------------------------------------------- common-mode reduction (Sect. 4.3, Eqs. 25-26)
 
 def _cm_case(nt=24):
     sc = W.scenario("single_pixel_small", nt_total=nt)
