@@ -884,7 +884,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int kPre = NS;
         constexpr int kZSkip = 2, kZEvery = share ? 3 : 8;
         RowC rc[2];
-        bool same = false;
+        bool same_tau = false, same_cube = false;
         long long z_row0 = 0;
         int z_pix = 0, z_chb = 0;
         // row constants of item j (and the coordinates its parked normals need)
@@ -934,9 +934,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     c.eb = c.ea * rp.tau_f;
                 }
             }
-            // the two rows read the same gathers (same table row, same cube cell, same paths)
-            same = rc[0].flags == rc[1].flags && rc[0].tau_j == rc[1].tau_j && rc[0].src_idx == rc[1].src_idx &&
-                   rc[0].sA == rc[1].sA && rc[0].sC00 == rc[1].sC00;
+            // the two rows read the same opacity gathers (same table row and path) and / or the
+            // same cube gathers (same cell and path)
+            same_tau = (rc[0].flags & kTauBox) == (rc[1].flags & kTauBox) && rc[0].tau_j == rc[1].tau_j &&
+                       rc[0].sA == rc[1].sA;
+            same_cube = (rc[0].flags & (kCubeBox | kHasSrc)) == (rc[1].flags & (kCubeBox | kHasSrc)) &&
+                        rc[0].src_idx == rc[1].src_idx && rc[0].sC00 == rc[1].sC00;
         };
         // one stage of this warp (ks of the current item): gathers, X, split, stores, arrival
         auto build_stage = [&](int ks) -> bool {
@@ -955,7 +958,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const float4 c01 = ld4(scon + 4 * quad);
                     const float4 c1 = ld4(scon + kKStage + 4 * quad);
                     float4 ta, td, q00, q10, q01, q11;
-                    auto gather = [&](const RowC& c) {
+                    auto gather_tau = [&](const RowC& c) {
                         if (c.flags & kTauBox) {
                             ta = ld4(stau + c.sA + 4 * quad);
                             td = ld4(stau + c.sA + kBoxW + 4 * quad);
@@ -964,6 +967,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                             ta = ld4(gA + kq);
                             td = ld4(gA + T.Kp + kq);
                         }
+                    };
+                    auto gather_cube = [&](const RowC& c) {
                         if (c.flags & kCubeBox) {
                             const float* b = slot + c.sC00 + 4 * quad;
                             q00 = ld4(b);
@@ -987,7 +992,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
                         const RowC& c = rc[i];
-                        if (i == 0 || !same) gather(c);
+                        if (i == 0 || !same_tau) gather_tau(c);
+                        if (i == 0 || !same_cube) gather_cube(c);
                         arg[i] = make_float4(fmaf(c.eb, td.x, c.ea * ta.x), fmaf(c.eb, td.y, c.ea * ta.y),
                                              fmaf(c.eb, td.z, c.ea * ta.z), fmaf(c.eb, td.w, c.ea * ta.w));
                         src[i].x = c.w00 * q00.x + c.w10 * q10.x + c.w01 * q01.x + c.w11 * q11.x;

@@ -253,7 +253,16 @@ def _mut_one_channel_two_freqs(s):
     s["cascade"] = [dict(kind="reflective", eta=0.9, T=20.0)]
 
 
+def _mut_64_spaxels_daisy(s):
+    """8 x 8 spaxels (more than a warp's 32 lanes in the row setup's per-sample spaxel loop) on a
+    daisy scan over the wind-advected screen."""
+    s["pix_offsets"] = W.grid_offsets(8, 15 * W.ARCSEC)
+    w = 2 * math.pi * 1.54
+    s["scan"] = dict(kind="daisy", params=(65 * W.ARCSEC, w, w / 50.0), phi0=0.0, theta0=47.8 * W.DEG)
+
+
 EDGE = {
+    "64_spaxels_daisy": ("ifu25", 40001, 45, _mut_64_spaxels_daisy),
     "outside_cube": ("single_pixel_small", 0, 130, _mut_outside),
     "pwv_clamped": ("single_pixel_small", 0, 64, _mut_clamp),
     "epl_screen_eta_table": ("single_pixel_small", 5, 200, _mut_epl_eta),
