@@ -106,6 +106,7 @@ __global__ void pink_phase2_kernel(DevTables T, float* state, PinkWork W, long l
 
 // Phase 3 reads, updates and writes out one group of up to 4 samples at a time,
 // with the next group's loads issued before the current group's recurrence.
+constexpr int kPinkPrefetch = 128;   // samples; ~40 MB of lines in flight over the GPU, inside L2
 template <int NP>
 __global__ __launch_bounds__(256) void pink_phase3_kernel(DevTables T, PinkWork W, long long t0,
                                                           long long nt, float* __restrict__ out) {
@@ -142,6 +143,13 @@ __global__ __launch_bounds__(256) void pink_phase3_kernel(DevTables T, PinkWork 
                 float nxt4[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) nxt4[q] = full_next ? o[(4 + q) * stride] : 0.f;
+                // and the outputs kPinkPrefetch samples ahead prefetched into L2 (the loads above
+                // then wait on L2, not HBM); only within the chunk
+                if (n + kPinkPrefetch + 4 <= b0) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(o + (kPinkPrefetch + q) * stride));
+                }
                 const float4 z4 = pink_normals4(n >> 2, i, ch, T.key0, T.key1);
                 const float zq[4] = {z4.x, z4.y, z4.z, z4.w};
 #pragma unroll
