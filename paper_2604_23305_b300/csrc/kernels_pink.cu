@@ -222,13 +222,14 @@ void pink_choose_chunks(long long nt, long long S, int& C, long long& L) {
     C = static_cast<int>((nt + L - 1) / L);
 }
 
+// Phases 1 and 2 (the chunk scan, which reads nothing of out) and phase 3 (the pass over out).
+// (Running the scan on a second stream beside the row setup measured 0.8 ms slower per step.)
 template <int NP>
-static cudaError_t launch_pink_np(const DevTables& T, float* state, const PinkWork& W, long long t0,
-                                  long long nt, float* out, cudaStream_t stream) {
+static cudaError_t launch_pink_scan_np(const DevTables& T, float* state, const PinkWork& W, long long t0,
+                                       long long nt, cudaStream_t stream) {
     const long long S = static_cast<long long>(T.n_pix) * T.n_ch;
-    const long long work = W.C * S;
     const int block = 256;
-    long long grid = (work + block - 1) / block;
+    long long grid = (W.C * S + block - 1) / block;
     if (grid > 148LL * 32) grid = 148LL * 32;
     pink_phase1_kernel<NP><<<static_cast<unsigned>(grid), block, 0, stream>>>(T, W, t0, nt);
     cudaError_t e = cudaGetLastError();
@@ -236,17 +237,38 @@ static cudaError_t launch_pink_np(const DevTables& T, float* state, const PinkWo
     long long g2 = (S * T.n_pole + block - 1) / block;
     if (g2 > 148LL * 32) g2 = 148LL * 32;
     pink_phase2_kernel<<<static_cast<unsigned>(g2), block, 0, stream>>>(T, state, W, nt);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+template <int NP>
+static cudaError_t launch_pink_apply_np(const DevTables& T, const PinkWork& W, long long t0, long long nt,
+                                        float* out, cudaStream_t stream) {
+    const long long S = static_cast<long long>(T.n_pix) * T.n_ch;
+    const int block = 256;
+    long long grid = (W.C * S + block - 1) / block;
+    if (grid > 148LL * 32) grid = 148LL * 32;
     pink_phase3_kernel<NP><<<static_cast<unsigned>(grid), block, 0, stream>>>(T, W, t0, nt, out);
     return cudaGetLastError();
 }
 
+static cudaError_t launch_pink_scan(const DevTables& T, float* state, const PinkWork& W, long long t0,
+                                    long long nt, cudaStream_t stream) {
+    if (T.n_pole <= 8) return launch_pink_scan_np<8>(T, state, W, t0, nt, stream);
+    if (T.n_pole <= 16) return launch_pink_scan_np<16>(T, state, W, t0, nt, stream);
+    return launch_pink_scan_np<kMaxPoles>(T, state, W, t0, nt, stream);
+}
+
+static cudaError_t launch_pink_apply(const DevTables& T, const PinkWork& W, long long t0, long long nt,
+                                     float* out, cudaStream_t stream) {
+    if (T.n_pole <= 8) return launch_pink_apply_np<8>(T, W, t0, nt, out, stream);
+    if (T.n_pole <= 16) return launch_pink_apply_np<16>(T, W, t0, nt, out, stream);
+    return launch_pink_apply_np<kMaxPoles>(T, W, t0, nt, out, stream);
+}
+
 cudaError_t launch_pink(const DevTables& T, float* state, const PinkWork& W, long long t0, long long nt,
                         float* out, cudaStream_t stream) {
-    if (T.n_pole <= 8) return launch_pink_np<8>(T, state, W, t0, nt, out, stream);
-    if (T.n_pole <= 16) return launch_pink_np<16>(T, state, W, t0, nt, out, stream);
-    return launch_pink_np<kMaxPoles>(T, state, W, t0, nt, out, stream);
+    const cudaError_t e = launch_pink_scan(T, state, W, t0, nt, stream);
+    return e != cudaSuccess ? e : launch_pink_apply(T, W, t0, nt, out, stream);
 }
 
 }  // namespace gateau
