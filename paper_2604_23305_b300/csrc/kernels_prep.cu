@@ -30,20 +30,21 @@ __device__ __forceinline__ double illumination(double r, double R, double t_edge
 }
 
 // A_b(l_q, m_p) for plane b = frequency nu[b].
-__global__ void aperture_kernel(float2* __restrict__ A, const double* __restrict__ nu, int B, int na, int ne,
-                                double d_az, double d_el, double R, double t_edge_db) {
-    const long long total = static_cast<long long>(B) * na * ne;
-    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
+__global__ void aperture_kernel(float2* __restrict__ A, const double* __restrict__ nu, int na, int ne, float inv_laz,
+                                float inv_lel, double R, float t_edge_20) {
+    // plane b = blockIdx.y; its wavelength over the aperture radius formed once per thread (FP64),
+    // the direction cosines in FP32 (the plane is FP32, and l, m stay far below float's limits)
+    const int b = blockIdx.y;
+    const float lam_R = static_cast<float>(kC / nu[b] / R);
+    const long long plane = static_cast<long long>(na) * ne;
+    float2* Ab = A + b * plane;
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < plane;
          t += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int b = static_cast<int>(t / (static_cast<long long>(na) * ne));
-        const int rem = static_cast<int>(t - static_cast<long long>(b) * na * ne);
-        const int q = rem / ne, p = rem - q * ne;
-        // FP32: the plane is FP32, and l, m stay far below float's range limits
-        const float lam = static_cast<float>(kC / nu[b]);
-        const float l = static_cast<float>(fft_offset(q, na) / (na * d_az));
-        const float m = static_cast<float>(fft_offset(p, ne) / (ne * d_el));
-        const float rr = lam * hypotf(l, m) / static_cast<float>(R);
-        A[t] = make_float2(rr < 1.f ? exp10f(static_cast<float>(t_edge_db / 20.0) * rr * rr) : 0.f, 0.f);
+        const int q = static_cast<int>(t / ne), p = static_cast<int>(t - static_cast<long long>(q) * ne);
+        const float l = static_cast<float>(q < na / 2 ? q : q - na) * inv_laz;
+        const float m = static_cast<float>(p < ne / 2 ? p : p - ne) * inv_lel;
+        const float rr = lam_R * hypotf(l, m);
+        Ab[t] = make_float2(rr < 1.f ? exp10f(t_edge_20 * rr * rr) : 0.f, 0.f);
     }
 }
 
@@ -66,11 +67,15 @@ __global__ void transpose_kernel(const float2* __restrict__ in, float2* __restri
 }
 
 // |E|^2 per plane and its maximum (one block per plane).
+// |E|^2 in place and its maximum per plane: blockIdx.y = plane, blockIdx.x strides over it; the
+// maximum is combined with an integer atomic max on the bits of the (non-negative) floats, so
+// peak must be zero on entry.
 __global__ void power_max_kernel(float2* __restrict__ E, long long plane, float* __restrict__ peak) {
     __shared__ float red[kPrepThreads / 32];
-    float2* e = E + blockIdx.x * plane;
+    float2* e = E + blockIdx.y * plane;
     float mx = 0.f;
-    for (long long t = threadIdx.x; t < plane; t += blockDim.x) {
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < plane;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
         const float2 v = e[t];
         const float pw = v.x * v.x + v.y * v.y;
         e[t] = make_float2(pw, 0.f);
@@ -83,7 +88,7 @@ __global__ void power_max_kernel(float2* __restrict__ E, long long plane, float*
     if (threadIdx.x == 0) {
         float m = 0.f;
         for (int w = 0; w < kPrepThreads / 32; ++w) m = fmaxf(m, red[w]);
-        peak[blockIdx.x] = m;
+        atomicMax(reinterpret_cast<int*>(peak) + blockIdx.y, __float_as_int(m));
     }
 }
 
@@ -182,7 +187,86 @@ cudaError_t launch_real_part(const float2* in, float* out, long long n, cudaStre
 }
 
 // 2-D transform of B planes [n0][n1] held in a (b is scratch); the result is left in a.
+// One-pass transforms of whole vectors in shared memory: a block takes V vectors of n points
+// (V n complex values, 32 KB), loads them in bit-reversed order, runs the log2 n radix-2 stages
+// in place (twiddles e^{sign 2 pi i p / len} from sincospif), and stores them back in place.
+// Vector v starts at (v / per_plane) * plane_stride + (v % per_plane) * vstride and its points
+// are kstride apart: rows of a plane (kstride 1, contiguous) or its columns (kstride = row
+// length; a block's V columns are adjacent, so each point's loads are coalesced).
+constexpr int kFftSmemPoints = 4096;            // V n <= this many complex values per block
+template <int SIGN>
+__global__ void __launch_bounds__(kPrepThreads) fft_smem_kernel(float2* a, long long nvec, int n, int log2n,
+                                                                 long long kstride, long long per_plane,
+                                                                 long long vstride, long long plane_stride, int V) {
+    extern __shared__ float2 sm[];
+    float2* tw = sm + V * n;                     // e^{sign 2 pi i m / n}, m < n / 2
+    const bool columns = kstride != 1;
+    const int nv = V * n;
+    for (int m = threadIdx.x; m < n / 2; m += blockDim.x) {
+        float sn, cs;
+        sincospif(2.0f * static_cast<float>(m) / static_cast<float>(n), &sn, &cs);   // exact power-of-two divisor
+        tw[m] = make_float2(cs, SIGN * sn);
+    }
+    for (long long v0 = static_cast<long long>(blockIdx.x) * V; v0 < nvec; v0 += static_cast<long long>(gridDim.x) * V) {
+        auto base = [&](long long v) { return (v / per_plane) * plane_stride + (v % per_plane) * vstride; };
+        for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+            // columns: the block's V vectors vary fastest (adjacent addresses); rows: the points do
+            const int vl = columns ? t % V : t / n, k = columns ? t / V : t % n;
+            const long long v = v0 + vl;
+            const int kr = static_cast<int>(__brev(static_cast<unsigned>(k)) >> (32 - log2n));
+            sm[vl * n + kr] = v < nvec ? a[base(v) + k * kstride] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        for (int half = 1, shift = log2n - 1; half < n; half <<= 1, --shift) {
+            for (int t = threadIdx.x; t < nv / 2; t += blockDim.x) {
+                const int vl = t / (n / 2), j = t % (n / 2);
+                const int pos = j & (half - 1);
+                const int i0 = vl * n + (j - pos) * 2 + pos, i1 = i0 + half;
+                const float2 wq = tw[pos << shift];            // e^{sign pi i pos / half}
+                const float2 u = sm[i0], w = sm[i1];
+                const float2 x = make_float2(w.x * wq.x - w.y * wq.y, w.x * wq.y + w.y * wq.x);
+                sm[i0] = make_float2(u.x + x.x, u.y + x.y);
+                sm[i1] = make_float2(u.x - x.x, u.y - x.y);
+            }
+            __syncthreads();
+        }
+        for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+            const int vl = columns ? t % V : t / n, k = columns ? t / V : t % n;
+            const long long v = v0 + vl;
+            if (v < nvec) a[base(v) + k * kstride] = sm[vl * n + k];
+        }
+        __syncthreads();
+    }
+}
+
+static cudaError_t fft_smem(float2* a, long long nvec, int n, long long kstride, long long per_plane,
+                            long long vstride, long long plane_stride, int sign, cudaStream_t stream) {
+    if (n <= 1) return cudaSuccess;                // a one-point transform is the identity
+    int log2n = 0;
+    while ((1 << log2n) < n) ++log2n;
+    const int V = n >= kFftSmemPoints ? 1 : (kFftSmemPoints / n < 16 ? kFftSmemPoints / n : 16);
+    long long grid = (nvec + V - 1) / V;
+    if (grid > 148LL * 16) grid = 148LL * 16;
+    const size_t bytes = (static_cast<size_t>(V) * n + n / 2) * sizeof(float2);   // data + twiddles
+    if (sign < 0)
+        fft_smem_kernel<-1><<<static_cast<unsigned>(grid), kPrepThreads, bytes, stream>>>(
+            a, nvec, n, log2n, kstride, per_plane, vstride, plane_stride, V);
+    else
+        fft_smem_kernel<1><<<static_cast<unsigned>(grid), kPrepThreads, bytes, stream>>>(
+            a, nvec, n, log2n, kstride, per_plane, vstride, plane_stride, V);
+    return cudaGetLastError();
+}
+
+// 2-D transform of B planes [n0][n1] in place in a (b: scratch of the same size).  Sides of at
+// most kFftSmemPoints points take one shared-memory pass per dimension (rows, then columns read
+// in place); longer sides go through the global Stockham passes and transposes.
 cudaError_t fft2_planes(float2* a, float2* b, int B, int n0, int n1, int sign, cudaStream_t stream) {
+    if (n0 <= kFftSmemPoints && n1 <= kFftSmemPoints) {
+        const long long plane = static_cast<long long>(n0) * n1;
+        cudaError_t e = fft_smem(a, static_cast<long long>(B) * n0, n1, 1, n0, n1, plane, sign, stream);   // rows
+        if (e != cudaSuccess) return e;
+        return fft_smem(a, static_cast<long long>(B) * n1, n0, n1, n1, 1, plane, sign, stream);            // columns
+    }
     const float2* r = nullptr;
     cudaError_t e = launch_fft_rows(a, b, static_cast<long long>(B) * n0, n1, sign, &r, stream);
     if (e != cudaSuccess) return e;
@@ -202,10 +286,15 @@ cudaError_t fft2_planes(float2* a, float2* b, int B, int n0, int n1, int sign, c
 cudaError_t launch_beam_planes(const double* nu, int B, int na, int ne, double d_az, double d_el, double R,
                                double t_edge_db, float2* F, float2* work, float* peak, cudaStream_t stream) {
     const long long plane = static_cast<long long>(na) * ne;
-    aperture_kernel<<<grid_for(plane * B), kPrepThreads, 0, stream>>>(F, nu, B, na, ne, d_az, d_el, R, t_edge_db);
+    const unsigned bx = static_cast<unsigned>((plane + kPrepThreads - 1) / kPrepThreads < 64 ? (plane + kPrepThreads - 1) / kPrepThreads : 64);
+    aperture_kernel<<<dim3(bx, B), kPrepThreads, 0, stream>>>(F, nu, na, ne, static_cast<float>(1.0 / (na * d_az)),
+                                                              static_cast<float>(1.0 / (ne * d_el)), R,
+                                                              static_cast<float>(t_edge_db / 20.0));
     cudaError_t e = fft2_planes(F, work, B, na, ne, -1, stream);
     if (e != cudaSuccess) return e;
-    power_max_kernel<<<B, kPrepThreads, 0, stream>>>(F, plane, peak);
+    e = cudaMemsetAsync(peak, 0, static_cast<size_t>(B) * sizeof(float), stream);
+    if (e != cudaSuccess) return e;
+    power_max_kernel<<<dim3(bx, B), kPrepThreads, 0, stream>>>(F, plane, peak);
     scale_planes_kernel<<<grid_for(plane * B), kPrepThreads, 0, stream>>>(F, plane, B, peak);
     return cudaGetLastError();
 }
