@@ -195,9 +195,12 @@ cudaError_t launch_real_part(const float2* in, float* out, long long n, cudaStre
 // length; a block's V columns are adjacent, so each point's loads are coalesced).
 constexpr int kFftSmemPoints = 4096;            // V n <= this many complex values per block
 template <int SIGN>
-__global__ void __launch_bounds__(kPrepThreads) fft_smem_kernel(float2* a, long long nvec, int n, int log2n,
-                                                                 long long kstride, long long per_plane,
-                                                                 long long vstride, long long plane_stride, int V) {
+// n, V and per_plane are powers of two, passed as their logarithms: every index below is a shift
+// or a mask.
+__global__ void __launch_bounds__(kPrepThreads) fft_smem_kernel(float2* a, long long nvec, int log2n, long long kstride,
+                                                                 int log2pp, long long vstride, long long plane_stride,
+                                                                 int log2V) {
+    const int n = 1 << log2n, V = 1 << log2V;
     extern __shared__ float2 sm[];
     float2* tw = sm + V * n;                     // e^{sign 2 pi i m / n}, m < n / 2
     const bool columns = kstride != 1;
@@ -207,11 +210,12 @@ __global__ void __launch_bounds__(kPrepThreads) fft_smem_kernel(float2* a, long 
         sincospif(2.0f * static_cast<float>(m) / static_cast<float>(n), &sn, &cs);   // exact power-of-two divisor
         tw[m] = make_float2(cs, SIGN * sn);
     }
+    const long long pp_mask = (1LL << log2pp) - 1;
     for (long long v0 = static_cast<long long>(blockIdx.x) * V; v0 < nvec; v0 += static_cast<long long>(gridDim.x) * V) {
-        auto base = [&](long long v) { return (v / per_plane) * plane_stride + (v % per_plane) * vstride; };
+        auto base = [&](long long v) { return (v >> log2pp) * plane_stride + (v & pp_mask) * vstride; };
         for (int t = threadIdx.x; t < nv; t += blockDim.x) {
             // columns: the block's V vectors vary fastest (adjacent addresses); rows: the points do
-            const int vl = columns ? t % V : t / n, k = columns ? t / V : t % n;
+            const int vl = columns ? (t & (V - 1)) : (t >> log2n), k = columns ? (t >> log2V) : (t & (n - 1));
             const long long v = v0 + vl;
             const int kr = static_cast<int>(__brev(static_cast<unsigned>(k)) >> (32 - log2n));
             sm[vl * n + kr] = v < nvec ? a[base(v) + k * kstride] : make_float2(0.f, 0.f);
@@ -219,7 +223,7 @@ __global__ void __launch_bounds__(kPrepThreads) fft_smem_kernel(float2* a, long 
         __syncthreads();
         for (int half = 1, shift = log2n - 1; half < n; half <<= 1, --shift) {
             for (int t = threadIdx.x; t < nv / 2; t += blockDim.x) {
-                const int vl = t / (n / 2), j = t % (n / 2);
+                const int vl = t >> (log2n - 1), j = t & (n / 2 - 1);
                 const int pos = j & (half - 1);
                 const int i0 = vl * n + (j - pos) * 2 + pos, i1 = i0 + half;
                 const float2 wq = tw[pos << shift];            // e^{sign pi i pos / half}
@@ -231,7 +235,7 @@ __global__ void __launch_bounds__(kPrepThreads) fft_smem_kernel(float2* a, long 
             __syncthreads();
         }
         for (int t = threadIdx.x; t < nv; t += blockDim.x) {
-            const int vl = columns ? t % V : t / n, k = columns ? t / V : t % n;
+            const int vl = columns ? (t & (V - 1)) : (t >> log2n), k = columns ? (t >> log2V) : (t & (n - 1));
             const long long v = v0 + vl;
             if (v < nvec) a[base(v) + k * kstride] = sm[vl * n + k];
         }
@@ -239,21 +243,27 @@ __global__ void __launch_bounds__(kPrepThreads) fft_smem_kernel(float2* a, long 
     }
 }
 
+static int ilog2(long long x) {
+    int l = 0;
+    while ((1LL << l) < x) ++l;
+    return l;
+}
+
 static cudaError_t fft_smem(float2* a, long long nvec, int n, long long kstride, long long per_plane,
                             long long vstride, long long plane_stride, int sign, cudaStream_t stream) {
     if (n <= 1) return cudaSuccess;                // a one-point transform is the identity
-    int log2n = 0;
-    while ((1 << log2n) < n) ++log2n;
+    const int log2n = ilog2(n), log2pp = ilog2(per_plane);
     const int V = n >= kFftSmemPoints ? 1 : (kFftSmemPoints / n < 16 ? kFftSmemPoints / n : 16);
+    const int log2V = ilog2(V);
     long long grid = (nvec + V - 1) / V;
     if (grid > 148LL * 16) grid = 148LL * 16;
     const size_t bytes = (static_cast<size_t>(V) * n + n / 2) * sizeof(float2);   // data + twiddles
     if (sign < 0)
         fft_smem_kernel<-1><<<static_cast<unsigned>(grid), kPrepThreads, bytes, stream>>>(
-            a, nvec, n, log2n, kstride, per_plane, vstride, plane_stride, V);
+            a, nvec, log2n, kstride, log2pp, vstride, plane_stride, log2V);
     else
         fft_smem_kernel<1><<<static_cast<unsigned>(grid), kPrepThreads, bytes, stream>>>(
-            a, nvec, n, log2n, kstride, per_plane, vstride, plane_stride, V);
+            a, nvec, log2n, kstride, log2pp, vstride, plane_stride, log2V);
     return cudaGetLastError();
 }
 
@@ -261,6 +271,7 @@ static cudaError_t fft_smem(float2* a, long long nvec, int n, long long kstride,
 // most kFftSmemPoints points take one shared-memory pass per dimension (rows, then columns read
 // in place); longer sides go through the global Stockham passes and transposes.
 cudaError_t fft2_planes(float2* a, float2* b, int B, int n0, int n1, int sign, cudaStream_t stream) {
+    if (n0 < 1 || n1 < 1 || (n0 & (n0 - 1)) || (n1 & (n1 - 1))) return cudaErrorInvalidValue;   // powers of two only
     if (n0 <= kFftSmemPoints && n1 <= kFftSmemPoints) {
         const long long plane = static_cast<long long>(n0) * n1;
         cudaError_t e = fft_smem(a, static_cast<long long>(B) * n0, n1, 1, n0, n1, plane, sign, stream);   // rows
