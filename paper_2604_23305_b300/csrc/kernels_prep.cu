@@ -221,16 +221,40 @@ __global__ void __launch_bounds__(kPrepThreads) fft_smem_kernel(float2* a, long 
             sm[vl * n + kr] = v < nvec ? a[base(v) + k * kstride] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        for (int half = 1, shift = log2n - 1; half < n; half <<= 1, --shift) {
+        // stages of half-size 2^lh; an odd count starts with one radix-2 stage, the rest go in
+        // fused pairs (half-sizes h, 2h: one radix-4 butterfly, one shared-memory round trip)
+        int lh = 0;
+        if (log2n & 1) {
             for (int t = threadIdx.x; t < nv / 2; t += blockDim.x) {
-                const int vl = t >> (log2n - 1), j = t & (n / 2 - 1);
-                const int pos = j & (half - 1);
-                const int i0 = vl * n + (j - pos) * 2 + pos, i1 = i0 + half;
-                const float2 wq = tw[pos << shift];            // e^{sign pi i pos / half}
+                const int i0 = 2 * t, i1 = i0 + 1;                 // half 1: twiddle 1
                 const float2 u = sm[i0], w = sm[i1];
-                const float2 x = make_float2(w.x * wq.x - w.y * wq.y, w.x * wq.y + w.y * wq.x);
-                sm[i0] = make_float2(u.x + x.x, u.y + x.y);
-                sm[i1] = make_float2(u.x - x.x, u.y - x.y);
+                sm[i0] = make_float2(u.x + w.x, u.y + w.y);
+                sm[i1] = make_float2(u.x - w.x, u.y - w.y);
+            }
+            __syncthreads();
+            lh = 1;
+        }
+        for (; lh < log2n; lh += 2) {
+            const int h = 1 << lh;
+            for (int t = threadIdx.x; t < nv / 4; t += blockDim.x) {
+                const int vl = t >> (log2n - 2), j = t & (n / 4 - 1);
+                const int pos = j & (h - 1), grp = j >> lh;
+                const int i0 = vl * n + (grp << (lh + 2)) + pos, i1 = i0 + h, i2 = i0 + 2 * h, i3 = i0 + 3 * h;
+                const float2 wa = tw[pos << (log2n - 1 - lh)];     // e^{sign pi i pos / h}
+                const float2 wb = tw[pos << (log2n - 2 - lh)];     // e^{sign pi i pos / (2 h)}
+                const float2 x0 = sm[i0], x1 = sm[i1], x2 = sm[i2], x3 = sm[i3];
+                const float2 a1 = make_float2(x1.x * wa.x - x1.y * wa.y, x1.x * wa.y + x1.y * wa.x);
+                const float2 a3 = make_float2(x3.x * wa.x - x3.y * wa.y, x3.x * wa.y + x3.y * wa.x);
+                const float2 y0 = make_float2(x0.x + a1.x, x0.y + a1.y), y1 = make_float2(x0.x - a1.x, x0.y - a1.y);
+                const float2 y2 = make_float2(x2.x + a3.x, x2.y + a3.y), y3 = make_float2(x2.x - a3.x, x2.y - a3.y);
+                // second stage: (y0, y2) with wb, (y1, y3) with wb e^{sign pi i / 2} = wb (sign i)
+                const float2 b2 = make_float2(y2.x * wb.x - y2.y * wb.y, y2.x * wb.y + y2.y * wb.x);
+                const float2 wc = make_float2(-SIGN * wb.y, SIGN * wb.x);
+                const float2 b3 = make_float2(y3.x * wc.x - y3.y * wc.y, y3.x * wc.y + y3.y * wc.x);
+                sm[i0] = make_float2(y0.x + b2.x, y0.y + b2.y);
+                sm[i2] = make_float2(y0.x - b2.x, y0.y - b2.y);
+                sm[i1] = make_float2(y1.x + b3.x, y1.y + b3.y);
+                sm[i3] = make_float2(y1.x - b3.x, y1.y - b3.y);
             }
             __syncthreads();
         }
