@@ -406,6 +406,7 @@ DevTables make_tables(const gateau_plan* p) {
     T.n_pix = d.n_pix;
     T.pix_off = p->d_pix.as<double>();
     T.pix_trig = T.pix_off ? T.pix_off + 2 * static_cast<size_t>(d.n_pix) : nullptr;
+    T.pix_trig_f = T.pix_off ? reinterpret_cast<const float*>(T.pix_off + 6 * static_cast<size_t>(d.n_pix)) : nullptr;
     T.f_sample = d.f_sample_hz;
     T.h_column = d.h_column_m;
     T.wind = d.wind_mps;
@@ -665,8 +666,13 @@ static gateau_status ensure_base(gateau_plan* p) {
             tr[2] = std::sin(dth);
             tr[3] = std::cos(dth);
         }
-        GATEAU_CUDA(grow(p, p->d_pix, tab.size() * sizeof(double)));
+        // and the same [n_pix][4] trigonometry in float (the row setup's FP32 angle additions)
+        std::vector<float> tab_f(4 * static_cast<size_t>(n));
+        for (size_t q = 0; q < tab_f.size(); ++q) tab_f[q] = static_cast<float>(tab[2 * static_cast<size_t>(n) + q]);
+        GATEAU_CUDA(grow(p, p->d_pix, tab.size() * sizeof(double) + tab_f.size() * sizeof(float)));
         GATEAU_CUDA(cudaMemcpy(p->d_pix.p, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
+        GATEAU_CUDA(cudaMemcpy(static_cast<char*>(p->d_pix.p) + tab.size() * sizeof(double), tab_f.data(),
+                               tab_f.size() * sizeof(float), cudaMemcpyHostToDevice));
         GATEAU_CUDA(grow(p, p->d_status, sizeof(unsigned int)));
         GATEAU_CUDA(cudaMemset(p->d_status.p, 0, sizeof(unsigned int)));
         int dev = 0;
@@ -1139,7 +1145,7 @@ gateau_status gateau_plan_estimate_bytes(const gateau_plan_desc* d, int n_ch, in
     const double Kp = static_cast<double>((d->n_freq + 31) / 32 * 32);
     const int np = pink_pole_count(d->pink_f_min_hz, d->f_sample_hz);
     const double n_pix = d->n_pix, nc = n_ch;
-    double b = n_pix * 6 * 8 + 64;                                   // spaxel offsets and trig, status word
+    double b = n_pix * (6 * 8 + 4 * 4) + 64;                         // spaxel offsets and trig, status word
     b += 2.0 * n_az * n_el * Kp * 4;                                 // source cube as set + scaled copy
     b += static_cast<double>(nx) * ny * 4;                           // screen
     b += 2.0 * n_pwv * Kp * 4;                                       // interleaved opacity table

@@ -47,6 +47,7 @@ struct DevTables {
     int n_pix;
     const double* pix_off;             // [n_pix][2]
     const double* pix_trig;            // [n_pix][4]: tan dphi, tan dth, sin dth, cos dth
+    const float* pix_trig_f;           // the same in float
     double f_sample, h_column, wind;
     int scan_kind;
     double sp[kMaxScanParams];

@@ -57,22 +57,27 @@ __device__ __forceinline__ double wrap_mod(double a, double m, double inv_m) {
 // What a row needs from its time sample alone (Sect. 2.4): the time, the scan pointing
 // and the trigonometry of it that every spaxel reuses.
 struct SampleGeom {
-    double t, phs, ths, tan_phs, tan_ths, sin_a, cos_a;   // a = ths + theta0
+    double t, phs, ths;
+    float tan_phs, tan_ths, sin_a, cos_a;                 // a = ths + theta0
 };
 
 __device__ __forceinline__ SampleGeom sample_geom(const DevTables& T, long long n) {
     SampleGeom g;
     g.t = static_cast<double>(n) / T.f_sample;
     scan_pointing(T, n, g.t, g.phs, g.ths);
-    g.tan_phs = tan(g.phs);
-    g.tan_ths = tan(g.ths);
-    sincos(g.ths + T.theta0, &g.sin_a, &g.cos_a);
+    g.tan_phs = static_cast<float>(tan(g.phs));
+    g.tan_ths = static_cast<float>(tan(g.ths));
+    double sa, ca;
+    sincos(g.ths + T.theta0, &sa, &ca);
+    g.sin_a = static_cast<float>(sa);
+    g.cos_a = static_cast<float>(ca);
     return g;
 }
 
 // Reciprocals of the per-plan divisors, formed once per thread.
 struct RowScales {
     double inv_pitch, inv_nx, inv_ny, inv_dpwv, inv_daz, inv_del;
+    float h_column;
 };
 
 __device__ __forceinline__ RowScales row_scales(const DevTables& T) {
@@ -83,20 +88,24 @@ __device__ __forceinline__ RowScales row_scales(const DevTables& T) {
     k.inv_dpwv = 1.0 / T.dpwv;
     k.inv_daz = 1.0 / T.daz;
     k.inv_del = 1.0 / T.del;
+    k.h_column = static_cast<float>(T.h_column);
     return k;
 }
 
 // Row (sample n, spaxel i).  The spaxel's offsets enter through the angle-addition
 // identities, tan(p + d) = (tan p + tan d) / (1 - tan p tan d) and
 // sin(a + d) = sin a cos d + cos a sin d, with tan d, sin d, cos d tabulated per spaxel.
+// FP64 where precision is spent: time, wind drift, screen coordinates and wrap, table row and
+// source cell; FP32 for the offsets' angle additions (a few tens of metres off the scan line at
+// ~1e-7 relative), the bilinear weights and the airmass.
 __device__ __forceinline__ RowParams make_row(const DevTables& T, const SampleGeom& g, const RowScales& k, int i) {
     const double dphi = T.pix_off[2 * i], dth = T.pix_off[2 * i + 1];
-    const double* tr = T.pix_trig + 4 * i;
+    const float* tr = T.pix_trig_f + 4 * i;
     const double az = g.phs + T.phi0 + dphi;                 // spaxel pointing (Sect. 2.4)
     const double el = g.ths + T.theta0 + dth;
     // Frozen-flow screen coordinates (Eq. 9) and periodic bilinear PWV.
-    const double x = T.h_column * ((g.tan_phs + tr[0]) / (1.0 - g.tan_phs * tr[0])) + T.wind * g.t;
-    const double y = T.h_column * ((g.tan_ths + tr[1]) / (1.0 - g.tan_ths * tr[1]));
+    const double x = static_cast<double>(k.h_column * ((g.tan_phs + tr[0]) / (1.f - g.tan_phs * tr[0]))) + T.wind * g.t;
+    const double y = static_cast<double>(k.h_column * ((g.tan_ths + tr[1]) / (1.f - g.tan_ths * tr[1])));
     double gx = wrap_mod(x * k.inv_pitch + 0.5 * T.nx, static_cast<double>(T.nx), k.inv_nx);
     double gy = wrap_mod(y * k.inv_pitch + 0.5 * T.ny, static_cast<double>(T.ny), k.inv_ny);
     if (!(gx >= 0.0 && gx < T.nx) || !(gy >= 0.0 && gy < T.ny)) {   // non-finite pointing
@@ -105,12 +114,12 @@ __device__ __forceinline__ RowParams make_row(const DevTables& T, const SampleGe
         gy = 0.0;
     }
     const int ix = static_cast<int>(floor(gx)), iy = static_cast<int>(floor(gy));
-    const double fx = gx - ix, fy = gy - iy;
+    const float fx = static_cast<float>(gx - ix), fy = static_cast<float>(gy - iy);
     const int ix1 = (ix + 1 == T.nx) ? 0 : ix + 1, iy1 = (iy + 1 == T.ny) ? 0 : iy + 1;
-    const double s00 = T.screen[static_cast<long long>(iy) * T.nx + ix];
-    const double s01 = T.screen[static_cast<long long>(iy) * T.nx + ix1];
-    const double s10 = T.screen[static_cast<long long>(iy1) * T.nx + ix];
-    const double s11 = T.screen[static_cast<long long>(iy1) * T.nx + ix1];
+    const float s00 = T.screen[static_cast<long long>(iy) * T.nx + ix];
+    const float s01 = T.screen[static_cast<long long>(iy) * T.nx + ix1];
+    const float s10 = T.screen[static_cast<long long>(iy1) * T.nx + ix];
+    const float s11 = T.screen[static_cast<long long>(iy1) * T.nx + ix1];
     const double pwv = (1 - fx) * (1 - fy) * s00 + fx * (1 - fy) * s01 + (1 - fx) * fy * s10 + fx * fy * s11;
     // Opacity-table row (linear in PWV, clamped) and airmass (Eq. 10).
     double u = (pwv - T.pwv_min) * k.inv_dpwv;
@@ -120,7 +129,7 @@ __device__ __forceinline__ RowParams make_row(const DevTables& T, const SampleGe
     }
     const int j = min(static_cast<int>(floor(u)), T.n_pwv - 2);
     RowParams rp;
-    rp.csc = 1.0f / static_cast<float>(g.sin_a * tr[3] + g.cos_a * tr[2]);
+    rp.csc = 1.0f / (g.sin_a * tr[3] + g.cos_a * tr[2]);
     rp.tau_j = j;
     rp.tau_f = static_cast<float>(u - j);
     rp.pwv = static_cast<float>(pwv);
