@@ -18,48 +18,62 @@ namespace {
 
 constexpr int kTkThreads = 256;
 
-// (re, im) normals of Fourier bin j: counter (q lo, q hi, i, 2^30 | ch), q = j >> 1, Box-Muller
-// pair j & 1.
-__device__ __forceinline__ float2 tk_normals(long long j, int i, int ch, uint32_t k0, uint32_t k1) {
-    const long long q = j >> 1;
-    const uint4 x = philox4x32_10(make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32),
-                                             static_cast<uint32_t>(i), 0x40000000u | static_cast<uint32_t>(ch)),
-                                  k0, k1);
-    return (j & 1) ? box_muller(x.z, x.w) : box_muller(x.x, x.y);
-}
-
-// Coefficient X_j / M of one channel (complex; real at the Nyquist bin, zero at DC or for A = 0):
-// sqrt(M f_s A f_j^-alpha / 4) / M = amp_ch f_j^(-alpha/2) with amp_ch = sqrt(M f_s A / 4) / M, the
-// power evaluated as 2^(-alpha/2 log2 f_j) in FP32 (the FFT runs in FP32 too).
-__device__ __forceinline__ float2 tk_coef(long long j, int M, float log2f_j, int i, int ch, int n_ch,
-                                          const double* A, const double* alpha, double f_sample, uint32_t k0,
-                                          uint32_t k1) {
-    if (ch >= n_ch || j == 0 || !(A[ch] > 0.0)) return make_float2(0.f, 0.f);
-    const float amp = static_cast<float>(sqrt(M * f_sample * A[ch] / 4.0) / M) *
-                      exp2f(-0.5f * static_cast<float>(alpha[ch]) * log2f_j);
-    const float2 z = tk_normals(j, i, ch, k0, k1);
-    if (2 * j == M) return make_float2(1.41421356237f * amp * z.x, 0.f);       // real Nyquist coefficient
-    return make_float2(amp * z.x, amp * z.y);
-}
-
-// Z[pair][j] = X^a_j + i X^b_j for the channel pair (2c, 2c + 1) of spaxel i, pair = i P + c.
+// The normals of Fourier bin j of channel ch come from the Philox draw with counter
+// (q lo, q hi, i, 2^30 | ch), q = j >> 1: Box-Muller on words (x, y) for even j, (z, w) for odd j.
+// Coefficients X_j / M of the channel pair (2c, 2c + 1) of spaxel i (complex; real at the Nyquist
+// bin, zero at DC or for A = 0): sqrt(M f_s A f_j^-alpha / 4) / M = amp_ch f_j^(-alpha/2) with
+// amp_ch = sqrt(M f_s A / 4) / M (FP64, once per thread and pair), the power evaluated as
+// 2^(-alpha/2 log2 f_j) in FP32 (the FFT runs in FP32 too).  Z[pair][j] = X^a_j + i X^b_j, and
+// the conjugate-symmetric half Z[pair][M - j] = conj(X^a_j) + i conj(X^b_j), pair = i P + c.
+// A thread takes the two bins j = 2q, 2q + 1 that one Philox draw per channel serves; blocks
+// stride over the pairs along y.
 __global__ void __launch_bounds__(kTkThreads) tk_spectrum_kernel(float2* __restrict__ Z, int M, int P, int n_pix,
                                                                  int n_ch, const double* __restrict__ A,
                                                                  const double* __restrict__ alpha, double f_sample,
                                                                  uint32_t k0, uint32_t k1) {
-    const long long half = M / 2 + 1;
-    const long long total = static_cast<long long>(n_pix) * P * half;
-    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
-         t += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const long long pair = t / half;
-        const long long j = t - pair * half;
+    const long long n_pairs = static_cast<long long>(n_pix) * P;
+    const float fstep = static_cast<float>(f_sample / M);
+    for (long long pair = blockIdx.y; pair < n_pairs; pair += gridDim.y) {
         const int i = static_cast<int>(pair / P), c = static_cast<int>(pair - static_cast<long long>(i) * P);
-        const float lf = j > 0 ? log2f(static_cast<float>(static_cast<double>(j) * f_sample / M)) : 0.f;
-        const float2 a = tk_coef(j, M, lf, i, 2 * c, n_ch, A, alpha, f_sample, k0, k1);
-        const float2 b = tk_coef(j, M, lf, i, 2 * c + 1, n_ch, A, alpha, f_sample, k0, k1);
+        float amp[2], ha[2];
+        bool on[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int ch = 2 * c + e;
+            on[e] = ch < n_ch && A[ch] > 0.0;
+            amp[e] = on[e] ? static_cast<float>(sqrt(M * f_sample * A[ch] / 4.0) / M) : 0.f;
+            ha[e] = on[e] ? -0.5f * static_cast<float>(alpha[ch]) : 0.f;
+        }
         float2* z = Z + pair * M;
-        z[j] = make_float2(a.x - b.y, a.y + b.x);
-        if (j > 0 && 2 * j < M) z[M - j] = make_float2(a.x + b.y, b.x - a.y);   // conj(a) + i conj(b)
+        for (long long q = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; 2 * q <= M / 2;
+             q += static_cast<long long>(gridDim.x) * blockDim.x) {
+            uint4 x[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                x[e] = philox4x32_10(make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32),
+                                                static_cast<uint32_t>(i), 0x40000000u | static_cast<uint32_t>(2 * c + e)),
+                                     k0, k1);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const long long j = 2 * q + h;
+                if (j > M / 2) break;
+                const float lf = j > 0 ? log2f(static_cast<float>(j) * fstep) : 0.f;
+                float2 cf[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    if (!on[e] || j == 0) {
+                        cf[e] = make_float2(0.f, 0.f);
+                        continue;
+                    }
+                    const float a = amp[e] * exp2f(ha[e] * lf);
+                    const float2 n = h ? box_muller(x[e].z, x[e].w) : box_muller(x[e].x, x[e].y);
+                    cf[e] = 2 * j == M ? make_float2(1.41421356237f * a * n.x, 0.f)   // real Nyquist coefficient
+                                       : make_float2(a * n.x, a * n.y);
+                }
+                z[j] = make_float2(cf[0].x - cf[1].y, cf[0].y + cf[1].x);
+                if (j > 0 && 2 * j < M) z[M - j] = make_float2(cf[0].x + cf[1].y, cf[1].x - cf[0].y);
+            }
+        }
     }
 }
 
@@ -158,8 +172,11 @@ cudaError_t launch_tk_realise(const double* A, const double* alpha, double f_sam
     if (M > (1LL << 30) || n_ch < 1 || n_pix < 1) return cudaErrorInvalidValue;
     const int P = (n_ch + 1) / 2;
     const long long n_pairs = static_cast<long long>(n_pix) * P;
-    tk_spectrum_kernel<<<grid_for(n_pairs * (M / 2 + 1), kTkThreads), kTkThreads, 0, stream>>>(
-        work0, static_cast<int>(M), P, n_pix, n_ch, A, alpha, f_sample, k0, k1);
+    const long long nq = M / 4 + 1;                  // thread items per pair (bins 2q, 2q + 1)
+    const dim3 sgrid(static_cast<unsigned>((nq + kTkThreads - 1) / kTkThreads < 64 ? (nq + kTkThreads - 1) / kTkThreads : 64),
+                     static_cast<unsigned>(n_pairs < 65535 ? n_pairs : 65535));
+    tk_spectrum_kernel<<<sgrid, kTkThreads, 0, stream>>>(work0, static_cast<int>(M), P, n_pix, n_ch, A, alpha,
+                                                         f_sample, k0, k1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const float2* in = nullptr;
