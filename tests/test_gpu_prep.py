@@ -55,3 +55,16 @@ def test_preprocessing_rejects_bad_sizes():
         prep.beam_far_field([300e9], 100, 64, AS, AS, 5.0, -10.0)
     with pytest.raises(L.GateauError):
         prep.smooth_screen(torch.zeros((48, 64), device="cuda"), 0.5, 5.0, -10.0)
+
+
+@pytest.mark.parametrize("shape", [(8, 8192), (4096, 16), (2048, 2)])
+def test_screen_smoothing_long_sides(shape):
+    """Sides up to 4096 points take one shared-memory pass per dimension (1-16 vectors per block);
+    longer sides (8192) take the global Stockham passes and transposes."""
+    rng = np.random.default_rng(9)
+    scr = rng.normal(0.9, 0.02, shape).astype(np.float32)
+    out = prep.smooth_screen(torch.from_numpy(scr).cuda(), 0.5, 3.0, -10.0).cpu().numpy()
+    want = O.smooth_screen(scr.astype(np.float64), 0.5, 3.0, -10.0)
+    err = np.abs(out - want).max()
+    print(f"screen smoothing {shape}: max |d| {err:.2e} mm")
+    assert err < 4e-6 * np.abs(want).max()
