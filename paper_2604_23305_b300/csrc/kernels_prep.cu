@@ -188,15 +188,15 @@ cudaError_t launch_real_part(const float2* in, float* out, long long n, cudaStre
 
 // 2-D transform of B planes [n0][n1] held in a (b is scratch); the result is left in a.
 // One-pass transforms of whole vectors in shared memory: a block takes V vectors of n points
-// (V n complex values, 32 KB), loads them in bit-reversed order, runs the log2 n radix-2 stages
-// in place (twiddles e^{sign 2 pi i p / len} from sincospif), and stores them back in place.
-// Vector v starts at (v / per_plane) * plane_stride + (v % per_plane) * vstride and its points
-// are kstride apart: rows of a plane (kstride 1, contiguous) or its columns (kstride = row
-// length; a block's V columns are adjacent, so each point's loads are coalesced).
+// (V n <= 4096 complex values, plus an n / 2 twiddle table e^{sign 2 pi i m / n} from sincospif),
+// loads them in bit-reversed order, runs the log2 n decimation-in-time stages in place (pairs of
+// stages fused into radix-4 butterflies), and stores them back in place.  Vector v starts at
+// (v / per_plane) * plane_stride + (v % per_plane) * vstride and its points are kstride apart:
+// rows of a plane (kstride 1, contiguous) or its columns (kstride = row length; a block's V
+// columns are adjacent, so each point's loads are coalesced).  n, V and per_plane are powers of
+// two, passed as their logarithms: every index is a shift or a mask.
 constexpr int kFftSmemPoints = 4096;            // V n <= this many complex values per block
 template <int SIGN>
-// n, V and per_plane are powers of two, passed as their logarithms: every index below is a shift
-// or a mask.
 __global__ void __launch_bounds__(kPrepThreads) fft_smem_kernel(float2* a, long long nvec, int log2n, long long kstride,
                                                                  int log2pp, long long vstride, long long plane_stride,
                                                                  int log2V) {
