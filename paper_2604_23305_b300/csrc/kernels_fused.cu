@@ -11,11 +11,12 @@
 //   N[row][ch] = X_hi G + bf16(X_hi^2) Q                    (noise terms, 1 product each)
 //
 // with X = X_hi + X_lo and H = H_hi + H_lo the BF16 hi/lo splits.  The
-// epilogue turns S into P_KID (Eq. 16) and N into sigma (Eqs. 17-18), draws the
-// white noise (Eq. 19) from Philox and writes out[n][i][ch].
+// epilogue turns S into P_KID (Eq. 16) and N into sigma (Eqs. 17-18), adds the
+// white noise (Eq. 19, Philox normals drawn while the item's MMAs run and parked
+// in free TMEM columns) and writes out[n][i][ch].
 //
-// Warp roles (448 threads, one CTA per SM, persistent over work items):
-//   warp 0        : one thread issuing bulk copies of the pre-tiled filter operands (A/B ring)
+// Warp roles (512 threads, one CTA per SM, persistent over work items):
+//   warp 0        : one thread issuing bulk copies of the pre-tiled filter operands (B ring)
 //   warp 1        : TMEM allocator + single-thread tcgen05.mma issuer
 //   warp 2        : one thread issuing tensor copies of the tile's opacity rows and cube texel
 //                   box (input ring); each spinning role has a warp of its own
