@@ -261,8 +261,15 @@ def _mut_64_spaxels_daisy(s):
     s["scan"] = dict(kind="daisy", params=(65 * W.ARCSEC, w, w / 50.0), phi0=0.0, theta0=47.8 * W.DEG)
 
 
+def _mut_wide_offsets(s):
+    """Spaxels up to 7' off the scan centre (8 x 8 at 2'): the row setup's FP32 angle additions over
+    offsets far larger than the IFU's, on a raster scan of the wind-advected screen."""
+    s["pix_offsets"] = W.grid_offsets(8, 120 * W.ARCSEC)
+
+
 EDGE = {
     "64_spaxels_daisy": ("ifu25", 40001, 45, _mut_64_spaxels_daisy),
+    "wide_offsets": ("ifu25", 120007, 37, _mut_wide_offsets),
     "outside_cube": ("single_pixel_small", 0, 130, _mut_outside),
     "pwv_clamped": ("single_pixel_small", 0, 64, _mut_clamp),
     "epl_screen_eta_table": ("single_pixel_small", 5, 200, _mut_epl_eta),
