@@ -138,6 +138,26 @@ def test_single_stage_emission_only():
     np.testing.assert_allclose(P[0], 0.9 * (1 - eta_atm[0]) * B273 + 0.1 * B40, rtol=1e-13)
 
 
+def test_sky_coupled_stage_by_hand():
+    """One sky-coupled stage (Sect. 2.5) with T_atm != T_cmb and eta_atm != 1/2: the stage emits
+    the sky it sees, (1 - eta_atm) B(T_atm) + eta_atm B(T_cmb), so
+    P = eta_k [eta_atm P_0 + (1 - eta_atm) B_atm] + (1 - eta_k) [(1 - eta_atm) B_atm + eta_atm B_cmb]
+    with P_0 = eta_t eta_surf eta_pol P_src + B_cmb (Eq. 11)."""
+    nu = np.array([220 * GHZ, 350 * GHZ])
+    eta_atm = np.array([[0.8, 0.3], [0.95, 0.6]])
+    P_src = np.array([[2e-22, 5e-23], [0.0, 1e-22]])
+    es = np.array([0.97, 0.95])
+    prim = O.expand_cascade([dict(kind="reflective", eta=0.9, T="sky")], nu)
+    P = O.cascade(P_src, eta_atm, nu, prim, 273.0, 2.725, 0.85, es, 0.5)
+    # Planck single-mode powers written out by the textbook closed form at each point.
+    B_atm = np.array([H * v / math.expm1(H * v / (KB * 273.0)) for v in nu])
+    B_cmb = np.array([H * v / math.expm1(H * v / (KB * 2.725)) for v in nu])
+    P0 = 0.85 * es * 0.5 * P_src + B_cmb
+    after_sky = eta_atm * P0 + (1 - eta_atm) * B_atm
+    stage_emission = (1 - eta_atm) * B_atm + eta_atm * B_cmb
+    np.testing.assert_allclose(P, 0.9 * after_sky + 0.1 * stage_emission, rtol=1e-13)
+
+
 # ---------------------------------------------------------------- dispersive element
 
 def test_lorentzian_closed_form_integral():
@@ -292,6 +312,90 @@ def test_scan_patterns():
     tab = np.random.default_rng(0).uniform(size=(20, 2))
     p, q = O.scan_pattern("custom", None, np.zeros(3), np.array([0, 7, 19]), tab)
     np.testing.assert_array_equal(np.stack([p, q], 1), tab[[0, 7, 19]])
+
+
+def test_daisy_quarter_periods():
+    """Eq. 8 at quarter periods of the petal and of the daisy cycle (omega = 5 Omega):
+    phi = r cos(Omega t) sin(omega t), theta = r sin(Omega t) sin(omega t)."""
+    r, w, Om = 1e-4, 5.0, 1.0
+    t = np.array([math.pi / (2 * w), math.pi / (2 * Om), math.pi / w, 3 * math.pi / (2 * w)])
+    phi, th = O.scan_pattern("daisy", (r, w, Om), t)
+    # omega t = pi/2, Omega t = pi/10: petal tip, rotated by pi/10.
+    # Omega t = pi/2, omega t = 5 pi/2: petal tip along +theta.
+    # omega t = pi: back at the centre whatever Omega t is.
+    # omega t = 3 pi/2, Omega t = 3 pi/10: tip of the opposite half-petal.
+    want_phi = [r * math.cos(math.pi / 10), 0.0, 0.0, -r * math.cos(3 * math.pi / 10)]
+    want_th = [r * math.sin(math.pi / 10), r, 0.0, -r * math.sin(3 * math.pi / 10)]
+    np.testing.assert_allclose(phi, want_phi, rtol=0, atol=1e-18)
+    np.testing.assert_allclose(th, want_th, rtol=0, atol=1e-18)
+
+
+def _linear_screen_geometry(nt):
+    """Two spaxels staring at (phi0, theta0) = (0.4, 0.7) rad over a screen linear in x and y."""
+    sc = W.scenario("single_pixel_small", nt_total=nt)
+    nx = ny = 64
+    ix, iy = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    sc["atmosphere"].update(screen=1.0 + 0.01 * ix + 0.004 * iy, pitch=0.5, h_column=1000.0, wind=2.0)
+    sc["f_sample"] = 4.0
+    sc["pix_offsets"] = np.array([[3e-3, -2e-3], [-4e-3, 5e-3]])
+    sc["scan"] = dict(kind="stare", params=(), phi0=0.4, theta0=0.7)
+    sc["noise"]["pink_f_min"] = 0.01
+    return sc
+
+
+def _expected_linear_screen_pwv(sc, n, pix):
+    """Eq. 9 without the scan offset: x = h tan(dphi_i) + u_w t, y = h tan(dtheta_i); grid
+    coordinates x / pitch + nx/2 (no wrap is reached here); the screen value there."""
+    atm = sc["atmosphere"]
+    off = sc["pix_offsets"][pix]
+    t = n / sc["f_sample"]
+    gx = (atm["h_column"] * np.tan(off[:, 0]) + atm["wind"] * t) / atm["pitch"] + 32
+    gy = atm["h_column"] * np.tan(off[:, 1]) / atm["pitch"] + 32
+    return 1.0 + 0.01 * gx + 0.004 * gy
+
+
+def test_row_geometry_offsets_follow_eqs_9_and_10():
+    """The screen coordinates use the scan pattern and the spaxel offset without the scan offset
+    (Eq. 9), while the pointing used for the source and for the airmass adds (phi0, theta0)
+    (Sect. 2.4, Eq. 10)."""
+    sc = _linear_screen_geometry(8)
+    n = np.repeat(np.arange(8), 2)
+    pix = np.tile(np.arange(2), 8)
+    t, az, el, pwv = O.row_geometry(sc, n, pix)
+    np.testing.assert_allclose(t, n / 4.0, rtol=0, atol=0)
+    np.testing.assert_allclose(az, 0.4 + sc["pix_offsets"][pix, 0], rtol=1e-15)
+    np.testing.assert_allclose(el, 0.7 + sc["pix_offsets"][pix, 1], rtol=1e-15)
+    np.testing.assert_allclose(pwv, _expected_linear_screen_pwv(sc, n, pix), rtol=1e-13)
+
+
+def test_simulate_takes_the_source_and_airmass_at_the_offset_pointing():
+    """Cold optics, T_cmb = 0, a flat unit filter and a constant cube that covers spaxel 0's
+    pointing (phi0 + dphi_0, theta0 + dtheta_0) but not spaxel 1's: with eta = exp(-tau_z(PWV))^csc(el)
+    at el = theta0 + dtheta_i (Eq. 10), P_KID = sum_nu w [eta_t eta_surf eta_pol C eta + (1 - eta) B_atm]."""
+    nt = 6
+    sc = _linear_screen_geometry(nt)
+    nf = sc["n_freq"]
+    sc["T_cmb"] = 0.0
+    sc["atmosphere"]["T_atm"] = 100.0
+    sc["cascade"] = [dict(kind="reflective", eta=1.0, T=0.0)]
+    C = 3e-22
+    sc["source"] = dict(cube=np.full((4, 4, nf), C), az0=0.401, daz=1e-3, el0=0.697, **{"del": 1e-3})
+    sc["dispersive"] = dict(kind="custom", f_c=np.array([330 * GHZ]), R=np.ones(1), eta_peak=np.ones(1),
+                            custom=np.ones((1, nf)))
+    parts = O.simulate(sc, 0, nt, white=False, pink=False, return_parts=True)
+    nu = O.frequency_grid(sc["f_lo"], sc["f_hi"], nf)
+    w = np.full(nf, nu[1] - nu[0])
+    w[0] = w[-1] = 0.5 * (nu[1] - nu[0])
+    es = np.exp(-(4 * math.pi * sc["rho_surf"] * nu / O.C_LIGHT) ** 2)
+    B_atm = np.array([H * v / math.expm1(H * v / (KB * 100.0)) for v in nu])
+    atm = sc["atmosphere"]
+    for i, inside in ((0, True), (1, False)):
+        n = np.arange(nt)
+        pwv = _expected_linear_screen_pwv(sc, n, np.full(nt, i))
+        tau = O.zenith_opacity(O.opacity_table(sc), atm["pwv_min"], atm["dpwv"], pwv)
+        eta = np.exp(-tau) ** (1.0 / math.sin(0.7 + sc["pix_offsets"][i, 1]))
+        P = 0.85 * es * 0.5 * (C if inside else 0.0) * eta + (1 - eta) * B_atm
+        np.testing.assert_allclose(parts["p_kid"][:, i, 0], P @ w, rtol=1e-12)
 
 
 # ---------------------------------------------------------------- random numbers
@@ -628,6 +732,18 @@ def test_common_mode_pure_atmosphere_is_zero_and_mean_pwv():
         assert np.abs(got).max() < 1e-10 * 31.0
     scu = _uniform_stare_scenario()
     assert abs(O.mean_zenith_pwv(scu, 16) - float(np.float32(1.2))) < 1e-12    # the screen holds float32
+
+
+def test_mean_zenith_pwv_of_a_linear_screen_drifting_with_the_wind():
+    """Two spaxels stare through a screen linear in x and y while it drifts at u_w: the mean over
+    every row (n, i), n < N, is the screen value at the mean grid coordinates, gx = 32 +
+    mean_i(h tan dphi_i) / pitch + u_w (N - 1) / (2 f_s pitch), gy = 32 + mean_i(h tan dtheta_i) / pitch."""
+    N = 16
+    sc = _linear_screen_geometry(N)
+    off = sc["pix_offsets"]
+    gx = 32 + (1000.0 * np.tan(off[:, 0]).mean() + 2.0 * (N - 1) / (2 * 4.0)) / 0.5
+    gy = 32 + 1000.0 * np.tan(off[:, 1]).mean() / 0.5
+    assert O.mean_zenith_pwv(sc, N) == pytest.approx(1.0 + 0.01 * gx + 0.004 * gy, rel=1e-13)
 
 
 # ---------------------------------------------------------------- preprocessing (Sect. 2.2, Eqs. 1-3)
