@@ -10,6 +10,12 @@ and pink noise on, output [t][pixel][channel] float32 (6.66 GB) in HBM.
 Prints one JSON line (rank 0).  N > 1 runs under torchrun: every rank simulates
 its own independent copy of the workload (weak scaling, no collective on the data
 path).  --impl reference times the FP64 oracle on the host cores instead.
+
+    python bench.py --record-traffic RAW.csv --traffic-samples S
+
+writes the fused kernel's DRAM traffic per full launch into the traffic record from
+an ncu capture (`ncu -i report --page raw --csv`) of a run over the first S samples;
+the bench line reports it only while the kernel source is the one captured.
 """
 from __future__ import annotations
 
@@ -35,8 +41,9 @@ METRIC = "detector-samples/s (pix·chan·t) split-BF16 vs plain FP32 GPU; servin
 UNIT = "detector-samples/s"
 WORKLOAD = "ifu25_raster_20min: 25 spaxels (5x5, 15\"), 347 filterbank channels R=500, 3000 freq 220-440 GHz, " \
            "192000 samples @160 Hz, 1024^2 PWV screen, 128x128x3000 source cube, 6-stage cascade, white+pink noise"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "fused_bf16x3_ifu25.md")
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "fused_bf16x3_traffic.json")
 FUSED_SRC = os.path.join(ROOT, "paper_2604_23305_b300", "csrc", "kernels_fused.cu")
+FULL_SAMPLES = 192000        # samples of the ifu25 scan (one full launch)
 
 
 def peaks():
@@ -104,18 +111,55 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def traffic_from_profile():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernel source."""
+def fused_source_hash() -> str:
+    return hashlib.sha256(open(FUSED_SRC, "rb").read()).hexdigest()[:16]
+
+
+def traffic_from_record():
+    """DRAM bytes per full launch of the fused kernel from the traffic record, or None when the
+    record was taken on another kernel source (the counters no longer describe this kernel)."""
     try:
-        text = open(PROFILE_SUMMARY).read()
-        want = hashlib.sha256(open(FUSED_SRC, "rb").read()).hexdigest()[:16]
-        src = [ln for ln in text.splitlines() if ln.startswith("kernel_source_sha256_16:")]
-        val = [ln for ln in text.splitlines() if ln.startswith("dram_bytes_per_full_launch:")]
-        if src and val and src[0].split(":", 1)[1].strip() == want:
-            return float(val[0].split(":", 1)[1].strip())
+        with open(TRAFFIC_RECORD) as f:
+            rec = json.load(f)
+        if rec.get("kernel_source_sha256_16") == fused_source_hash():
+            return float(rec["dram_bytes_per_full_launch"])
     except Exception:
         pass
     return None
+
+
+def record_traffic(raw_csv: str, samples: int, command: str) -> dict:
+    """Parse the raw page of an ncu capture (one row per launch) and write the traffic record:
+    the fused launches' dram__bytes_read.sum + dram__bytes_write.sum, scaled from the captured
+    samples to a full launch (the kernel's work is linear in the samples: tiles x channel groups)."""
+    import csv
+    with open(raw_csv, newline="") as f:
+        rows = list(csv.reader(f))
+    head = rows[0]
+    col = {name: i for i, name in enumerate(head)}
+    units = rows[1]
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
+    tscale = {"nsecond": 1e-9, "usecond": 1e-6, "msecond": 1e-3, "second": 1.0, "ns": 1e-9, "us": 1e-6, "ms": 1e-3}
+
+    def val(r, name, table):
+        return float(r[col[name]].replace(",", "")) * table.get(units[col[name]], 1.0)
+
+    launches = [r for r in rows[2:] if "fused_bf16x3" in r[col["Kernel Name"]]]
+    if not launches:
+        raise SystemExit("no fused_bf16x3 launch in " + raw_csv)
+    rd = [val(r, "dram__bytes_read.sum", scale) for r in launches]
+    wr = [val(r, "dram__bytes_write.sum", scale) for r in launches]
+    dur = [val(r, "gpu__time_duration.sum", tscale) for r in launches]
+    per = (sum(rd) + sum(wr)) / len(launches)
+    rec = {"kernel": "fused_bf16x3_kernel", "kernel_source_sha256_16": fused_source_hash(),
+           "captured_samples": samples, "full_samples": FULL_SAMPLES, "launches": len(launches),
+           "dram_read_bytes": sum(rd) / len(launches), "dram_write_bytes": sum(wr) / len(launches),
+           "duration_s": sum(dur) / len(launches),
+           "dram_bytes_per_full_launch": per * FULL_SAMPLES / samples, "command": command}
+    with open(TRAFFIC_RECORD, "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    return rec
 
 
 def oracle_rate(sc, nt_sample: int, white=True, pink=True):
@@ -137,13 +181,28 @@ def blas_threads():
 
 
 def cpu_baseline(sc, budget_s=12.0):
+    """The FP64 oracle as it stands on the host: once with numpy's default BLAS threads (only the
+    matrix products of Eqs. 16-17 run on them; everything else runs on one core), once with BLAS
+    held to one thread."""
     probe = 16
     r0, dt0 = oracle_rate(sc, probe)
     nt = max(probe, min(sc["nt_total"], int(probe * budget_s / max(dt0, 1e-3)) // 4 * 4))
     rate, dt = oracle_rate(sc, nt)
-    return {"value": rate, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+    single = None
+    try:
+        from threadpoolctl import threadpool_limits
+        with threadpool_limits(limits=1, user_api="blas"):
+            nt1 = max(probe, nt // 2 // 4 * 4)
+            rate1, dt1 = oracle_rate(sc, nt1)
+        single = {"value": rate1, "unit": UNIT, "cores": 1,
+                  "sample": f"first {nt1} samples, BLAS held to one thread, {dt1:.1f} s"}
+    except Exception:
+        pass
+    return {"value": rate, "unit": UNIT, "cores": blas_threads(), "nproc": os.cpu_count(), "kind": "oracle",
+            "threads": "BLAS threads for the matrix products of Eqs. 16-17 (= cores); the rest on one core",
             "sample": f"first {nt} samples of the scan (all 25 spaxels x 347 channels, white+pink noise), "
-                      f"FP64 numpy oracle, {dt:.1f} s"}
+                      f"FP64 numpy oracle, {dt:.1f} s",
+            "single_thread": single}
 
 
 def serving_leg(n_requests: int, seed: int = 2, budget_bytes: float = 120e9, max_active: int = 16,
@@ -255,7 +314,13 @@ def main():
     ap.add_argument("--skip-kelvin", action="store_true")
     ap.add_argument("--skip-tk", action="store_true")
     ap.add_argument("--skip-prep", action="store_true")
+    ap.add_argument("--record-traffic", default=None, metavar="RAW_CSV")
+    ap.add_argument("--traffic-samples", type=int, default=16384)
+    ap.add_argument("--traffic-command", default="")
     args = ap.parse_args()
+    if args.record_traffic:
+        print(json.dumps(record_traffic(args.record_traffic, args.traffic_samples, args.traffic_command)))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
 
@@ -316,7 +381,7 @@ def main():
     exec_flops = 5 * 2.0 * 128 * n_half * n_groups * info.n_freq_padded * tiles
     achieved = alg_flops / (contract_ms / 1e3) / 1e12
     roofline = {"bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
-                "frac": achieved / bf16_peak, "traffic": traffic_from_profile(),
+                "frac": achieved / bf16_peak, "traffic": traffic_from_record(),
                 "kernel": "fused_bf16x3_kernel" if args.precision == "bf16x3" else "psd_fp32+contract_fp32",
                 "peak_source": f"{peak_kind} bf16 dense burst (MEASURED_PEAKS.json)",
                 "algorithmic_flops_per_launch": alg_flops, "executed_mma_flops_per_launch": exec_flops,

@@ -292,6 +292,19 @@ gateau_status gateau_plan_get_vector(gateau_plan* plan, int which, double* out, 
 gateau_status gateau_plan_get_state(gateau_plan* plan, long long* next_t0, double* pink_state);
 gateau_status gateau_plan_set_state(gateau_plan* plan, long long next_t0, const double* pink_state);
 
+/* Budget of each pipeline wait of the fused split-BF16 kernel, in SM clock cycles
+ * (clock64; default 4e9, about 2 s at 2 GHz).  A wait that runs out sets
+ * GATEAU_STATUS_WAIT_TIMEOUT in the plan's status word, every role of the kernel
+ * stops, the kernel waits (with the default budget, whatever this one is) for its
+ * own copies and tensor-core operations in flight, frees its tensor memory and
+ * returns, so the CUDA context stays usable and gateau_plan_status reports
+ * ETIMEOUT.  The output of that run is incomplete.  A budget far below a
+ * pipeline stage's latency (0, say) makes a run time out on purpose, which is how
+ * the time-out path is tested; it affects later runs of this plan only.  The
+ * bounded waits are the kernel's guard against a pipeline that stops making
+ * progress (Sect. 2.5-2.6 give no counterpart).  EINVAL for a negative budget. */
+gateau_status gateau_plan_set_wait_budget(gateau_plan* plan, long long cycles);
+
 /* Phase timing.  With timing enabled, every run records CUDA events on its
  * stream around each phase; gateau_plan_get_timing synchronises the plan's last
  * stream, adds the elapsed milliseconds per phase since the previous call into
@@ -495,9 +508,13 @@ gateau_status gateau_server_request_result(gateau_server* server, int request, i
  *   out            : device [nt][n_pix][n_ch], the noise is added in place
  *   seed           : the plan seed (Philox key), so the draws match gateau_run
  * Sizes with n_pix * n_ch * n_pole above 1048576 are rejected (EINVAL) before
- * anything is enqueued.  The first call on a device looks up the scratch
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the scratch and leave their
+ * anything is enqueued; longer scans take fewer, longer chunks so that their
+ * states fit.  The first call on a device looks up the scratch address
+ * (cudaGetSymbolAddress) with that device current.  Under CUDA's default lazy
+ * module loading that lookup can load the library's device code on that device,
+ * which reserves the array and may synchronise: real-time callers should make
+ * one warm-up call at start-up, before their loop and before any stream
+ * capture; later calls reserve nothing.  All calls share the scratch and leave their
  * chunk states in it (nothing in it needs to start at zero: every state is
  * written before it is read), so calls whose kernels overlap on the GPU --
  * on different streams, or from different threads -- race; serialise them. */

@@ -114,6 +114,7 @@ SIGNATURES = {
     "gateau_plan_set_state": (C.c_int, [PlanP, C.c_longlong, dp]),
     "gateau_hex_offsets": (C.c_int, [C.c_int, C.c_double, dp, C.c_int, C.POINTER(C.c_int)]),
     "gateau_plan_set_timing": (C.c_int, [PlanP, C.c_int]),
+    "gateau_plan_set_wait_budget": (C.c_int, [PlanP, C.c_longlong]),
     "gateau_plan_get_timing": (C.c_int, [PlanP, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "gateau_plan_estimate_bytes": (C.c_int, [C.POINTER(PlanDesc), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                              C.c_int, C.c_longlong, C.c_longlong, C.POINTER(C.c_size_t)]),

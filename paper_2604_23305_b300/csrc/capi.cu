@@ -126,6 +126,8 @@ struct gateau_plan {
     double pitch = 0;
     int n_pwv = 0;
     double pwv_min = 0, dpwv = 0;
+    std::vector<double> tau_host;     // zenith opacity [n_pwv][n_freq] as set (FP64)
+    double screen_mean = 0;           // mean PWV of the screen (mm)
     std::vector<StageSpec> stages;
     int disp_kind = 0, n_ch = 0;
     std::vector<double> eta_filt;      // [n_ch][n_freq]
@@ -147,12 +149,14 @@ struct gateau_plan {
     int n_pole = 0;
     std::vector<double> pink_a, pink_r, pink_d;
     bool dirty = true;
+    bool ref_dirty = true;           // the reference spectrum (screen mean, table, theta0, cascade) changed
 
     // device memory
     DevBuf d_pix, d_cube, d_cube_raw, d_screen, d_tau, d_custom, d_c, d_HGQ, d_fusedB, d_pink, d_state, d_status;
     DevBuf d_tb, d_dip;              // skydip fit [2][n_ch] float for the epilogues; FP64 scratch of the fit
     DevBuf d_tk, d_tkz;              // Timmer-Koenig pink TOD [tk_n][n_pix][n_ch]; its FFT scratch
     DevBuf d_hw, d_cm;               // common-mode reduction: eta_filt w (FP64); log eta_z, S_j, PWV sum
+    DevBuf d_ref;                    // per channel: k_B 1e9 S_ref and N_ref of the reference spectrum
     bool cube_scale_dirty = true;    // d_cube = d_cube_raw * c2 / k_B must be recomputed
     DevBuf d_rows, d_tiles, d_X, d_agg, d_stage[2];
     FusedOperands fused{};
@@ -186,7 +190,7 @@ struct gateau_plan {
         track_streams();
         DevBuf* bufs[] = {&d_pix, &d_cube, &d_cube_raw, &d_screen, &d_tau, &d_custom, &d_c, &d_HGQ, &d_fusedB, &d_pink,
                           &d_state, &d_status, &d_rows, &d_tiles, &d_X, &d_agg, &d_stage[0], &d_stage[1],
-                          &d_tb, &d_dip, &d_tk, &d_tkz, &d_hw, &d_cm};
+                          &d_tb, &d_dip, &d_tk, &d_tkz, &d_hw, &d_cm, &d_ref};
         for (DevBuf* b : bufs) b->release(mo);
         if (mo.mem) cudaStreamDestroy(mo.mem);       // its pending frees still complete
         for (int i = 0; i < 2; ++i) {
@@ -216,7 +220,7 @@ size_t device_bytes(const gateau_plan* p) {
     const DevBuf* bufs[] = {&p->d_pix, &p->d_cube, &p->d_cube_raw, &p->d_screen, &p->d_tau, &p->d_custom, &p->d_c,
                             &p->d_HGQ, &p->d_fusedB, &p->d_pink, &p->d_state, &p->d_status, &p->d_rows,
                             &p->d_tiles, &p->d_X, &p->d_agg, &p->d_stage[0], &p->d_stage[1], &p->d_tb, &p->d_dip,
-                            &p->d_tk, &p->d_tkz, &p->d_hw, &p->d_cm};
+                            &p->d_tk, &p->d_tkz, &p->d_hw, &p->d_cm, &p->d_ref};
     size_t s = 0;
     for (const DevBuf* b : bufs) s += b->bytes;
     return s;
@@ -240,44 +244,17 @@ gateau_status fetch_floats(const float* src, size_t n, int mem, std::vector<floa
     return GATEAU_OK;
 }
 
-// Rebuild the derived tables (cascade collapse, filters, pink filters) and upload them.
-gateau_status finalize(gateau_plan* p) {
-    if (!p->dirty) return GATEAU_OK;
+// Contraction operands in device units (w in GHz, X in kelvin), FP64 [n_ch][Kp]:
+//   H = eta w_GHz;  G = H gamma (nu_GHz + beta);  Q = eta^2 w_GHz
+// with gamma = h 1e9 / k_B and beta = 2 Delta_Al / (eta_pb h 1e9) (Sect. 2.5 Eq. 16, Sect. 2.6 Eq. 17).
+void filter_operands(const gateau_plan* p, std::vector<double>& H, std::vector<double>& G, std::vector<double>& Q) {
     const gateau_plan_desc& d = p->desc;
-    const int nf = d.n_freq, Kp = p->Kp;
-    // cascade collapse (Sect. 2.5)
-    std::vector<PrimStage> prim;
-    std::string err;
-    if (!expand_stages(p->stages, p->nu, prim, err)) return fail(GATEAU_EINVAL, "%s", err.c_str());
-    collapse_cascade(p->nu, prim, d.T_atm_K, d.T_cmb_K, d.eta_taper, d.rho_surf_m, d.eta_pol, p->c0, p->c1, p->c2);
-    // per-frequency device vectors (kelvin units: divide by k_B)
-    std::vector<float> cv(3 * static_cast<size_t>(Kp), 0.f);
-    for (int k = 0; k < nf; ++k) {
-        cv[k] = static_cast<float>(p->c0[k] / kKB);
-        cv[Kp + k] = static_cast<float>(p->c1[k] / kKB);
-        cv[2 * Kp + k] = static_cast<float>(p->c2[k] / kKB);
-    }
-    // Regrouped per 16-point stage for the fused kernel: [Kp/16][c0 + c1, c1][16].
-    const int ks = fused_kstage();
-    for (int b = 0; b < Kp / ks; ++b) {
-        for (int k = 0; k < ks; ++k) {
-            const int kk = b * ks + k;
-            cv.push_back(kk < nf ? static_cast<float>((p->c0[kk] + p->c1[kk]) / kKB) : 0.f);
-        }
-        for (int k = 0; k < ks; ++k) cv.push_back(cv[static_cast<size_t>(Kp) + b * ks + k]);
-    }
-    GATEAU_CUDA(grow(p, p->d_c, cv.size() * sizeof(float)));
-    GATEAU_CUDA(cudaMemcpy(p->d_c.p, cv.data(), cv.size() * sizeof(float), cudaMemcpyHostToDevice));
-    p->fused.c_tiled = p->d_c.as<float>() + 3 * static_cast<size_t>(Kp);
-    p->cube_scale_dirty = true;
-
-    // contraction operands, device units: w in GHz, X in kelvin.
-    //   H = eta w_GHz;  G = H gamma (nu_GHz + beta);  Q = eta^2 w_GHz
-    // with gamma = h 1e9 / k_B and beta = 2 Delta_Al / (eta_pb h 1e9) (Eq. 17).
-    const int n_ch = p->n_ch;
+    const int nf = d.n_freq, Kp = p->Kp, n_ch = p->n_ch;
     const double gamma = kH * 1e9 / kKB;
     const double beta = 2.0 * d.delta_al_J / (d.eta_pb * kH * 1e9);
-    std::vector<double> H(static_cast<size_t>(n_ch) * Kp, 0.0), G(H.size(), 0.0), Q(H.size(), 0.0);
+    H.assign(static_cast<size_t>(n_ch) * Kp, 0.0);
+    G.assign(H.size(), 0.0);
+    Q.assign(H.size(), 0.0);
     for (int c = 0; c < n_ch; ++c)
         for (int k = 0; k < nf; ++k) {
             const double eta = p->eta_filt[static_cast<size_t>(c) * nf + k];
@@ -287,7 +264,71 @@ gateau_status finalize(gateau_plan* p) {
             G[i] = H[i] * gamma * (p->nu[k] * 1e-9 + beta);
             Q[i] = eta * eta * wg;
         }
-    p->n_ch_pad = (n_ch + 63) / 64 * 64;
+}
+
+// Reference spectrum: the source-free collapse (Sect. 2.5) at the screen's mean PWV and the
+// base elevation theta_0 (Eq. 10), X_ref = c0 + c1 (1 - e_ref).  Both contraction paths run on
+// D = X - X_ref instead of X.  D stays small wherever the line of sight sees about the mean sky,
+// so the FP32 and split-BF16 rounding is relative to the sky's fluctuation rather than to the
+// whole loading, and the source term, orders of magnitude below the atmosphere's, survives it.
+// The integrals of Eqs. 16-17 are linear in X plus a term in X^2, so with X = D + X_ref
+//   sum H X           = sum H D + S_ref,                         S_ref = sum H X_ref
+//   sum G X + Q X^2   = sum (G + 2 Q X_ref) D + Q D^2 + N_ref,   N_ref = sum G X_ref + Q X_ref^2:
+// only the G operand changes, and the epilogues add two per-channel constants.  The kernels form
+// D = c_ref - c1 e + e P'_src with c_ref = fp32(c1 e_ref); X_ref is taken as
+// (c0 + c1) / k_B - c_ref in FP64, so X = D + X_ref holds for the values the kernels use.
+gateau_status build_reference(gateau_plan* p) {
+    const gateau_plan_desc& d = p->desc;
+    const int nf = d.n_freq, Kp = p->Kp, n_ch = p->n_ch;
+    std::vector<double> eref(nf, 1.0);
+    if (!p->tau_host.empty() && p->n_pwv >= 2) {
+        double u = (p->screen_mean - p->pwv_min) / p->dpwv;
+        u = std::min(std::max(u, 0.0), static_cast<double>(p->n_pwv - 1));
+        const int j = std::min(static_cast<int>(floor(u)), p->n_pwv - 2);
+        const double f = u - j;
+        const double sn = sin(p->theta0);
+        const double csc = sn > 1e-3 ? 1.0 / sn : 1.0;      // any reference is exact; this one is near the sky
+        for (int k = 0; k < nf; ++k) {
+            const double tau = (1.0 - f) * p->tau_host[static_cast<size_t>(j) * nf + k] +
+                               f * p->tau_host[static_cast<size_t>(j + 1) * nf + k];
+            eref[k] = exp(-csc * tau);
+        }
+    }
+    std::vector<float> c1f(Kp, 0.f), cref(Kp, 0.f);
+    std::vector<double> xref(Kp, 0.0);
+    for (int k = 0; k < nf; ++k) {
+        c1f[k] = static_cast<float>(p->c1[k] / kKB);
+        cref[k] = static_cast<float>(p->c1[k] / kKB * eref[k]);
+        xref[k] = (p->c0[k] + p->c1[k]) / kKB - static_cast<double>(cref[k]);
+    }
+    // c_ref [Kp], then per 16-point stage for the fused kernel: [Kp/16][c_ref, c1][16]
+    std::vector<float> cv(cref);
+    const int ks = fused_kstage();
+    for (int b = 0; b < Kp / ks; ++b) {
+        for (int k = 0; k < ks; ++k) cv.push_back(cref[b * ks + k]);
+        for (int k = 0; k < ks; ++k) cv.push_back(c1f[b * ks + k]);
+    }
+    GATEAU_CUDA(cudaMemcpy(p->d_c.as<float>() + 3 * static_cast<size_t>(Kp), cv.data(), cv.size() * sizeof(float),
+                           cudaMemcpyHostToDevice));
+
+    std::vector<double> H, G, Q;
+    filter_operands(p, H, G, Q);
+    const int stride = p->n_ch_pad;
+    std::vector<float> rv(2 * static_cast<size_t>(stride), 0.f);
+    for (int c = 0; c < n_ch; ++c) {
+        double s_ref = 0.0, n_ref = 0.0;
+        for (int k = 0; k < nf; ++k) {
+            const size_t i = static_cast<size_t>(c) * Kp + k;
+            s_ref += H[i] * xref[k];
+            n_ref += (G[i] + Q[i] * xref[k]) * xref[k];
+            G[i] += 2.0 * Q[i] * xref[k];
+        }
+        rv[c] = static_cast<float>(kKB * 1e9 * s_ref);     // P_KID of the reference (W)
+        rv[stride + c] = static_cast<float>(n_ref);
+    }
+    GATEAU_CUDA(grow(p, p->d_ref, rv.size() * sizeof(float)));
+    GATEAU_CUDA(cudaMemcpy(p->d_ref.p, rv.data(), rv.size() * sizeof(float), cudaMemcpyHostToDevice));
+
     if (d.precision == GATEAU_PREC_FP32) {
         std::vector<float> hgq(3 * static_cast<size_t>(p->n_ch_pad) * Kp, 0.f);
         const size_t mat = static_cast<size_t>(p->n_ch_pad) * Kp;
@@ -299,18 +340,48 @@ gateau_status finalize(gateau_plan* p) {
         GATEAU_CUDA(grow(p, p->d_HGQ, hgq.size() * sizeof(float)));
         GATEAU_CUDA(cudaMemcpy(p->d_HGQ.p, hgq.data(), hgq.size() * sizeof(float), cudaMemcpyHostToDevice));
     } else {
-        const int n_groups = (n_ch + 175) / 176;   // groups of <= 176 channels: B stages fit the rings
-        const int n_half = ((n_ch + n_groups - 1) / n_groups + 15) / 16 * 16;
         std::vector<uint16_t> tiled;
         size_t stage_elems = 0;
-        fused_tile_operands(H.data(), G.data(), Q.data(), n_ch, Kp, n_half, n_groups, tiled, stage_elems);
+        fused_tile_operands(H.data(), G.data(), Q.data(), n_ch, Kp, p->fused.n_half, p->fused.n_groups, tiled,
+                            stage_elems);
         GATEAU_CUDA(grow(p, p->d_fusedB, tiled.size() * sizeof(uint16_t)));
         GATEAU_CUDA(cudaMemcpy(p->d_fusedB.p, tiled.data(), tiled.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
         p->fused.B = p->d_fusedB.as<uint16_t>();
-        p->fused.n_half = n_half;
+        p->fused.stage_elems = stage_elems;
+    }
+    p->ref_dirty = false;
+    return GATEAU_OK;
+}
+
+// Rebuild the derived tables (cascade collapse, channel grouping, skydip, pink filters) and upload them.
+gateau_status finalize_tables(gateau_plan* p) {
+    const gateau_plan_desc& d = p->desc;
+    const int nf = d.n_freq, Kp = p->Kp;
+    // cascade collapse (Sect. 2.5)
+    std::vector<PrimStage> prim;
+    std::string err;
+    if (!expand_stages(p->stages, p->nu, prim, err)) return fail(GATEAU_EINVAL, "%s", err.c_str());
+    collapse_cascade(p->nu, prim, d.T_atm_K, d.T_cmb_K, d.eta_taper, d.rho_surf_m, d.eta_pol, p->c0, p->c1, p->c2);
+    // per-frequency device vectors (kelvin units: divide by k_B): c0, c1, c2; then c_ref and its
+    // per-stage tiling, written by build_reference
+    std::vector<float> cv(3 * static_cast<size_t>(Kp), 0.f);
+    for (int k = 0; k < nf; ++k) {
+        cv[k] = static_cast<float>(p->c0[k] / kKB);
+        cv[Kp + k] = static_cast<float>(p->c1[k] / kKB);
+        cv[2 * Kp + k] = static_cast<float>(p->c2[k] / kKB);
+    }
+    GATEAU_CUDA(grow(p, p->d_c, 6 * static_cast<size_t>(Kp) * sizeof(float)));
+    GATEAU_CUDA(cudaMemcpy(p->d_c.p, cv.data(), cv.size() * sizeof(float), cudaMemcpyHostToDevice));
+    p->fused.c_tiled = p->d_c.as<float>() + 4 * static_cast<size_t>(Kp);
+    p->cube_scale_dirty = true;
+
+    const int n_ch = p->n_ch;
+    p->n_ch_pad = (n_ch + 63) / 64 * 64;
+    if (d.precision != GATEAU_PREC_FP32) {
+        const int n_groups = (n_ch + 175) / 176;   // groups of <= 176 channels: B stages fit the rings
+        p->fused.n_half = ((n_ch + n_groups - 1) / n_groups + 15) / 16 * 16;
         p->fused.n_groups = n_groups;
         p->fused.n_kstage = Kp / fused_kstage();
-        p->fused.stage_elems = stage_elems;
     }
 
     // brightness-temperature scale (Sect. 2.7): the skydip runs on the device (FP64), its fit
@@ -397,7 +468,16 @@ gateau_status finalize(gateau_plan* p) {
         GATEAU_CUDA(cudaMemset(p->d_state.p, 0, state_bytes));
     }
     p->dirty = false;
+    p->ref_dirty = true;
     return GATEAU_OK;
+}
+
+gateau_status finalize(gateau_plan* p) {
+    if (p->dirty) {
+        const gateau_status st = finalize_tables(p);
+        if (st != GATEAU_OK) return st;
+    }
+    return p->ref_dirty ? build_reference(p) : GATEAU_OK;
 }
 
 DevTables make_tables(const gateau_plan* p) {
@@ -436,6 +516,9 @@ DevTables make_tables(const gateau_plan* p) {
     T.c0 = p->d_c.as<float>();
     T.c1 = T.c0 + p->Kp;
     T.c2 = T.c0 + 2 * p->Kp;
+    T.cref = T.c0 + 3 * p->Kp;
+    T.ref_pk = p->d_ref.as<float>();
+    T.ref_n = T.ref_pk ? T.ref_pk + p->n_ch_pad : nullptr;
     T.n_ch = p->n_ch;
     T.n_ch_pad = p->n_ch_pad;
     const size_t mat = static_cast<size_t>(p->n_ch_pad) * p->Kp;
@@ -473,6 +556,9 @@ gateau_status validate_run(const gateau_plan* p, long long t0, long long nt, con
     gateau_status st = check_complete(p);
     if (st != GATEAU_OK) return st;
     if (t0 < 0 || nt <= 0) return fail(GATEAU_EINVAL, "need t0 >= 0 and nt > 0 (got t0=%lld nt=%lld)", t0, nt);
+    if (nt > (1LL << 31) / p->desc.n_pix)       // nt * n_pix > 2^31, compared without forming the product
+        return fail(GATEAU_EINVAL, "nt * n_pix must stay below 2^31 rows per call");
+    if (t0 > (1LL << 62)) return fail(GATEAU_EINVAL, "t0 must stay below 2^62");   // t0 + nt cannot overflow
     if (!out) return fail(GATEAU_EINVAL, "out is NULL");
     if ((p->desc.noise_flags & GATEAU_NOISE_PINK) && t0 != 0 && t0 != p->next_t0)
         return fail(GATEAU_EORDER, "t0=%lld does not continue the previous chunk (next t0 is %lld, or 0 to restart)", t0,
@@ -482,8 +568,6 @@ gateau_status validate_run(const gateau_plan* p, long long t0, long long nt, con
                     t0 + nt);
     if (p->scan_kind == GATEAU_SCAN_CUSTOM && t0 + nt > p->n_custom)
         return fail(GATEAU_EINVAL, "custom scan has %lld samples, run needs %lld", p->n_custom, t0 + nt);
-    if (nt * static_cast<long long>(p->desc.n_pix) > (1LL << 31))
-        return fail(GATEAU_EINVAL, "nt * n_pix must stay below 2^31 rows per call");
     return GATEAU_OK;
 }
 
@@ -643,6 +727,7 @@ gateau_status gateau_plan_create(const gateau_plan_desc* desc, gateau_plan** out
     p->nu = make_grid(d.n_freq, d.f_lo_hz, d.f_hi_hz);
     p->w = make_trapezoid(p->nu);
     p->Kp = (d.n_freq + 31) / 32 * 32;
+    p->fused.wait_cycles = kDefaultWaitCycles;
     *out = p.release();
     return GATEAU_OK;
 }
@@ -719,15 +804,17 @@ gateau_status gateau_set_atmosphere_screen(gateau_plan* p, const float* screen, 
     if (st != GATEAU_OK) return st;
     const size_t n = static_cast<size_t>(nx) * ny;
     GATEAU_CUDA(grow(p, p->d_screen, n * sizeof(float)));
-    if (is_epl) {
-        std::vector<float> h;
-        st = fetch_floats(screen, n, mem, h);
-        if (st != GATEAU_OK) return st;
+    std::vector<float> h;
+    st = fetch_floats(screen, n, mem, h);
+    if (st != GATEAU_OK) return st;
+    if (is_epl)
         for (float& v : h) v = static_cast<float>(static_cast<double>(v) / 6.587 + pwv0_mm);   // Eq. 4
-        GATEAU_CUDA(cudaMemcpy(p->d_screen.p, h.data(), n * sizeof(float), cudaMemcpyHostToDevice));
-    } else {
-        GATEAU_CUDA(cudaMemcpy(p->d_screen.p, screen, n * sizeof(float), kind_of(mem)));
-    }
+    GATEAU_CUDA(cudaMemcpy(p->d_screen.p, h.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    double sum = 0.0;                  // the reference spectrum's PWV
+    for (float v : h) sum += v;
+    const double mean = sum / static_cast<double>(n);
+    if (!p->has_screen || mean != p->screen_mean) p->ref_dirty = true;
+    p->screen_mean = mean;
     p->nx = nx;
     p->ny = ny;
     p->pitch = pitch_m;
@@ -764,6 +851,8 @@ gateau_status gateau_set_atmosphere_table(gateau_plan* p, const float* table, in
         }
     GATEAU_CUDA(grow(p, p->d_tau, padded.size() * sizeof(float)));
     GATEAU_CUDA(cudaMemcpy(p->d_tau.p, padded.data(), padded.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if (tau != p->tau_host) p->ref_dirty = true;
+    p->tau_host = std::move(tau);
     p->n_pwv = n_pwv;
     p->pwv_min = pwv_min_mm;
     p->dpwv = dpwv_mm;
@@ -856,6 +945,7 @@ gateau_status gateau_set_scan(gateau_plan* p, int kind, const double* params, in
     p->scan_kind = kind;
     for (int i = 0; i < kMaxScanParams; ++i) p->sp[i] = i < n_params ? params[i] : 0.0;
     p->phi0 = phi0_rad;
+    if (!p->has_scan || theta0_rad != p->theta0) p->ref_dirty = true;   // the reference spectrum's elevation
     p->theta0 = theta0_rad;
     p->n_custom = kind == GATEAU_SCAN_CUSTOM ? n_custom : 0;
     if (p->kelvin) p->dirty = true;    // the skydip runs at the base elevation theta0
@@ -920,11 +1010,12 @@ gateau_status gateau_common_mode(gateau_plan* p, long long t0, long long nt, con
     gateau_status st = check_complete(p);
     if (st != GATEAU_OK) return st;
     if (t0 < 0 || nt <= 0) return fail(GATEAU_EINVAL, "need t0 >= 0 and nt > 0");
+    if (nt > (1LL << 31) / p->desc.n_pix) return fail(GATEAU_EINVAL, "nt * n_pix must stay below 2^31");
+    if (t0 > (1LL << 62)) return fail(GATEAU_EINVAL, "t0 must stay below 2^62");
     if (!std::isfinite(pwv_mean_mm) || !std::isfinite(r_out_rad)) return fail(GATEAU_EINVAL, "non-finite argument");
     if (p->scan_kind == GATEAU_SCAN_CUSTOM && t0 + nt > p->n_custom)
         return fail(GATEAU_EINVAL, "custom scan has %lld samples, the reduction needs %lld", p->n_custom, t0 + nt);
     const int n_pix = p->desc.n_pix, n_ch = p->n_ch, nf = p->desc.n_freq;
-    if (nt * static_cast<long long>(n_pix) > (1LL << 31)) return fail(GATEAU_EINVAL, "nt * n_pix must stay below 2^31");
     // S_j (Eq. 26): spaxels farther than r_out from the IFU centre
     std::vector<unsigned char> off(n_pix, 0);
     int n_out = 0;
@@ -1280,6 +1371,13 @@ gateau_status gateau_plan_set_state(gateau_plan* p, long long next_t0, const dou
         GATEAU_CUDA(cudaMemcpy(p->d_state.p, h.data(), n * sizeof(float), cudaMemcpyHostToDevice));
     }
     p->next_t0 = next_t0;
+    return GATEAU_OK;
+}
+
+gateau_status gateau_plan_set_wait_budget(gateau_plan* p, long long cycles) {
+    if (!p) return fail(GATEAU_EINVAL, "plan is NULL");
+    if (cycles < 0) return fail(GATEAU_EINVAL, "the wait budget must be >= 0 cycles");
+    p->fused.wait_cycles = cycles;
     return GATEAU_OK;
 }
 

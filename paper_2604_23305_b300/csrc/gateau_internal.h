@@ -72,12 +72,17 @@ struct DevTables {
     const float* c0;                   // [Kp] kelvin
     const float* c1;                   // [Kp] kelvin
     const float* c2;                   // [Kp] kelvin per (W/Hz), folded into cube
-    // contraction operands, fp32 [n_ch_pad][Kp] (plain path)
+    // Reference spectrum X_ref = c0 + c1 (1 - e_ref) (source-free, mean PWV, base elevation): the
+    // contractions run on D = X - X_ref = c_ref - c1 e + e P'_src
+    const float* cref;                 // [Kp] c1 e_ref, kelvin
+    const float* ref_pk;               // [n_ch_pad] k_B 1e9 sum H X_ref (W), added to P_KID
+    const float* ref_n;                // [n_ch_pad] sum G X_ref + Q X_ref^2, added to N
+    // contraction operands, fp32 [n_ch_pad][Kp] (plain path), on D
     int n_ch, n_ch_pad;
     const float* H;                    // eta_filt * w_GHz
-    const float* G;                    // H * gamma (nu_GHz + beta)
+    const float* G;                    // H * gamma (nu_GHz + beta) + 2 Q X_ref
     const float* Q;                    // eta_filt^2 * w_GHz
-    // epilogue scales: P_KID = kb1e9 * S1,  sigma = kB * sqrt(noise_scale * N)
+    // epilogue scales: P_KID = kb1e9 * S1 + ref_pk,  sigma = kB * sqrt(noise_scale * (N + ref_n))
     float kb1e9;
     float kB;
     float noise_scale;                 // 1e9 * f_sample
@@ -104,8 +109,11 @@ struct FusedOperands {
     int n_kstage;                      // K stages of fused_kstage() points
     size_t stage_elems;                // bf16 elements per (group, kstage) block
     int tma_inputs;                    // 1: opacity rows and cube texels are staged by tensor copies
-    const float* c_tiled;              // [Kp/16][2][16] c0 + c1 and c1 per stage (kelvin)
+    const float* c_tiled;              // [Kp/16][2][16] c_ref and c1 per stage (kelvin)
+    long long wait_cycles;             // budget of each pipeline wait (clock64 cycles); drains keep their own
 };
+
+constexpr long long kDefaultWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
 // Opaque 128-byte tensor-map descriptors (CUtensorMap) for the staged inputs.
 struct __align__(64) TensorMapBytes {

@@ -1,19 +1,25 @@
 // Fused split-BF16 tcgen05 kernel: steps (b)-(f) of the hot path in one pass.
 //
 // For a tile of 128 consecutive time samples of one spaxel and a group of NH
-// channels, the kernel builds the post-cascade spectrum X[row][nu] (Sect. 2.5,
-// via the exact collapse c0 + c1 (1 - eta_atm) + c2 eta_atm P_src) slice by
-// slice in shared memory -- it never reaches HBM -- and contracts it on the
+// channels, the kernel builds the post-cascade spectrum (Sect. 2.5, via the
+// exact collapse X = c0 + c1 (1 - eta_atm) + c2 eta_atm P_src) as its difference
+// D = X - X_ref from the plan's source-free reference spectrum
+// X_ref = c0 + c1 (1 - e_ref), i.e. D = c_ref - c1 eta_atm + eta_atm P'_src, slice
+// by slice in shared memory -- it never reaches HBM -- and contracts it on the
 // 5th-generation tensor cores against the filter matrices (Sect. 2.5, Eq. 16;
 // Sect. 2.6, Eq. 17):
 //
-//   S[row][ch] = X_hi H_hi + X_lo H_hi + X_hi H_lo         (split BF16, FP32 accumulate)
-//   N[row][ch] = X_hi G + bf16(X_hi^2) Q                    (noise terms, 1 product each)
+//   S[row][ch] = D_hi H_hi + D_lo H_hi + D_hi H_lo         (split BF16, FP32 accumulate)
+//   N[row][ch] = D_hi G' + bf16(D_hi^2) Q                   (noise terms, 1 product each)
 //
-// with X = X_hi + X_lo and H = H_hi + H_lo the BF16 hi/lo splits.  The
-// epilogue turns S into P_KID (Eq. 16) and N into sigma (Eqs. 17-18), adds the
-// white noise (Eq. 19, Philox normals drawn while the item's MMAs run and parked
-// in free TMEM columns) and writes out[n][i][ch].
+// with D = D_hi + D_lo and H = H_hi + H_lo the BF16 hi/lo splits and
+// G' = G + 2 Q X_ref (the cross term of X^2 = (D + X_ref)^2).  D is small next to
+// X wherever the sky is near its mean, so the rounding of the split products is
+// relative to the sky's fluctuation, not to the whole loading, and the faint
+// source term survives it.  The epilogue adds the reference's integrals
+// (per-channel constants), turns S into P_KID (Eq. 16) and N into sigma
+// (Eqs. 17-18), adds the white noise (Eq. 19, Philox normals drawn while the
+// item's MMAs run and parked in free TMEM columns) and writes out[n][i][ch].
 //
 // Warp roles (512 threads, one CTA per SM, persistent over work items):
 //   warp 0        : one thread issuing bulk copies of the pre-tiled filter operands (B ring)
@@ -44,8 +50,8 @@ namespace gateau {
 
 constexpr int kTileM = kTileRows;    // rows per tile (TMEM lanes)
 constexpr int kKStage = 16;          // spectral points per pipeline stage (one K=16 MMA step)
-constexpr int kAMats = 3;            // X_hi, X_lo, bf16(X^2)
-constexpr int kBMats = 4;            // H_hi, H_lo, G, Q
+constexpr int kAMats = 3;            // D_hi, D_lo, bf16(D_hi^2)
+constexpr int kBMats = 4;            // H_hi, H_lo, G', Q
 constexpr int kProdWarps = 8;
 constexpr int kProdWarp0 = 4;               // warps 0..3: operand TMA, MMA, input TMA, peer copier
 constexpr int kEpiWarp0 = kProdWarp0 + kProdWarps;
@@ -59,11 +65,16 @@ constexpr int kInSlots = 6;          // input-ring depth (stages of staged gathe
 constexpr int kBoxW = 20;
 constexpr int kCubeBoxBytes = kCubeBoxAz * kCubeBoxEl * kBoxW * 4;    // 3840
 constexpr int kTauBoxBytes = 2 * kTauBoxRows * kBoxW * 4;             // (tau_j, dtau_j) rows: 1280
-constexpr int kConstBytes = 2 * kKStage * 4;                          // c0 + c1 and c1 of the stage
+constexpr int kConstBytes = 2 * kKStage * 4;                          // c_ref and c1 of the stage
 constexpr int kTauOff = kCubeBoxBytes;
 constexpr int kConstOff = kCubeBoxBytes + kTauBoxBytes;
 constexpr int kInSlotBytes = (kConstOff + kConstBytes + 127) / 128 * 128;
-constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+constexpr long long kWaitCycles = kDefaultWaitCycles;   // drains on the exit path: ~2 s at 2 GHz
+// Grace on the exit path of an aborted shared tile: a peer's row copies into this CTA complete on
+// stage barriers that an aborted loader may never have armed, so no drain reports them; each CTA
+// waits this long after its last copy was issued before it arrives on the final cluster barrier,
+// which the peer must pass before it can exit (a 2 KB copy lands in about a microsecond).
+constexpr long long kAbortGraceCycles = 2000000LL;      // ~1 ms
 
 int fused_kstage() { return kKStage; }
 
@@ -171,7 +182,7 @@ bool fused_encode_input_maps(const float* tau, int n_pwv, const float* cube, int
 }
 
 // ---- shared-memory plan -------------------------------------------------------
-// The spectrum rows (A: X_hi, X_lo, bf16(X^2)) and the filter operands (B: H_hi, H_lo, G, Q)
+// The spectrum rows (A: D_hi, D_lo, bf16(D_hi^2)) and the filter operands (B: H_hi, H_lo, G', Q)
 // of a stage live in two rings of their own.  A slot is reused only after the rows have been
 // built again (and, for a shared tile, copied from the peer), a long round trip, so the A ring
 // is the deeper one; a B slot only waits for its copy from L2.
@@ -180,11 +191,14 @@ struct SmemPlan {
     size_t a_bytes, b_bytes, b_off, in_off, bar_off, total;
 };
 
-__host__ __device__ inline SmemPlan smem_plan(int n_half) {
-    SmemPlan p;
+constexpr size_t kBarReserve = 512;     // mbarriers, TMEM address slot and abort flag
+constexpr int kMaxHalf = 176;           // channels per group: 2 x 176 accumulator columns + parked normals
+
+__host__ __device__ constexpr SmemPlan smem_plan(int n_half) {
+    SmemPlan p{};
     p.a_bytes = static_cast<size_t>(kAMats) * kTileM * kKStage * 2;
     p.b_bytes = static_cast<size_t>(kBMats) * n_half * kKStage * 2;
-    const size_t bar_reserve = 512;
+    const size_t bar_reserve = kBarReserve;
     const size_t in_bytes = static_cast<size_t>(kInSlots) * kInSlotBytes;
     const long long avail = static_cast<long long>(kMaxSmem) - 1024 - bar_reserve - in_bytes;
     p.nsa = 0;
@@ -206,7 +220,44 @@ __host__ __device__ inline SmemPlan smem_plan(int n_half) {
     return p;
 }
 
-size_t fused_smem_bytes() { return smem_plan(176).total; }
+size_t fused_smem_bytes() { return smem_plan(kMaxHalf).total; }
+
+// What the barrier protocol below assumes of the ring depths (each checked at compile time for
+// every group width the plan can choose, and again at launch):
+//  * the MMA issuer takes stage pairs: the A ring holds whole pairs (nsa even), so a pair's
+//    stage-full and stage-free barriers serve slots 2p and 2p + 1;
+//  * nsb <= nsa: the operand loader refills the B slot of stage g after the MMAs of stage
+//    g - nsb, by which time the A-slot pair barrier of stage g has left the phase of stage
+//    g - nsa, and no barrier a loader or the issuer waits on can run two phases ahead of it;
+//  * an item's first nsa stages are built before the previous item's epilogue (kPre = nsa): their
+//    slots are freed by the previous item's MMAs alone, which need no epilogue;
+//  * the barriers (3 nsa + 2 kInSlots, three item barriers, the TMEM slot and abort flag, nsa / 2
+//    first-stage B releases) fit the reserved bytes;
+//  * a pair's expected transaction bytes (B operands and, for a shared tile, the peer's rows of
+//    both stages) stay below the mbarrier's 2^20 limit;
+//  * the rings start on 1024-byte (A) and 16-byte (B, bulk copies) boundaries.
+constexpr bool ring_protocol_ok(const SmemPlan& p) {
+    return p.nsa >= 2 && p.nsa % 2 == 0 && p.nsb >= 2 && p.nsb <= p.nsa &&
+           8 * (3 * p.nsa + 2 * kInSlots + 5 + p.nsa / 2) <= static_cast<int>(kBarReserve) &&
+           2 * (p.b_bytes + static_cast<size_t>(kAMats) * kTileM * kKStage) < (size_t(1) << 20) &&
+           p.a_bytes % 1024 == 0 && p.b_off % 1024 == 0 && p.b_bytes % 16 == 0 && p.in_off % 128 == 0 &&
+           p.total <= static_cast<size_t>(kMaxSmem);
+}
+
+constexpr bool ring_protocol_ok_for_all_groups() {
+    for (int nh = 16; nh <= kMaxHalf; nh += 16)
+        if (!ring_protocol_ok(smem_plan(nh))) return false;
+    return true;
+}
+
+static_assert(ring_protocol_ok_for_all_groups(), "ring depths break the barrier protocol");
+static_assert(kTileM == 128, "M = 128 MMAs: one TMEM lane per tile row");
+static_assert(kProdWarps == 8 && kThreads == 512, "warp roles: 4 single-thread roles, 8 producers, 4 epilogue");
+static_assert(kThreads / 32 - kProdWarp0 == 4 + kProdWarps, "acc_empty counts every epilogue-sharing warp");
+static_assert(3 * (kProdWarps / 2) == kThreads / 32 - kProdWarp0 && 16 * (kProdWarps / 2) == kTileM / 2,
+              "shared tiles: three groups of four producer warps, 16 rows each, build a CTA's 64 rows");
+static_assert(16 * kProdWarps == kTileM, "independent CTAs: eight producer warps build the 128 rows");
+static_assert(kInSlotBytes % 128 == 0, "input slots start on 128-byte boundaries (tensor copies)");
 
 // ---- PTX wrappers ------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -237,16 +288,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: returns false (and raises the abort flag) when the budget runs out
-// or another role has already aborted.
+// Bounded wait: returns false (and raises the abort flag) when the budget (clock64 cycles, a
+// run-time parameter) runs out or another role has already aborted.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          unsigned int* status) {
+                                          unsigned int* status, long long budget) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t_start = clock64();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (clock64() - t_start > kWaitCycles) {
+        if (clock64() - t_start > budget) {
             *abort_flag = 1;
             atomicOr(status, GATEAU_STATUS_WAIT_TIMEOUT);
             return false;
@@ -258,12 +309,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 // polls the thread sleeps, so idle waiters do not take shared-memory issue slots from the
 // roles on the critical path.
 __device__ __forceinline__ bool mbar_wait_idle(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                               unsigned int* status) {
+                                               unsigned int* status, long long budget) {
     const long long t_start = clock64();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (clock64() - t_start > kWaitCycles) {
+        if (clock64() - t_start > budget) {
             *abort_flag = 1;
             atomicOr(status, GATEAU_STATUS_WAIT_TIMEOUT);
             return false;
@@ -444,16 +495,22 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // each building half of the tile's spectrum rows and copying it to the peer.
 struct Work {
     long long tiles_per_pix, n_items;
+    int n_pix;
     int share;
 };
 
-// Item it = tile * n_groups + group; tile = pix * tiles_per_pix + tile-in-pixel.
+// Item it = (tile-in-pixel * n_pix + pix) * n_groups + group: items are walked time tile by time
+// tile, all spaxels of one time tile next to each other.  The CTAs resident at one moment then
+// look at one stretch of the scan -- the IFU's spaxels see neighbouring cube texels -- and write
+// neighbouring output rows ([n][pix][ch]), so cube boxes hit L2 and output lines fill together.
+// tile = pix * tiles_per_pix + tile-in-pixel indexes the TileInfo records.
 __device__ __forceinline__ void item_coords(const Work& w, int n_groups, long long it, long long& tile, int& pix,
                                             long long& row0, int& nrows, int& grp, long long nt) {
-    tile = it / n_groups;
-    grp = static_cast<int>(it - tile * n_groups);
-    pix = static_cast<int>(tile / w.tiles_per_pix);
-    const long long tl = tile - static_cast<long long>(pix) * w.tiles_per_pix;
+    const long long u = it / n_groups;
+    grp = static_cast<int>(it - u * n_groups);
+    const long long tl = u / w.n_pix;
+    pix = static_cast<int>(u - tl * w.n_pix);
+    tile = static_cast<long long>(pix) * w.tiles_per_pix + tl;
     row0 = tl * kTileM;                                // sample offset within the run
     const long long rem = nt - row0;
     nrows = rem < kTileM ? static_cast<int>(rem) : kTileM;
@@ -550,6 +607,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int n_chunks = NH / 16;
     const bool white = (T.noise_flags & GATEAU_NOISE_WHITE) != 0;
     constexpr int kZChunks = 10;
+    static_assert(kZChunks * 16 == 2 * (256 - kMaxHalf), "parked normals fill the columns [176, 256) and [432, 512)");
     const int epi_role = warp >= kEpiWarp0 ? 0 : (warp < kProdWarp0 + 4 ? 1 : 2);
     const int cut1 = (n_chunks + 2) / 3, cut2 = cut1 + (n_chunks - cut1 + 1) / 2;
     const int unit_lo = 4 * (epi_role == 0 ? 0 : (epi_role == 1 ? cut1 : cut2));
@@ -587,7 +645,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto epilogue_item = [&](long long j) -> bool {
         // tcgen05.ld is warp-collective: take the wait's outcome warp-uniformly.
         if (n_zunits) tmem_wait_st();            // this warp's parked normals of item j have landed
-        const bool okw = mbar_wait(acc_full, static_cast<uint32_t>(j & 1), abort_flag, T.status);
+        const bool okw = mbar_wait(acc_full, static_cast<uint32_t>(j & 1), abort_flag, T.status, F.wait_cycles);
         if (!__all_sync(0xffffffffu, okw)) return false;
         tc_fence_after();
         const int quad = warp & 3;
@@ -633,6 +691,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ka = *reinterpret_cast<const float2*>(T.tb_a + chq);   // padded arrays, chq even
                 kb = *reinterpret_cast<const float2*>(T.tb_b + chq);
             }
+            // the reference spectrum's P_KID and N (padded to n_ch_pad, chq even)
+            float2 rpk = make_float2(0.f, 0.f), rn = make_float2(0.f, 0.f);
+            if (chq < T.n_ch) {
+                rpk = *reinterpret_cast<const float2*>(T.ref_pk + chq);
+                rn = *reinterpret_cast<const float2*>(T.ref_n + chq);
+            }
 #pragma unroll
             for (int rr = 0; rr < 2; ++rr) {
                 const int R = R0 + 8 * rr;
@@ -644,9 +708,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int ch = chq + e;
                     if (ch < T.n_ch) {
                         const int k = 2 * rr + e;
-                        const float pk = T.kb1e9 * __uint_as_float(sr[k]);
+                        const float pk = fmaf(T.kb1e9, __uint_as_float(sr[k]), e ? rpk.y : rpk.x);
                         // k_B outside the root: k_B^2 times N would leave the normal float range
-                        const float sigma = T.kB * sqrt_approx(T.noise_scale * fmaxf(__uint_as_float(nr[k]), 0.f));
+                        const float nn = __uint_as_float(nr[k]) + (e ? rn.y : rn.x);
+                        const float sigma = T.kB * sqrt_approx(T.noise_scale * fmaxf(nn, 0.f));
                         orow[ch] = fmaf(e ? ka.y : ka.x, fmaf(sigma, e ? zz.y : zz.x, pk), e ? kb.y : kb.x);
                     }
                 }
@@ -695,7 +760,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 bool ok = true;
                 for (int ks = 0; ks < n_ks; ++ks) {
                     if (g >= NSB) {
-                        if (!mbar_wait((sf & 1) ? empty_bar(sf) : bfree_first(sf), pf, abort_flag, T.status)) {
+                        if (!mbar_wait((sf & 1) ? empty_bar(sf) : bfree_first(sf), pf, abort_flag, T.status, F.wait_cycles)) {
                             ok = false;
                             break;
                         }
@@ -710,8 +775,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 if (!ok) break;
             }
-            for (long long q = (g > NSB ? g - NSB : 0); q < g; ++q)  // no copy in flight at exit
+            for (long long q = (g > NSB ? g - NSB : 0); q < g; ++q) {   // no copy in flight at exit
+                if ((q & 1) == 0 && q + 1 < g) continue;   // stages 2p, 2p + 1 share one barrier phase
                 mbar_drain(full_a(static_cast<int>(q % NS)), static_cast<uint32_t>((q / NS) & 1));
+            }
         }
     } else if (warp == 2) {
         if (lane == 0) {
@@ -730,7 +797,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t bytes = kConstBytes + (tau_box ? kTauBoxBytes : 0) + (cube_box ? kCubeBoxBytes : 0);
                 bool ok = true;
                 for (int ks = 0; ks < n_ks; ++ks) {
-                    if (g >= kInSlots && !mbar_wait(empty_in(s), ph ^ 1u, abort_flag, T.status)) {
+                    if (g >= kInSlots && !mbar_wait(empty_in(s), ph ^ 1u, abort_flag, T.status, F.wait_cycles)) {
                         ok = false;
                         break;
                     }
@@ -752,7 +819,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 3) {
         // ---------------- shared tiles: this CTA's rows of each stage -> the peer ----------------
         // Off the producers' critical path: they signal rows_ready and go on; this thread issues
-        // the three 2 KB bulk copies (its 64 rows of X_hi, X_lo, bf16(X^2)) into the peer's
+        // the three 2 KB bulk copies (its 64 rows of D_hi, D_lo, bf16(D_hi^2)) into the peer's
         // shared memory, completing on the peer's stage-full barrier, then arrives on ours.
         if (share && lane == 0) {
             constexpr uint32_t amat = kTileM * kKStage * 2;
@@ -762,7 +829,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             for (long long j = 0; j < my_items && ok; ++j) {
                 for (int ks = 0; ks < n_ks; ++ks) {
-                    if (!mbar_wait(rows_ready(s), par, abort_flag, T.status)) {
+                    if (!mbar_wait(rows_ready(s), par, abort_flag, T.status, F.wait_cycles)) {
                         ok = false;
                         break;
                     }
@@ -797,12 +864,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             for (long long j = 0; j < my_items && ok; ++j) {
                 if (j > 0) {
-                    ok = mbar_wait(acc_empty, static_cast<uint32_t>((j - 1) & 1), abort_flag, T.status);
+                    ok = mbar_wait(acc_empty, static_cast<uint32_t>((j - 1) & 1), abort_flag, T.status, F.wait_cycles);
                     if (!ok) break;
                     tc_fence_after();
                 }
                 for (int ks = 0; ks < n_ks; ks += 2) {               // n_ks is even (Kp % 32 == 0)
-                    if (!mbar_wait(full_a(s), par, abort_flag, T.status)) {
+                    if (!mbar_wait(full_a(s), par, abort_flag, T.status, F.wait_cycles)) {
                         ok = false;
                         break;
                     }
@@ -944,8 +1011,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         };
         // one stage of this warp (ks of the current item): gathers, X, split, stores, arrival
         auto build_stage = [&](int ks) -> bool {
-                bool okw = (g < NS || mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, T.status)) &&
-                           mbar_wait(full_in(si), phi, abort_flag, T.status);
+                bool okw = (g < NS || mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, T.status, F.wait_cycles)) &&
+                           mbar_wait(full_in(si), phi, abort_flag, T.status, F.wait_cycles);
                 okw = __all_sync(0xffffffffu, okw);      // the warp signals as one
                 if (!okw) return false;
                 uint8_t* a0 = smem + s * sp.a_bytes;
@@ -954,9 +1021,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const float* slot =
                         reinterpret_cast<const float*>(smem + sp.in_off + static_cast<size_t>(si) * kInSlotBytes);
                     const float* stau = slot + kTauOff / 4;
-                    const float* scon = slot + kConstOff / 4;                // [c0 + c1][16], [c1][16]
+                    const float* scon = slot + kConstOff / 4;                // [c_ref][16], [c1][16]
                     const int kq = ks * kKStage + 4 * quad;                  // first point of this thread
-                    const float4 c01 = ld4(scon + 4 * quad);
+                    const float4 cr = ld4(scon + 4 * quad);
                     const float4 c1 = ld4(scon + kKStage + 4 * quad);
                     float4 ta, td, q00, q10, q01, q11;
                     auto gather_tau = [&](const RowC& c) {
@@ -988,7 +1055,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     };
                     // Read everything this stage needs from the input slot, then release the slot so
-                    // the next gathers land while this warp computes.  X = (c0 + c1) + e (P'_src - c1).
+                    // the next gathers land while this warp computes.  D = (c_ref - c1 e) + e P'_src.
                     float4 arg[2], src[2];
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
@@ -1006,10 +1073,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (lane == 0) mbar_arrive(empty_in(si));
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
-                        x[i][0] = fmaf(ex2_approx(arg[i].x), src[i].x - c1.x, c01.x);
-                        x[i][1] = fmaf(ex2_approx(arg[i].y), src[i].y - c1.y, c01.y);
-                        x[i][2] = fmaf(ex2_approx(arg[i].z), src[i].z - c1.z, c01.z);
-                        x[i][3] = fmaf(ex2_approx(arg[i].w), src[i].w - c1.w, c01.w);
+                        const float e0 = ex2_approx(arg[i].x), e1 = ex2_approx(arg[i].y);
+                        const float e2 = ex2_approx(arg[i].z), e3 = ex2_approx(arg[i].w);
+                        x[i][0] = fmaf(e0, src[i].x, fmaf(-c1.x, e0, cr.x));
+                        x[i][1] = fmaf(e1, src[i].y, fmaf(-c1.y, e1, cr.y));
+                        x[i][2] = fmaf(e2, src[i].z, fmaf(-c1.z, e2, cr.z));
+                        x[i][3] = fmaf(e3, src[i].w, fmaf(-c1.w, e3, cr.w));
                     }
                 }
 #pragma unroll
@@ -1021,7 +1090,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const __nv_bfloat162 h2 = __floats2bfloat162_rn(xa, xb);
                         hi[q] = *reinterpret_cast<const uint32_t*>(&h2);
                         lo[q] = pack_bf16(xa - __low2float(h2), xb - __high2float(h2));
-                        const __nv_bfloat162 s2 = __hmul2(h2, h2);            // bf16(X_hi^2) for the noise term
+                        const __nv_bfloat162 s2 = __hmul2(h2, h2);            // bf16(D_hi^2) for the noise term
                         sq[q] = *reinterpret_cast<const uint32_t*>(&s2);
                     }
                     const size_t off = core_offset(rr[i], 4 * quad, kTileM);  // 8-byte aligned
@@ -1079,6 +1148,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp >= kProdWarp0) tmem_wait_st();     // no parked normals in flight (a role may have stopped early)
     tc_fence_before();
     __syncthreads();
+    if (share && *abort_flag) {                 // aborted shared tile: the row copies already issued land first
+        if (threadIdx.x == 0) {
+            const long long t_start = clock64();
+            while (clock64() - t_start < kAbortGraceCycles) {
+            }
+        }
+        __syncthreads();
+    }
     if (share) cluster_sync_all();              // no copy into or out of our shared memory in flight
     tc_fence_after();
     if (warp == 1) {
@@ -1091,10 +1168,12 @@ cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, cons
                                 const TensorMapBytes& tm_cube, const RowParams* rows, const TileInfo* tiles,
                                 long long t0, long long nt, float* out, int n_sm, cudaStream_t stream) {
     const SmemPlan sp = smem_plan(F.n_half);
-    if (sp.nsb < 2) return cudaErrorInvalidConfiguration;
+    if (F.n_half < 16 || F.n_half > kMaxHalf || F.n_half % 16 || !ring_protocol_ok(sp) || F.n_kstage % 2)
+        return cudaErrorInvalidConfiguration;
     Work w;
     w.tiles_per_pix = (nt + kTileM - 1) / kTileM;
     w.n_items = w.tiles_per_pix * T.n_pix * F.n_groups;
+    w.n_pix = T.n_pix;
     w.share = F.n_groups == 2 ? 1 : 0;
     if (w.n_items == 0) return cudaSuccess;
     auto kernel = w.share ? fused_bf16x3_kernel<1> : fused_bf16x3_kernel<0>;

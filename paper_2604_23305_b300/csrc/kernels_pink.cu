@@ -5,8 +5,9 @@
 // The recurrence is linear, so a run of nt samples is cut into C chunks of L
 // samples scanned in parallel:
 //   phase 1: each (chunk, sequence) computes its end state from a zero start;
-//   phase 2: each (sequence, pole) combines the chunk states in order in FP64,
-//            s_in[c+1] = a^len(c) s_in[c] + agg[c], seeded by the carried state;
+//   phase 2: each (sequence, pole) combines the chunk states in order,
+//            s_in[c+1] = a^len(c) s_in[c] + agg[c], seeded by the carried state
+//            (FP32: a^len = 2^(len log2 a) to ~1e-6 relative, a few dozen steps);
 //   phase 3: each (chunk, sequence) reruns its chunk from s_in[c] and adds y.
 // Threads of a warp own consecutive channels of one spaxel, so every sample
 // step reads and writes 128 contiguous bytes of out.  The poles are held in
@@ -90,17 +91,26 @@ __global__ void pink_phase2_kernel(DevTables T, float* state, PinkWork W, long l
         const long long s = idx / np;
         const int j = static_cast<int>(idx - s * np);
         const int ch = static_cast<int>(s % T.n_ch);
-        const double a = T.pink_a[ch * np + j];
-        const double aL = pow(a, static_cast<double>(W.L));
-        double carry = state[idx];
-        for (int c = 0; c < W.C; ++c) {
-            const long long len = min(W.L, nt - c * W.L);
-            float* slot = W.agg + (c * S + s) * np + j;
-            const double agg = *slot;
-            *slot = static_cast<float>(carry);
-            carry = (len == W.L ? aL : pow(a, static_cast<double>(len))) * carry + agg;
+        const float la = log2f(T.pink_a[ch * np + j]);      // poles 0 < a < 1
+        const float aL = exp2f(static_cast<float>(W.L) * la);
+        float carry = state[idx];
+        // chunk states are loaded eight at a time, so the loads do not wait on the carry chain
+        constexpr int kAhead = 8;
+        for (int c0 = 0; c0 < W.C; c0 += kAhead) {
+            float agg[kAhead];
+#pragma unroll
+            for (int u = 0; u < kAhead; ++u)
+                agg[u] = c0 + u < W.C ? W.agg[(static_cast<long long>(c0 + u) * S + s) * np + j] : 0.f;
+#pragma unroll
+            for (int u = 0; u < kAhead; ++u) {
+                const int c = c0 + u;
+                if (c >= W.C) break;
+                const long long len = min(W.L, nt - c * W.L);
+                W.agg[(static_cast<long long>(c) * S + s) * np + j] = carry;
+                carry = fmaf(len == W.L ? aL : exp2f(static_cast<float>(len) * la), carry, agg[u]);
+            }
         }
-        state[idx] = static_cast<float>(carry);
+        state[idx] = carry;
     }
 }
 

@@ -236,8 +236,10 @@ cudaError_t launch_row_setup(const DevTables& T, long long t0, long long nt, Row
 
 // ---------------------------------------------------------------------------
 // Spectral power after the cascade, FP32 (Sect. 2.5), using the exact collapse
-// P = c0 + c1 (1 - eta_atm) + c2 eta_atm P_src with eta_atm = exp(-csc tau_z).
-// One block per row, 4 consecutive frequencies per thread.
+// P = c0 + c1 (1 - eta_atm) + c2 eta_atm P_src with eta_atm = exp(-csc tau_z), written as its
+// difference from the plan's source-free reference spectrum X_ref = c0 + c1 (1 - e_ref):
+// D = c1 e_ref - c1 eta_atm + eta_atm c2 P_src (the contraction adds back the reference's
+// integrals).  One block per row, 4 consecutive frequencies per thread.
 // ---------------------------------------------------------------------------
 __global__ void psd_fp32_kernel(DevTables T, const RowParams* __restrict__ rows, long long r0,
                                 float* __restrict__ X) {
@@ -256,7 +258,7 @@ __global__ void psd_fp32_kernel(DevTables T, const RowParams* __restrict__ rows,
     for (int k = threadIdx.x * 4; k < T.Kp; k += blockDim.x * 4) {
         const float4 a4 = *reinterpret_cast<const float4*>(tA + k);
         const float4 d4 = *reinterpret_cast<const float4*>(tD + k);
-        const float4 c04 = *reinterpret_cast<const float4*>(T.c0 + k);
+        const float4 cr4 = *reinterpret_cast<const float4*>(T.cref + k);
         const float4 c14 = *reinterpret_cast<const float4*>(T.c1 + k);
         float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
         if (has_src) {
@@ -273,10 +275,8 @@ __global__ void psd_fp32_kernel(DevTables T, const RowParams* __restrict__ rows,
 #define GATEAU_PSD(c)                                                  \
     {                                                                  \
         const float tau = fmaf(rp.tau_f, d4.c, a4.c);                  \
-        const float arg = rp.csc * tau;                                \
-        const float e = expf(-arg);                                    \
-        const float ome = -expm1f(-arg);                               \
-        o.c = c04.c + c14.c * ome + e * p.c;                           \
+        const float e = expf(-rp.csc * tau);                           \
+        o.c = fmaf(e, p.c, fmaf(-c14.c, e, cr4.c));                    \
     }
         GATEAU_PSD(x) GATEAU_PSD(y) GATEAU_PSD(z) GATEAU_PSD(w)
 #undef GATEAU_PSD
@@ -313,9 +313,10 @@ cudaError_t launch_psd_fp32(const DevTables& T, const RowParams* rows, long long
 }
 
 // ---------------------------------------------------------------------------
-// FP32 SIMT contraction.  For a block of 128 rows x 64 channels:
-//   S1[r][ch] = sum_k X[r][k] H[ch][k]                      (Eq. 16, kelvin*GHz)
-//   N [r][ch] = sum_k X[r][k] G[ch][k] + X[r][k]^2 Q[ch][k]  (Eq. 17 without 2 kB^2 1e9)
+// FP32 SIMT contraction of D = X - X_ref.  For a block of 128 rows x 64 channels:
+//   S1[r][ch] = sum_k D[r][k] H[ch][k]                      (Eq. 16, kelvin*GHz, less the reference's)
+//   N [r][ch] = sum_k D[r][k] G[ch][k] + D[r][k]^2 Q[ch][k]  (Eq. 17 without 2 kB^2 1e9, less the
+//               reference's; G carries the cross term 2 Q X_ref)
 // 256 threads, each 8 rows x 4 consecutive channels, K in steps of 16 with a
 // register-prefetched shared-memory tile.
 // ---------------------------------------------------------------------------
@@ -420,8 +421,8 @@ __global__ __launch_bounds__(256) void contract_fp32_kernel(DevTables T, const f
         for (int j = 0; j < 4; ++j) {
             const int ch = ch0 + j;
             if (ch < T.n_ch) {
-                const float pk = T.kb1e9 * s1[i][j];
-                const float sigma = T.kB * sqrtf(T.noise_scale * fmaxf(sn[i][j], 0.f));
+                const float pk = fmaf(T.kb1e9, s1[i][j], T.ref_pk[ch]);
+                const float sigma = T.kB * sqrtf(T.noise_scale * fmaxf(sn[i][j] + T.ref_n[ch], 0.f));
                 const float v = fmaf(sigma, f4_get(z, j), pk);
                 orow[ch] = T.tb_a ? fmaf(T.tb_a[ch], v, T.tb_b[ch]) : v;   // K (Sect. 2.7) or W
             }

@@ -68,7 +68,8 @@ extern "C" gateau_status gateau_pink_noise_noalloc(const float* pink_a, const fl
     if (per_chunk > static_cast<long long>(kNoallocScratchFloats))
         return noalloc_fail(GATEAU_EINVAL, "n_pix * n_ch * n_pole = " + std::to_string(per_chunk) +
                                                " exceeds the 1048576 floats of fixed scratch");
-    if (nt * n_pix > (1LL << 31)) return noalloc_fail(GATEAU_EINVAL, "nt * n_pix must stay below 2^31");
+    if (nt > (1LL << 31) / n_pix)               // nt * n_pix > 2^31, compared without forming the product
+        return noalloc_fail(GATEAU_EINVAL, "nt * n_pix must stay below 2^31");
     float* scratch = nullptr;
     cudaError_t e = scratch_address(&scratch);
     if (e != cudaSuccess)

@@ -264,6 +264,10 @@ class Plan:
             ptr = _dptr(keep)
         L.check(self._lib.gateau_plan_set_state(self._h, next_t0, ptr))
 
+    def set_wait_budget(self, cycles: int):
+        """Budget of each pipeline wait of the fused kernel in SM clock cycles (default 4e9)."""
+        L.check(self._lib.gateau_plan_set_wait_budget(self._h, int(cycles)))
+
     def set_timing(self, enable: bool = True):
         L.check(self._lib.gateau_plan_set_timing(self._h, 1 if enable else 0))
 

@@ -135,6 +135,9 @@ def test_argument_validation():
     assert lib.gateau_set_cascade(p._h, 1, bad) == L.EINVAL
     assert lib.gateau_set_dispersive_element(p._h, 7, 3, None, None, None, None) == L.EINVAL
     assert lib.gateau_set_scan(p._h, L.SCAN_DAISY, None, 0, 0.0, 0.0, None, 0, 0) == L.EINVAL
+    assert lib.gateau_plan_set_wait_budget(p._h, -1) == L.EINVAL
+    assert lib.gateau_plan_set_wait_budget(None, 100) == L.EINVAL
+    assert lib.gateau_plan_set_wait_budget(p._h, 0) == L.OK
     d = L.PlanDesc()
     out = L.PlanP()
     assert lib.gateau_plan_create(C.byref(d), C.byref(out)) == L.EINVAL and not out.value

@@ -98,7 +98,81 @@ def test_source_only_difference(precision):
     err_src = np.abs(d_got - d_ref).max() / scale
     err_tot = np.abs(d_got - d_ref).max() / np.abs(ref["p_kid"]).max()
     print(f"{precision}: source-only max error {err_src:.3e} of the source peak, {err_tot:.3e} of the total")
+    # The source peak is ~1e-5 of the total loading; both paths contract the spectrum's
+    # difference from the plan's reference spectrum, so the source term is resolved to a few
+    # percent of its own peak rather than to the rounding of the whole loading.
+    assert err_src < 2e-2
     assert err_tot < (2e-6 if precision == "fp32" else 5e-5)
+
+
+# ---------------------------------------------------------------- bounded waits
+
+def test_wait_timeout_is_reported_and_the_context_stays_usable():
+    """A wait budget of 0 cycles makes the fused kernel's first unmet pipeline wait run out
+    (independent CTAs: 64 channels, one group).  The kernel stops every role, drains its own
+    copies, frees its tensor memory and returns: the status word carries WAIT_TIMEOUT, the plan
+    reports ETIMEOUT, and a fresh plan then runs correctly on the same context."""
+    import ctypes as C
+    sc, ref = oracle("single_pixel_small", 0, 256, key="signal")
+    p = Plan(sc, precision="bf16x3", white=False, pink=False)
+    p.set_wait_budget(0)
+    p.run(0, 256)
+    flags = C.c_uint(0)
+    st = L.lib().gateau_plan_status(p._h, C.byref(flags))
+    assert st == L.ETIMEOUT
+    assert flags.value & L.STATUS_WAIT_TIMEOUT
+    p.close()
+    got, fl, _ = gpu_run(sc, "bf16x3", 0, 256)
+    assert fl & ~L.STATUS_PWV_CLAMPED == 0
+    assert rel_err(got, ref["p_kid"]) < SIGNAL_TOL["bf16x3"]
+    with pytest.raises(L.GateauError):
+        Plan(sc, precision="bf16x3").set_wait_budget(-1)
+
+
+# ---------------------------------------------------------------- serving shape range
+
+_SERVING_SHAPES = [
+    # (hexagon rings, channels, spectral points, first sample, samples)
+    (4, 347, 6000, 0, 130),       # 61 spaxels, two channel groups (cluster-shared tiles), longest grid
+    (1, 100, 6000, 1000, 200),    # 7 spaxels, one group of 112 columns, longest grid
+    (2, 100, 1000, 37, 150),      # 19 spaxels, shortest grid
+    (0, 347, 1000, 0, 300),       # one spaxel, two groups, shortest grid
+]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("R_hex,n_ch,n_freq,t0,nt", _SERVING_SHAPES)
+def test_serving_shapes_signal_parity(precision, R_hex, n_ch, n_freq, t0, nt):
+    """Requests of the serving range (hexagonal IFUs of 1-61 spaxels, 100-347 channels, 1000-6000
+    points, daisy scan) against the oracle, noiseless, over several tiles and a ragged tail."""
+    from paper_2604_23305_b300 import serve as S
+    key = ("serving", R_hex, n_ch, n_freq, t0, nt)
+    if key not in _oracle_cache:
+        req = dict(R_hex=R_hex, n_pix=1 + 3 * R_hex * (R_hex + 1), n_ch=n_ch, n_freq=n_freq, nt=t0 + nt)
+        sc = S.ServingInputs(seed=5).scenario(req, 3)
+        _oracle_cache[key] = (sc, O.simulate(sc, t0, nt, white=False, pink=False, return_parts=True))
+    sc, ref = _oracle_cache[key]
+    got, flags, _ = gpu_run(sc, precision, t0, nt)
+    err = rel_err(got, ref["p_kid"])
+    print(f"{precision} hex R={R_hex} n_ch={n_ch} n_freq={n_freq} t0={t0} nt={nt}: max rel err {err:.3e}")
+    assert err < SIGNAL_TOL[precision]
+    assert flags & ~L.STATUS_PWV_CLAMPED == 0
+
+
+def test_serving_shape_white_noise_parity():
+    """White noise of a 61-spaxel, 6000-point request, sample by sample (split-BF16 path)."""
+    from paper_2604_23305_b300 import serve as S
+    req = dict(R_hex=4, n_pix=61, n_ch=347, n_freq=6000, nt=140)
+    sc = S.ServingInputs(seed=5).scenario(req, 4)
+    ref = O.simulate(sc, 0, 140, white=True, pink=False, return_parts=True)
+    got, _, _ = gpu_run(sc, "bf16x3", 0, 140, white=True)
+    got0, _, _ = gpu_run(sc, "bf16x3", 0, 140, white=False)
+    sigma = ref["sigma"]
+    z = ref["p_wn"] / sigma
+    bound = SIGMA_TOL["bf16x3"] * sigma * (np.abs(z) + 0.1) + 1e-6 * np.abs(ref["p_kid"])
+    worst = np.max(np.abs((got - got0) - ref["p_wn"]) / bound)
+    print(f"serving shape white noise worst error / bound = {worst:.3f}")
+    assert worst <= 1.0
 
 
 # ---------------------------------------------------------------- noise

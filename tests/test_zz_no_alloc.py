@@ -62,3 +62,59 @@ def test_noalloc_pink_matches_gateau_run_on_two_calls():
     st = lib.gateau_pink_noise_noalloc(a.data_ptr(), r.data_ptr(), d.data_ptr(), 10000, n_ch, n_pole, seed,
                                        0, 4, state.data_ptr(), out.data_ptr(), stream)
     assert st == L.EINVAL and b"fixed scratch" in lib.gateau_last_error()
+
+
+def _default_chunks(nt, S):
+    """The allocating path's chunk count (148 x 1024 scans in flight, >= 64 samples a chunk)."""
+    c = min(-(-148 * 1024 // S), -(-nt // 64))
+    c = max(c, 1)
+    L_ = -(-(-(-nt // c)) // 4) * 4
+    return -(-nt // L_)
+
+
+def test_noalloc_pink_caps_its_chunks_and_allocates_nothing():
+    """A scan long enough that the allocating path's chunk states (n_pix n_ch n_pole per chunk)
+    would not fit the 4 MiB of fixed scratch: the entry point takes fewer, longer chunks and still
+    matches gateau_run's pink noise.  The calls after the first on this device (which looks up the
+    scratch address and may load the library's module) leave the device's free memory unchanged."""
+    assert torch.cuda.is_available()
+    lib = L.lib()
+    nt = 1200
+    sc = W.scenario("ifu25", nt_total=nt)
+    with_pink = Plan(sc, precision="fp32", white=False, pink=True)
+    ref = with_pink.run(0, nt)
+    base = Plan(sc, precision="fp32", white=False, pink=False)
+    out = base.run(0, nt)
+    torch.cuda.synchronize()
+    signal = out.clone()
+    info = with_pink.info()
+    n_pix, n_ch, n_pole = info.n_pix, info.n_ch, info.n_pole
+    S = n_pix * n_ch
+    assert S * n_pole * _default_chunks(nt, S) > (1 << 20)      # the cap is needed here
+    a = torch.tensor(with_pink.get_vector(L.VEC_PINK_A, n_ch * n_pole), dtype=torch.float32, device="cuda")
+    r = torch.tensor(with_pink.get_vector(L.VEC_PINK_R, n_ch * n_pole), dtype=torch.float32, device="cuda")
+    d = torch.tensor(with_pink.get_vector(L.VEC_PINK_D, n_ch), dtype=torch.float32, device="cuda")
+    state = torch.zeros((n_pix, n_ch, n_pole), dtype=torch.float32, device="cuda")
+    warm_state = torch.zeros_like(state)
+    warm_out = torch.zeros((4, n_pix, n_ch), dtype=torch.float32, device="cuda")
+    seed = int(sc["noise"]["seed"])
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = lib.gateau_pink_noise_noalloc(a.data_ptr(), r.data_ptr(), d.data_ptr(), n_pix, n_ch, n_pole, seed,
+                                       0, 4, warm_state.data_ptr(), warm_out.data_ptr(), stream)
+    assert st == L.OK, lib.gateau_last_error()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    st = lib.gateau_pink_noise_noalloc(a.data_ptr(), r.data_ptr(), d.data_ptr(), n_pix, n_ch, n_pole, seed,
+                                       0, nt, state.data_ptr(), out.data_ptr(), stream)
+    assert st == L.OK, lib.gateau_last_error()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+    got = out.double().cpu().numpy()
+    want = ref.double().cpu().numpy()
+    sig = signal.double().cpu().numpy()
+    pink = want - sig
+    rms = np.sqrt(np.mean(pink ** 2, axis=0, keepdims=True))
+    worst = np.max(np.abs(got - want) / (1e-4 * rms + 1e-6 * np.abs(sig)))
+    assert worst <= 1.0, worst
