@@ -206,20 +206,39 @@ def cpu_baseline(sc, budget_s=12.0):
 
 
 def serving_leg(n_requests: int, seed: int = 2, budget_bytes: float = 120e9, max_active: int = 16,
-                chunk_samples: int = 4096, max_chunk_bytes: int = 32 << 20, builders: int = 6):
+                chunk_samples: int = 4096, max_chunk_bytes: int = 32 << 20, builders: int = 6,
+                shared_launches: bool = False):
     """The serving workload: n_requests simulations (hexagonal IFUs of 1-61 spaxels, 100-347
     channels, 1000-6000 spectral points, 10 s - 10 min at 160 Hz) through the native server,
     admitted by a device-memory budget.  First all requests arrive at once (saturated: the
     server's capacity in requests/s), then Poisson arrivals at 0.75 x that capacity; latency =
-    arrival -> last chunk of TOD on the host."""
+    arrival -> last chunk of TOD on the host.  shared_launches: chunks in rounds whose
+    contractions share persistent fused launches, instead of one launch sequence per request."""
     from paper_2604_23305_b300 import Plan
     from paper_2604_23305_b300.serve import Server, ServingInputs, build_requests, serving_requests
 
     shapes = serving_requests(n_requests, seed)
     scs, reqs = build_requests(shapes, ServingInputs(seed), chunk_samples)
-    make = lambda i: Plan(scs[i], precision="bf16x3", device_inputs=False)
+    # tile autotuner: one plan per channel class (16-channel blocks) is tuned before the runs; every
+    # request's plan then takes its class's choice from the cache when it is created
+    t = time.perf_counter()
+    classes, choices = {}, {}
+    for i, r in enumerate(shapes):
+        classes.setdefault((r["n_ch"] + 15) // 16, i)
+    for c, i in sorted(classes.items()):
+        p = Plan(scs[i], precision="bf16x3", device_inputs=False)
+        ch = p.autotune(nt_sample=1024)
+        choices[c] = (ch["n_groups"], ch["ring_b"])
+        p.close()
+    tune_s = time.perf_counter() - t
+
+    def make(i):
+        p = Plan(scs[i], precision="bf16x3", device_inputs=False)
+        p.autotune(nt_sample=1024)                                  # from the cache
+        return p
     srv = Server(int(budget_bytes), max_active=max_active, chunk_samples=chunk_samples,
-                 max_chunk_bytes=max_chunk_bytes, n_streams=max_active, n_builders=builders)
+                 max_chunk_bytes=max_chunk_bytes, n_streams=max_active, n_builders=builders,
+                 shared_launches=shared_launches)
     srv.run(reqs[:4], make)                                       # warm-up (not reported)
     sat = srv.run(reqs, make)
     capacity = sat["n_done"] / sat["makespan_s"]
@@ -229,9 +248,12 @@ def serving_leg(n_requests: int, seed: int = 2, budget_bytes: float = 120e9, max
     st = srv.run([dict(r, arrival_s=float(a)) for r, a in zip(reqs, arrivals)], make)
     srv.close()
     keys = ("p50_latency_s", "p99_latency_s", "mean_latency_s", "max_latency_s", "makespan_s", "throughput",
-            "detector_samples", "peak_bytes", "peak_active", "overlap", "n_done", "n_failed")
+            "detector_samples", "peak_bytes", "peak_active", "overlap", "n_done", "n_failed", "rounds", "mean_round")
     out = {k: st[k] for k in keys}
-    out.update(requests=n_requests, budget_bytes=int(budget_bytes), max_active=max_active, plan_builders=builders,
+    out.update(scheduler="shared persistent launches in rounds" if shared_launches else "a stream per request",
+               autotune={"classes": len(classes), "seconds": tune_s,
+                         "choices": {str(16 * c): list(v) for c, v in sorted(choices.items())}},
+               requests=n_requests, budget_bytes=int(budget_bytes), max_active=max_active, plan_builders=builders,
                chunk_samples=chunk_samples, capacity_req_per_s=capacity, arrival_rate_req_per_s=rate,
                saturated={k: sat[k] for k in ("makespan_s", "throughput", "p50_latency_s", "p99_latency_s",
                                               "overlap")},
@@ -314,6 +336,7 @@ def main():
     ap.add_argument("--skip-kelvin", action="store_true")
     ap.add_argument("--skip-tk", action="store_true")
     ap.add_argument("--skip-prep", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default fused tiles")
     ap.add_argument("--record-traffic", default=None, metavar="RAW_CSV")
     ap.add_argument("--traffic-samples", type=int, default=16384)
     ap.add_argument("--traffic-command", default="")
@@ -345,6 +368,7 @@ def main():
     nt = sc["nt_total"]
     per_step = W.detector_samples(sc)
     plan = Plan(sc, precision=args.precision, white=True, pink=True)
+    tune = plan.autotune(nt_sample=4096) if args.precision == "bf16x3" and not args.no_autotune else None
     out = torch.empty((nt, plan.n_pix, plan.n_ch), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
@@ -375,8 +399,8 @@ def main():
     contract_ms = phase_ms[2] / max(runs, 1)
     alg_flops = 6.0 * n_freq * per_step                      # 3 contractions x 2 N_f per detector sample
     info = plan.info()
-    n_groups = (n_ch + 175) // 176
-    n_half = ((n_ch + n_groups - 1) // n_groups + 15) // 16 * 16
+    n_groups = info.tile_groups if args.precision == "bf16x3" else (n_ch + 175) // 176
+    n_half = info.tile_half if args.precision == "bf16x3" else ((n_ch + n_groups - 1) // n_groups + 15) // 16 * 16
     tiles = math.ceil(nt / 128) * plan.n_pix
     exec_flops = 5 * 2.0 * 128 * n_half * n_groups * info.n_freq_padded * tiles
     achieved = alg_flops / (contract_ms / 1e3) / 1e12
@@ -401,6 +425,11 @@ def main():
                          "l2": "working set > L2: 197 MB source cube read and 6.66 GB output written per step",
                          "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
               "roofline": roofline, "gpu_launches": launches, "clocks": clk.summary(), "status_flags": flags,
+              "autotune": None if tune is None else {
+                  "choice": {"channel_groups": info.tile_groups, "channels_per_group": info.tile_half,
+                             "ring_a": info.ring_a, "ring_b": info.ring_b},
+                  "sample": "first 4096 samples of the scan", "ms": tune["ms"], "default_ms": tune["default_ms"],
+                  "candidates": tune["candidates"]},
               "staged_inputs": info.staged_inputs}
 
     # plain FP32 path on the same workload and GPU (the baseline the fused path is measured against)
@@ -570,6 +599,8 @@ def main():
     if not args.skip_serving:
         torch.cuda.empty_cache()
         result["serving"] = serving_leg(args.serving_requests, seed=2 + 100 * rank)
+        result["serving_shared_launches"] = serving_leg(args.serving_requests, seed=2 + 100 * rank,
+                                                        shared_launches=True)
     if rank == 0 and world == 1 and not args.skip_cpu:
         result["cpu_baseline"] = cpu_baseline(sc)
     if rank == 0:

@@ -141,6 +141,12 @@ typedef struct {
     size_t device_bytes;           /* device memory owned by the plan                           */
     int staged_inputs;             /* 1 when the fused kernel stages its gathers by tensor copies
                                       (set by the first BF16X3 run; 0 before it or on fallback)   */
+    int tile_groups, tile_half;    /* BF16X3 fused tiles (after prepare): channel groups and the
+                                      channels of a group (2 groups: 2-CTA clusters share tiles)  */
+    int ring_a, ring_b;            /* pipeline depths the fused kernel takes: spectrum-row stages
+                                      and filter-operand stages in shared memory                   */
+    double tune_ms;                /* gateau_plan_autotune: the chosen tiles' time on the tuning
+                                      sample (ms; 0 when not measured by this plan)               */
 } gateau_plan_info;
 
 /* Host-built FP64 tables, for inspection and tests (gateau_plan_get_vector). */
@@ -214,7 +220,11 @@ gateau_status gateau_set_dispersive_element(gateau_plan* plan, int kind, int n_c
 
 /* Pink detector noise (Sect. 2.6, Eq. 20) per channel: one-sided PSD level
  * A[ch] (W^2/Hz at 1 Hz, 0 disables the channel) and slope alpha[ch] in
- * [0, 3] (host arrays [n_ch]).  Realised by a pole-zero filter: poles at
+ * [0, 3] (host arrays [n_ch]).  A = NULL puts every channel's knee at 1 Hz:
+ * A[ch] is then the white noise level NEP^2 (Eq. 17, the one-sided white PSD)
+ * of the source-free sky at the screen's mean PWV and the scan's base
+ * elevation, evaluated in FP64 when the plan is prepared (and again when the
+ * screen, table, scan, cascade or dispersive element change).  Realised by a pole-zero filter: poles at
  * f_min 10^(j/3) up to f_sample/2, zeros 10^(alpha/6) above each pole,
  * matched-z, parallel (partial-fraction) form, zero state at sample 0.
  * Requires gateau_set_dispersive_element first (ESTATE otherwise). */
@@ -291,6 +301,41 @@ gateau_status gateau_plan_get_vector(gateau_plan* plan, int which, double* out, 
  * get).  Synchronises the plan's last stream. */
 gateau_status gateau_plan_get_state(gateau_plan* plan, long long* next_t0, double* pink_state);
 gateau_status gateau_plan_set_state(gateau_plan* plan, long long next_t0, const double* pink_state);
+
+/* Tile shapes of the fused split-BF16 kernel.  A tile is 128 consecutive samples of
+ * one spaxel (one TMEM lane per sample) x a group of channels, built and contracted
+ * in stages of 16 spectral points (one K = 16 MMA step), so the rows and the spectral
+ * stage are fixed by the tensor-core shapes; what a plan chooses is the channel
+ * split and the pipeline depth.  n_groups: channel groups of at most 176 channels
+ * (>= ceil(n_ch / 176), and n_ch / n_groups >= 1; 0 restores the default, the fewest
+ * groups); exactly 2 groups run as 2-CTA clusters that build every spectrum row once
+ * and share it, any other count as independent CTAs.  ring_b: the deepest ring of
+ * filter-operand stages to take, 2..6 (0: the default 4), as far as shared memory
+ * leaves room for at least as many spectrum-row stages.  Takes effect at the next
+ * prepare or run; results are the same for every choice (within the split-BF16
+ * tolerance; bit-identical output is not promised across choices).  EINVAL
+ * outside those ranges. */
+gateau_status gateau_plan_set_tiles(gateau_plan* plan, int n_groups, int ring_b);
+
+/* Tile autotuner (project-written): for a BF16X3 plan with all setters done, time
+ * every candidate (channel groups: the fewest, one more, and 2 when that is not
+ * already a candidate; B-ring depths 2..6 that fit) on the first nt_sample samples
+ * of the scan (CUDA events on `stream`, one warm-up and two timed launches of the
+ * fused kernel each, into device scratch owned by the plan and freed afterwards),
+ * keep the fastest, and cache it for the process under the plan's shape class (its
+ * channel count in 16-channel blocks, which fixes every candidate's group width and
+ * ring depths).  A later plan of a cached class
+ * takes the cached choice without measuring.  The run state of the plan (next
+ * sample, pink-filter states) is not touched.  *out (may be NULL) receives the
+ * chosen n_groups, ring_b, its time and how many candidates were timed (0: from the
+ * cache).  Synchronous.  EINVAL for a FP32 plan or nt_sample < 1. */
+typedef struct {
+    int n_groups, n_half, ring_b, ring_a;
+    double ms;                     /* the chosen tiles' time per launch on the sample (ms)      */
+    double default_ms;             /* the default tiles' time on the same sample (ms; 0 if cached) */
+    int candidates;                /* configurations timed (0: taken from the cache)            */
+} gateau_tile_choice;
+gateau_status gateau_plan_autotune(gateau_plan* plan, long long nt_sample, void* stream, gateau_tile_choice* out);
 
 /* Budget of each pipeline wait of the fused split-BF16 kernel, in SM clock cycles
  * (clock64; default 4e9, about 2 s at 2 GHz).  A wait that runs out sets
@@ -380,10 +425,18 @@ gateau_status gateau_mean_zenith_pwv(gateau_plan* plan, long long n_total, doubl
 gateau_status gateau_common_mode(gateau_plan* plan, long long t0, long long nt, const float* tb, float* out,
                                  double pwv_mean_mm, double r_out_rad, void* stream);
 
-/* Several plans' chunks on one stream.  plans[k] runs samples t0s[k] ..
- * t0s[k]+nts[k]-1 into outs[k] (device) exactly as gateau_run would, with the
- * same chunk-order rules and bit-identical results, enqueued in k order.
- * 0 < n <= 256; the whole batch is validated before anything is enqueued. */
+/* Several plans' chunks on one stream, the way a server batches the time chunks
+ * of its admitted requests.  plans[k] runs samples t0s[k] .. t0s[k]+nts[k]-1
+ * into outs[k] (device) exactly as gateau_run would, with the same chunk-order
+ * rules and bit-identical results.  The split-BF16 contractions of all the
+ * batch's plans share persistent launches of the fused kernel -- one launch for
+ * the plans with two channel groups (177-352 channels: 2-CTA clusters) and one
+ * for the others, each over every work item (time tile x spaxel x channel
+ * group) of up to 32 plans -- so uneven requests fill the GPU together; the
+ * row setup and the noise phases stay per plan.  FP32 plans run one by one.
+ * The phase timing of gateau_plan_get_timing reports a shared launch under
+ * each of its plans; the launch count counts it once.  0 < n <= 256; the whole
+ * batch is validated before anything is enqueued. */
 gateau_status gateau_run_batch(gateau_plan* const* plans, const long long* t0s, const long long* nts,
                                float* const* outs, int n, void* stream);
 
@@ -420,7 +473,8 @@ typedef struct gateau_server gateau_server;
 
 typedef struct {
     size_t budget_bytes;        /* device memory for admitted requests: their plans (as
-                                   requested) plus two chunk buffers each */
+                                   requested) plus two chunk buffers each (three with shared
+                                   launches) */
     int max_active;             /* requests admitted at once (slots), 1..256 */
     long long chunk_samples;    /* time samples per chunk, >= 1 ... */
     size_t max_chunk_bytes;     /* ... reduced so that one chunk's TOD stays within this many
@@ -435,6 +489,16 @@ typedef struct {
                                    (gateau_plan_prepare) admitted requests' plans while the
                                    running requests' chunks are launched; 0 builds on the thread
                                    running the server (always so in a dry run) */
+    int shared_launches;        /* 0: every request's chunks run on its own stream (their kernels
+                                   overlap through the streams).  1: rounds -- the next chunk of
+                                   every admitted request with a free chunk buffer -- each run as
+                                   one gateau_run_batch on the server's compute stream, so the
+                                   requests' split-BF16 contractions share persistent fused
+                                   launches; each request's checksum and copy to the host follow
+                                   its round on its own stream, which runs at a higher priority
+                                   than the compute stream.  A round is formed when none is in
+                                   flight, or when one is and every active request can join; each
+                                   request has three chunk buffers.  Results are identical. */
 } gateau_server_desc;
 
 typedef struct {
@@ -466,6 +530,8 @@ typedef struct {
     int peak_active;                       /* most requests admitted at once */
     double overlap;                        /* mean number of requests with chunks in flight,
                                               sampled at every chunk launch */
+    long long rounds;                      /* shared launches: rounds run (gateau_run_batch calls) */
+    double mean_round;                     /* shared launches: mean requests per round */
 } gateau_server_stats;
 
 /* Create / destroy a server.  Create allocates the pinned host staging

@@ -701,6 +701,21 @@ class Instrument:
     prim: list
     eta_surf: np.ndarray
     pink: list
+    pink_A: np.ndarray      # pink level per channel (W^2/Hz at 1 Hz)
+
+
+def reference_nep2(sc: dict, nu, w, eta_filt, prim, eta_surf) -> np.ndarray:
+    """NEP^2 per channel (W^2/Hz, Eq. 17) of the source-free sky at the screen's mean PWV and the
+    scan's base elevation theta_0: the white noise level of the observation as planned.  It is
+    the one-sided white PSD (Eq. 18: sigma^2 = NEP^2 f_s / 2), so a pink level A = NEP^2 puts the
+    knee, where the pink PSD equals the white one, at 1 Hz."""
+    atm = sc["atmosphere"]
+    pwv = np.array([screen_pwv_field(sc).mean()])
+    tau = zenith_opacity(opacity_table(sc), atm["pwv_min"], atm["dpwv"], pwv)
+    eta = atmospheric_transmission(tau, np.array([sc["scan"]["theta0"]]))
+    P = cascade(np.zeros_like(eta), eta, nu, prim, atm["T_atm"], sc["T_cmb"], sc["eta_taper"], eta_surf,
+                sc["eta_pol"])
+    return nep_squared(eta_filt, w, P, nu, sc["delta_al"], sc["eta_pb"])[0]
 
 
 def build_instrument(sc: dict) -> Instrument:
@@ -713,12 +728,17 @@ def build_instrument(sc: dict) -> Instrument:
     eta_surf = ruze_efficiency(sc["rho_surf"], nu)
     pink = []
     noise = sc.get("noise", {})
-    A = np.asarray(noise.get("pink_A", np.zeros(eta_filt.shape[0])), dtype=F64)
-    alpha = np.asarray(noise.get("pink_alpha", np.ones(eta_filt.shape[0])), dtype=F64)
-    for ch in range(eta_filt.shape[0]):
+    n_ch = eta_filt.shape[0]
+    if "pink_alpha" in noise and noise.get("pink_A") is None:
+        # no level given: the knee at 1 Hz (Sect. 2.6 reading), A = the planned white level NEP^2
+        A = reference_nep2(sc, nu, w, eta_filt, prim, eta_surf)
+    else:
+        A = np.asarray(noise.get("pink_A", np.zeros(n_ch)), dtype=F64)
+    alpha = np.asarray(noise.get("pink_alpha", np.ones(n_ch)), dtype=F64)
+    for ch in range(n_ch):
         pink.append(pink_design(float(alpha[ch]), float(A[ch]), noise.get("pink_f_min", 1e-3),
                                 sc["f_sample"]))
-    return Instrument(nu=nu, w=w, eta_filt=eta_filt, prim=prim, eta_surf=eta_surf, pink=pink)
+    return Instrument(nu=nu, w=w, eta_filt=eta_filt, prim=prim, eta_surf=eta_surf, pink=pink, pink_A=A)
 
 
 def screen_pwv_field(sc: dict) -> np.ndarray:
@@ -863,7 +883,7 @@ def simulate(sc: dict, t0: int, nt: int, inst: Instrument | None = None,
     if pink and pink_tk is not None:
         assert t0 + nt <= pink_tk
         noise = sc.get("noise", {})
-        A = np.asarray(noise.get("pink_A", np.zeros(n_ch)), dtype=F64)
+        A = inst.pink_A
         alpha = np.asarray(noise.get("pink_alpha", np.ones(n_ch)), dtype=F64)
         for i in range(n_pix):
             for ch in range(n_ch):

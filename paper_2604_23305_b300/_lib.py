@@ -46,13 +46,19 @@ class Stage(C.Structure):
 class PlanInfo(C.Structure):
     _fields_ = [("n_freq", C.c_int), ("n_freq_padded", C.c_int), ("n_ch", C.c_int), ("n_pix", C.c_int),
                 ("n_pole", C.c_int), ("next_t0", C.c_longlong), ("device_bytes", C.c_size_t),
-                ("staged_inputs", C.c_int)]
+                ("staged_inputs", C.c_int), ("tile_groups", C.c_int), ("tile_half", C.c_int),
+                ("ring_a", C.c_int), ("ring_b", C.c_int), ("tune_ms", C.c_double)]
+
+
+class TileChoice(C.Structure):
+    _fields_ = [("n_groups", C.c_int), ("n_half", C.c_int), ("ring_b", C.c_int), ("ring_a", C.c_int),
+                ("ms", C.c_double), ("default_ms", C.c_double), ("candidates", C.c_int)]
 
 
 class ServerDesc(C.Structure):
     _fields_ = [("budget_bytes", C.c_size_t), ("max_active", C.c_int), ("chunk_samples", C.c_longlong),
                 ("max_chunk_bytes", C.c_size_t), ("n_streams", C.c_int), ("dry_run", C.c_int),
-                ("dry_seconds_per_sample", C.c_double), ("n_builders", C.c_int)]
+                ("dry_seconds_per_sample", C.c_double), ("n_builders", C.c_int), ("shared_launches", C.c_int)]
 
 
 class Request(C.Structure):
@@ -65,7 +71,7 @@ class ServerStats(C.Structure):
                 ("p50_latency_s", C.c_double), ("p99_latency_s", C.c_double), ("mean_latency_s", C.c_double),
                 ("max_latency_s", C.c_double), ("makespan_s", C.c_double), ("detector_samples", C.c_double),
                 ("throughput", C.c_double), ("peak_bytes", C.c_size_t), ("peak_active", C.c_int),
-                ("overlap", C.c_double)]
+                ("overlap", C.c_double), ("rounds", C.c_longlong), ("mean_round", C.c_double)]
 
 
 PlanP = C.c_void_p
@@ -115,6 +121,8 @@ SIGNATURES = {
     "gateau_hex_offsets": (C.c_int, [C.c_int, C.c_double, dp, C.c_int, C.POINTER(C.c_int)]),
     "gateau_plan_set_timing": (C.c_int, [PlanP, C.c_int]),
     "gateau_plan_set_wait_budget": (C.c_int, [PlanP, C.c_longlong]),
+    "gateau_plan_set_tiles": (C.c_int, [PlanP, C.c_int, C.c_int]),
+    "gateau_plan_autotune": (C.c_int, [PlanP, C.c_longlong, C.c_void_p, C.c_void_p]),
     "gateau_plan_get_timing": (C.c_int, [PlanP, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "gateau_plan_estimate_bytes": (C.c_int, [C.POINTER(PlanDesc), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                              C.c_int, C.c_longlong, C.c_longlong, C.POINTER(C.c_size_t)]),

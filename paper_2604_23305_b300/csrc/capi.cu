@@ -6,9 +6,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <memory>
-#include <string>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "gateau_internal.h"
@@ -106,6 +107,15 @@ struct DevBuf {
 
 }  // namespace
 
+namespace {
+// Tile autotuner cache: shape class -> (channel groups, B-ring depth), shared by every plan of the
+// process.  The class is the channel count in 16-channel blocks, which fixes every candidate's
+// group width and ring depths; spaxels and spectral points change how many items and stages a
+// launch has, not which tiles fit.
+std::mutex g_tune_mu;
+std::map<int, std::pair<int, int>> g_tune_cache;
+}  // namespace
+
 namespace gateau {
 // Lets other translation units report through gateau_last_error().
 void set_last_error(const std::string& msg) { g_last_error = msg; }
@@ -132,6 +142,7 @@ struct gateau_plan {
     int disp_kind = 0, n_ch = 0;
     std::vector<double> eta_filt;      // [n_ch][n_freq]
     std::vector<double> pink_A, pink_alpha;
+    bool pink_auto = false;          // pink level from the reference spectrum's NEP^2 (knee at 1 Hz)
     int scan_kind = GATEAU_SCAN_STARE;
     double sp[kMaxScanParams] = {0};
     double phi0 = 0, theta0 = 0;
@@ -150,6 +161,9 @@ struct gateau_plan {
     std::vector<double> pink_a, pink_r, pink_d;
     bool dirty = true;
     bool ref_dirty = true;           // the reference spectrum (screen mean, table, theta0, cascade) changed
+    int tile_groups = 0;             // fused tiles: channel groups (0: the default rule), set or tuned
+    int tile_ring_b = 0;             // fused tiles: deepest B ring (0: the default)
+    double tune_ms = 0.0;            // the tuned configuration's time on the tuning sample (0: not measured)
 
     // device memory
     DevBuf d_pix, d_cube, d_cube_raw, d_screen, d_tau, d_custom, d_c, d_HGQ, d_fusedB, d_pink, d_state, d_status;
@@ -157,6 +171,7 @@ struct gateau_plan {
     DevBuf d_tk, d_tkz;              // Timmer-Koenig pink TOD [tk_n][n_pix][n_ch]; its FFT scratch
     DevBuf d_hw, d_cm;               // common-mode reduction: eta_filt w (FP64); log eta_z, S_j, PWV sum
     DevBuf d_ref;                    // per channel: k_B 1e9 S_ref and N_ref of the reference spectrum
+    DevBuf d_tune;                   // tile autotuner: output of the timed sample runs
     bool cube_scale_dirty = true;    // d_cube = d_cube_raw * c2 / k_B must be recomputed
     DevBuf d_rows, d_tiles, d_X, d_agg, d_stage[2];
     FusedOperands fused{};
@@ -190,7 +205,7 @@ struct gateau_plan {
         track_streams();
         DevBuf* bufs[] = {&d_pix, &d_cube, &d_cube_raw, &d_screen, &d_tau, &d_custom, &d_c, &d_HGQ, &d_fusedB, &d_pink,
                           &d_state, &d_status, &d_rows, &d_tiles, &d_X, &d_agg, &d_stage[0], &d_stage[1],
-                          &d_tb, &d_dip, &d_tk, &d_tkz, &d_hw, &d_cm, &d_ref};
+                          &d_tb, &d_dip, &d_tk, &d_tkz, &d_hw, &d_cm, &d_ref, &d_tune};
         for (DevBuf* b : bufs) b->release(mo);
         if (mo.mem) cudaStreamDestroy(mo.mem);       // its pending frees still complete
         for (int i = 0; i < 2; ++i) {
@@ -220,7 +235,7 @@ size_t device_bytes(const gateau_plan* p) {
     const DevBuf* bufs[] = {&p->d_pix, &p->d_cube, &p->d_cube_raw, &p->d_screen, &p->d_tau, &p->d_custom, &p->d_c,
                             &p->d_HGQ, &p->d_fusedB, &p->d_pink, &p->d_state, &p->d_status, &p->d_rows,
                             &p->d_tiles, &p->d_X, &p->d_agg, &p->d_stage[0], &p->d_stage[1], &p->d_tb, &p->d_dip,
-                            &p->d_tk, &p->d_tkz, &p->d_hw, &p->d_cm, &p->d_ref};
+                            &p->d_tk, &p->d_tkz, &p->d_hw, &p->d_cm, &p->d_ref, &p->d_tune};
     size_t s = 0;
     for (const DevBuf* b : bufs) s += b->bytes;
     return s;
@@ -266,6 +281,27 @@ void filter_operands(const gateau_plan* p, std::vector<double>& H, std::vector<d
         }
 }
 
+// Transmission of the reference sky per point: exp(-csc(theta_0) tau_z) at the screen's mean PWV,
+// tau_z interpolated linearly between the table's PWV rows (clamped to the table), Eq. 10 at the
+// scan's base elevation.  1 before the table is set.
+std::vector<double> reference_transmission(const gateau_plan* p) {
+    const int nf = p->desc.n_freq;
+    std::vector<double> eref(nf, 1.0);
+    if (p->tau_host.empty() || p->n_pwv < 2) return eref;
+    double u = (p->screen_mean - p->pwv_min) / p->dpwv;
+    u = std::min(std::max(u, 0.0), static_cast<double>(p->n_pwv - 1));
+    const int j = std::min(static_cast<int>(floor(u)), p->n_pwv - 2);
+    const double f = u - j;
+    const double sn = sin(p->theta0);
+    const double csc = sn > 1e-3 ? 1.0 / sn : 1.0;      // elevations below 0.06 deg: a zenith reference
+    for (int k = 0; k < nf; ++k) {
+        const double tau = (1.0 - f) * p->tau_host[static_cast<size_t>(j) * nf + k] +
+                           f * p->tau_host[static_cast<size_t>(j + 1) * nf + k];
+        eref[k] = exp(-csc * tau);
+    }
+    return eref;
+}
+
 // Reference spectrum: the source-free collapse (Sect. 2.5) at the screen's mean PWV and the
 // base elevation theta_0 (Eq. 10), X_ref = c0 + c1 (1 - e_ref).  Both contraction paths run on
 // D = X - X_ref instead of X.  D stays small wherever the line of sight sees about the mean sky,
@@ -280,20 +316,7 @@ void filter_operands(const gateau_plan* p, std::vector<double>& H, std::vector<d
 gateau_status build_reference(gateau_plan* p) {
     const gateau_plan_desc& d = p->desc;
     const int nf = d.n_freq, Kp = p->Kp, n_ch = p->n_ch;
-    std::vector<double> eref(nf, 1.0);
-    if (!p->tau_host.empty() && p->n_pwv >= 2) {
-        double u = (p->screen_mean - p->pwv_min) / p->dpwv;
-        u = std::min(std::max(u, 0.0), static_cast<double>(p->n_pwv - 1));
-        const int j = std::min(static_cast<int>(floor(u)), p->n_pwv - 2);
-        const double f = u - j;
-        const double sn = sin(p->theta0);
-        const double csc = sn > 1e-3 ? 1.0 / sn : 1.0;      // any reference is exact; this one is near the sky
-        for (int k = 0; k < nf; ++k) {
-            const double tau = (1.0 - f) * p->tau_host[static_cast<size_t>(j) * nf + k] +
-                               f * p->tau_host[static_cast<size_t>(j + 1) * nf + k];
-            eref[k] = exp(-csc * tau);
-        }
-    }
+    const std::vector<double> eref = reference_transmission(p);
     std::vector<float> c1f(Kp, 0.f), cref(Kp, 0.f);
     std::vector<double> xref(Kp, 0.0);
     for (int k = 0; k < nf; ++k) {
@@ -340,6 +363,13 @@ gateau_status build_reference(gateau_plan* p) {
         GATEAU_CUDA(grow(p, p->d_HGQ, hgq.size() * sizeof(float)));
         GATEAU_CUDA(cudaMemcpy(p->d_HGQ.p, hgq.data(), hgq.size() * sizeof(float), cudaMemcpyHostToDevice));
     } else {
+        // channel groups of at most 176 (the accumulators of a group fill 352 of the 512 TMEM
+        // columns): the default is the fewest groups; a set or tuned count may use more
+        const int n_groups = p->tile_groups > 0 ? p->tile_groups : (n_ch + 175) / 176;
+        p->fused.n_groups = n_groups;
+        p->fused.n_half = ((n_ch + n_groups - 1) / n_groups + 15) / 16 * 16;
+        p->fused.n_kstage = Kp / fused_kstage();
+        p->fused.ring_b = p->tile_ring_b > 0 ? p->tile_ring_b : kDefaultRingB;
         std::vector<uint16_t> tiled;
         size_t stage_elems = 0;
         fused_tile_operands(H.data(), G.data(), Q.data(), n_ch, Kp, p->fused.n_half, p->fused.n_groups, tiled,
@@ -377,12 +407,6 @@ gateau_status finalize_tables(gateau_plan* p) {
 
     const int n_ch = p->n_ch;
     p->n_ch_pad = (n_ch + 63) / 64 * 64;
-    if (d.precision != GATEAU_PREC_FP32) {
-        const int n_groups = (n_ch + 175) / 176;   // groups of <= 176 channels: B stages fit the rings
-        p->fused.n_half = ((n_ch + n_groups - 1) / n_groups + 15) / 16 * 16;
-        p->fused.n_groups = n_groups;
-        p->fused.n_kstage = Kp / fused_kstage();
-    }
 
     // brightness-temperature scale (Sect. 2.7): the skydip runs on the device (FP64), its fit
     // comes back for gateau_plan_get_vector and for the pink coefficients below
@@ -414,6 +438,25 @@ gateau_status finalize_tables(gateau_plan* p) {
     } else {
         p->tb_a.clear();
         p->tb_b.clear();
+    }
+
+    // pink level with no A given: the knee at 1 Hz, A = NEP^2 (Eq. 17) of the source-free sky at the
+    // screen's mean PWV and the base elevation, the one-sided white PSD of Eq. 18
+    if (p->pink_auto) {
+        const std::vector<double> eref = reference_transmission(p);
+        const double gr = 2.0 * d.delta_al_J / d.eta_pb;
+        p->pink_A.assign(n_ch, 0.0);
+        for (int c = 0; c < n_ch; ++c) {
+            double shot = 0.0, bunching = 0.0, absorbed = 0.0;
+            for (int k = 0; k < nf; ++k) {
+                const double P = p->c0[k] + p->c1[k] * (1.0 - eref[k]);
+                const double ew = p->eta_filt[static_cast<size_t>(c) * nf + k] * p->w[k];
+                shot += ew * P * kH * p->nu[k];
+                bunching += ew * p->eta_filt[static_cast<size_t>(c) * nf + k] * P * P;
+                absorbed += ew * P;
+            }
+            p->pink_A[c] = 2.0 * (shot + bunching + gr * absorbed);
+        }
     }
 
     // pink filters (Sect. 2.6, Eq. 20)
@@ -599,8 +642,9 @@ struct PhaseTimer {
     }
 };
 
-// Enqueue one validated run.
-gateau_status enqueue_run(gateau_plan* p, long long t0, long long nt, float* out, cudaStream_t stream) {
+// A validated run in three phases, so that a batch can put several plans' contractions into
+// shared launches.  Phase 1: derived tables, chunk bookkeeping and the row setup.
+gateau_status run_rows(gateau_plan* p, long long t0, long long nt, cudaStream_t stream, bool reset_state = true) {
     gateau_status st = finalize(p);
     if (st != GATEAU_OK) return st;
     const gateau_plan_desc& d = p->desc;
@@ -613,7 +657,7 @@ gateau_status enqueue_run(gateau_plan* p, long long t0, long long nt, float* out
         p->timed.push_back(t);
     }
     PhaseTimer tm{p, stream};
-    if (t0 == 0) {
+    if (t0 == 0 && reset_state) {
         GATEAU_CUDA(cudaMemsetAsync(p->d_state.p, 0, static_cast<size_t>(d.n_pix) * p->n_ch * p->n_pole * sizeof(float),
                                     stream));
     }
@@ -641,8 +685,33 @@ gateau_status enqueue_run(gateau_plan* p, long long t0, long long nt, float* out
     GATEAU_CUDA(launch_row_setup(T, t0, nt, R, tiles, stream));
     GATEAU_CUDA(tm.end(GATEAU_PHASE_ROWS));
     p->launches += 1;
+    return GATEAU_OK;
+}
+
+// The split-BF16 contraction of a run, as one job of a fused launch.
+FusedRunDesc fused_run(const gateau_plan* p, long long t0, long long nt, float* out) {
+    FusedRunDesc r;
+    r.T = make_tables(p);
+    r.F = p->fused;
+    r.tm_tau = p->tm_tau;
+    r.tm_cube = p->tm_cube;
+    r.rows = p->d_rows.as<RowParams>();
+    r.tiles = p->d_tiles.as<TileInfo>();
+    r.t0 = t0;
+    r.nt = nt;
+    r.out = out;
+    return r;
+}
+
+// Phase 2 for one plan alone: the contraction (FP32 baseline, or one fused launch).
+gateau_status run_contract(gateau_plan* p, long long t0, long long nt, float* out, cudaStream_t stream) {
+    const gateau_plan_desc& d = p->desc;
+    PhaseTimer tm{p, stream};
     if (d.precision == GATEAU_PREC_FP32) {
         // Unfused baseline: spectra in HBM chunk by chunk, then the SIMT contraction.
+        const DevTables T = make_tables(p);
+        const RowParams* R = p->d_rows.as<RowParams>();
+        const long long rows = nt * d.n_pix;
         const long long chunk = std::min<long long>(rows, 131072);
         GATEAU_CUDA(grow(p, p->d_X, static_cast<size_t>(chunk) * p->Kp * sizeof(float)));
         // Timing covers the whole chunk loop: SPECTRUM and CONTRACT alternate, so the
@@ -656,11 +725,19 @@ gateau_status enqueue_run(gateau_plan* p, long long t0, long long nt, float* out
         }
         GATEAU_CUDA(tm.end(GATEAU_PHASE_CONTRACT));
     } else {
+        const FusedRunDesc r = fused_run(p, t0, nt, out);
         GATEAU_CUDA(tm.begin(GATEAU_PHASE_CONTRACT));
-        GATEAU_CUDA(launch_fused_bf16x3(T, p->fused, p->tm_tau, p->tm_cube, R, tiles, t0, nt, out, p->n_sm, stream));
+        GATEAU_CUDA(launch_fused_runs(&r, 1, p->n_sm, stream));
         GATEAU_CUDA(tm.end(GATEAU_PHASE_CONTRACT));
         p->launches += 1;
     }
+    return GATEAU_OK;
+}
+
+// Phase 3: pink noise (Sect. 2.6) and the chunk bookkeeping.
+gateau_status run_noise(gateau_plan* p, long long t0, long long nt, float* out, cudaStream_t stream) {
+    const gateau_plan_desc& d = p->desc;
+    PhaseTimer tm{p, stream};
     if ((d.noise_flags & GATEAU_NOISE_PINK) && p->tk_n > 0) {
         // exact pink noise: the plan's realisation of samples [t0, t0 + nt), added elementwise
         const long long S = static_cast<long long>(d.n_pix) * p->n_ch;
@@ -669,6 +746,7 @@ gateau_status enqueue_run(gateau_plan* p, long long t0, long long nt, float* out
         GATEAU_CUDA(tm.end(GATEAU_PHASE_PINK));
         p->launches += 1;
     } else if (d.noise_flags & GATEAU_NOISE_PINK) {
+        const DevTables T = make_tables(p);
         PinkWork W;
         pink_choose_chunks(nt, static_cast<long long>(d.n_pix) * p->n_ch, W.C, W.L);
         GATEAU_CUDA(grow(p, p->d_agg, static_cast<size_t>(W.C) * d.n_pix * p->n_ch * p->n_pole * sizeof(float)));
@@ -683,6 +761,14 @@ gateau_status enqueue_run(gateau_plan* p, long long t0, long long nt, float* out
     p->last_stream = stream;
     p->ran = true;
     return GATEAU_OK;
+}
+
+// Enqueue one validated run.
+gateau_status enqueue_run(gateau_plan* p, long long t0, long long nt, float* out, cudaStream_t stream) {
+    gateau_status st = run_rows(p, t0, nt, stream);
+    if (st == GATEAU_OK) st = run_contract(p, t0, nt, out, stream);
+    if (st == GATEAU_OK) st = run_noise(p, t0, nt, out, stream);
+    return st;
 }
 
 }  // namespace
@@ -728,6 +814,7 @@ gateau_status gateau_plan_create(const gateau_plan_desc* desc, gateau_plan** out
     p->w = make_trapezoid(p->nu);
     p->Kp = (d.n_freq + 31) / 32 * 32;
     p->fused.wait_cycles = kDefaultWaitCycles;
+    p->fused.ring_b = kDefaultRingB;
     *out = p.release();
     return GATEAU_OK;
 }
@@ -813,7 +900,10 @@ gateau_status gateau_set_atmosphere_screen(gateau_plan* p, const float* screen, 
     double sum = 0.0;                  // the reference spectrum's PWV
     for (float v : h) sum += v;
     const double mean = sum / static_cast<double>(n);
-    if (!p->has_screen || mean != p->screen_mean) p->ref_dirty = true;
+    if (!p->has_screen || mean != p->screen_mean) {
+        p->ref_dirty = true;
+        if (p->pink_auto) p->dirty = true;   // the automatic pink level follows the reference sky
+    }
     p->screen_mean = mean;
     p->nx = nx;
     p->ny = ny;
@@ -851,7 +941,10 @@ gateau_status gateau_set_atmosphere_table(gateau_plan* p, const float* table, in
         }
     GATEAU_CUDA(grow(p, p->d_tau, padded.size() * sizeof(float)));
     GATEAU_CUDA(cudaMemcpy(p->d_tau.p, padded.data(), padded.size() * sizeof(float), cudaMemcpyHostToDevice));
-    if (tau != p->tau_host) p->ref_dirty = true;
+    if (tau != p->tau_host) {
+        p->ref_dirty = true;
+        if (p->pink_auto) p->dirty = true;
+    }
     p->tau_host = std::move(tau);
     p->n_pwv = n_pwv;
     p->pwv_min = pwv_min_mm;
@@ -913,12 +1006,14 @@ gateau_status gateau_set_dispersive_element(gateau_plan* p, int kind, int n_ch, 
 }
 
 gateau_status gateau_set_pink_noise(gateau_plan* p, const double* A, const double* alpha) {
-    if (!p || !A || !alpha) return fail(GATEAU_EINVAL, "plan, A and alpha must be non-NULL");
+    if (!p || !alpha) return fail(GATEAU_EINVAL, "plan and alpha must be non-NULL");
     if (!p->has_disp) return fail(GATEAU_ESTATE, "set the dispersive element before the pink noise");
     for (int c = 0; c < p->n_ch; ++c)
-        if (!(A[c] >= 0.0) || !(alpha[c] >= 0.0 && alpha[c] <= 3.0))
+        if ((A && !(A[c] >= 0.0)) || !(alpha[c] >= 0.0 && alpha[c] <= 3.0))
             return fail(GATEAU_EINVAL, "channel %d: need A >= 0 and 0 <= alpha <= 3", c);
-    p->pink_A.assign(A, A + p->n_ch);
+    p->pink_auto = A == nullptr;
+    if (A) p->pink_A.assign(A, A + p->n_ch);
+    else p->pink_A.assign(p->n_ch, 0.0);          // set from the reference spectrum when prepared
     p->pink_alpha.assign(alpha, alpha + p->n_ch);
     p->has_pink = true;
     p->dirty = true;
@@ -945,7 +1040,10 @@ gateau_status gateau_set_scan(gateau_plan* p, int kind, const double* params, in
     p->scan_kind = kind;
     for (int i = 0; i < kMaxScanParams; ++i) p->sp[i] = i < n_params ? params[i] : 0.0;
     p->phi0 = phi0_rad;
-    if (!p->has_scan || theta0_rad != p->theta0) p->ref_dirty = true;   // the reference spectrum's elevation
+    if (!p->has_scan || theta0_rad != p->theta0) {   // the reference spectrum's elevation
+        p->ref_dirty = true;
+        if (p->pink_auto) p->dirty = true;
+    }
     p->theta0 = theta0_rad;
     p->n_custom = kind == GATEAU_SCAN_CUSTOM ? n_custom : 0;
     if (p->kelvin) p->dirty = true;    // the skydip runs at the base elevation theta0
@@ -1217,8 +1315,36 @@ gateau_status gateau_run_batch(gateau_plan* const* plans, const long long* t0s, 
         st = ensure_base(plans[k]);
         if (st != GATEAU_OK) return st;
     }
+    const cudaStream_t cs = static_cast<cudaStream_t>(stream);
     for (int k = 0; k < n; ++k) {
-        gateau_status st = enqueue_run(plans[k], t0s[k], nts[k], outs[k], static_cast<cudaStream_t>(stream));
+        gateau_status st = run_rows(plans[k], t0s[k], nts[k], cs);
+        if (st != GATEAU_OK) return st;
+    }
+    // The FP32 baseline runs plan by plan; the split-BF16 contractions of the batch share
+    // persistent launches, one per launch mode (shared tiles for two channel groups, independent
+    // CTAs otherwise) and per fused_max_jobs() plans.
+    std::vector<int> mode[2];
+    for (int k = 0; k < n; ++k) {
+        gateau_plan* p = plans[k];
+        if (p->desc.precision == GATEAU_PREC_FP32) {
+            gateau_status st = run_contract(p, t0s[k], nts[k], outs[k], cs);
+            if (st != GATEAU_OK) return st;
+        } else {
+            mode[p->fused.n_groups == 2 ? 1 : 0].push_back(k);
+        }
+    }
+    for (const std::vector<int>& ks : mode)
+        for (size_t a = 0; a < ks.size(); a += static_cast<size_t>(fused_max_jobs())) {
+            const size_t b = std::min(ks.size(), a + static_cast<size_t>(fused_max_jobs()));
+            std::vector<FusedRunDesc> runs;
+            for (size_t i = a; i < b; ++i) runs.push_back(fused_run(plans[ks[i]], t0s[ks[i]], nts[ks[i]], outs[ks[i]]));
+            for (size_t i = a; i < b; ++i) GATEAU_CUDA((PhaseTimer{plans[ks[i]], cs}.begin(GATEAU_PHASE_CONTRACT)));
+            GATEAU_CUDA(launch_fused_runs(runs.data(), static_cast<int>(runs.size()), plans[ks[a]]->n_sm, cs));
+            for (size_t i = a; i < b; ++i) GATEAU_CUDA((PhaseTimer{plans[ks[i]], cs}.end(GATEAU_PHASE_CONTRACT)));
+            plans[ks[a]]->launches += 1;          // one launch for the whole group, counted once
+        }
+    for (int k = 0; k < n; ++k) {
+        gateau_status st = run_noise(plans[k], t0s[k], nts[k], outs[k], cs);
         if (st != GATEAU_OK) return st;
     }
     return GATEAU_OK;
@@ -1285,6 +1411,13 @@ gateau_status gateau_plan_get_info(gateau_plan* p, gateau_plan_info* info) {
     info->next_t0 = p->next_t0;
     info->device_bytes = device_bytes(p);
     info->staged_inputs = p->fused.tma_inputs;
+    info->tile_groups = info->tile_half = info->ring_a = info->ring_b = 0;
+    if (p->desc.precision == GATEAU_PREC_BF16X3 && p->fused.n_half > 0) {
+        info->tile_groups = p->fused.n_groups;
+        info->tile_half = p->fused.n_half;
+        info->ring_b = fused_ring_depths(p->fused.n_half, p->fused.ring_b, &info->ring_a);
+    }
+    info->tune_ms = p->tune_ms;
     return GATEAU_OK;
 }
 
@@ -1312,6 +1445,8 @@ gateau_status gateau_plan_get_vector(gateau_plan* p, int which, double* out, siz
         else if (which == GATEAU_VEC_C1) tmp = c1;
         else if (which == GATEAU_VEC_C2) tmp = c2;
         else {
+            if (p->pink_auto && p->dirty && which != GATEAU_VEC_PINK_A)
+                return fail(GATEAU_ESTATE, "the automatic pink level is set when the plan is prepared");
             const int np = pink_pole_count(d.pink_f_min_hz, d.f_sample_hz);
             std::vector<double> a(static_cast<size_t>(p->n_ch) * np), r(a.size()), dd(p->n_ch);
             for (int c = 0; c < p->n_ch; ++c)
@@ -1371,6 +1506,136 @@ gateau_status gateau_plan_set_state(gateau_plan* p, long long next_t0, const dou
         GATEAU_CUDA(cudaMemcpy(p->d_state.p, h.data(), n * sizeof(float), cudaMemcpyHostToDevice));
     }
     p->next_t0 = next_t0;
+    return GATEAU_OK;
+}
+
+gateau_status gateau_plan_set_tiles(gateau_plan* p, int n_groups, int ring_b) {
+    if (!p) return fail(GATEAU_EINVAL, "plan is NULL");
+    if (ring_b != 0 && (ring_b < 2 || ring_b > kMaxRingB)) return fail(GATEAU_EINVAL, "ring_b must be 0 or 2..%d", kMaxRingB);
+    if (n_groups < 0) return fail(GATEAU_EINVAL, "n_groups must be >= 0");
+    if (n_groups > 0 && p->has_disp) {
+        const int n_ch = p->n_ch;
+        if (n_groups > n_ch || ((n_ch + n_groups - 1) / n_groups + 15) / 16 * 16 > 176)
+            return fail(GATEAU_EINVAL, "%d channels do not split into %d groups of 1..176", n_ch, n_groups);
+    }
+    p->tile_groups = n_groups;
+    p->tile_ring_b = ring_b;
+    p->tune_ms = 0.0;
+    p->ref_dirty = true;
+    return GATEAU_OK;
+}
+
+gateau_status gateau_plan_autotune(gateau_plan* p, long long nt_sample, void* stream, gateau_tile_choice* out) {
+    if (!p) return fail(GATEAU_EINVAL, "plan is NULL");
+    if (p->desc.precision != GATEAU_PREC_BF16X3) return fail(GATEAU_EINVAL, "only split-BF16 plans have fused tiles");
+    if (nt_sample < 1) return fail(GATEAU_EINVAL, "nt_sample must be >= 1");
+    gateau_status st = check_complete(p);
+    if (st != GATEAU_OK) return st;
+    st = ensure_base(p);
+    if (st != GATEAU_OK) return st;
+    if (p->scan_kind == GATEAU_SCAN_CUSTOM) nt_sample = std::min(nt_sample, p->n_custom);
+    nt_sample = std::min(nt_sample, (1LL << 31) / p->desc.n_pix);
+    const int n_ch = p->n_ch;
+    const int key = (n_ch + 15) / 16;
+    gateau_tile_choice res{};
+    bool cached = false;
+    std::pair<int, int> choice;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);   // held for the lookup only: plans build in parallel
+        auto f = g_tune_cache.find(key);
+        if (f != g_tune_cache.end()) {
+            cached = true;
+            choice = f->second;
+        }
+    }
+    if (cached) {
+        p->tile_groups = choice.first;
+        p->tile_ring_b = choice.second;
+        p->ref_dirty = true;
+        st = finalize(p);
+        if (st != GATEAU_OK) return st;
+        res.n_groups = p->fused.n_groups;
+        res.n_half = p->fused.n_half;
+        res.ring_b = fused_ring_depths(p->fused.n_half, p->fused.ring_b, &res.ring_a);
+        if (out) *out = res;
+        return GATEAU_OK;
+    }
+    const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    const bool timing = p->timing;
+    p->timing = false;
+    struct Restore {                    // the plan's timing flag, whatever happens below
+        gateau_plan* p;
+        bool t;
+        ~Restore() { p->timing = t; }
+    } restore{p, timing};
+    const size_t out_bytes = static_cast<size_t>(nt_sample) * p->desc.n_pix * n_ch * sizeof(float);
+    GATEAU_CUDA(grow(p, p->d_tune, out_bytes));
+    p->tile_groups = 0;
+    p->tile_ring_b = 0;
+    p->ref_dirty = true;
+    st = run_rows(p, 0, nt_sample, cs, false);          // rows of the sample: the same for every tile choice
+    if (st != GATEAU_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GATEAU_CUDA(cudaEventCreate(&e0));
+    GATEAU_CUDA(cudaEventCreate(&e1));
+    struct Events {
+        cudaEvent_t a, b;
+        ~Events() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } evs{e0, e1};
+    const int g0 = (n_ch + 175) / 176;
+    std::vector<int> groups{g0, g0 + 1};
+    if (g0 != 2 && g0 + 1 != 2) groups.push_back(2);
+    double best_ms = 1e300, default_ms = 0.0;
+    int best_g = g0, best_rb = kDefaultRingB, n_timed = 0;
+    for (int g : groups) {
+        if (g > n_ch || ((n_ch + g - 1) / g + 15) / 16 * 16 > 176) continue;
+        const int n_half = ((n_ch + g - 1) / g + 15) / 16 * 16;
+        for (int rb = 2; rb <= kMaxRingB; ++rb) {
+            if (fused_ring_depths(n_half, rb, nullptr) != rb) continue;   // that depth does not fit
+            p->tile_groups = g;
+            p->tile_ring_b = rb;
+            p->ref_dirty = true;
+            st = finalize(p);
+            if (st != GATEAU_OK) return st;
+            const FusedRunDesc r = fused_run(p, 0, nt_sample, p->d_tune.as<float>());
+            GATEAU_CUDA(launch_fused_runs(&r, 1, p->n_sm, cs));           // warm-up
+            GATEAU_CUDA(cudaEventRecord(e0, cs));
+            for (int rep = 0; rep < 2; ++rep) GATEAU_CUDA(launch_fused_runs(&r, 1, p->n_sm, cs));
+            GATEAU_CUDA(cudaEventRecord(e1, cs));
+            GATEAU_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            GATEAU_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            const double per = ms / 2.0;
+            ++n_timed;
+            if (g == g0 && rb == kDefaultRingB) default_ms = per;
+            if (per < best_ms) {
+                best_ms = per;
+                best_g = g;
+                best_rb = rb;
+            }
+        }
+    }
+    p->tile_groups = best_g;
+    p->tile_ring_b = best_rb;
+    p->ref_dirty = true;
+    st = finalize(p);
+    if (st != GATEAU_OK) return st;
+    p->tune_ms = best_ms;
+    p->d_tune.release(p->mo);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = std::make_pair(best_g, best_rb);
+    }
+    res.n_groups = p->fused.n_groups;
+    res.n_half = p->fused.n_half;
+    res.ring_b = fused_ring_depths(p->fused.n_half, p->fused.ring_b, &res.ring_a);
+    res.ms = best_ms;
+    res.default_ms = default_ms;
+    res.candidates = n_timed;
+    if (out) *out = res;
     return GATEAU_OK;
 }
 

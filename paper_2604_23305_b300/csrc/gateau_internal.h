@@ -111,9 +111,12 @@ struct FusedOperands {
     int tma_inputs;                    // 1: opacity rows and cube texels are staged by tensor copies
     const float* c_tiled;              // [Kp/16][2][16] c_ref and c1 per stage (kelvin)
     long long wait_cycles;             // budget of each pipeline wait (clock64 cycles); drains keep their own
+    int ring_b;                        // deepest B ring (filter-operand stages) to use, 2..kMaxRingB
 };
 
 constexpr long long kDefaultWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+constexpr int kDefaultRingB = 4;       // B-ring depth the fused kernel takes unless tuned
+constexpr int kMaxRingB = 6;
 
 // Opaque 128-byte tensor-map descriptors (CUtensorMap) for the staged inputs.
 struct __align__(64) TensorMapBytes {
@@ -129,6 +132,22 @@ cudaError_t launch_psd_fp32(const DevTables& T, const RowParams* rows, long long
                             float* X, cudaStream_t stream);
 cudaError_t launch_contract_fp32(const DevTables& T, const float* X, long long r0, long long nrows,
                                  long long t0, long long nt, float* out, cudaStream_t stream);
+// One plan's run for a fused launch (several when a server batches its requests' chunks).
+struct FusedRunDesc {
+    DevTables T;
+    FusedOperands F;
+    TensorMapBytes tm_tau, tm_cube;
+    const RowParams* rows;
+    const TileInfo* tiles;
+    long long t0, nt;
+    float* out;
+};
+// One persistent launch over the work items of 1..fused_max_jobs() runs of one launch mode (all
+// with two channel groups, or none with two).
+cudaError_t launch_fused_runs(const FusedRunDesc* runs, int n, int n_sm, cudaStream_t stream);
+int fused_max_jobs();
+// B-ring depth (return) and A-ring depth (*nsa) the fused kernel takes for n_half and ring_b.
+int fused_ring_depths(int n_half, int ring_b, int* nsa);
 cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, const TensorMapBytes& tm_tau,
                                 const TensorMapBytes& tm_cube, const RowParams* rows, const TileInfo* tiles,
                                 long long t0, long long nt, float* out, int n_sm, cudaStream_t stream);

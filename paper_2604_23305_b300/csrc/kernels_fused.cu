@@ -44,6 +44,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <memory>
+
 #include "device_common.cuh"
 
 namespace gateau {
@@ -194,7 +196,9 @@ struct SmemPlan {
 constexpr size_t kBarReserve = 512;     // mbarriers, TMEM address slot and abort flag
 constexpr int kMaxHalf = 176;           // channels per group: 2 x 176 accumulator columns + parked normals
 
-__host__ __device__ constexpr SmemPlan smem_plan(int n_half) {
+// Ring depths for channel groups of n_half: the deepest B ring up to ring_b (2..kMaxRingB) whose
+// stages leave room for at least as many A slots (at most 8, whole pairs).
+__host__ __device__ constexpr SmemPlan smem_plan(int n_half, int ring_b = kDefaultRingB) {
     SmemPlan p{};
     p.a_bytes = static_cast<size_t>(kAMats) * kTileM * kKStage * 2;
     p.b_bytes = static_cast<size_t>(kBMats) * n_half * kKStage * 2;
@@ -203,7 +207,7 @@ __host__ __device__ constexpr SmemPlan smem_plan(int n_half) {
     const long long avail = static_cast<long long>(kMaxSmem) - 1024 - bar_reserve - in_bytes;
     p.nsa = 0;
     p.nsb = 0;
-    for (int nsb = 4; nsb >= 2; --nsb) {
+    for (int nsb = ring_b; nsb >= 2; --nsb) {
         long long nsa = (avail - static_cast<long long>(nsb) * p.b_bytes) / static_cast<long long>(p.a_bytes);
         if (nsa > 8) nsa = 8;
         nsa &= ~1LL;                               // whole stage pairs
@@ -221,6 +225,12 @@ __host__ __device__ constexpr SmemPlan smem_plan(int n_half) {
 }
 
 size_t fused_smem_bytes() { return smem_plan(kMaxHalf).total; }
+
+int fused_ring_depths(int n_half, int ring_b, int* nsa) {
+    const SmemPlan p = smem_plan(n_half, ring_b);
+    if (nsa) *nsa = p.nsa;
+    return p.nsb;
+}
 
 // What the barrier protocol below assumes of the ring depths (each checked at compile time for
 // every group width the plan can choose, and again at launch):
@@ -246,7 +256,8 @@ constexpr bool ring_protocol_ok(const SmemPlan& p) {
 
 constexpr bool ring_protocol_ok_for_all_groups() {
     for (int nh = 16; nh <= kMaxHalf; nh += 16)
-        if (!ring_protocol_ok(smem_plan(nh))) return false;
+        for (int rb = 2; rb <= kMaxRingB; ++rb)
+            if (!ring_protocol_ok(smem_plan(nh, rb))) return false;
     return true;
 }
 
@@ -491,41 +502,60 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 // ---- work decomposition ------------------------------------------------------
-// share = 1: the two channel groups of a tile run on the two CTAs of a cluster,
-// each building half of the tile's spectrum rows and copying it to the peer.
-struct Work {
-    long long tiles_per_pix, n_items;
-    int n_pix;
-    int share;
+// A launch runs the work items of one or more plans' runs ("jobs"; several when a server batches
+// the time chunks of its requests into one launch).  Everything an item reads of its plan lives in
+// its job, in the kernel's parameter space (the tensor maps must be there or in global memory for
+// the tensor copies).  Items are numbered job by job; a CTA (or a cluster, for shared tiles) takes
+// every gridDim-th item of that numbering, whatever job it belongs to.
+struct __align__(128) FusedJob {   // (CUtensorMap is 128-byte aligned)
+    CUtensorMap tm_tau, tm_cube;       // staged inputs of this plan
+    DevTables T;
+    FusedOperands F;
+    const RowParams* rows;
+    const TileInfo* tiles;
+    long long t0, nt;                  // the run: samples t0 .. t0 + nt - 1
+    float* out;                        // [nt][n_pix][n_ch]
+    long long tiles_per_pix;
+    long long item0, n_items;          // this job's items in the launch's numbering
 };
 
-// Item it = (tile-in-pixel * n_pix + pix) * n_groups + group: items are walked time tile by time
-// tile, all spaxels of one time tile next to each other.  The CTAs resident at one moment then
-// look at one stretch of the scan -- the IFU's spaxels see neighbouring cube texels -- and write
-// neighbouring output rows ([n][pix][ch]), so cube boxes hit L2 and output lines fill together.
-// tile = pix * tiles_per_pix + tile-in-pixel indexes the TileInfo records.
-__device__ __forceinline__ void item_coords(const Work& w, int n_groups, long long it, long long& tile, int& pix,
-                                            long long& row0, int& nrows, int& grp, long long nt) {
-    const long long u = it / n_groups;
-    grp = static_cast<int>(it - u * n_groups);
-    const long long tl = u / w.n_pix;
-    pix = static_cast<int>(u - tl * w.n_pix);
-    tile = static_cast<long long>(pix) * w.tiles_per_pix + tl;
+constexpr int kMaxJobs = 32;           // 32 jobs of 896 bytes stay inside the 32 KB of kernel parameters
+
+template <int NJ>
+struct FusedLaunch {
+    FusedJob job[NJ];
+    int n_jobs;
+    int layout_half;                   // channels per CTA that size the rings: the widest job's
+    int ring_b;                        // deepest B ring the layout may take (the jobs' smallest choice)
+    long long n_items;                 // items of all jobs
+    long long wait_cycles;             // budget of each pipeline wait (clock64 cycles)
+};
+static_assert(sizeof(FusedLaunch<kMaxJobs>) <= 32764, "the job table must fit the kernel parameter space");
+
+// Item li of job J: li = (tile-in-pixel * n_pix + pix) * n_groups + group.  A job's items are
+// walked time tile by time tile, all spaxels of one time tile next to each other.  The CTAs
+// resident at one moment then look at one stretch of the scan -- the IFU's spaxels see
+// neighbouring cube texels -- and write neighbouring output rows ([n][pix][ch]), so cube boxes hit
+// L2 and output lines fill together.  tile = pix * tiles_per_pix + tile-in-pixel indexes the
+// TileInfo records.
+__device__ __forceinline__ void item_coords(const FusedJob& J, long long li, long long& tile, int& pix,
+                                            long long& row0, int& nrows, int& grp) {
+    const int n_groups = J.F.n_groups;
+    const long long u = li / n_groups;
+    grp = static_cast<int>(li - u * n_groups);
+    const long long tl = u / J.T.n_pix;
+    pix = static_cast<int>(u - tl * J.T.n_pix);
+    tile = static_cast<long long>(pix) * J.tiles_per_pix + tl;
     row0 = tl * kTileM;                                // sample offset within the run
-    const long long rem = nt - row0;
+    const long long rem = J.nt - row0;
     nrows = rem < kTileM ? static_cast<int>(rem) : kTileM;
 }
 
-template <int kShare>
-__global__ void __launch_bounds__(kThreads, 1)
-    fused_bf16x3_kernel(const __grid_constant__ CUtensorMap tm_tau, const __grid_constant__ CUtensorMap tm_cube,
-                        DevTables T, FusedOperands F, const RowParams* __restrict__ rows,
-                        const TileInfo* __restrict__ tiles, long long t0, long long nt, Work work,
-                        float* __restrict__ out) {
+template <int kShare, int NJ>
+__global__ void __launch_bounds__(kThreads, 1) fused_bf16x3_kernel(const __grid_constant__ FusedLaunch<NJ> L) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int NH = F.n_half;
-    const SmemPlan sp = smem_plan(NH);
+    const SmemPlan sp = smem_plan(L.layout_half, L.ring_b);   // ring layout: the widest job's channel group
     const int NS = sp.nsa;                       // A-ring depth
     const int NSB = sp.nsb;                      // B-ring depth
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + sp.bar_off);
@@ -584,18 +614,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (share) cluster_sync_all();              // the peer's barriers exist before any remote arrival
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const uint32_t d_sig = tmem_base;            // columns [0, NH)
-    const uint32_t d_noi = tmem_base + 256;      // columns [256, 256 + NH)
+    const uint32_t d_sig = tmem_base;            // columns [0, n_half)
+    const uint32_t d_noi = tmem_base + 256;      // columns [256, 256 + n_half)
+    unsigned int* const status0 = L.job[0].T.status;   // a wait that runs out marks every job (teardown)
 
-    const int n_ks = T.Kp / kKStage;
     // Work units: tiles shared by a cluster, or (tile, group) items for independent CTAs.
-    const long long n_units = share ? work.n_items / 2 : work.n_items;
+    const long long n_units = share ? L.n_items / 2 : L.n_items;
     const long long ubase = share ? blockIdx.x / 2 : blockIdx.x;
     const long long ustride = share ? gridDim.x / 2 : gridDim.x;
     const long long my_items = n_units > ubase ? (n_units - ubase + ustride - 1) / ustride : 0;
     auto item_of = [&](long long j) {
         const long long u = ubase + j * ustride;
         return share ? u * 2 + rank : u;
+    };
+    // The job of launch item it (jobs hold whole tiles, so both items of a shared tile are in one).
+    auto job_of = [&](long long it) -> const FusedJob& {
+        int k = 0;
+        if constexpr (NJ > 1)
+            while (k + 1 < L.n_jobs && it >= L.job[k + 1].item0) ++k;
+        return L.job[k];
     };
 
     // ---------------- epilogue of one item: this warp's share of the units ----------------
@@ -604,23 +641,34 @@ __global__ void __launch_bounds__(kThreads, 1)
     // quadrant's chunks are split over three warps (the epilogue warp and one warp of each producer
     // group, idle while the accumulators drain) in runs of whole chunks.  (Runs weighted by the cost
     // of drawing normals in the epilogue measured slower: the time per unit is not set by the draw.)
-    const int n_chunks = NH / 16;
-    const bool white = (T.noise_flags & GATEAU_NOISE_WHITE) != 0;
     constexpr int kZChunks = 10;
     static_assert(kZChunks * 16 == 2 * (256 - kMaxHalf), "parked normals fill the columns [176, 256) and [432, 512)");
     const int epi_role = warp >= kEpiWarp0 ? 0 : (warp < kProdWarp0 + 4 ? 1 : 2);
-    const int cut1 = (n_chunks + 2) / 3, cut2 = cut1 + (n_chunks - cut1 + 1) / 2;
-    const int unit_lo = 4 * (epi_role == 0 ? 0 : (epi_role == 1 ? cut1 : cut2));
-    const int unit_hi = 4 * (epi_role == 0 ? cut1 : (epi_role == 1 ? cut2 : n_chunks));
-    const int zu_all = white ? 4 * min(n_chunks, kZChunks) : 0;       // units with parked normals
+    // This warp's units of an item of job J (they depend on the job's group width and noise flags).
+    struct Split {
+        int unit_lo, unit_hi, zu_all, n_zunits;
+        bool white;
+    };
+    auto split_of = [&](const FusedJob& J) {
+        Split q;
+        const int n_chunks = J.F.n_half / 16;
+        q.white = (J.T.noise_flags & GATEAU_NOISE_WHITE) != 0;
+        const int cut1 = (n_chunks + 2) / 3, cut2 = cut1 + (n_chunks - cut1 + 1) / 2;
+        q.unit_lo = 4 * (epi_role == 0 ? 0 : (epi_role == 1 ? cut1 : cut2));
+        q.unit_hi = 4 * (epi_role == 0 ? cut1 : (epi_role == 1 ? cut2 : n_chunks));
+        q.zu_all = q.white ? 4 * min(n_chunks, kZChunks) : 0;              // units with parked normals
+        const int zu_hi = q.white ? min(q.unit_hi, q.zu_all) : q.unit_lo;   // parked units [unit_lo, zu_hi)
+        q.n_zunits = zu_hi > q.unit_lo ? zu_hi - q.unit_lo : 0;
+        return q;
+    };
     const int lq = lane & 3, lr = lane >> 2;
     const bool odd = (lane & 1) != 0;
     // White normals of Eq. 19 for rows (R0, R0 + 8) x channel pairs (chq, chq + 1) of this thread,
     // tile row R0 at sample trow0: a quad's Philox draw serves two lanes (the two channel pairs of
     // the quad); lanes l and l ^ 1 draw it for rows R0 and R0 + 8 respectively and swap the halves
     // the other needs.  Warp-collective (shuffles).
-    auto white_pair = [&](long long trow0, int pix, int chq, float2& z0, float2& z1) {
-        const float4 z = white_normals4_fast(trow0 + (odd ? 8 : 0), pix, chq >> 2, T.key0, T.key1);
+    auto white_pair = [&](const FusedJob& J, long long trow0, int pix, int chq, float2& z0, float2& z1) {
+        const float4 z = white_normals4_fast(trow0 + (odd ? 8 : 0), pix, chq >> 2, J.T.key0, J.T.key1);
         const float sx = odd ? z.x : z.z, sy = odd ? z.y : z.w;     // what the partner needs
         const float rx = __shfl_xor_sync(0xffffffffu, sx, 1);
         const float ry = __shfl_xor_sync(0xffffffffu, sy, 1);
@@ -632,36 +680,39 @@ __global__ void __launch_bounds__(kThreads, 1)
     // columns the accumulators leave free, [176, 256) and [432, 512): chunks 0..9 of a group, 16
     // columns each (a group's chunk 10 is drawn in the epilogue).  A unit is stored with the shape
     // the epilogue loads it with.
-    const int zu_hi = white ? min(unit_hi, zu_all) : unit_lo;       // parked units [unit_lo, zu_hi)
-    const int n_zunits = zu_hi > unit_lo ? zu_hi - unit_lo : 0;
     auto zcol = [](int k) -> uint32_t { return k < 5 ? 176u + 16u * k : 432u + 16u * (k - 5); };
-    auto park_unit = [&](int k, long long row0, int pix, int ch_base) {
-        const int u = unit_lo + k, ck = u >> 2, h = (u >> 1) & 1, g = u & 1, tq = warp & 3;
+    auto park_unit = [&](const FusedJob& J, const Split& q, int k, long long row0, int pix, int ch_base) {
+        const int u = q.unit_lo + k, ck = u >> 2, h = (u >> 1) & 1, g = u & 1, tq = warp & 3;
         float2 z0, z1;
-        white_pair(t0 + row0 + tq * 32 + 16 * h + lr, pix, ch_base + 16 * ck + 8 * g + 2 * lq, z0, z1);
+        white_pair(J, J.t0 + row0 + tq * 32 + 16 * h + lr, pix, ch_base + 16 * ck + 8 * g + 2 * lq, z0, z1);
         const float zv[4] = {z0.x, z0.y, z1.x, z1.y};
         tmem_st16x256b_x1(tmem_base + zcol(ck) + 8 * g + (static_cast<uint32_t>(tq * 32 + 16 * h) << 16), zv);
     };
     auto epilogue_item = [&](long long j) -> bool {
         // tcgen05.ld is warp-collective: take the wait's outcome warp-uniformly.
-        if (n_zunits) tmem_wait_st();            // this warp's parked normals of item j have landed
-        const bool okw = mbar_wait(acc_full, static_cast<uint32_t>(j & 1), abort_flag, T.status, F.wait_cycles);
+        tmem_wait_st();                          // this warp's parked normals of item j have landed
+        const bool okw = mbar_wait(acc_full, static_cast<uint32_t>(j & 1), abort_flag, status0, L.wait_cycles);
         if (!__all_sync(0xffffffffu, okw)) return false;
         tc_fence_after();
         const int quad = warp & 3;
         const int r = quad * 32 + lane;
         const long long it = item_of(j);
+        const FusedJob& J = job_of(it);
+        const DevTables& T = J.T;
+        const Split q = split_of(J);
+        const bool white = q.white;
+        const int zu_all = q.zu_all;
         long long tile, row0;
         int pix, nrows, grp;
-        item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
-        const int ch_base = grp * NH;
+        item_coords(J, it - J.item0, tile, pix, row0, nrows, grp);
+        const int ch_base = grp * J.F.n_half;
         // Each 16-lane half of the quadrant is read with the 16x256b shape: a thread holds rows R0
         // and R0 + 8 for channel pairs 2 (lane % 4) + {0, 1} of both 8-channel groups of the chunk,
         // so one store instruction covers 8 rows x 16 contiguous bytes (the 32x32b shape, one row
         // per lane, scattered each store over 32 rows).
         (void)r;
         const long long S_row = static_cast<long long>(T.n_pix) * T.n_ch;
-        float* obase = out + (row0 * T.n_pix + pix) * static_cast<long long>(T.n_ch);
+        float* obase = J.out + (row0 * T.n_pix + pix) * static_cast<long long>(T.n_ch);
         // Unit u = (chunk u / 4, half (u / 2) % 2, 8-channel group u % 2): one 16x256b load of each
         // of S, N and the parked normals (a thread: rows R0 and R0 + 8 x channels chq, chq + 1).
         // TMEM reads run one unit ahead: the loads of unit u + 1 are issued before unit u is
@@ -683,7 +734,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 z0 = make_float2(__uint_as_float(zr[0]), __uint_as_float(zr[1]));
                 z1 = make_float2(__uint_as_float(zr[2]), __uint_as_float(zr[3]));
             } else if (white) {
-                white_pair(t0 + row0 + R0, pix, chq, z0, z1);
+                white_pair(J, J.t0 + row0 + R0, pix, chq, z0, z1);
             }
             // output scale: brightness temperature a P + b (Sect. 2.7), or W (a = 1, b = 0)
             float2 ka = make_float2(1.f, 1.f), kb = make_float2(0.f, 0.f);
@@ -718,8 +769,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         };
         uint32_t sa[4], na[4], za[4] = {0u, 0u, 0u, 0u}, sb[4], nb[4], zb[4] = {0u, 0u, 0u, 0u};
-        const int u_end = unit_hi;
-        int u = unit_lo;
+        const int u_end = q.unit_hi;
+        int u = q.unit_lo;
         if (u < u_end) issue(u, sa, na, za);
         while (u < u_end) {
             tmem_wait_ld_regs(sa, na, za);
@@ -750,24 +801,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             int s = 0, sa = 0;
             int sf = 0;                // A slot of stage g - NSB
             uint32_t pf = 0;           // its pass parity over the A ring
-            const uint32_t bytes = static_cast<uint32_t>(sp.b_bytes);
-            // a shared tile also receives the peer's half of the rows (3 matrices x 64 rows x 16 points)
-            const uint32_t expect = bytes + (share ? static_cast<uint32_t>(kAMats * kTileM * kKStage) : 0u);
             for (long long j = 0; j < my_items && !*abort_flag; ++j) {
                 const long long it = item_of(j);
-                const int grp = static_cast<int>(it % F.n_groups);
-                const uint16_t* src = F.B + static_cast<size_t>(grp) * n_ks * F.stage_elems;
+                const FusedJob& J = job_of(it);
+                const int n_ks = J.T.Kp / kKStage;
+                const int grp = static_cast<int>((it - J.item0) % J.F.n_groups);
+                const uint16_t* src = J.F.B + static_cast<size_t>(grp) * n_ks * J.F.stage_elems;
+                // this job's operands of a stage (its group width; the slot is sized for the widest)
+                const uint32_t bytes = static_cast<uint32_t>(kBMats * J.F.n_half * kKStage * 2);
+                // a shared tile also receives the peer's half of the rows (3 matrices x 64 rows x 16 points)
+                const uint32_t expect = bytes + (share ? static_cast<uint32_t>(kAMats * kTileM * kKStage) : 0u);
                 bool ok = true;
                 for (int ks = 0; ks < n_ks; ++ks) {
                     if (g >= NSB) {
-                        if (!mbar_wait((sf & 1) ? empty_bar(sf) : bfree_first(sf), pf, abort_flag, T.status, F.wait_cycles)) {
+                        if (!mbar_wait((sf & 1) ? empty_bar(sf) : bfree_first(sf), pf, abort_flag, status0, L.wait_cycles)) {
                             ok = false;
                             break;
                         }
                         if (++sf == NS) { sf = 0; pf ^= 1u; }
                     }
                     mbar_arrive_expect_tx(full_a(sa), expect);
-                    bulk_g2s(smem_u32(smem + sp.b_off + s * sp.b_bytes), src + ks * F.stage_elems, bytes,
+                    bulk_g2s(smem_u32(smem + sp.b_off + s * sp.b_bytes), src + ks * J.F.stage_elems, bytes,
                              full_a(sa));
                     ++g;
                     if (++s == NSB) s = 0;
@@ -788,26 +842,28 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t ph = 0;
             for (long long j = 0; j < my_items && !*abort_flag; ++j) {
                 const long long it = item_of(j);
+                const FusedJob& J = job_of(it);
+                const int n_ks = J.T.Kp / kKStage;
                 long long tile, row0;
                 int pix, nrows, grp;
-                item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
-                const TileInfo ti = tiles[tile];
-                const bool tau_box = F.tma_inputs && (ti.flags & TILE_TAU_FITS);
-                const bool cube_box = F.tma_inputs && (ti.flags & TILE_CUBE_FITS);
+                item_coords(J, it - J.item0, tile, pix, row0, nrows, grp);
+                const TileInfo ti = J.tiles[tile];
+                const bool tau_box = J.F.tma_inputs && (ti.flags & TILE_TAU_FITS);
+                const bool cube_box = J.F.tma_inputs && (ti.flags & TILE_CUBE_FITS);
                 const uint32_t bytes = kConstBytes + (tau_box ? kTauBoxBytes : 0) + (cube_box ? kCubeBoxBytes : 0);
                 bool ok = true;
                 for (int ks = 0; ks < n_ks; ++ks) {
-                    if (g >= kInSlots && !mbar_wait(empty_in(s), ph ^ 1u, abort_flag, T.status, F.wait_cycles)) {
+                    if (g >= kInSlots && !mbar_wait(empty_in(s), ph ^ 1u, abort_flag, status0, L.wait_cycles)) {
                         ok = false;
                         break;
                     }
                     uint8_t* slot = smem + sp.in_off + static_cast<size_t>(s) * kInSlotBytes;
                     mbar_arrive_expect_tx(full_in(s), bytes);
-                    bulk_g2s(smem_u32(slot + kConstOff), F.c_tiled + static_cast<size_t>(ks) * 2 * kKStage,
+                    bulk_g2s(smem_u32(slot + kConstOff), J.F.c_tiled + static_cast<size_t>(ks) * 2 * kKStage,
                              kConstBytes, full_in(s));
-                    if (cube_box) tensor3d_g2s(smem_u32(slot), &tm_cube, ks * kKStage, ti.ie0, ti.ia0, full_in(s));
+                    if (cube_box) tensor3d_g2s(smem_u32(slot), &J.tm_cube, ks * kKStage, ti.ie0, ti.ia0, full_in(s));
                     if (tau_box)
-                        tensor2d_g2s(smem_u32(slot + kTauOff), &tm_tau, ks * kKStage, 2 * ti.j0, full_in(s));
+                        tensor2d_g2s(smem_u32(slot + kTauOff), &J.tm_tau, ks * kKStage, 2 * ti.j0, full_in(s));
                     ++g;
                     if (++s == kInSlots) { s = 0; ph ^= 1u; }
                 }
@@ -828,8 +884,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t par = 0;
             bool ok = true;
             for (long long j = 0; j < my_items && ok; ++j) {
+                const int n_ks = job_of(item_of(j)).T.Kp / kKStage;
                 for (int ks = 0; ks < n_ks; ++ks) {
-                    if (!mbar_wait(rows_ready(s), par, abort_flag, T.status, F.wait_cycles)) {
+                    if (!mbar_wait(rows_ready(s), par, abort_flag, status0, L.wait_cycles)) {
                         ok = false;
                         break;
                     }
@@ -848,28 +905,31 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc = make_idesc(NH);
             // slot-0 descriptors and the per-slot steps of the start-address field
             const uint32_t a_mat = kTileM * kKStage * 2;                // bytes per A matrix
-            const uint32_t b_mat = static_cast<uint32_t>(NH) * kKStage * 2;
             const uint32_t a_base = smem_u32(smem), b_base = smem_u32(smem + sp.b_off);
             const uint64_t dx0 = smem_desc(a_base + 0 * a_mat, 128, 256), dx1 = smem_desc(a_base + 1 * a_mat, 128, 256),
                            dx2 = smem_desc(a_base + 2 * a_mat, 128, 256);
-            const uint64_t dh0 = smem_desc(b_base + 0 * b_mat, 128, 256), dh1 = smem_desc(b_base + 1 * b_mat, 128, 256),
-                           dh2 = smem_desc(b_base + 2 * b_mat, 128, 256), dh3 = smem_desc(b_base + 3 * b_mat, 128, 256);
             const uint32_t a_step = static_cast<uint32_t>(sp.a_bytes >> 4), b_step = static_cast<uint32_t>(sp.b_bytes >> 4);
             int s = 0, sb = 0;
             uint32_t par = 0;
             long long n_pairs = 0;                                     // stage pairs committed
             bool ok = true;
             for (long long j = 0; j < my_items && ok; ++j) {
+                // the item's job: its group width sets N and where the B matrices sit in a slot
+                const FusedJob& J = job_of(item_of(j));
+                const int n_ks = J.T.Kp / kKStage;
+                const uint32_t idesc = make_idesc(J.F.n_half);
+                const uint32_t b_mat = static_cast<uint32_t>(J.F.n_half) * kKStage * 2;
+                const uint64_t dh0 = smem_desc(b_base + 0 * b_mat, 128, 256), dh1 = smem_desc(b_base + 1 * b_mat, 128, 256),
+                               dh2 = smem_desc(b_base + 2 * b_mat, 128, 256), dh3 = smem_desc(b_base + 3 * b_mat, 128, 256);
                 if (j > 0) {
-                    ok = mbar_wait(acc_empty, static_cast<uint32_t>((j - 1) & 1), abort_flag, T.status, F.wait_cycles);
+                    ok = mbar_wait(acc_empty, static_cast<uint32_t>((j - 1) & 1), abort_flag, status0, L.wait_cycles);
                     if (!ok) break;
                     tc_fence_after();
                 }
                 for (int ks = 0; ks < n_ks; ks += 2) {               // n_ks is even (Kp % 32 == 0)
-                    if (!mbar_wait(full_a(s), par, abort_flag, T.status, F.wait_cycles)) {
+                    if (!mbar_wait(full_a(s), par, abort_flag, status0, L.wait_cycles)) {
                         ok = false;
                         break;
                     }
@@ -941,7 +1001,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int flags, tau_j, src_idx, sA, sC00;     // staged offsets in floats, without the quad
             float w00, w10, w01, w11, ea, eb;
         };
-        long long g = pgrp;                          // global stage index = item * n_ks + ks
+        long long g = pgrp;                          // this CTA's stage index over its items
         int s = pgrp % NS, si = pgrp % kInSlots;
         uint32_t ph = 0, phi = 0;
         bool ok = true;
@@ -955,24 +1015,28 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool same_tau = false, same_cube = false;
         long long z_row0 = 0;
         int z_pix = 0, z_chb = 0;
+        const FusedJob* Jp = &L.job[0];              // the job of the item being built
         // row constants of item j (and the coordinates its parked normals need)
         auto row_consts = [&](long long j) {
             {
                 const long long it = item_of(j);
+                const FusedJob& J = job_of(it);
+                Jp = &J;
+                const DevTables& T = J.T;
                 long long tile, row0;
                 int pix, nrows, grp;
-                item_coords(work, F.n_groups, it, tile, pix, row0, nrows, grp, nt);
+                item_coords(J, it - J.item0, tile, pix, row0, nrows, grp);
                 z_row0 = row0;
                 z_pix = pix;
-                z_chb = grp * NH;
-                const TileInfo ti = tiles[tile];
+                z_chb = grp * J.F.n_half;
+                const TileInfo ti = J.tiles[tile];
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
                     const int r = rr[i];
                     const bool valid = r < nrows;
                     RowParams rp;
                     if (valid) {
-                        rp = rows[static_cast<long long>(pix) * nt + row0 + r];
+                        rp = J.rows[static_cast<long long>(pix) * J.nt + row0 + r];
                     } else {
                         rp.csc = 1.f; rp.tau_j = ti.j0; rp.tau_f = 0.f; rp.src_idx = -1; rp.src_fa = 0.f;
                         rp.src_fe = 0.f; rp.src_cell = -1;
@@ -984,10 +1048,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const bool has_src = valid && rp.src_idx >= 0;
                     // staged boxes, with a range check that sends a row to the global path otherwise
                     const int dj = rp.tau_j - ti.j0;
-                    const bool tau_box = F.tma_inputs && (ti.flags & TILE_TAU_FITS) && dj >= 0 && dj <= kTauBoxRows - 1;
+                    const bool tau_box = J.F.tma_inputs && (ti.flags & TILE_TAU_FITS) && dj >= 0 && dj <= kTauBoxRows - 1;
                     const int da = has_src ? (rp.src_cell >> 16) - ti.ia0 : 0;
                     const int de = has_src ? (rp.src_cell & 0xffff) - ti.ie0 : 0;
-                    const bool cube_box = has_src && F.tma_inputs && (ti.flags & TILE_CUBE_FITS) && da >= 0 &&
+                    const bool cube_box = has_src && J.F.tma_inputs && (ti.flags & TILE_CUBE_FITS) && da >= 0 &&
                                           da <= kCubeBoxAz - 2 && de >= 0 && de <= kCubeBoxEl - 2;
                     RowC& c = rc[i];
                     c.flags = (has_src ? kHasSrc : 0) | (tau_box ? kTauBox : 0) | (cube_box ? kCubeBox : 0);
@@ -1011,8 +1075,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         };
         // one stage of this warp (ks of the current item): gathers, X, split, stores, arrival
         auto build_stage = [&](int ks) -> bool {
-                bool okw = (g < NS || mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, T.status, F.wait_cycles)) &&
-                           mbar_wait(full_in(si), phi, abort_flag, T.status, F.wait_cycles);
+                bool okw = (g < NS || mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, status0, L.wait_cycles)) &&
+                           mbar_wait(full_in(si), phi, abort_flag, status0, L.wait_cycles);
                 okw = __all_sync(0xffffffffu, okw);      // the warp signals as one
                 if (!okw) return false;
                 uint8_t* a0 = smem + s * sp.a_bytes;
@@ -1031,6 +1095,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             ta = ld4(stau + c.sA + 4 * quad);
                             td = ld4(stau + c.sA + kBoxW + 4 * quad);
                         } else {
+                            const DevTables& T = Jp->T;
                             const float* gA = T.tau + static_cast<long long>(2 * c.tau_j) * T.Kp;
                             ta = ld4(gA + kq);
                             td = ld4(gA + T.Kp + kq);
@@ -1044,6 +1109,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             q01 = ld4(b + kBoxW);
                             q11 = ld4(b + kCubeBoxEl * kBoxW + kBoxW);
                         } else if (c.flags & kHasSrc) {
+                            const DevTables& T = Jp->T;
                             const float* g00 = T.cube + c.src_idx + kq;
                             const float* g10 = g00 + static_cast<long long>(T.n_el) * T.Kp;
                             q00 = ld4(g00);
@@ -1109,12 +1175,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                 while (si >= kInSlots) { si -= kInSlots; phi ^= 1u; }
                 return true;
         };
+        long long gbase = 0;                         // this CTA's stages before item j
         for (long long j = 0; j < my_items && ok; ++j) {
-            // the stages of item j built by this warp (g advances by kStep, across items too:
-            // ks = first ks >= 0 with (j n_ks + ks) mod kStep == pgrp)
-            int ks = share ? static_cast<int>(((pgrp - j * n_ks) % kStep + kStep) % kStep) : 0;
-            int zk = 0, built = 0;
             row_consts(j);
+            const int n_ks = Jp->T.Kp / kKStage;
+            const Split zq = split_of(*Jp);
+            const int n_zunits = zq.n_zunits;
+            // the stages of item j built by this warp (g advances by kStep, across items too:
+            // ks = first ks >= 0 with (gbase + ks) mod kStep == pgrp)
+            int ks = share ? static_cast<int>(((pgrp - gbase) % kStep + kStep) % kStep) : 0;
+            gbase += n_ks;
+            int zk = 0, built = 0;
             if (j > 0) {
                 for (; ks < n_ks && ks < kPre; ks += kStep)
                     if (!(ok = build_stage(ks))) break;
@@ -1125,21 +1196,24 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (; ks < n_ks; ks += kStep) {
                 if (!(ok = build_stage(ks))) break;
                 if (zk < n_zunits && built >= kZSkip && (built - kZSkip) % kZEvery == 0)
-                    park_unit(zk++, z_row0, z_pix, z_chb);
+                    park_unit(*Jp, zq, zk++, z_row0, z_pix, z_chb);
                 ++built;
             }
             if (!ok) break;
-            while (zk < n_zunits) park_unit(zk++, z_row0, z_pix, z_chb);
+            while (zk < n_zunits) park_unit(*Jp, zq, zk++, z_row0, z_pix, z_chb);
         }
         if (ok && my_items > 0) ok = epilogue_item(my_items - 1);   // this warp's share of the last epilogue
     } else if (warp >= kEpiWarp0) {
         // ---------------- epilogue warps (independent CTAs; shared tiles use them as producers) ----
         for (long long j = 0; j < my_items; ++j) {
-            if (n_zunits) {                        // idle while item j's MMAs run: park its normals now
+            const long long it = item_of(j);
+            const FusedJob& J = job_of(it);
+            const Split zq = split_of(J);
+            if (zq.n_zunits) {                     // idle while item j's MMAs run: park its normals now
                 long long tile, row0;
                 int pix, nrows, grp;
-                item_coords(work, F.n_groups, item_of(j), tile, pix, row0, nrows, grp, nt);
-                for (int k = 0; k < n_zunits; ++k) park_unit(k, row0, pix, grp * NH);
+                item_coords(J, it - J.item0, tile, pix, row0, nrows, grp);
+                for (int k = 0; k < zq.n_zunits; ++k) park_unit(J, zq, k, row0, pix, grp * J.F.n_half);
             }
             if (!epilogue_item(j)) break;
         }
@@ -1148,6 +1222,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp >= kProdWarp0) tmem_wait_st();     // no parked normals in flight (a role may have stopped early)
     tc_fence_before();
     __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag)        // a wait ran out: every job of the launch is incomplete
+        for (int k = 0; k < L.n_jobs; ++k) atomicOr(L.job[k].T.status, GATEAU_STATUS_WAIT_TIMEOUT);
     if (share && *abort_flag) {                 // aborted shared tile: the row copies already issued land first
         if (threadIdx.x == 0) {
             const long long t_start = clock64();
@@ -1164,32 +1240,60 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, const TensorMapBytes& tm_tau,
-                                const TensorMapBytes& tm_cube, const RowParams* rows, const TileInfo* tiles,
-                                long long t0, long long nt, float* out, int n_sm, cudaStream_t stream) {
-    const SmemPlan sp = smem_plan(F.n_half);
-    if (F.n_half < 16 || F.n_half > kMaxHalf || F.n_half % 16 || !ring_protocol_ok(sp) || F.n_kstage % 2)
-        return cudaErrorInvalidConfiguration;
-    Work w;
-    w.tiles_per_pix = (nt + kTileM - 1) / kTileM;
-    w.n_items = w.tiles_per_pix * T.n_pix * F.n_groups;
-    w.n_pix = T.n_pix;
-    w.share = F.n_groups == 2 ? 1 : 0;
-    if (w.n_items == 0) return cudaSuccess;
-    auto kernel = w.share ? fused_bf16x3_kernel<1> : fused_bf16x3_kernel<0>;
+// Build the job table of a launch and launch it.  All runs share the launch mode: two channel
+// groups each (2-CTA clusters with shared tiles), or any other group count (independent CTAs).
+template <int NJ>
+static cudaError_t launch_jobs(const FusedRunDesc* runs, int n, int n_sm, cudaStream_t stream) {
+    std::unique_ptr<FusedLaunch<NJ>> Lp(new (std::nothrow) FusedLaunch<NJ>());   // ~27 KB: not on the stack
+    if (!Lp) return cudaErrorMemoryAllocation;
+    FusedLaunch<NJ>& L = *Lp;
+    memset(&L, 0, sizeof(L));
+    const int share = runs[0].F.n_groups == 2 ? 1 : 0;
+    int layout = 16, ring_b = kMaxRingB;
+    long long items = 0, wait = kDefaultWaitCycles;
+    for (int k = 0; k < n; ++k) {
+        const FusedRunDesc& r = runs[k];
+        const FusedOperands& F = r.F;
+        if (F.n_half < 16 || F.n_half > kMaxHalf || F.n_half % 16 || F.n_kstage % 2 || F.n_kstage * kKStage != r.T.Kp ||
+            F.ring_b < 2 || F.ring_b > kMaxRingB ||
+            (F.n_groups == 2 ? 1 : 0) != share || F.n_groups < 1 || r.nt < 1 || r.T.n_pix < 1)
+            return cudaErrorInvalidConfiguration;
+        FusedJob& J = L.job[k];
+        memcpy(&J.tm_tau, &r.tm_tau, sizeof(J.tm_tau));
+        memcpy(&J.tm_cube, &r.tm_cube, sizeof(J.tm_cube));
+        J.T = r.T;
+        J.F = F;
+        J.rows = r.rows;
+        J.tiles = r.tiles;
+        J.t0 = r.t0;
+        J.nt = r.nt;
+        J.out = r.out;
+        J.tiles_per_pix = (r.nt + kTileM - 1) / kTileM;
+        J.item0 = items;
+        J.n_items = J.tiles_per_pix * r.T.n_pix * F.n_groups;
+        items += J.n_items;
+        layout = F.n_half > layout ? F.n_half : layout;
+        ring_b = F.ring_b < ring_b ? F.ring_b : ring_b;
+        wait = F.wait_cycles < wait ? F.wait_cycles : wait;
+    }
+    L.n_jobs = n;
+    L.layout_half = layout;
+    L.ring_b = ring_b;
+    L.n_items = items;
+    L.wait_cycles = wait;
+    const SmemPlan sp = smem_plan(layout, ring_b);
+    if (!ring_protocol_ok(sp)) return cudaErrorInvalidConfiguration;
+    auto kernel = share ? fused_bf16x3_kernel<1, NJ> : fused_bf16x3_kernel<0, NJ>;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(sp.total));
     if (e != cudaSuccess) return e;
-    CUtensorMap mt, mc;
-    memcpy(&mt, &tm_tau, sizeof(mt));
-    memcpy(&mc, &tm_cube, sizeof(mc));
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = sp.total;
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     long long grid;
-    if (w.share) {
+    if (share) {
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = 2;
         attr[0].val.clusterDim.y = 1;
@@ -1201,17 +1305,40 @@ cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, cons
         e = cudaOccupancyMaxActiveClusters(&max_clusters, kernel, &cfg);
         if (e != cudaSuccess) return e;
         if (max_clusters < 1) return cudaErrorInvalidConfiguration;
-        const long long tiles = w.n_items / 2;
+        const long long tiles = items / 2;
         grid = 2 * (tiles < max_clusters ? tiles : max_clusters);
     } else {
         cfg.attrs = nullptr;
         cfg.numAttrs = 0;
-        grid = w.n_items < n_sm ? w.n_items : n_sm;
+        grid = items < n_sm ? items : n_sm;
     }
     cfg.gridDim = dim3(static_cast<unsigned>(grid));
-    e = cudaLaunchKernelEx(&cfg, kernel, mt, mc, T, F, rows, tiles, t0, nt, w, out);
+    e = cudaLaunchKernelEx(&cfg, kernel, L);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+cudaError_t launch_fused_runs(const FusedRunDesc* runs, int n, int n_sm, cudaStream_t stream) {
+    if (n < 1 || n > kMaxJobs) return cudaErrorInvalidValue;
+    return n == 1 ? launch_jobs<1>(runs, n, n_sm, stream) : launch_jobs<kMaxJobs>(runs, n, n_sm, stream);
+}
+
+int fused_max_jobs() { return kMaxJobs; }
+
+cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, const TensorMapBytes& tm_tau,
+                                const TensorMapBytes& tm_cube, const RowParams* rows, const TileInfo* tiles,
+                                long long t0, long long nt, float* out, int n_sm, cudaStream_t stream) {
+    FusedRunDesc r;
+    r.T = T;
+    r.F = F;
+    r.tm_tau = tm_tau;
+    r.tm_cube = tm_cube;
+    r.rows = rows;
+    r.tiles = tiles;
+    r.t0 = t0;
+    r.nt = nt;
+    r.out = out;
+    return launch_fused_runs(&r, 1, n_sm, stream);
 }
 
 }  // namespace gateau

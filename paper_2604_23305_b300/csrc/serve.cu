@@ -11,6 +11,15 @@
 // plan when the last chunk is on the host.  Latency = arrival -> last chunk on
 // the host; p50/p99 over the requests that completed.
 //
+// With shared launches the chunks go in rounds instead: a round takes the next
+// chunk of every admitted request that has a free chunk buffer and runs them as
+// one gateau_run_batch on the server's compute stream, so the requests'
+// contractions share persistent launches of the fused kernel (uneven requests
+// fill the GPU together); two rounds are in flight, and each request's checksum
+// and copy to the host wait for its round on the request's own stream.  The
+// persistent launches hold every SM while they run, so the whole round -- row
+// setups, shared contractions, noise -- stays on the compute stream.
+//
 // A dry-run mode replays the same scheduling decisions on a virtual clock with
 // no CUDA call, so the admission, slot and budget logic is testable on a host
 // without a GPU.  Plans can be built (factory + gateau_plan_prepare: filter
@@ -83,6 +92,10 @@ __global__ void tod_sum_parts(const double* __restrict__ part, double* __restric
 
 enum { kPending = 0, kActive = 1, kDone = 2, kFailed = 3, kBuilding = 4 };
 
+// Chunks in flight per request: two on the request's own stream; three with shared launches, so
+// that a full round can be queued while the copies of the round before last are still running.
+constexpr int kMaxDepth = 3;
+
 // Builder threads: create (factory) and prepare the plans of admitted requests.
 struct Builders {
     std::mutex mu;
@@ -109,18 +122,18 @@ struct Req {
     long long chunk = 0;             // samples per chunk
     size_t chunk_bytes = 0;
     long long next_t0 = 0, done_t0 = 0;
-    long long launched = 0, retired = 0;   // chunk counters (slot = counter & 1)
+    long long launched = 0, retired = 0;   // chunk counters (slot = counter mod the chunk depth)
     int stream = 0, pin = -1;
-    Slot slot[2];
+    Slot slot[kMaxDepth];
     double sum = 0.0, sumsq = 0.0;
     double t_admit = 0.0, t_done = 0.0;
 };
 
 // Pinned host staging of one admitted request: two chunk buffers + two checksum pairs.
 struct PinPair {
-    float* buf[2] = {nullptr, nullptr};
-    double* sums = nullptr;          // [2][2]
-    cudaEvent_t ev[2] = {nullptr, nullptr};
+    float* buf[kMaxDepth] = {nullptr, nullptr, nullptr};
+    double* sums = nullptr;          // [kMaxDepth][2]
+    cudaEvent_t ev[kMaxDepth] = {nullptr, nullptr, nullptr};
 };
 
 gateau_status server_fail(gateau_status st, const std::string& msg) {
@@ -145,6 +158,8 @@ using namespace gateau;
 
 struct gateau_server {
     gateau_server_desc d{};
+    cudaStream_t batch_stream = nullptr;   // shared launches: the rounds' compute stream
+    cudaEvent_t round_ev[2] = {nullptr, nullptr};
     std::vector<cudaStream_t> streams;
     std::vector<PinPair> pins;
     std::vector<int> free_pins;
@@ -176,26 +191,39 @@ gateau_status gateau_server_create(const gateau_server_desc* desc, gateau_server
     if (d.budget_bytes == 0) return server_fail(GATEAU_EINVAL, "budget_bytes must be > 0");
     if (d.dry_run && !(d.dry_seconds_per_sample >= 0.0))
         return server_fail(GATEAU_EINVAL, "dry_seconds_per_sample must be >= 0");
-    if (!d.dry_run && static_cast<double>(d.max_chunk_bytes) * 2.0 * d.max_active > 16.0 * (1ull << 30))
-        return server_fail(GATEAU_EINVAL, "pinned staging 2 x max_active x max_chunk_bytes must stay <= 16 GiB");
+    const int depth = d.shared_launches ? 3 : 2;   // chunks in flight per request
+    if (!d.dry_run && static_cast<double>(d.max_chunk_bytes) * depth * d.max_active > 16.0 * (1ull << 30))
+        return server_fail(GATEAU_EINVAL, "pinned staging (2, or 3 with shared launches) x max_active x max_chunk_bytes "
+                                          "must stay <= 16 GiB");
     gateau_server* s = new (std::nothrow) gateau_server();
     if (!s) return server_fail(GATEAU_ENOMEM, "host allocation failed");
     s->d = d;
     if (!d.dry_run) {
         cudaError_t e = cudaSuccess;
+        // With shared launches the requests' streams (checksums and copies to the host) take
+        // priority over the compute stream, so their small kernels get SMs between the rounds.
+        int prio_low = 0, prio_high = 0;
+        if (d.shared_launches) {
+            e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+            if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->batch_stream, cudaStreamNonBlocking, prio_low);
+            for (int r = 0; r < 2 && e == cudaSuccess; ++r)
+                e = cudaEventCreateWithFlags(&s->round_ev[r], cudaEventDisableTiming);
+        }
         for (int i = 0; i < d.n_streams && e == cudaSuccess; ++i) {
             cudaStream_t st = nullptr;
-            e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+            e = d.shared_launches ? cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio_high)
+                                  : cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
             if (e == cudaSuccess) s->streams.push_back(st);
         }
         s->pins.resize(d.max_active);
         for (int i = 0; i < d.max_active && e == cudaSuccess; ++i) {
             PinPair& p = s->pins[i];
-            for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            for (int b = 0; b < depth && e == cudaSuccess; ++b) {
                 e = cudaHostAlloc(reinterpret_cast<void**>(&p.buf[b]), d.max_chunk_bytes, cudaHostAllocDefault);
                 if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.ev[b], cudaEventDisableTiming);
             }
-            if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&p.sums), 4 * sizeof(double), cudaHostAllocDefault);
+            if (e == cudaSuccess)
+                e = cudaHostAlloc(reinterpret_cast<void**>(&p.sums), 2 * kMaxDepth * sizeof(double), cudaHostAllocDefault);
         }
         if (e != cudaSuccess) {
             gateau_server_destroy(s);
@@ -209,15 +237,19 @@ gateau_status gateau_server_create(const gateau_server_desc* desc, gateau_server
 
 void gateau_server_destroy(gateau_server* s) {
     if (!s) return;
+    if (s->batch_stream) cudaStreamSynchronize(s->batch_stream);
     for (cudaStream_t st : s->streams) cudaStreamSynchronize(st);
     for (PinPair& p : s->pins) {
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kMaxDepth; ++b) {
             if (p.buf[b]) cudaFreeHost(p.buf[b]);
             if (p.ev[b]) cudaEventDestroy(p.ev[b]);
         }
         if (p.sums) cudaFreeHost(p.sums);
     }
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : s->round_ev)
+        if (ev) cudaEventDestroy(ev);
+    if (s->batch_stream) cudaStreamDestroy(s->batch_stream);
     delete s;
 }
 
@@ -236,11 +268,16 @@ gateau_status gateau_server_run(gateau_server* srv, const gateau_request* reques
     }
     const gateau_server_desc& d = srv->d;
     const bool dry = d.dry_run != 0;
+    const bool shared = d.shared_launches != 0;
+    const int depth = shared ? 3 : 2;                                 // chunks in flight per request
     srv->reqs.assign(n, Req{});
     std::vector<Req>& R = srv->reqs;
     srv->free_pins.clear();
     for (int i = d.max_active - 1; i >= 0; --i) srv->free_pins.push_back(i);
     std::vector<double> stream_free(std::max(d.n_streams, 1), 0.0);   // dry run: virtual stream clocks
+    double batch_free = 0.0;                                          // dry run: the compute stream's clock
+    long long rounds_launched = 0, rounds_retired = 0, round_members = 0;
+    double round_end[2] = {0.0, 0.0};                                 // dry run: virtual round completions
 
     const auto t_start = std::chrono::steady_clock::now();
     double vclock = 0.0;
@@ -287,9 +324,10 @@ gateau_status gateau_server_run(gateau_server* srv, const gateau_request* reques
         if (dry) return;
         q.pin = srv->free_pins.back();
         srv->free_pins.pop_back();
-        cudaStream_t st = srv->streams[q.stream];
+        // with shared launches the chunk buffers are written on the compute stream first
+        cudaStream_t st = shared ? srv->batch_stream : srv->streams[q.stream];
         cudaError_t e = cudaSuccess;
-        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        for (int b = 0; b < depth && e == cudaSuccess; ++b) {
             e = cudaMallocAsync(reinterpret_cast<void**>(&q.slot[b].d_out), q.chunk_bytes, st);
             if (e == cudaSuccess)
                 e = cudaMallocAsync(reinterpret_cast<void**>(&q.slot[b].d_part), (2 * kSumBlocks + 2) * sizeof(double), st);
@@ -351,23 +389,23 @@ gateau_status gateau_server_run(gateau_server* srv, const gateau_request* reques
             Req& q = R[i];
             if (q.state != kActive) continue;
             while (q.retired < q.launched) {
-                Slot& sl = q.slot[q.retired & 1];
+                Slot& sl = q.slot[q.retired % depth];
                 if (dry) {
                     if (sl.t_end > t) break;
                 } else {
-                    const cudaError_t e = cudaEventQuery(srv->pins[q.pin].ev[q.retired & 1]);
+                    const cudaError_t e = cudaEventQuery(srv->pins[q.pin].ev[q.retired % depth]);
                     if (e == cudaErrorNotReady) break;
                     if (e != cudaSuccess) {
                         run_status = GATEAU_ECUDA;
                         run_error = std::string("chunk completion: ") + cudaGetErrorString(e);
                         break;
                     }
-                    const double* cs = srv->pins[q.pin].sums + 2 * (q.retired & 1);
+                    const double* cs = srv->pins[q.pin].sums + 2 * (q.retired % depth);
                     q.sum += cs[0];
                     q.sumsq += cs[1];
                     if (q.r.host_out) {
                         const size_t row = static_cast<size_t>(q.r.n_pix) * q.r.n_ch;
-                        memcpy(q.r.host_out + static_cast<size_t>(sl.t0) * row, srv->pins[q.pin].buf[q.retired & 1],
+                        memcpy(q.r.host_out + static_cast<size_t>(sl.t0) * row, srv->pins[q.pin].buf[q.retired % depth],
                                static_cast<size_t>(sl.nt) * row * sizeof(float));
                     }
                 }
@@ -391,7 +429,7 @@ gateau_status gateau_server_run(gateau_server* srv, const gateau_request* reques
             if (row_bytes > d.max_chunk_bytes) chunk = 0;
             q.chunk = chunk;
             q.chunk_bytes = static_cast<size_t>(chunk) * row_bytes;
-            const size_t need = q.r.device_bytes + 2 * q.chunk_bytes + 2 * (2 * kSumBlocks + 2) * sizeof(double);
+            const size_t need = q.r.device_bytes + depth * (q.chunk_bytes + (2 * kSumBlocks + 2) * sizeof(double));
             if (chunk == 0 || need > d.budget_bytes) {   // can never run
                 q.state = kFailed;
                 q.t_admit = q.t_done = now();
@@ -442,56 +480,159 @@ gateau_status gateau_server_run(gateau_server* srv, const gateau_request* reques
         }
 
         // 3. launch chunks: every active request keeps two in flight
-        for (int i = 0; i < n && run_status == GATEAU_OK; ++i) {
-            Req& q = R[i];
-            if (q.state != kActive) continue;
-            while (q.launched - q.retired < 2 && q.next_t0 < q.r.nt) {
-                Slot& sl = q.slot[q.launched & 1];
-                const long long len = std::min(q.chunk, q.r.nt - q.next_t0);
+        // The checksum and the copy to the host of a chunk written into slot b of request q, on
+        // the request's stream (false: a CUDA error, recorded in run_status).
+        auto post_chunk = [&](Req& q, int b, long long len) -> bool {
+            cudaStream_t st = srv->streams[q.stream];
+            PinPair& pp = srv->pins[q.pin];
+            Slot& sl = q.slot[b];
+            const long long n_el = len * q.r.n_pix * q.r.n_ch;
+            tod_partial_sums<<<kSumBlocks, kSumThreads, 0, st>>>(sl.d_out, n_el, sl.d_part);
+            tod_sum_parts<<<1, 32, 0, st>>>(sl.d_part, sl.d_part + 2 * kSumBlocks);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(pp.sums + 2 * b, sl.d_part + 2 * kSumBlocks, 2 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(pp.buf[b], sl.d_out, static_cast<size_t>(n_el) * sizeof(float),
+                                    cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaEventRecord(pp.ev[b], st);
+            if (e != cudaSuccess) {
+                run_status = GATEAU_ECUDA;
+                run_error = std::string("chunk launch: ") + cudaGetErrorString(e);
+                return false;
+            }
+            return true;
+        };
+        auto count_overlap = [&]() {
+            int inflight = 0;
+            for (const Req& o : R)
+                if (o.state == kActive && o.launched > o.retired) ++inflight;
+            overlap_sum += inflight;
+            ++overlap_n;
+        };
+        if (shared) {
+            // rounds that finished on the compute stream
+            while (rounds_retired < rounds_launched) {
+                const int r = static_cast<int>(rounds_retired & 1);
                 if (dry) {
-                    const double work = static_cast<double>(len) * q.r.n_pix * q.r.n_ch * d.dry_seconds_per_sample;
-                    const double start = std::max(now(), stream_free[q.stream]);
-                    sl.t_end = start + work;
-                    stream_free[q.stream] = sl.t_end;
+                    if (round_end[r] > t) break;
+                } else if (cudaEventQuery(srv->round_ev[r]) != cudaSuccess) {
+                    break;                         // not ready (or an error that the chunk events report)
+                }
+                ++rounds_retired;
+            }
+            // A round: the next chunk of every active request with a free buffer.  A round is formed
+            // when none is in flight (the GPU would idle), or when one is in flight and every active
+            // request can join (a second, full round queued behind it); so rounds stay whole instead
+            // of splitting as the requests' copies to the host finish one by one.
+            std::vector<int> members;
+            int waiting = 0;
+            for (int i = 0; i < n; ++i) {
+                const Req& q = R[i];
+                if (q.state != kActive || q.next_t0 >= q.r.nt) continue;
+                if (q.launched - q.retired < depth) members.push_back(i);
+                else ++waiting;
+            }
+            const long long pending = rounds_launched - rounds_retired;
+            if (!(pending == 0 || (pending == 1 && waiting == 0))) members.clear();
+            if (!members.empty()) {
+                std::vector<gateau_plan*> plans;
+                std::vector<long long> t0s, nts;
+                std::vector<float*> outs;
+                double work = 0.0;
+                for (int i : members) {
+                    Req& q = R[i];
+                    const long long len = std::min(q.chunk, q.r.nt - q.next_t0);
+                    plans.push_back(q.plan);
+                    t0s.push_back(q.next_t0);
+                    nts.push_back(len);
+                    outs.push_back(q.slot[q.launched % depth].d_out);
+                    work += static_cast<double>(len) * q.r.n_pix * q.r.n_ch * d.dry_seconds_per_sample;
+                }
+                const int r = static_cast<int>(rounds_launched & 1);
+                bool enqueued = true;
+                if (dry) {
+                    const double start = std::max(now(), batch_free);
+                    batch_free = start + work;
+                    round_end[r] = batch_free;
                 } else {
-                    cudaStream_t st = srv->streams[q.stream];
-                    PinPair& pp = srv->pins[q.pin];
-                    const int b = static_cast<int>(q.launched & 1);
-                    gateau_status gs = gateau_run(q.plan, q.next_t0, len, sl.d_out, st);
-                    if (gs != GATEAU_OK) {                 // nothing of this chunk was enqueued
-                        cudaStreamSynchronize(st);         // earlier chunks of this request
-                        finish(q, i, kFailed);
+                    // the whole round on the compute stream (the persistent launches hold every SM,
+                    // so the round's own row setup and noise run between them there); round_ev[r]
+                    // marks its end, after which each request's checksum and copy follow on its stream
+                    gateau_status gs = gateau_run_batch(plans.data(), t0s.data(), nts.data(), outs.data(),
+                                                        static_cast<int>(members.size()), srv->batch_stream);
+                    if (gs != GATEAU_OK) {                 // nothing of this round was enqueued
+                        enqueued = false;
+                        cudaStreamSynchronize(srv->batch_stream);
+                        for (int i : members) {
+                            cudaStreamSynchronize(srv->streams[R[i].stream]);
+                            finish(R[i], i, kFailed);
+                        }
                         progress = true;
-                        break;
-                    }
-                    const long long n_el = len * q.r.n_pix * q.r.n_ch;
-                    tod_partial_sums<<<kSumBlocks, kSumThreads, 0, st>>>(sl.d_out, n_el, sl.d_part);
-                    tod_sum_parts<<<1, 32, 0, st>>>(sl.d_part, sl.d_part + 2 * kSumBlocks);
-                    cudaError_t e = cudaGetLastError();
-                    if (e == cudaSuccess)
-                        e = cudaMemcpyAsync(pp.sums + 2 * b, sl.d_part + 2 * kSumBlocks, 2 * sizeof(double),
-                                            cudaMemcpyDeviceToHost, st);
-                    if (e == cudaSuccess)
-                        e = cudaMemcpyAsync(pp.buf[b], sl.d_out, static_cast<size_t>(n_el) * sizeof(float),
-                                            cudaMemcpyDeviceToHost, st);
-                    if (e == cudaSuccess) e = cudaEventRecord(pp.ev[b], st);
-                    if (e != cudaSuccess) {
-                        run_status = GATEAU_ECUDA;
-                        run_error = std::string("chunk launch: ") + cudaGetErrorString(e);
-                        break;
+                    } else {
+                        cudaError_t e = cudaEventRecord(srv->round_ev[r], srv->batch_stream);
+                        for (size_t m = 0; m < members.size() && e == cudaSuccess; ++m)
+                            e = cudaStreamWaitEvent(srv->streams[R[members[m]].stream], srv->round_ev[r], 0);
+                        if (e != cudaSuccess) {
+                            run_status = GATEAU_ECUDA;
+                            run_error = std::string("round launch: ") + cudaGetErrorString(e);
+                        }
+                        for (size_t m = 0; m < members.size() && run_status == GATEAU_OK; ++m) {
+                            Req& q = R[members[m]];
+                            post_chunk(q, static_cast<int>(q.launched % depth), nts[m]);
+                        }
                     }
                 }
-                sl.busy = true;
-                sl.t0 = q.next_t0;
-                sl.nt = len;
-                q.next_t0 += len;
-                ++q.launched;
-                progress = true;
-                int inflight = 0;
-                for (const Req& o : R)
-                    if (o.state == kActive && o.launched > o.retired) ++inflight;
-                overlap_sum += inflight;
-                ++overlap_n;
+                if (run_status != GATEAU_OK) break;
+                if (enqueued) {
+                    for (size_t m = 0; m < members.size(); ++m) {
+                        Req& q = R[members[m]];
+                        Slot& sl = q.slot[q.launched % depth];
+                        sl.busy = true;
+                        sl.t0 = q.next_t0;
+                        sl.nt = nts[m];
+                        if (dry) sl.t_end = round_end[r];
+                        q.next_t0 += nts[m];
+                        ++q.launched;
+                    }
+                    ++rounds_launched;
+                    round_members += static_cast<long long>(members.size());
+                    count_overlap();
+                    progress = true;
+                }
+            }
+        } else {
+            for (int i = 0; i < n && run_status == GATEAU_OK; ++i) {
+                Req& q = R[i];
+                if (q.state != kActive) continue;
+                while (q.launched - q.retired < depth && q.next_t0 < q.r.nt) {
+                    Slot& sl = q.slot[q.launched % depth];
+                    const long long len = std::min(q.chunk, q.r.nt - q.next_t0);
+                    if (dry) {
+                        const double work = static_cast<double>(len) * q.r.n_pix * q.r.n_ch * d.dry_seconds_per_sample;
+                        const double start = std::max(now(), stream_free[q.stream]);
+                        sl.t_end = start + work;
+                        stream_free[q.stream] = sl.t_end;
+                    } else {
+                        cudaStream_t st = srv->streams[q.stream];
+                        gateau_status gs = gateau_run(q.plan, q.next_t0, len, sl.d_out, st);
+                        if (gs != GATEAU_OK) {                 // nothing of this chunk was enqueued
+                            cudaStreamSynchronize(st);         // earlier chunks of this request
+                            finish(q, i, kFailed);
+                            progress = true;
+                            break;
+                        }
+                        if (!post_chunk(q, static_cast<int>(q.launched % depth), len)) break;
+                    }
+                    sl.busy = true;
+                    sl.t0 = q.next_t0;
+                    sl.nt = len;
+                    q.next_t0 += len;
+                    ++q.launched;
+                    progress = true;
+                    count_overlap();
+                }
             }
         }
         if (run_status != GATEAU_OK) break;
@@ -503,7 +644,7 @@ gateau_status gateau_server_run(gateau_server* srv, const gateau_request* reques
             for (const Req& q : R)
                 if (q.state == kActive && q.retired < q.launched) {
                     busy = true;
-                    t_next = std::min(t_next, q.slot[q.retired & 1].t_end);
+                    t_next = std::min(t_next, q.slot[q.retired % depth].t_end);
                 }
             const double t_now = now();
             const bool arrival_ahead = next < n && R[next].state == kPending && requests[next].arrival_s > t_now;
@@ -537,6 +678,7 @@ gateau_status gateau_server_run(gateau_server* srv, const gateau_request* reques
             if (q.state == kBuilding) q.state = kFailed;
     }
     if (run_status != GATEAU_OK) {                 // release whatever is still admitted
+        if (srv->batch_stream) cudaStreamSynchronize(srv->batch_stream);
         for (cudaStream_t st : srv->streams) cudaStreamSynchronize(st);
         for (int i = 0; i < n; ++i)
             if (R[i].state == kActive) finish(R[i], i, kFailed);
@@ -572,6 +714,8 @@ gateau_status gateau_server_run(gateau_server* srv, const gateau_request* reques
         st.peak_bytes = peak_bytes;
         st.peak_active = peak_active;
         st.overlap = overlap_n ? overlap_sum / overlap_n : 0.0;
+        st.rounds = rounds_launched;
+        st.mean_round = rounds_launched ? static_cast<double>(round_members) / rounds_launched : 0.0;
         *stats = st;
     }
     if (run_status != GATEAU_OK) return server_fail(run_status, run_error);

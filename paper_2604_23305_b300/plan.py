@@ -116,9 +116,12 @@ class Plan:
         self.n_ch = int(np.asarray(disp["f_c"]).size)
         self.set_cascade(sc["cascade"])
         self.set_dispersive(disp)
-        if "pink_A" in noise:
-            A, al = _f64(noise["pink_A"]), _f64(noise["pink_alpha"])
-            L.check(self._lib.gateau_set_pink_noise(self._h, _dptr(A), _dptr(al)))
+        if "pink_alpha" in noise:
+            # no level given: the library sets the knee at 1 Hz (A = the planned white level NEP^2)
+            A = noise.get("pink_A")
+            A = None if A is None else _f64(A)
+            al = _f64(noise["pink_alpha"])
+            L.check(self._lib.gateau_set_pink_noise(self._h, None if A is None else _dptr(A), _dptr(al)))
         if noise.get("pink_tk"):
             self.set_pink_timmer_koenig(int(noise["pink_tk"]))
         if upload:
@@ -264,6 +267,19 @@ class Plan:
             ptr = _dptr(keep)
         L.check(self._lib.gateau_plan_set_state(self._h, next_t0, ptr))
 
+    def set_tiles(self, n_groups: int = 0, ring_b: int = 0):
+        """Fused-kernel tiles: channel groups (0: the fewest) and the deepest B ring (0: the default)."""
+        L.check(self._lib.gateau_plan_set_tiles(self._h, int(n_groups), int(ring_b)))
+
+    def autotune(self, nt_sample: int = 1024, stream=None) -> dict:
+        """Time the candidate tiles on the first nt_sample samples and keep the fastest (cached per
+        shape class for the process).  Returns the choice."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        ch = L.TileChoice()
+        L.check(self._lib.gateau_plan_autotune(self._h, int(nt_sample), C.c_void_p(s.cuda_stream), C.byref(ch)))
+        return {f: getattr(ch, f) for f, _ in L.TileChoice._fields_}
+
     def set_wait_budget(self, cycles: int):
         """Budget of each pipeline wait of the fused kernel in SM clock cycles (default 4e9)."""
         L.check(self._lib.gateau_plan_set_wait_budget(self._h, int(cycles)))
@@ -288,6 +304,22 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def run_batch(plans, t0s, nts, outs=None, stream=None):
+    """gateau_run_batch: every plan's chunk [t0, t0 + nt) in one batch on one stream; the split-BF16
+    contractions share persistent fused launches.  Returns the device output tensors."""
+    import torch
+    n = len(plans)
+    if outs is None:
+        outs = [torch.empty((nt, p.n_pix, p.n_ch), dtype=torch.float32, device="cuda") for p, nt in zip(plans, nts)]
+    s = stream if stream is not None else torch.cuda.current_stream()
+    hp = (L.PlanP * n)(*[p._h for p in plans])
+    a0 = (C.c_longlong * n)(*[int(t) for t in t0s])
+    an = (C.c_longlong * n)(*[int(t) for t in nts])
+    ao = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    L.check(L.lib().gateau_run_batch(hp, a0, an, ao, n, C.c_void_p(s.cuda_stream)))
+    return outs
 
 
 def hex_offsets(R_hex: int, spacing_rad: float) -> np.ndarray:

@@ -28,7 +28,7 @@ class Server:
 
     def __init__(self, budget_bytes: int, max_active: int = 16, chunk_samples: int = 4096,
                  max_chunk_bytes: int = 32 << 20, n_streams: int | None = None, dry_run: bool = False,
-                 dry_seconds_per_sample: float = 0.0, n_builders: int = 0):
+                 dry_seconds_per_sample: float = 0.0, n_builders: int = 0, shared_launches: bool = False):
         self._lib = L.lib()
         d = L.ServerDesc()
         d.budget_bytes = int(budget_bytes)
@@ -39,6 +39,7 @@ class Server:
         d.dry_run = 1 if dry_run else 0
         d.dry_seconds_per_sample = float(dry_seconds_per_sample)
         d.n_builders = int(n_builders)
+        d.shared_launches = 1 if shared_launches else 0
         self._h = L.ServerP()
         L.check(self._lib.gateau_server_create(C.byref(d), C.byref(self._h)))
         self.n = 0
@@ -162,8 +163,8 @@ class ServingInputs:
             dispersive=dict(kind="filterbank", f_c=W.geometric_channels(220e9, 440e9, n_ch),
                             R=np.full(n_ch, 500.0), eta_peak=np.full(n_ch, 0.16)),
         )
-        A, alpha = W.pink_levels(n_ch, self.seed + 7 + index)
-        sc["noise"] = dict(seed=1000 + index, pink_A=A, pink_alpha=alpha, pink_f_min=fs / nt)
+        _, alpha = W.pink_levels(n_ch, self.seed + 7 + index)
+        sc["noise"] = dict(seed=1000 + index, pink_A=None, pink_alpha=alpha, pink_f_min=fs / nt)
         return sc
 
 

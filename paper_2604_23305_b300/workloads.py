@@ -160,7 +160,9 @@ def three_stage_cascade() -> list[dict]:
 
 
 def pink_levels(n_ch: int, seed: int, nep_ref=1e-17):
-    """Per-channel pink level A (W^2/Hz at 1 Hz) and slope alpha ~ U[0.5, 1.5]."""
+    """Per-channel pink level A (W^2/Hz at 1 Hz) and slope alpha ~ U[0.5, 1.5].  The scenarios give
+    only the slopes: with no level the knee sits at 1 Hz (the simulator sets A to each channel's
+    white noise level); explicit levels remain for tests."""
     rng = np.random.default_rng(seed)
     A = (nep_ref ** 2) * rng.uniform(0.5, 2.0, n_ch)
     alpha = rng.uniform(0.5, 1.5, n_ch)
@@ -208,15 +210,15 @@ def scenario(name: str, nt_total: int | None = None, seed: int = 0, noise_seed: 
             dispersive=dict(kind="filterbank", f_c=f_c, R=np.full(64, 300.0),
                             eta_peak=np.full(64, 0.16)),
         )
-        A, alpha = pink_levels(64, seed + 7)
-        sc["noise"] = dict(seed=noise_seed, pink_A=A, pink_alpha=alpha, pink_f_min=fs / nt)
+        _, alpha = pink_levels(64, seed + 7)
+        sc["noise"] = dict(seed=noise_seed, pink_A=None, pink_alpha=alpha, pink_f_min=fs / nt)
         return sc
     if name in ("single_pixel_wide", "ifu25"):
         n_freq, f_lo, f_hi, fs = 3000, 220 * GHZ, 440 * GHZ, 160.0
         nu = np.linspace(f_lo, f_hi, n_freq)
         f_c = geometric_channels(f_lo, f_hi, 347)
         tab, pmin, dp = opacity_table(nu)
-        A, alpha = pink_levels(347, seed + 7)
+        _, alpha = pink_levels(347, seed + 7)
         if name == "single_pixel_wide":
             nt = 96000 if nt_total is None else nt_total
             sc = _base(n_freq, f_lo, f_hi, fs, np.zeros((1, 2)), nt)
@@ -245,7 +247,7 @@ def scenario(name: str, nt_total: int | None = None, seed: int = 0, noise_seed: 
             dispersive=dict(kind="filterbank", f_c=f_c, R=np.full(347, 500.0),
                             eta_peak=np.full(347, 0.16)),
         )
-        sc["noise"] = dict(seed=noise_seed, pink_A=A, pink_alpha=alpha, pink_f_min=f_min)
+        sc["noise"] = dict(seed=noise_seed, pink_A=None, pink_alpha=alpha, pink_f_min=f_min)
         return sc
     raise ValueError(f"unknown scenario {name!r}")
 

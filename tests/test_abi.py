@@ -97,7 +97,10 @@ def test_dispersive_kinds_match_oracle(kind):
 
 
 def test_pink_coefficients_match_oracle():
-    sc, p = _plan("ifu25", nt=100)
+    # explicit levels: the automatic level (knee at 1 Hz) needs the plan prepared on a device
+    sc = W.scenario("ifu25", nt_total=100)
+    sc["noise"]["pink_A"] = W.pink_levels(347, 7)[0]
+    p = Plan(sc, upload=False)
     inst = O.build_instrument(sc)
     info = p.info()
     npole = info.n_pole
@@ -138,6 +141,11 @@ def test_argument_validation():
     assert lib.gateau_plan_set_wait_budget(p._h, -1) == L.EINVAL
     assert lib.gateau_plan_set_wait_budget(None, 100) == L.EINVAL
     assert lib.gateau_plan_set_wait_budget(p._h, 0) == L.OK
+    assert lib.gateau_plan_set_tiles(p._h, 0, 1) == L.EINVAL and lib.gateau_plan_set_tiles(p._h, 0, 7) == L.EINVAL
+    assert lib.gateau_plan_set_tiles(p._h, 65, 0) == L.EINVAL           # 64 channels: at most 64 groups
+    assert lib.gateau_plan_set_tiles(p._h, -1, 0) == L.EINVAL
+    assert lib.gateau_plan_set_tiles(p._h, 2, 3) == L.OK and lib.gateau_plan_set_tiles(p._h, 0, 0) == L.OK
+    assert lib.gateau_plan_autotune(p._h, 0, None, None) == L.EINVAL
     d = L.PlanDesc()
     out = L.PlanP()
     assert lib.gateau_plan_create(C.byref(d), C.byref(out)) == L.EINVAL and not out.value

@@ -310,7 +310,6 @@ def _mut_few_channels(s):
     d = s["dispersive"]
     s["dispersive"] = dict(kind="filterbank", f_c=np.asarray(d["f_c"])[5:22], R=np.asarray(d["R"])[5:22],
                            eta_peak=np.asarray(d["eta_peak"])[5:22])
-    s["noise"]["pink_A"] = s["noise"]["pink_A"][5:22]
     s["noise"]["pink_alpha"] = s["noise"]["pink_alpha"][5:22]
 
 
@@ -322,7 +321,6 @@ def _mut_one_channel_two_freqs(s):
     s["source"]["cube"] = np.ascontiguousarray(s["source"]["cube"][:, :, :2])
     s["dispersive"] = dict(kind="lorentzian", f_c=np.array([300.5e9]), R=np.array([100.0]),
                            eta_peak=np.array([0.5]))
-    s["noise"]["pink_A"] = s["noise"]["pink_A"][:1]
     s["noise"]["pink_alpha"] = s["noise"]["pink_alpha"][:1]
     s["cascade"] = [dict(kind="reflective", eta=0.9, T=20.0)]
 
@@ -420,3 +418,21 @@ def test_signal_parity_across_channel_groupings(n_ch):
     worst = np.max(np.abs((got_w - got) - ref["p_wn"]) / bound)
     print(f"bf16x3 {n_ch} channels: white noise worst error / bound = {worst:.3f}")
     assert worst <= 1.0
+
+
+def test_automatic_pink_level_matches_the_oracle():
+    """No pink level given: the library sets each channel's A to the white level NEP^2 of the
+    reference sky (knee at 1 Hz) when the plan is prepared; the filter it builds (residues and direct
+    term, gain folded in) equals the oracle's."""
+    sc = W.scenario("ifu25", nt_total=300)
+    assert sc["noise"].get("pink_A") is None
+    p = Plan(sc, precision="bf16x3", white=True, pink=True)
+    p.prepare()
+    inst = O.build_instrument(sc)
+    n_ch, npole = p.n_ch, p.info().n_pole
+    r = p.get_vector(L.VEC_PINK_R, n_ch * npole).reshape(n_ch, npole)
+    d = p.get_vector(L.VEC_PINK_D, n_ch)
+    for ch in (0, 100, 346):
+        des = inst.pink[ch]
+        np.testing.assert_allclose(r[ch], des.g * des.r, rtol=1e-9)
+        assert d[ch] == pytest.approx(des.g * des.d, rel=1e-9)

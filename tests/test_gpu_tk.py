@@ -84,7 +84,8 @@ def test_tk_full_size_sampled_series():
         del out, p
         torch.cuda.empty_cache()
     noise = sc["noise"]
+    inst_A = O.build_instrument(sc).pink_A          # the knee at 1 Hz: A = the planned white level
     for k, (i, ch) in enumerate(picks):
-        want = O.pink_tk_realisation(noise["seed"], float(noise["pink_A"][ch]), float(noise["pink_alpha"][ch]),
+        want = O.pink_tk_realisation(noise["seed"], float(inst_A[ch]), float(noise["pink_alpha"][ch]),
                                      sc["f_sample"], nt, i, ch)
         _check(series[True][k][:, None], series[False][k][:, None], want[:, None], f"ifu25 ({i}, {ch})")

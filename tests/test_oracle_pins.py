@@ -805,3 +805,24 @@ def test_screen_smoothing_conserves_and_keeps_constants():
     assert abs(out.sum() - scr.sum()) < 1e-9 * abs(scr.sum())
     np.testing.assert_allclose(O.smooth_screen(np.full((32, 32), 0.7), 0.5, 5.0, -10.0), 0.7, rtol=1e-12)
     assert out.std() < scr.std()
+
+
+def test_pink_knee_at_one_hz_is_the_white_level():
+    """With no pink level given, A = the planned white level: on a source-free stare through a
+    uniform screen (the sky then is the reference sky), A equals the simulated white noise's own
+    one-sided PSD 2 sigma^2 / f_s (Eq. 18), so pink and white PSDs cross at 1 Hz; a screen with the
+    same mean PWV gives the same A (the reference takes the screen's mean)."""
+    sc = _uniform_stare_scenario()
+    assert sc["noise"].get("pink_A") is None and "pink_alpha" in sc["noise"]
+    inst = O.build_instrument(sc)
+    parts = O.simulate(sc, 0, 4, inst=inst, white=True, pink=False, return_parts=True)
+    white_psd = 2.0 * parts["sigma"][0, 0, :] ** 2 / sc["f_sample"]
+    np.testing.assert_allclose(inst.pink_A, white_psd, rtol=1e-12)
+    for ch in (0, 31, 63):
+        des = inst.pink[ch]
+        one_sided_at_1hz = des.g ** 2 * abs(O.pink_transfer(des.a, des.b, 1.0, sc["f_sample"])) ** 2 * 2.0 / sc["f_sample"]
+        assert one_sided_at_1hz == pytest.approx(white_psd[ch], rel=1e-12)
+    c = float(np.float32(1.2))                       # the uniform screen's value, as stored
+    checker = np.where((np.indices((32, 32)).sum(axis=0) % 2) == 0, c - 0.25, c + 0.25)   # same mean, exactly
+    sc2 = dict(sc, atmosphere=dict(sc["atmosphere"], screen=checker))
+    np.testing.assert_allclose(O.build_instrument(sc2).pink_A, inst.pink_A, rtol=1e-12)

@@ -46,19 +46,23 @@ def test_request_results_are_the_same_alone_and_in_the_mix():
         srv.close()
 
     # the mix: four requests at once, plans built on the server thread (all four then have chunks
-    # in flight together) and on three builder threads (they start as their plans are ready)
-    for builders in (0, 3):
+    # in flight together) and on three builder threads (they start as their plans are ready); chunks
+    # on the requests' own streams, or in rounds whose contractions share persistent fused launches
+    for builders, shared in ((0, False), (3, False), (0, True), (3, True)):
         srv = Server(budget_bytes=8 << 30, max_active=4, chunk_samples=CHUNK, max_chunk_bytes=16 << 20,
-                     n_streams=4, n_builders=builders)
+                     n_streams=4, n_builders=builders, shared_launches=shared)
         outs = outputs(reqs)
         st = srv.run([dict(r, host_out=o) for r, o in zip(reqs, outs)], make)
         assert st["n_done"] == 4 and st["n_failed"] == 0
         assert st["peak_active"] == 4
         if builders == 0:
             assert st["overlap"] > 1.0                   # requests had chunks in flight together
+        if shared and builders == 0:
+            assert st["mean_round"] > 1.0                # rounds held several requests' chunks
         assert 0 < st["p50_latency_s"] <= st["p99_latency_s"] <= st["max_latency_s"]
         for i in range(4):
-            assert np.array_equal(outs[i], alone[i][0]), f"request {i} differs in the mix ({builders} builders)"
+            assert np.array_equal(outs[i], alone[i][0]), \
+                f"request {i} differs in the mix ({builders} builders, shared launches {shared})"
             assert srv.result(i)["checksum"] == alone[i][1]
             assert np.isfinite(outs[i]).all() and np.abs(outs[i]).max() > 0
         srv.close()

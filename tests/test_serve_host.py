@@ -123,3 +123,23 @@ def test_plan_memory_estimate_covers_the_inputs_and_grows_with_the_chunk():
     assert estimate_bytes(sc, 128, precision="fp32") > small                # FP32 operands + spectrum chunk
     with pytest.raises(L.GateauError):
         estimate_bytes(sc, 0)
+
+
+def test_shared_launch_rounds_batch_every_active_request():
+    # rounds of one chunk per request on one compute stream, two rounds in flight: requests 0 and 1
+    # (2 chunks x 0.5 s) share rounds [0, 1] and [1, 2]; request 2 arrives at 0.5 and waits for a
+    # round slot (both in flight until 1.0), then runs its chunks in rounds [2, 2.5] and [2.5, 3]
+    s = dry(shared_launches=True)
+    st = s.run([req(), req(), req(arrival=0.5)], lambda i: 1)
+    assert st["n_done"] == 3 and st["n_failed"] == 0
+    assert [s.result(i)["latency_s"] for i in range(3)] == pytest.approx([2.0, 2.0, 2.5])
+    assert st["rounds"] == 4
+    assert st["mean_round"] == pytest.approx(6 / 4)
+    assert st["makespan_s"] == pytest.approx(3.0)
+
+
+def test_shared_launch_rounds_respect_slots_and_budget():
+    s = dry(shared_launches=True, max_active=2)
+    st = s.run([req() for _ in range(5)], lambda i: 1)
+    assert st["n_done"] == 5 and st["peak_active"] == 2
+    assert st["mean_round"] <= 2.0
