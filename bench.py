@@ -337,6 +337,7 @@ def main():
     ap.add_argument("--skip-tk", action="store_true")
     ap.add_argument("--skip-prep", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default fused tiles")
+    ap.add_argument("--skip-graph", action="store_true")
     ap.add_argument("--record-traffic", default=None, metavar="RAW_CSV")
     ap.add_argument("--traffic-samples", type=int, default=16384)
     ap.add_argument("--traffic-command", default="")
@@ -563,6 +564,43 @@ def main():
                                    "screen": list(scr.shape), "smooth_screen_ms": 1e3 * t_scr,
                                    "dish_m": 10.0, "edge_taper_db": -10.0}
         del cube, pc, scr, ps
+        torch.cuda.empty_cache()
+
+    # CUDA graphs where launches are the cost: a small request (1 spaxel, 64 channels, 512 points)
+    # simulated in 64 chunks of 64 samples, launched one call at a time or replayed from one graph
+    if rank == 0 and not args.skip_graph:
+        gsc = W.scenario("single_pixel_small", nt_total=4096)
+        gp = Plan(gsc, precision=args.precision, white=True, pink=True)
+        gout = torch.empty((4096, gp.n_pix, gp.n_ch), dtype=torch.float32, device="cuda")
+        gchunks = [(t, 64) for t in range(0, 4096, 64)]
+
+        def gdirect():
+            for t0, n in gchunks:
+                gp.run(t0, n, gout[t0:t0 + n])
+        gdirect()
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            gdirect()
+        graph.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            gdirect()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_direct = e0.elapsed_time(e1) / 5
+        e0.record(stream)
+        for _ in range(5):
+            graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_graph = e0.elapsed_time(e1) / 5
+        result["cuda_graph"] = {"workload": "1 spaxel, 64 channels, 512 points: 64 chunks of 64 samples",
+                                "kernels_per_chunk": 5, "direct_ms": t_direct, "graph_ms": t_graph,
+                                "speedup": t_direct / t_graph}
+        del graph, gout, gp
         torch.cuda.empty_cache()
 
     # end to end through the C ABI with host buffers: inputs uploaded from pinned host memory by

@@ -273,7 +273,11 @@ gateau_status gateau_set_output_kelvin(gateau_plan* plan, int enable, double pwv
  * synchronising.  t0 must be 0 (restarts the pink-noise state) or the end of
  * the previous chunk (EORDER otherwise), so a scan may be produced in chunks
  * of any size with results identical to one call.  The first call after a
- * setter uploads derived tables (synchronous).  ESTATE if the source,
+ * setter uploads derived tables (synchronous).  Once the plan is prepared and a
+ * first run has sized its buffers for chunks of this length, a run enqueues
+ * stream work only, so runs can be captured into a CUDA graph and replayed (a
+ * replay repeats the captured chunks; the chunk at t0 = 0 resets the pink-filter
+ * states within the graph).  ESTATE if the source,
  * screen, table, cascade, dispersive element or scan is missing. */
 gateau_status gateau_run(gateau_plan* plan, long long t0, long long nt, float* dev_out, void* stream);
 

@@ -44,7 +44,10 @@
 #include <math.h>
 #include <string.h>
 
+#include <map>
 #include <memory>
+#include <mutex>
+#include <tuple>
 
 #include "device_common.cuh"
 
@@ -1284,9 +1287,47 @@ static cudaError_t launch_jobs(const FusedRunDesc* runs, int n, int n_sm, cudaSt
     const SmemPlan sp = smem_plan(layout, ring_b);
     if (!ring_protocol_ok(sp)) return cudaErrorInvalidConfiguration;
     auto kernel = share ? fused_bf16x3_kernel<1, NJ> : fused_bf16x3_kernel<0, NJ>;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(sp.total));
+    // The kernel's shared-memory limit (set once per kernel and device, to the most any plan takes)
+    // and, for clusters, how many fit at this size (queried once per kernel, size and device): a
+    // launch is then stream work alone, so a run can be captured into a CUDA graph.
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    int max_clusters = 0;
+    {
+        static std::mutex mu;
+        static std::map<std::pair<const void*, int>, bool> limit_set;
+        static std::map<std::tuple<const void*, size_t, int>, int> ready;   // -> clusters that fit (0: none)
+        std::lock_guard<std::mutex> lk(mu);
+        const void* kf = reinterpret_cast<const void*>(kernel);
+        if (!limit_set.count(std::make_pair(kf, dev))) {
+            static_assert(kMaxSmem <= 227 * 1024, "the fused kernel's shared memory stays within an SM's opt-in limit");
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+            if (e != cudaSuccess) return e;
+            limit_set[std::make_pair(kf, dev)] = true;
+        }
+        const auto key = std::make_tuple(kf, sp.total, dev);
+        auto f = ready.find(key);
+        if (f == ready.end()) {
+            if (share) {
+                cudaLaunchConfig_t q = {};
+                cudaLaunchAttribute a[1];
+                a[0].id = cudaLaunchAttributeClusterDimension;
+                a[0].val.clusterDim.x = 2;
+                a[0].val.clusterDim.y = 1;
+                a[0].val.clusterDim.z = 1;
+                q.attrs = a;
+                q.numAttrs = 1;
+                q.blockDim = dim3(kThreads);
+                q.dynamicSmemBytes = sp.total;
+                q.gridDim = dim3(static_cast<unsigned>(n_sm / 2 * 2));
+                e = cudaOccupancyMaxActiveClusters(&max_clusters, kernel, &q);
+                if (e != cudaSuccess) return e;
+            }
+            f = ready.emplace(key, max_clusters).first;
+        }
+        max_clusters = f->second;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = sp.total;
@@ -1300,10 +1341,6 @@ static cudaError_t launch_jobs(const FusedRunDesc* runs, int n, int n_sm, cudaSt
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cfg.gridDim = dim3(static_cast<unsigned>(n_sm / 2 * 2));
-        int max_clusters = 0;
-        e = cudaOccupancyMaxActiveClusters(&max_clusters, kernel, &cfg);
-        if (e != cudaSuccess) return e;
         if (max_clusters < 1) return cudaErrorInvalidConfiguration;
         const long long tiles = items / 2;
         grid = 2 * (tiles < max_clusters ? tiles : max_clusters);
