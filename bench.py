@@ -196,8 +196,8 @@ def cpu_baseline(sc, budget_s=12.0):
             rate1, dt1 = oracle_rate(sc, nt1)
         single = {"value": rate1, "unit": UNIT, "cores": 1,
                   "sample": f"first {nt1} samples, BLAS held to one thread, {dt1:.1f} s"}
-    except Exception:
-        pass
+    except Exception as exc:                       # reported, not hidden
+        single = {"error": repr(exc)}
     return {"value": rate, "unit": UNIT, "cores": blas_threads(), "nproc": os.cpu_count(), "kind": "oracle",
             "threads": "BLAS threads for the matrix products of Eqs. 16-17 (= cores); the rest on one core",
             "sample": f"first {nt} samples of the scan (all 25 spaxels x 347 channels, white+pink noise), "
