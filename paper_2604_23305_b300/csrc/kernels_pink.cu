@@ -5,9 +5,9 @@
 // The recurrence is linear, so a run of nt samples is cut into C chunks of L
 // samples scanned in parallel:
 //   phase 1: each (chunk, sequence) computes its end state from a zero start;
-//   phase 2: each (sequence, pole) combines the chunk states in order,
-//            s_in[c+1] = a^len(c) s_in[c] + agg[c], seeded by the carried state
-//            (FP32: a^len = 2^(len log2 a) to ~1e-6 relative, a few dozen steps);
+//   phase 2: each (sequence, pole) combines the chunk states along time,
+//            s_in[c+1] = a^len(c) s_in[c] + agg[c], seeded by the carried state, as a
+//            warp-shuffle associative scan of the chunks' affine maps (FP32);
 //   phase 3: each (chunk, sequence) reruns its chunk from s_in[c] and adds y.
 // Threads of a warp own consecutive channels of one spaxel, so every sample
 // step reads and writes 128 contiguous bytes of out.  The poles are held in
@@ -83,34 +83,52 @@ __global__ __launch_bounds__(256) void pink_phase1_kernel(DevTables T, PinkWork 
     }
 }
 
+// Phase 2: chunk c of a (sequence, pole) maps its incoming state s to a^len(c) s + agg[c], so the
+// chunk states follow from composing these affine maps along time -- an associative scan, done
+// here as a warp-shuffle scan: one warp per (sequence, pole), lanes = 32 consecutive chunks,
+// log2(32) compose steps (f_hi o f_lo = (a_hi a_lo, a_hi b_lo + b_hi)), the running state carried
+// from one block of 32 chunks to the next.  FP32: a^len = 2^(len log2 a) to ~1e-6 relative.
 __global__ void pink_phase2_kernel(DevTables T, float* state, PinkWork W, long long nt) {
     const long long S = static_cast<long long>(T.n_pix) * T.n_ch;
     const int np = T.n_pole;
-    for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < S * np;
-         idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const long long warp0 = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
+    const long long n_warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+    for (long long idx = warp0; idx < S * np; idx += n_warps) {          // warp-uniform
         const long long s = idx / np;
         const int j = static_cast<int>(idx - s * np);
         const int ch = static_cast<int>(s % T.n_ch);
-        const float la = log2f(T.pink_a[ch * np + j]);      // poles 0 < a < 1
-        const float aL = exp2f(static_cast<float>(W.L) * la);
+        const float la = log2f(T.pink_a[ch * np + j]);                  // poles 0 < a < 1
         float carry = state[idx];
-        // chunk states are loaded eight at a time, so the loads do not wait on the carry chain
-        constexpr int kAhead = 8;
-        for (int c0 = 0; c0 < W.C; c0 += kAhead) {
-            float agg[kAhead];
-#pragma unroll
-            for (int u = 0; u < kAhead; ++u)
-                agg[u] = c0 + u < W.C ? W.agg[(static_cast<long long>(c0 + u) * S + s) * np + j] : 0.f;
-#pragma unroll
-            for (int u = 0; u < kAhead; ++u) {
-                const int c = c0 + u;
-                if (c >= W.C) break;
-                const long long len = min(W.L, nt - c * W.L);
-                W.agg[(static_cast<long long>(c) * S + s) * np + j] = carry;
-                carry = fmaf(len == W.L ? aL : exp2f(static_cast<float>(len) * la), carry, agg[u]);
+        for (int c0 = 0; c0 < W.C; c0 += 32) {
+            const int c = c0 + lane;
+            const bool live = c < W.C;
+            float* slot = W.agg + (static_cast<long long>(live ? c : 0) * S + s) * np + j;
+            // this lane's chunk map; lanes past the last chunk carry the identity
+            float A = 1.f, B = 0.f;
+            if (live) {
+                A = exp2f(static_cast<float>(min(W.L, nt - static_cast<long long>(c) * W.L)) * la);
+                B = *slot;
             }
+            // inclusive scan: lane c ends with the composition of chunks c0 .. c
+            for (int d = 1; d < 32; d <<= 1) {
+                const float Ap = __shfl_up_sync(0xffffffffu, A, d);
+                const float Bp = __shfl_up_sync(0xffffffffu, B, d);
+                if (lane >= d) {
+                    B = fmaf(A, Bp, B);
+                    A *= Ap;
+                }
+            }
+            // chunk c's incoming state: the composition of chunks c0 .. c - 1 applied to the carry
+            float Ain = __shfl_up_sync(0xffffffffu, A, 1), Bin = __shfl_up_sync(0xffffffffu, B, 1);
+            if (lane == 0) {
+                Ain = 1.f;
+                Bin = 0.f;
+            }
+            if (live) *slot = fmaf(Ain, carry, Bin);
+            carry = fmaf(__shfl_sync(0xffffffffu, A, 31), carry, __shfl_sync(0xffffffffu, B, 31));
         }
-        state[idx] = carry;
+        if (lane == 0) state[idx] = carry;
     }
 }
 
@@ -244,7 +262,7 @@ static cudaError_t launch_pink_scan_np(const DevTables& T, float* state, const P
     pink_phase1_kernel<NP><<<static_cast<unsigned>(grid), block, 0, stream>>>(T, W, t0, nt);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    long long g2 = (S * T.n_pole + block - 1) / block;
+    long long g2 = (S * T.n_pole * 32 + block - 1) / block;      // one warp per (sequence, pole)
     if (g2 > 148LL * 32) g2 = 148LL * 32;
     pink_phase2_kernel<<<static_cast<unsigned>(g2), block, 0, stream>>>(T, state, W, nt);
     return cudaGetLastError();
