@@ -8,6 +8,8 @@
 // the linear convolution of I cos(el') with F on the cube's grid times A_p dphi dtheta, done as a
 // product of transforms on grids of twice the cube's size.  Every 2-D transform is two passes of
 // the batched row FFT with a tiled transpose after each.  Frequencies go through in batches.
+#include <mutex>
+#include <set>
 #include <utility>
 
 #include "gateau_internal.h"
@@ -188,26 +190,42 @@ cudaError_t launch_real_part(const float2* in, float* out, long long n, cudaStre
 
 // 2-D transform of B planes [n0][n1] held in a (b is scratch); the result is left in a.
 // One-pass transforms of whole vectors in shared memory: a block takes V vectors of n points
-// (V n <= 4096 complex values, plus an n / 2 twiddle table e^{sign 2 pi i m / n} from sincospif),
-// loads them in bit-reversed order, runs the log2 n decimation-in-time stages in place (pairs of
-// stages fused into radix-4 butterflies), and stores them back in place.  Vector v starts at
-// (v / per_plane) * plane_stride + (v % per_plane) * vstride and its points are kstride apart:
-// rows of a plane (kstride 1, contiguous) or its columns (kstride = row length; a block's V
-// columns are adjacent, so each point's loads are coalesced).  n, V and per_plane are powers of
-// two, passed as their logarithms: every index is a shift or a mask.
+// (V n <= 4096 complex values), loads them in bit-reversed order, runs the log2 n
+// decimation-in-time stages in place (pairs of stages fused into radix-4 butterflies), and stores
+// them back in place.  Vector v starts at (v / per_plane) * plane_stride + (v % per_plane) * vstride
+// and its points are kstride apart: rows of a plane (kstride 1, contiguous) or its columns
+// (kstride = row length; a block's V columns are adjacent, so each point's loads are coalesced).
+// n, V and per_plane are powers of two, passed as their logarithms: every index is a shift or a mask.
+//
+// Shared-memory layout.  A bank row holds 16 complex values, and a half-warp's 8-byte accesses are
+// conflict-free when they fall in 16 distinct slots (index mod 16).  The bit-reversed scatter, the
+// column loads (16 vectors at one point) and the early radix-4 stages (strides 1, 4, 16 in a
+// vector) would each put a half-warp on one or a few slots, so point k of vector vl is held at
+//   vl (n + 1) + swz(k),   swz(k) = k ^ (((k >> 4) * 5 ^ (k >> 8)) & 15):
+// the odd vector stride spreads adjacent vectors over the slots, and the XOR (a permutation of the
+// 16 slots of each bank row, chosen by its row index) spreads strided points; an exhaustive count
+// over every access pattern of the kernel gives no conflict for n = 64, 128, 256 and 4096 and at
+// most two-way for the other sides.  The twiddles sit after the data as one table per stage size,
+// tw[h + p] = e^{sign pi i p / h} (h a power of two, p < h), which a half-warp reads contiguously.
 constexpr int kFftSmemPoints = 4096;            // V n <= this many complex values per block
+__device__ __forceinline__ int fft_swz(int k) { return k ^ ((((k >> 4) * 5) ^ (k >> 8)) & 15); }
+
+size_t fft_smem_bytes(int n, int V) { return (static_cast<size_t>(V) * (n + 1) + n) * sizeof(float2); }
+
 template <int SIGN>
 __global__ void __launch_bounds__(kPrepThreads) fft_smem_kernel(float2* a, long long nvec, int log2n, long long kstride,
                                                                  int log2pp, long long vstride, long long plane_stride,
                                                                  int log2V) {
     const int n = 1 << log2n, V = 1 << log2V;
+    const int sv = n + 1;                        // vector stride in shared memory
     extern __shared__ float2 sm[];
-    float2* tw = sm + V * n;                     // e^{sign 2 pi i m / n}, m < n / 2
+    float2* tw = sm + V * sv;                    // tw[h + p] = e^{sign pi i p / h}, 1 <= h + p < n
     const bool columns = kstride != 1;
     const int nv = V * n;
-    for (int m = threadIdx.x; m < n / 2; m += blockDim.x) {
+    for (int m = 1 + threadIdx.x; m < n; m += blockDim.x) {
+        const int lh = 31 - __clz(m);
         float sn, cs;
-        sincospif(2.0f * static_cast<float>(m) / static_cast<float>(n), &sn, &cs);   // exact power-of-two divisor
+        sincospif(static_cast<float>(m - (1 << lh)) / static_cast<float>(1 << lh), &sn, &cs);   // exact divisor
         tw[m] = make_float2(cs, SIGN * sn);
     }
     const long long pp_mask = (1LL << log2pp) - 1;
@@ -218,7 +236,7 @@ __global__ void __launch_bounds__(kPrepThreads) fft_smem_kernel(float2* a, long 
             const int vl = columns ? (t & (V - 1)) : (t >> log2n), k = columns ? (t >> log2V) : (t & (n - 1));
             const long long v = v0 + vl;
             const int kr = static_cast<int>(__brev(static_cast<unsigned>(k)) >> (32 - log2n));
-            sm[vl * n + kr] = v < nvec ? a[base(v) + k * kstride] : make_float2(0.f, 0.f);
+            sm[vl * sv + fft_swz(kr)] = v < nvec ? a[base(v) + k * kstride] : make_float2(0.f, 0.f);
         }
         __syncthreads();
         // stages of half-size 2^lh; an odd count starts with one radix-2 stage, the rest go in
@@ -226,7 +244,8 @@ __global__ void __launch_bounds__(kPrepThreads) fft_smem_kernel(float2* a, long 
         int lh = 0;
         if (log2n & 1) {
             for (int t = threadIdx.x; t < nv / 2; t += blockDim.x) {
-                const int i0 = 2 * t, i1 = i0 + 1;                 // half 1: twiddle 1
+                const int vl = t >> (log2n - 1), j = t & (n / 2 - 1);
+                const int i0 = vl * sv + fft_swz(2 * j), i1 = vl * sv + fft_swz(2 * j + 1);   // half 1: twiddle 1
                 const float2 u = sm[i0], w = sm[i1];
                 sm[i0] = make_float2(u.x + w.x, u.y + w.y);
                 sm[i1] = make_float2(u.x - w.x, u.y - w.y);
@@ -239,9 +258,11 @@ __global__ void __launch_bounds__(kPrepThreads) fft_smem_kernel(float2* a, long 
             for (int t = threadIdx.x; t < nv / 4; t += blockDim.x) {
                 const int vl = t >> (log2n - 2), j = t & (n / 4 - 1);
                 const int pos = j & (h - 1), grp = j >> lh;
-                const int i0 = vl * n + (grp << (lh + 2)) + pos, i1 = i0 + h, i2 = i0 + 2 * h, i3 = i0 + 3 * h;
-                const float2 wa = tw[pos << (log2n - 1 - lh)];     // e^{sign pi i pos / h}
-                const float2 wb = tw[pos << (log2n - 2 - lh)];     // e^{sign pi i pos / (2 h)}
+                const int k0 = (grp << (lh + 2)) + pos, vb = vl * sv;
+                const int i0 = vb + fft_swz(k0), i1 = vb + fft_swz(k0 + h), i2 = vb + fft_swz(k0 + 2 * h),
+                          i3 = vb + fft_swz(k0 + 3 * h);
+                const float2 wa = tw[h + pos];                     // e^{sign pi i pos / h}
+                const float2 wb = tw[2 * h + pos];                 // e^{sign pi i pos / (2 h)}
                 const float2 x0 = sm[i0], x1 = sm[i1], x2 = sm[i2], x3 = sm[i3];
                 const float2 a1 = make_float2(x1.x * wa.x - x1.y * wa.y, x1.x * wa.y + x1.y * wa.x);
                 const float2 a3 = make_float2(x3.x * wa.x - x3.y * wa.y, x3.x * wa.y + x3.y * wa.x);
@@ -261,7 +282,7 @@ __global__ void __launch_bounds__(kPrepThreads) fft_smem_kernel(float2* a, long 
         for (int t = threadIdx.x; t < nv; t += blockDim.x) {
             const int vl = columns ? (t & (V - 1)) : (t >> log2n), k = columns ? (t >> log2V) : (t & (n - 1));
             const long long v = v0 + vl;
-            if (v < nvec) a[base(v) + k * kstride] = sm[vl * n + k];
+            if (v < nvec) a[base(v) + k * kstride] = sm[vl * sv + fft_swz(k)];
         }
         __syncthreads();
     }
@@ -281,7 +302,23 @@ static cudaError_t fft_smem(float2* a, long long nvec, int n, long long kstride,
     const int log2V = ilog2(V);
     long long grid = (nvec + V - 1) / V;
     if (grid > 148LL * 16) grid = 148LL * 16;
-    const size_t bytes = (static_cast<size_t>(V) * n + n / 2) * sizeof(float2);   // data + twiddles
+    const size_t bytes = fft_smem_bytes(n, V);    // data + twiddles: up to 64 KB + 16 B
+    {   // the opt-in above 48 KB of dynamic shared memory, once per device (both signs)
+        static std::mutex mu;
+        static std::set<int> done;
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        std::lock_guard<std::mutex> lk(mu);
+        if (!done.count(dev)) {
+            const int mx = static_cast<int>(fft_smem_bytes(kFftSmemPoints, 1));
+            e = cudaFuncSetAttribute(fft_smem_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(fft_smem_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+            if (e != cudaSuccess) return e;
+            done.insert(dev);
+        }
+    }
     if (sign < 0)
         fft_smem_kernel<-1><<<static_cast<unsigned>(grid), kPrepThreads, bytes, stream>>>(
             a, nvec, log2n, kstride, log2pp, vstride, plane_stride, log2V);
