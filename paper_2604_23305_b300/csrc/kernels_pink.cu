@@ -29,7 +29,7 @@ __device__ __forceinline__ float2 pole_pair(const float* x, int ch, int np, int 
 
 // Samples are visited in groups of the 4 that one Philox call serves (m = n >> 2).
 template <int NP>
-__global__ __launch_bounds__(256) void pink_phase1_kernel(DevTables T, PinkWork W, long long t0,
+__global__ __launch_bounds__(256, 3) void pink_phase1_kernel(DevTables T, PinkWork W, long long t0,
                                                           long long nt) {
     const long long S = static_cast<long long>(T.n_pix) * T.n_ch;
     const int np = T.n_pole;
@@ -136,7 +136,7 @@ __global__ void pink_phase2_kernel(DevTables T, float* state, PinkWork W, long l
 // with the next group's loads issued before the current group's recurrence.
 constexpr int kPinkPrefetch = 128;   // samples; ~40 MB of lines in flight over the GPU, inside L2
 template <int NP>
-__global__ __launch_bounds__(256) void pink_phase3_kernel(DevTables T, PinkWork W, long long t0,
+__global__ __launch_bounds__(256, 2) void pink_phase3_kernel(DevTables T, PinkWork W, long long t0,
                                                           long long nt, float* __restrict__ out) {
     const long long S = static_cast<long long>(T.n_pix) * T.n_ch;
     const int np = T.n_pole;
@@ -240,13 +240,33 @@ __global__ __launch_bounds__(256) void pink_phase3_kernel(DevTables T, PinkWork 
     }
 }
 
+// Chunking.  Every (chunk, sequence) is one thread of phases 1 and 3 doing L samples, so a phase
+// runs in rounds of the threads resident on the GPU (148 SMs x the blocks per SM that the launch
+// bounds pin: 3 of 256 threads for phase 1, 2 for phase 3), each round as long as one chunk.  C is
+// chosen to minimise (L + 16) x (rounds of phase 3 + 0.75 rounds of phase 1) (0.75: a phase-1
+// round's time against a phase-3 round's, measured; 16: a thread's fixed work -- poles, state --
+// in samples), i.e. to fill the last round of both phases: with 25 x 347 sequences, 18 chunks (a
+// fixed 148 K-thread target) left phase 3 three rounds with 18 of 296 blocks in the last; 26
+// chunks fill three rounds of phase 3 and two of phase 1 to 99 %.  At least 64 samples per chunk;
+// on a tie the fewer chunks (less state).
+constexpr int kPink1Blocks = 3, kPink3Blocks = 2;
 void pink_choose_chunks(long long nt, long long S, int& C, long long& L) {
-    const long long target = 148LL * 1024;           // enough independent scans to fill the GPU
-    long long c = (target + S - 1) / S;
-    const long long cmax = (nt + 63) / 64;            // at least 64 samples per chunk
-    if (c > cmax) c = cmax;
-    if (c < 1) c = 1;
-    L = ((nt + c - 1) / c + 3) / 4 * 4;
+    const long long cap1 = 148LL * kPink1Blocks * 256, cap3 = 148LL * kPink3Blocks * 256;
+    const long long cmax = (nt + 63) / 64 > 1 ? (nt + 63) / 64 : 1;
+    long long best_c = 1;
+    double best = -1.0;
+    for (long long c = 1; c <= cmax; ++c) {
+        const long long l = ((nt + c - 1) / c + 3) / 4 * 4;
+        const long long cc = (nt + l - 1) / l, U = cc * S;
+        const double cost = static_cast<double>(l + 16) * (static_cast<double>((U + cap3 - 1) / cap3) +
+                                                      0.75 * static_cast<double>((U + cap1 - 1) / cap1));
+        if (best < 0.0 || cost < best) {
+            best = cost;
+            best_c = c;
+        }
+        if (c * S > 16 * cap3) break;                 // past 16 rounds the last one costs under 7 %
+    }
+    L = ((nt + best_c - 1) / best_c + 3) / 4 * 4;
     C = static_cast<int>((nt + L - 1) / L);
 }
 

@@ -65,10 +65,20 @@ def test_noalloc_pink_matches_gateau_run_on_two_calls():
 
 
 def _default_chunks(nt, S):
-    """The allocating path's chunk count (148 x 1024 scans in flight, >= 64 samples a chunk)."""
-    c = min(-(-148 * 1024 // S), -(-nt // 64))
-    c = max(c, 1)
-    L_ = -(-(-(-nt // c)) // 4) * 4
+    """The allocating path's chunk count: the C (>= 64 samples a chunk) that minimises
+    (L + 16) x (rounds of phase 3 + 0.75 rounds of phase 1), with 148 x 2 x 256 and 148 x 3 x 256
+    threads resident per round."""
+    cap1, cap3 = 148 * 3 * 256, 148 * 2 * 256
+    best, best_c = None, 1
+    for c in range(1, max(-(-nt // 64), 1) + 1):
+        l_ = -(-(-(-nt // c)) // 4) * 4
+        u = -(-nt // l_) * S
+        cost = (l_ + 16) * (-(-u // cap3) + 0.75 * -(-u // cap1))
+        if best is None or cost < best:
+            best, best_c = cost, c
+        if c * S > 16 * cap3:
+            break
+    L_ = -(-(-(-nt // best_c)) // 4) * 4
     return -(-nt // L_)
 
 
@@ -79,7 +89,7 @@ def test_noalloc_pink_caps_its_chunks_and_allocates_nothing():
     scratch address and may load the library's module) leave the device's free memory unchanged."""
     assert torch.cuda.is_available()
     lib = L.lib()
-    nt = 1200
+    nt = 4096
     sc = W.scenario("ifu25", nt_total=nt)
     with_pink = Plan(sc, precision="fp32", white=False, pink=True)
     ref = with_pink.run(0, nt)
