@@ -184,13 +184,14 @@ __global__ __launch_bounds__(256, 2) void pink_phase3_kernel(DevTables T, PinkWo
                 for (int q = 0; q < 4; ++q) {
                     const float z = zq[q];
                     const float2 zz = make_float2(z, z);
-                    float2 y2 = make_float2(d * z, 0.f);
+                    float2 ya = make_float2(d * z, 0.f), yb = make_float2(0.f, 0.f);   // two short sum chains
 #pragma unroll
                     for (int h = 0; h < NH; ++h) {
                         st[h] = fma2(av[h], st[h], zz);
-                        y2 = fma2(rv[h], st[h], y2);
+                        if (h & 1) yb = fma2(rv[h], st[h], yb);
+                        else ya = fma2(rv[h], st[h], ya);
                     }
-                    const float y = y2.x + y2.y;
+                    const float y = (ya.x + ya.y) + (yb.x + yb.y);
                     o[q * stride] = cur4[q] + y;
                 }
                 n += 4;
@@ -220,13 +221,14 @@ __global__ __launch_bounds__(256, 2) void pink_phase3_kernel(DevTables T, PinkWo
                 if (q >= q0 && q < q1) {
                     const float z = f4_get(z4, q);
                     const float2 zz = make_float2(z, z);
-                    float2 y2 = make_float2(d * z, 0.f);
+                    float2 ya = make_float2(d * z, 0.f), yb = make_float2(0.f, 0.f);   // two short sum chains
 #pragma unroll
                     for (int h = 0; h < NH; ++h) {
                         st[h] = fma2(av[h], st[h], zz);
-                        y2 = fma2(rv[h], st[h], y2);
+                        if (h & 1) yb = fma2(rv[h], st[h], yb);
+                        else ya = fma2(rv[h], st[h], ya);
                     }
-                    const float y = y2.x + y2.y;
+                    const float y = (ya.x + ya.y) + (yb.x + yb.y);
                     o[(q - q0) * stride] = cur[q] + y;
                 }
             }
