@@ -370,7 +370,14 @@ def main():
     sc = W.scenario(args.workload, nt_total=args.nt, **replica_seeds(rank))
     nt = sc["nt_total"]
     per_step = W.detector_samples(sc)
+    # plan build, reported apart from the steps: inputs uploaded, then the FP64 plan (cascade collapse,
+    # filter matrices, reference spectrum, operand tiling, pink design) on the host and the device
+    torch.cuda.synchronize()
+    t_build = time.perf_counter()
     plan = Plan(sc, precision=args.precision, white=True, pink=True)
+    plan.prepare()
+    torch.cuda.synchronize()
+    build_ms = 1e3 * (time.perf_counter() - t_build)
     tune = plan.autotune(nt_sample=4096) if args.precision == "bf16x3" and not args.no_autotune else None
     out = torch.empty((nt, plan.n_pix, plan.n_ch), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -433,7 +440,11 @@ def main():
                              "ring_a": info.ring_a, "ring_b": info.ring_b},
                   "sample": "first 4096 samples of the scan", "ms": tune["ms"], "default_ms": tune["default_ms"],
                   "candidates": tune["candidates"]},
-              "staged_inputs": info.staged_inputs}
+              "staged_inputs": info.staged_inputs,
+              "plan_build": {"ms": build_ms, "device_bytes": int(info.device_bytes),
+                             "what": "inputs uploaded (screen, opacity table, cube) + plan preparation: FP64 cascade "
+                                     "collapse, filter matrices, reference spectrum, split-BF16 operand tiling, pink "
+                                     "filter design; not in the steps, autotuning not included"}}
 
     # plain FP32 path on the same workload and GPU (the baseline the fused path is measured against)
     if not args.skip_fp32 and args.precision == "bf16x3":
