@@ -137,6 +137,9 @@ struct gateau_plan {
     int n_pwv = 0;
     double pwv_min = 0, dpwv = 0;
     std::vector<double> tau_host;     // zenith opacity [n_pwv][n_freq] as set (FP64)
+    std::vector<float> table_raw;     // the table as last set (values before any conversion)
+    std::vector<float> tau_f;         // tau_host rounded to float (the device rows of a transmission table)
+    bool table_is_opacity = false;
     double screen_mean = 0;           // mean PWV of the screen (mm)
     std::vector<StageSpec> stages;
     int disp_kind = 0, n_ch = 0;
@@ -166,7 +169,7 @@ struct gateau_plan {
     double tune_ms = 0.0;            // the tuned configuration's time on the tuning sample (0: not measured)
 
     // device memory
-    DevBuf d_pix, d_cube, d_cube_raw, d_screen, d_tau, d_custom, d_c, d_HGQ, d_fusedB, d_pink, d_state, d_status;
+    DevBuf d_pix, d_cube, d_cube_raw, d_screen, d_tau, d_tau_rows, d_custom, d_c, d_HGQ, d_fusedB, d_pink, d_state, d_status;
     DevBuf d_tb, d_dip;              // skydip fit [2][n_ch] float for the epilogues; FP64 scratch of the fit
     DevBuf d_tk, d_tkz;              // Timmer-Koenig pink TOD [tk_n][n_pix][n_ch]; its FFT scratch
     DevBuf d_hw, d_cm;               // common-mode reduction: eta_filt w (FP64); log eta_z, S_j, PWV sum
@@ -203,7 +206,7 @@ struct gateau_plan {
 
     ~gateau_plan() {
         track_streams();
-        DevBuf* bufs[] = {&d_pix, &d_cube, &d_cube_raw, &d_screen, &d_tau, &d_custom, &d_c, &d_HGQ, &d_fusedB, &d_pink,
+        DevBuf* bufs[] = {&d_pix, &d_cube, &d_cube_raw, &d_screen, &d_tau, &d_tau_rows, &d_custom, &d_c, &d_HGQ, &d_fusedB, &d_pink,
                           &d_state, &d_status, &d_rows, &d_tiles, &d_X, &d_agg, &d_stage[0], &d_stage[1],
                           &d_tb, &d_dip, &d_tk, &d_tkz, &d_hw, &d_cm, &d_ref, &d_tune};
         for (DevBuf* b : bufs) b->release(mo);
@@ -232,7 +235,7 @@ cudaError_t grow(gateau_plan* p, DevBuf& b, size_t n) {
 }
 
 size_t device_bytes(const gateau_plan* p) {
-    const DevBuf* bufs[] = {&p->d_pix, &p->d_cube, &p->d_cube_raw, &p->d_screen, &p->d_tau, &p->d_custom, &p->d_c,
+    const DevBuf* bufs[] = {&p->d_pix, &p->d_cube, &p->d_cube_raw, &p->d_screen, &p->d_tau, &p->d_tau_rows, &p->d_custom, &p->d_c,
                             &p->d_HGQ, &p->d_fusedB, &p->d_pink, &p->d_state, &p->d_status, &p->d_rows,
                             &p->d_tiles, &p->d_X, &p->d_agg, &p->d_stage[0], &p->d_stage[1], &p->d_tb, &p->d_dip,
                             &p->d_tk, &p->d_tkz, &p->d_hw, &p->d_cm, &p->d_ref, &p->d_tune};
@@ -891,14 +894,23 @@ gateau_status gateau_set_atmosphere_screen(gateau_plan* p, const float* screen, 
     if (st != GATEAU_OK) return st;
     const size_t n = static_cast<size_t>(nx) * ny;
     GATEAU_CUDA(grow(p, p->d_screen, n * sizeof(float)));
+    // PWV values on the host: a PWV screen in host memory is read (and uploaded) in place; an EPL
+    // screen is converted first (Eq. 4), a device screen fetched
     std::vector<float> h;
-    st = fetch_floats(screen, n, mem, h);
-    if (st != GATEAU_OK) return st;
-    if (is_epl)
-        for (float& v : h) v = static_cast<float>(static_cast<double>(v) / 6.587 + pwv0_mm);   // Eq. 4
-    GATEAU_CUDA(cudaMemcpy(p->d_screen.p, h.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    const float* hv = screen;
+    if (is_epl || mem == GATEAU_MEM_DEVICE) {
+        st = fetch_floats(screen, n, mem, h);
+        if (st != GATEAU_OK) return st;
+        if (is_epl)
+            for (float& v : h) v = static_cast<float>(static_cast<double>(v) / 6.587 + pwv0_mm);   // Eq. 4
+        hv = h.data();
+    }
+    if (!is_epl && mem == GATEAU_MEM_DEVICE)
+        GATEAU_CUDA(cudaMemcpy(p->d_screen.p, screen, n * sizeof(float), cudaMemcpyDeviceToDevice));
+    else
+        GATEAU_CUDA(cudaMemcpy(p->d_screen.p, hv, n * sizeof(float), cudaMemcpyHostToDevice));
     double sum = 0.0;                  // the reference spectrum's PWV
-    for (float v : h) sum += v;
+    for (size_t i = 0; i < n; ++i) sum += hv[i];
     const double mean = sum / static_cast<double>(n);
     if (!p->has_screen || mean != p->screen_mean) {
         p->ref_dirty = true;
@@ -919,33 +931,53 @@ gateau_status gateau_set_atmosphere_table(gateau_plan* p, const float* table, in
     if (n_pwv < 2 || !(dpwv_mm > 0.0)) return fail(GATEAU_EINVAL, "table needs n_pwv >= 2 and dpwv > 0");
     gateau_status st = ensure_base(p);
     if (st != GATEAU_OK) return st;
-    const size_t nf = p->desc.n_freq, Kp = p->Kp;
+    const size_t nf = p->desc.n_freq, Kp = p->Kp, n = static_cast<size_t>(n_pwv) * nf;
     std::vector<float> h;
-    st = fetch_floats(table, static_cast<size_t>(n_pwv) * nf, mem, h);
-    if (st != GATEAU_OK) return st;
-    // Interleaved [n_pwv][2][Kp]: row 2j holds tau_j, row 2j+1 tau_{j+1} - tau_j (0 for the last j).
-    std::vector<double> tau(static_cast<size_t>(n_pwv) * nf);
-    for (int j = 0; j < n_pwv; ++j)
-        for (size_t k = 0; k < nf; ++k) {
-            double v = h[j * nf + k];
-            if (!is_opacity) v = -log(std::max(v, 1e-30));
-            if (!(v >= 0.0) || !std::isfinite(v)) return fail(GATEAU_EINVAL, "opacity must be finite and >= 0 (row %d, point %zu)", j, k);
-            tau[j * nf + k] = v;
+    const float* hv = table;                // the values on the host: in place, or fetched from the device
+    if (mem == GATEAU_MEM_DEVICE) {
+        st = fetch_floats(table, n, mem, h);
+        if (st != GATEAU_OK) return st;
+        hv = h.data();
+    }
+    // The FP64 opacities (the reference spectrum and the skydip read them) are formed again only
+    // when the values change; the device rows are uploaded on every call.
+    const bool same = p->has_table && p->n_pwv == n_pwv && p->table_is_opacity == (is_opacity != 0) &&
+                      p->table_raw.size() == n && memcmp(p->table_raw.data(), hv, n * sizeof(float)) == 0;
+    if (!same) {
+        std::vector<double> tau(n);
+        std::vector<float> tf(n);
+        for (int j = 0; j < n_pwv; ++j)
+            for (size_t k = 0; k < nf; ++k) {
+                double v = hv[j * nf + k];
+                if (!is_opacity) v = -log(std::max(v, 1e-30));
+                if (!(v >= 0.0) || !std::isfinite(v)) return fail(GATEAU_EINVAL, "opacity must be finite and >= 0 (row %d, point %zu)", j, k);
+                tau[j * nf + k] = v;
+                tf[j * nf + k] = static_cast<float>(v);
+            }
+        if (tau != p->tau_host) {
+            p->ref_dirty = true;
+            if (p->pink_auto) p->dirty = true;
         }
-    std::vector<float> padded(static_cast<size_t>(2 * n_pwv) * Kp, 0.f);
-    for (int j = 0; j < n_pwv; ++j)
-        for (size_t k = 0; k < nf; ++k) {
-            const float t0f = static_cast<float>(tau[j * nf + k]);
-            padded[(2 * j) * Kp + k] = t0f;
-            if (j + 1 < n_pwv) padded[(2 * j + 1) * Kp + k] = static_cast<float>(tau[(j + 1) * nf + k]) - t0f;
-        }
-    GATEAU_CUDA(grow(p, p->d_tau, padded.size() * sizeof(float)));
-    GATEAU_CUDA(cudaMemcpy(p->d_tau.p, padded.data(), padded.size() * sizeof(float), cudaMemcpyHostToDevice));
-    if (tau != p->tau_host) {
-        p->ref_dirty = true;
+        p->tau_host = std::move(tau);
+        p->tau_f = std::move(tf);
+        p->table_raw.assign(hv, hv + n);
+        p->table_is_opacity = is_opacity != 0;
+    }
+    if (pwv_min_mm != p->pwv_min || dpwv_mm != p->dpwv) {
+        p->ref_dirty = true;                 // the reference PWV's row moves
         if (p->pink_auto) p->dirty = true;
     }
-    p->tau_host = std::move(tau);
+    // Device: the rows tau_j as float (an opacity table is that already), then interleaved
+    // [n_pwv][2][Kp] -- row 2j tau_j, row 2j+1 tau_{j+1} - tau_j (0 for the last j) -- by a kernel.
+    GATEAU_CUDA(grow(p, p->d_tau_rows, n * sizeof(float)));
+    GATEAU_CUDA(grow(p, p->d_tau, static_cast<size_t>(2 * n_pwv) * Kp * sizeof(float)));
+    if (is_opacity)
+        GATEAU_CUDA(cudaMemcpy(p->d_tau_rows.p, table, n * sizeof(float), kind_of(mem)));
+    else
+        GATEAU_CUDA(cudaMemcpy(p->d_tau_rows.p, p->tau_f.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    GATEAU_CUDA(launch_tau_interleave(p->d_tau_rows.as<float>(), n_pwv, static_cast<int>(nf), static_cast<int>(Kp),
+                                      p->d_tau.as<float>(), nullptr));
+    GATEAU_CUDA(cudaStreamSynchronize(nullptr));
     p->n_pwv = n_pwv;
     p->pwv_min = pwv_min_mm;
     p->dpwv = dpwv_mm;
@@ -1365,7 +1397,7 @@ gateau_status gateau_plan_estimate_bytes(const gateau_plan_desc* d, int n_ch, in
     double b = n_pix * (6 * 8 + 4 * 4) + 64;                         // spaxel offsets and trig, status word
     b += 2.0 * n_az * n_el * Kp * 4;                                 // source cube as set + scaled copy
     b += static_cast<double>(nx) * ny * 4;                           // screen
-    b += 2.0 * n_pwv * Kp * 4;                                       // interleaved opacity table
+    b += 2.0 * n_pwv * Kp * 4 + static_cast<double>(n_pwv) * d->n_freq * 4;   // interleaved opacity table + its rows as set
     b += 5.0 * Kp * 4;                                               // c0, c1, c2 + per-stage tiling
     if (d->precision == GATEAU_PREC_FP32) {
         b += 3.0 * ((n_ch + 63) / 64 * 64) * Kp * 4;                 // FP32 H, G, Q

@@ -126,6 +126,7 @@ struct __align__(64) TensorMapBytes {
 // ---- kernel launchers (each enqueues on `stream`, returns cudaGetLastError) ----
 cudaError_t launch_row_setup(const DevTables& T, long long t0, long long nt, RowParams* rows,
                              TileInfo* tiles, cudaStream_t stream);
+cudaError_t launch_tau_interleave(const float* rows, int n_pwv, int nf, int Kp, float* out, cudaStream_t stream);
 cudaError_t launch_scale_cube(const float* raw, const float* c2, long long n_texels, int Kp, float* out,
                               cudaStream_t stream);
 cudaError_t launch_psd_fp32(const DevTables& T, const RowParams* rows, long long r0, long long nrows,

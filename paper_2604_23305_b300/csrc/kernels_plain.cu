@@ -305,6 +305,25 @@ cudaError_t launch_scale_cube(const float* raw, const float* c2, long long n_tex
     return cudaGetLastError();
 }
 
+// The opacity table as the kernels read it, [n_pwv][2][Kp]: row 2j holds tau_j, row 2j+1
+// tau_{j+1} - tau_j (float difference; 0 for the last j), zero past n_freq.  One block per output row.
+__global__ void tau_interleave_kernel(const float* __restrict__ rows, int n_pwv, int nf, int Kp, float* __restrict__ out) {
+    const int r = blockIdx.x, j = r >> 1;
+    const float* a = rows + static_cast<size_t>(j) * nf;
+    float* o = out + static_cast<size_t>(r) * Kp;
+    for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
+        float v = 0.f;
+        if (k < nf) v = (r & 1) ? (j + 1 < n_pwv ? a[nf + k] - a[k] : 0.f) : a[k];
+        o[k] = v;
+    }
+}
+
+cudaError_t launch_tau_interleave(const float* rows, int n_pwv, int nf, int Kp, float* out, cudaStream_t stream) {
+    if (n_pwv <= 0) return cudaSuccess;
+    tau_interleave_kernel<<<static_cast<unsigned>(2 * n_pwv), 256, 0, stream>>>(rows, n_pwv, nf, Kp, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_psd_fp32(const DevTables& T, const RowParams* rows, long long r0, long long nrows,
                             float* X, cudaStream_t stream) {
     if (nrows <= 0) return cudaSuccess;
