@@ -1311,15 +1311,17 @@ gateau_status gateau_run_host(gateau_plan* p, long long t0, long long nt, float*
         }
     }
     // Chunks of about 256 MB of output, double-buffered: chunk c runs on `s`
-    // while chunk c-1 is copied to the host on the copy stream.
+    // while chunk c-1 is copied to the host on the copy stream.  The copies are the
+    // slower side, so the first chunk is an eighth as long: the link starts sooner.
     const long long per_sample = static_cast<long long>(p->desc.n_pix) * std::max(p->n_ch, 1);
     const long long chunk = std::max<long long>(128, std::min<long long>(nt, (256LL << 20) / (4 * per_sample)) / 128 * 128);
+    const long long first = std::max<long long>(128, chunk / 8 / 128 * 128);
     const size_t chunk_bytes = static_cast<size_t>(std::min(chunk, nt)) * per_sample * sizeof(float);
     for (int i = 0; i < 2; ++i) GATEAU_CUDA(grow(p, p->d_stage[i], chunk_bytes));
     int c = 0;
-    for (long long a = 0; a < nt; a += chunk, ++c) {
+    for (long long a = 0, len = 0; a < nt; a += len, ++c) {
         const int b = c & 1;
-        const long long len = std::min(chunk, nt - a);
+        len = std::min(c == 0 ? first : chunk, nt - a);
         if (c >= 2) GATEAU_CUDA(cudaStreamWaitEvent(s, p->ev_copied[b], 0));
         st = enqueue_run(p, t0 + a, len, p->d_stage[b].as<float>(), s);
         if (st != GATEAU_OK) return st;
