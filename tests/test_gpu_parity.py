@@ -339,6 +339,14 @@ def _mut_wide_offsets(s):
     s["pix_offsets"] = W.grid_offsets(8, 120 * W.ARCSEC)
 
 
+def _mut_max_channels(s):
+    """The largest channel count the ABI takes (4096): 24 channel groups of the fused kernel on
+    independent CTAs, 64 blocks of the FP32 contraction."""
+    f_c = W.geometric_channels(221e9, 439e9, 4096)
+    s["dispersive"] = dict(kind="lorentzian", f_c=f_c, R=np.full(4096, 500.0), eta_peak=np.full(4096, 0.16))
+    s["noise"]["pink_alpha"] = np.resize(np.asarray(s["noise"]["pink_alpha"]), 4096)
+
+
 EDGE = {
     "64_spaxels_daisy": ("ifu25", 40001, 45, _mut_64_spaxels_daisy),
     "wide_offsets": ("ifu25", 120007, 37, _mut_wide_offsets),
@@ -350,6 +358,7 @@ EDGE = {
     "17_channels": ("single_pixel_small", 0, 257, _mut_few_channels),
     "1_channel_2_freqs": ("single_pixel_small", 0, 33, _mut_one_channel_two_freqs),
     "one_sample": ("ifu25", 77, 1, None),
+    "4096_channels": ("single_pixel_small", 3, 61, _mut_max_channels),
 }
 
 
@@ -366,6 +375,26 @@ def test_edge_cases(precision, case):
         assert flags & L.STATUS_PWV_CLAMPED
     else:
         assert flags == 0
+
+
+def test_empty_negative_and_oversized_runs_are_refused():
+    """nt = 0 (an empty run), nt < 0, t0 < 0, nt n_pix above 2^31 rows and a NULL output are
+    refused before anything is enqueued (EINVAL, the device untouched), and the plan then runs a
+    ragged 37-sample chunk that matches the oracle."""
+    sc, ref = oracle("ifu25", 0, 37)
+    p = Plan(sc, precision="bf16x3", white=False, pink=False)
+    out = torch.full((37, p.n_pix, p.n_ch), -1.0, dtype=torch.float32, device="cuda")
+    lib = L.lib()
+    ptr = out.data_ptr()
+    for t0, nt in ((0, 0), (0, -5), (-1, 10), (0, (1 << 31) // p.n_pix + 1)):
+        assert lib.gateau_run(p._h, t0, nt, ptr, None) == L.EINVAL, (t0, nt)
+    assert lib.gateau_run(p._h, 0, 37, None, None) == L.EINVAL
+    torch.cuda.synchronize()
+    assert bool((out == -1.0).all())                    # nothing was written
+    got = p.run(0, 37, out)
+    torch.cuda.synchronize()
+    assert p.status() == 0
+    assert rel_err(got.cpu().numpy().astype(np.float64), ref["p_kid"]) < SIGNAL_TOL["bf16x3"]
 
 
 # ---------------------------------------------------------------- full size, sampled
