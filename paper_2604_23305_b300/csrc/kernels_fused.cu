@@ -198,6 +198,11 @@ struct SmemPlan {
 
 constexpr size_t kBarReserve = 512;     // mbarriers, TMEM address slot and abort flag
 constexpr int kMaxHalf = 176;           // channels per group: 2 x 176 accumulator columns + parked normals
+// The reference spectrum's per-channel P_KID and N of a CTA's channel group sit in a static shared
+// array (1408 B, before the dynamic rings: the dynamic base is aligned up to 1024 B inside the slack
+// the plan reserves) in a single-job launch of shared tiles, where a CTA's group is fixed: the epilogue
+// reads them from shared memory instead of issuing global loads between its TMEM reads and its stores.
+// (Global loads there cost ~0.9 ms per ifu25 launch, measured with clock64 counters.)
 
 // Ring depths for channel groups of n_half: the deepest B ring up to ring_b (2..kMaxRingB) whose
 // stages leave room for at least as many A slots (at most 8, whole pairs).
@@ -612,6 +617,16 @@ __global__ void __launch_bounds__(kThreads, 1) fused_bf16x3_kernel(const __grid_
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    __shared__ __align__(16) float ref_s[2 * kMaxHalf];           // [2][kMaxHalf]: P_KID, N of the group
+    if constexpr (kShare && NJ == 1) {
+        const FusedJob& J0 = L.job[0];
+        const int cb = static_cast<int>(rank) * J0.F.n_half;       // this CTA's channel group
+        for (int c = threadIdx.x; c < kMaxHalf; c += blockDim.x) {
+            const bool in = c < J0.F.n_half && cb + c < J0.T.n_ch;
+            ref_s[c] = in ? J0.T.ref_pk[cb + c] : 0.f;
+            ref_s[kMaxHalf + c] = in ? J0.T.ref_n[cb + c] : 0.f;
+        }
+    }
     tc_fence_before();
     __syncthreads();
     if (share) cluster_sync_all();              // the peer's barriers exist before any remote arrival
@@ -745,9 +760,14 @@ __global__ void __launch_bounds__(kThreads, 1) fused_bf16x3_kernel(const __grid_
                 ka = *reinterpret_cast<const float2*>(T.tb_a + chq);   // padded arrays, chq even
                 kb = *reinterpret_cast<const float2*>(T.tb_b + chq);
             }
-            // the reference spectrum's P_KID and N (padded to n_ch_pad, chq even)
+            // the reference spectrum's P_KID and N (padded to n_ch_pad, chq even): from shared memory
+            // in a single-job launch of shared tiles, else from global memory
             float2 rpk = make_float2(0.f, 0.f), rn = make_float2(0.f, 0.f);
-            if (chq < T.n_ch) {
+            if constexpr (kShare && NJ == 1) {
+                const int cl = chq - ch_base;                            // even, < kMaxHalf
+                rpk = *reinterpret_cast<const float2*>(ref_s + cl);
+                rn = *reinterpret_cast<const float2*>(ref_s + kMaxHalf + cl);
+            } else if (chq < T.n_ch) {
                 rpk = *reinterpret_cast<const float2*>(T.ref_pk + chq);
                 rn = *reinterpret_cast<const float2*>(T.ref_n + chq);
             }
