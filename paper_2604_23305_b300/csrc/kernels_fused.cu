@@ -771,23 +771,27 @@ __global__ void __launch_bounds__(kThreads, 1) fused_bf16x3_kernel(const __grid_
                 rpk = *reinterpret_cast<const float2*>(T.ref_pk + chq);
                 rn = *reinterpret_cast<const float2*>(T.ref_n + chq);
             }
+            // The four outputs (rows R0, R0 + 8 x channels chq, chq + 1) are formed without branches,
+            // so their dependent chains (the square root on the special-function unit among them)
+            // overlap; only the stores are guarded (a ragged last tile, channels past n_ch).
+            float v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int rr = k >> 1, e = k & 1;
+                const float2 zz = rr ? z1 : z0;
+                const float pk = fmaf(T.kb1e9, __uint_as_float(sr[k]), e ? rpk.y : rpk.x);
+                // k_B outside the root: k_B^2 times N would leave the normal float range
+                const float nn = __uint_as_float(nr[k]) + (e ? rn.y : rn.x);
+                const float sigma = T.kB * sqrt_approx(T.noise_scale * fmaxf(nn, 0.f));
+                v[k] = fmaf(e ? ka.y : ka.x, fmaf(sigma, e ? zz.y : zz.x, pk), e ? kb.y : kb.x);
+            }
 #pragma unroll
             for (int rr = 0; rr < 2; ++rr) {
                 const int R = R0 + 8 * rr;
-                if (R >= nrows) continue;
-                float* orow = obase + R * S_row;
-                const float2 zz = rr ? z1 : z0;
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int ch = chq + e;
-                    if (ch < T.n_ch) {
-                        const int k = 2 * rr + e;
-                        const float pk = fmaf(T.kb1e9, __uint_as_float(sr[k]), e ? rpk.y : rpk.x);
-                        // k_B outside the root: k_B^2 times N would leave the normal float range
-                        const float nn = __uint_as_float(nr[k]) + (e ? rn.y : rn.x);
-                        const float sigma = T.kB * sqrt_approx(T.noise_scale * fmaxf(nn, 0.f));
-                        orow[ch] = fmaf(e ? ka.y : ka.x, fmaf(sigma, e ? zz.y : zz.x, pk), e ? kb.y : kb.x);
-                    }
+                if (R < nrows) {
+                    float* orow = obase + R * S_row;
+                    if (chq < T.n_ch) orow[chq] = v[2 * rr];
+                    if (chq + 1 < T.n_ch) orow[chq + 1] = v[2 * rr + 1];
                 }
             }
         };
