@@ -288,6 +288,99 @@ __global__ void __launch_bounds__(kPrepThreads) fft_smem_kernel(float2* a, long 
     }
 }
 
+// 256-point transforms (the planes of a 128 x 128 cube) in two radix-16 passes, 256 = 16 x 16, with
+// the 16-point DFTs in registers.  Point p = j + 16 m of a vector.  Pass 1, thread (vector, j):
+// Z_j[k1] = sum_m x[j + 16 m] W16^(m k1), times the twiddle W256^(j k1), into shared memory; pass 2,
+// thread (vector, k1): X[k1 + 16 k2] = sum_j Z_j[k1] W16^(j k2), with W_N = e^{sign 2 pi i / N}.  One
+// shared-memory round trip per transform (the general kernel takes one per pair of radix-2 stages),
+// in the layout [vector][k1][j] with strides 273 and 17 complex values: both passes, in either
+// thread order (rows: j fastest; columns: the vector fastest), touch 16 distinct bank slots per
+// half-warp.  Loads and stores to global memory stay coalesced as in the general kernel.
+constexpr int kF16VS = 273, kF16RS = 17;
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// In place: x[c] <- sum_a x[a] W4^(a c) over (a0, a1, a2, a3), W4 = sign i.
+template <int SIGN>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+    const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
+    const float2 t = make_float2(-SIGN * d13.y, SIGN * d13.x);           // W4 (x1 - x3)
+    a0 = cadd(s02, s13);
+    a1 = cadd(d02, t);
+    a2 = csub(s02, s13);
+    a3 = csub(d02, t);
+}
+
+// In place, natural order in and out: x[k] <- sum_m x[m] W16^(m k), as m = 4a + b, k = c + 4d:
+// radix-4 over a for each b, the twiddles W16^(b c), radix-4 over b for each c.
+template <int SIGN>
+__device__ __forceinline__ void dft16(float2 (&x)[16]) {
+    constexpr float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, h = 0.70710678118654752f;   // cos, sin pi/8; cos pi/4
+#pragma unroll
+    for (int b = 0; b < 4; ++b) dft4<SIGN>(x[b], x[4 + b], x[8 + b], x[12 + b]);   // y_b[c] sits at x[4c + b]
+    // W16^e = (cos(pi e / 8), sign sin(pi e / 8)) for e = b c
+    const float2 w1 = make_float2(c1, SIGN * s1), w2 = make_float2(h, SIGN * h), w3 = make_float2(s1, SIGN * c1);
+    const float2 w4 = make_float2(0.f, SIGN * 1.f), w6 = make_float2(-h, SIGN * h), w9 = make_float2(-c1, -SIGN * s1);
+    x[4 + 1] = cmul(x[4 + 1], w1);    // c = 1: b = 1, 2, 3 -> e = 1, 2, 3
+    x[4 + 2] = cmul(x[4 + 2], w2);
+    x[4 + 3] = cmul(x[4 + 3], w3);
+    x[8 + 1] = cmul(x[8 + 1], w2);    // c = 2: e = 2, 4, 6
+    x[8 + 2] = cmul(x[8 + 2], w4);
+    x[8 + 3] = cmul(x[8 + 3], w6);
+    x[12 + 1] = cmul(x[12 + 1], w3);  // c = 3: e = 3, 6, 9
+    x[12 + 2] = cmul(x[12 + 2], w6);
+    x[12 + 3] = cmul(x[12 + 3], w9);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) dft4<SIGN>(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);   // X[c + 4d] at x[4c + d]
+    float2 y[16];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) y[c + 4 * d] = x[4 * c + d];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[k] = y[k];
+}
+
+template <int SIGN>
+__global__ void __launch_bounds__(kPrepThreads, 2) fft256_kernel(float2* a, long long nvec, long long kstride, int log2pp,
+                                                               long long vstride, long long plane_stride) {
+    __shared__ float2 sm[16 * kF16VS];
+    __shared__ float2 tw[256];                       // W256^e
+    const bool columns = kstride != 1;
+    for (int e = threadIdx.x; e < 256; e += blockDim.x) {
+        float sn, cs;
+        sincospif(static_cast<float>(e) / 128.0f, &sn, &cs);   // exact power-of-two divisor
+        tw[e] = make_float2(cs, SIGN * sn);
+    }
+    const int t = threadIdx.x;                       // 256 threads: 16 vectors x 16
+    const int vl = columns ? (t & 15) : (t >> 4), q = columns ? (t >> 4) : (t & 15);   // q: j in pass 1, k1 in pass 2
+    const long long pp_mask = (1LL << log2pp) - 1;
+    __syncthreads();
+    for (long long v0 = static_cast<long long>(blockIdx.x) * 16; v0 < nvec; v0 += static_cast<long long>(gridDim.x) * 16) {
+        const long long v = v0 + vl;
+        const bool live = v < nvec;
+        float2* base = a + (live ? (v >> log2pp) * plane_stride + (v & pp_mask) * vstride : 0);
+        float2 x[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) x[m] = live ? base[(q + 16 * m) * kstride] : make_float2(0.f, 0.f);
+        dft16<SIGN>(x);                              // Z_j[k1] at x[k1], j = q
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) sm[vl * kF16VS + k1 * kF16RS + q] = cmul(x[k1], tw[(q * k1) & 255]);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) x[j] = sm[vl * kF16VS + q * kF16RS + j];   // k1 = q
+        dft16<SIGN>(x);                              // X[k1 + 16 k2] at x[k2]
+        if (live)
+#pragma unroll
+            for (int k2 = 0; k2 < 16; ++k2) base[(q + 16 * k2) * kstride] = x[k2];
+        __syncthreads();                             // the next group's stores reuse sm
+    }
+}
+
 static int ilog2(long long x) {
     int l = 0;
     while ((1LL << l) < x) ++l;
@@ -297,6 +390,18 @@ static int ilog2(long long x) {
 static cudaError_t fft_smem(float2* a, long long nvec, int n, long long kstride, long long per_plane,
                             long long vstride, long long plane_stride, int sign, cudaStream_t stream) {
     if (n <= 1) return cudaSuccess;                // a one-point transform is the identity
+    if (n == 256) {                                // two radix-16 passes in registers
+        long long grid = (nvec + 15) / 16;
+        if (grid > 148LL * 16) grid = 148LL * 16;
+        const int log2pp = ilog2(per_plane);
+        if (sign < 0)
+            fft256_kernel<-1><<<static_cast<unsigned>(grid), kPrepThreads, 0, stream>>>(a, nvec, kstride, log2pp,
+                                                                                      vstride, plane_stride);
+        else
+            fft256_kernel<1><<<static_cast<unsigned>(grid), kPrepThreads, 0, stream>>>(a, nvec, kstride, log2pp,
+                                                                                     vstride, plane_stride);
+        return cudaGetLastError();
+    }
     const int log2n = ilog2(n), log2pp = ilog2(per_plane);
     const int V = n >= kFftSmemPoints ? 1 : (kFftSmemPoints / n < 16 ? kFftSmemPoints / n : 16);
     const int log2V = ilog2(V);
