@@ -208,7 +208,7 @@ def cpu_baseline(sc, budget_s=12.0, workload="ifu25"):
 
 
 def serving_leg(n_requests: int, seed: int = 2, budget_bytes: float = 120e9, max_active: int = 16,
-                chunk_samples: int = 4096, max_chunk_bytes: int = 32 << 20, builders: int = 6,
+                chunk_samples: int = 32768, max_chunk_bytes: int = 256 << 20, builders: int = 6,
                 shared_launches: bool = False):
     """The serving workload: n_requests simulations (hexagonal IFUs of 1-61 spaxels, 100-347
     channels, 1000-6000 spectral points, 10 s - 10 min at 160 Hz) through the native server,
