@@ -206,7 +206,8 @@ cudaError_t launch_common_mode(const float* tb, float* out, const RowParams* row
 
 // Preprocessing (Sect. 2.2, Eqs. 1-3), kernels_prep.cu.  Planes are complex [B][n0][n1] with n0, n1
 // powers of two.  fft2_planes: 2-D transform in place in a (b scratch).  launch_beam_planes: the far
-// field F of B frequencies nu[0..B) (device FP64) on an na x ne offset grid, peak-normalised, into F.
+// field F of B frequencies nu[0..B) (device FP64) on an na x ne offset grid into F, peak-normalised
+// (normalise) or with its peak in peak[b] only.
 // launch_convolve_source_batch: Eq. 1 for frequencies f0 .. f0+B-1 of the cube I [n_az][n_el][n_freq]
 // into P (same layout), with scratch planes K, S, work of B (2 n_az)(2 n_el) each and peak [B].
 // launch_smooth_screen: the screen [ny][nx] smoothed by the normalised footprint, scratch planes of
@@ -214,7 +215,8 @@ cudaError_t launch_common_mode(const float* tb, float* out, const RowParams* row
 cudaError_t fft2_planes(float2* a, float2* b, int B, int n0, int n1, int sign, cudaStream_t stream);
 cudaError_t launch_real_part(const float2* in, float* out, long long n, cudaStream_t stream);
 cudaError_t launch_beam_planes(const double* nu, int B, int na, int ne, double d_az, double d_el, double R,
-                               double t_edge_db, float2* F, float2* work, float* peak, cudaStream_t stream);
+                               double t_edge_db, float2* F, float2* work, float* peak, cudaStream_t stream,
+                               bool normalise = true);
 cudaError_t launch_convolve_source_batch(const float* I, float* P, const double* nu, int B, int f0, int n_freq,
                                          int n_az, int n_el, double el0, double d_az, double d_el, double R,
                                          double t_edge_db, float2* K, float2* S, float2* work, float* peak,

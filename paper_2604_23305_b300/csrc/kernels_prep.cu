@@ -34,15 +34,18 @@ __device__ __forceinline__ double illumination(double r, double R, double t_edge
 // A_b(l_q, m_p) for plane b = frequency nu[b].
 __global__ void aperture_kernel(float2* __restrict__ A, const double* __restrict__ nu, int na, int ne, float inv_laz,
                                 float inv_lel, double R, float t_edge_20) {
-    // plane b = blockIdx.y; its wavelength over the aperture radius formed once per thread (FP64),
-    // the direction cosines in FP32 (the plane is FP32, and l, m stay far below float's limits)
+    // plane b = blockIdx.y; its wavelength over the aperture radius formed once per block (FP64
+    // divisions run at 1/64 of the FP32 rate on this part: once per thread they were most of the
+    // kernel), the direction cosines in FP32 (the plane is FP32, and l, m stay far below float's limits)
     const int b = blockIdx.y;
-    const float lam_R = static_cast<float>(kC / nu[b] / R);
-    const long long plane = static_cast<long long>(na) * ne;
-    float2* Ab = A + b * plane;
-    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < plane;
-         t += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int q = static_cast<int>(t / ne), p = static_cast<int>(t - static_cast<long long>(q) * ne);
+    __shared__ float s_lam_R;
+    if (threadIdx.x == 0) s_lam_R = static_cast<float>(kC / nu[b] / R);
+    __syncthreads();
+    const float lam_R = s_lam_R;
+    const int plane = na * ne;                       // <= 4096 x 4096: 32-bit indices within a plane
+    float2* Ab = A + static_cast<long long>(b) * plane;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < plane; t += gridDim.x * blockDim.x) {
+        const int q = t / ne, p = t - q * ne;
         const float l = static_cast<float>(q < na / 2 ? q : q - na) * inv_laz;
         const float m = static_cast<float>(p < ne / 2 ? p : p - ne) * inv_lel;
         const float rr = lam_R * hypotf(l, m);
@@ -94,29 +97,56 @@ __global__ void power_max_kernel(float2* __restrict__ E, long long plane, float*
     }
 }
 
-__global__ void scale_planes_kernel(float2* __restrict__ E, long long plane, int B, const float* __restrict__ peak) {
-    const long long total = plane * B;
-    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
+// E /= its plane's maximum: blockIdx.y = plane, blockIdx.x strides over it.
+__global__ void scale_planes_kernel(float2* __restrict__ E, long long plane, const float* __restrict__ peak) {
+    float2* e = E + blockIdx.y * plane;
+    const float s = 1.f / peak[blockIdx.y];
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < plane;
          t += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const float s = 1.f / peak[t / plane];
-        E[t] = make_float2(E[t].x * s, E[t].y * s);
+        const float2 v = e[t];
+        e[t] = make_float2(v.x * s, v.y * s);
     }
 }
 
 // Source planes: S[b][a][e] = I[a][e][f0 + b] cos(el0 + e d_el) inside the cube, 0 in the padding.
+// The cube runs along frequency and the planes along elevation, so a block moves a 32 (elevation)
+// x 32 (frequency) tile of row a through shared memory: both the reads and the writes are coalesced.
+// grid (padded elevation / 32, frequencies of the batch / 32, padded azimuth), block 32 x 8.
 __global__ void source_planes_kernel(const float* __restrict__ I, float2* __restrict__ S, int B, int f0, int n_freq,
                                      int n_az, int n_el, double el0, double d_el) {
+    __shared__ float tile[32][33];                   // [elevation][frequency]
     const int na = 2 * n_az, ne = 2 * n_el;
-    const long long total = static_cast<long long>(B) * na * ne;
-    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
+    const int e0 = blockIdx.x * 32, b0 = blockIdx.y * 32, a = blockIdx.z;
+    const bool in_cube = a < n_az;
+    if (in_cube) {
+        for (int y = threadIdx.y; y < 32; y += 8) {
+            const int e = e0 + y, b = b0 + threadIdx.x;
+            float v = 0.f;
+            if (e < n_el && b < B)
+                v = I[(static_cast<size_t>(a) * n_el + e) * n_freq + f0 + b] * cosf(static_cast<float>(el0 + e * d_el));
+            tile[y][threadIdx.x] = v;
+        }
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        const int b = b0 + y, e = e0 + threadIdx.x;
+        if (b < B && e < ne)
+            S[(static_cast<size_t>(b) * na + a) * ne + e] = make_float2(in_cube && e < n_el ? tile[threadIdx.x][y] : 0.f, 0.f);
+    }
+}
+
+// S *= K / peak of its plane (the beam's normalisation, applied here: its transform is linear):
+// blockIdx.y = plane, blockIdx.x strides over it.
+__global__ void multiply_scaled_kernel(float2* __restrict__ S, const float2* __restrict__ K, long long plane,
+                                       const float* __restrict__ peak) {
+    float2* s = S + blockIdx.y * plane;
+    const float2* k = K + blockIdx.y * plane;
+    const float r = 1.f / peak[blockIdx.y];
+    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < plane;
          t += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int b = static_cast<int>(t / (static_cast<long long>(na) * ne));
-        const int rem = static_cast<int>(t - static_cast<long long>(b) * na * ne);
-        const int a = rem / ne, e = rem - a * ne;
-        float v = 0.f;
-        if (a < n_az && e < n_el)
-            v = I[(static_cast<size_t>(a) * n_el + e) * n_freq + f0 + b] * static_cast<float>(cos(el0 + e * d_el));
-        S[t] = make_float2(v, 0.f);
+        const float2 a = s[t], kb = k[t];
+        const float2 b = make_float2(kb.x * r, kb.y * r);
+        s[t] = make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
     }
 }
 
@@ -128,17 +158,23 @@ __global__ void multiply_kernel(float2* __restrict__ S, const float2* __restrict
     }
 }
 
-// P[a][e][f0 + b] = scale Re S[b][a][e] for the cube's cells.
+// P[a][e][f0 + b] = scale Re S[b][a][e] for the cube's cells, through 32 (elevation) x 32
+// (frequency) tiles of row a in shared memory (coalesced on both sides).
+// grid (n_el / 32, frequencies of the batch / 32, n_az), block 32 x 8.
 __global__ void gather_planes_kernel(const float2* __restrict__ S, float* __restrict__ P, int B, int f0, int n_freq,
                                      int n_az, int n_el, float scale) {
+    __shared__ float tile[32][33];                   // [frequency][elevation]
     const int ne = 2 * n_el;
     const long long plane = static_cast<long long>(2 * n_az) * ne;
-    const long long total = static_cast<long long>(B) * n_az * n_el;
-    for (long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; t < total;
-         t += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int cell = static_cast<int>(t / B), b = static_cast<int>(t - static_cast<long long>(cell) * B);
-        const int a = cell / n_el, e = cell - a * n_el;
-        P[static_cast<size_t>(cell) * n_freq + f0 + b] = scale * S[b * plane + static_cast<long long>(a) * ne + e].x;
+    const int e0 = blockIdx.x * 32, b0 = blockIdx.y * 32, a = blockIdx.z;
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        const int b = b0 + y, e = e0 + threadIdx.x;
+        tile[y][threadIdx.x] = (b < B && e < n_el) ? S[b * plane + static_cast<long long>(a) * ne + e].x : 0.f;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        const int e = e0 + y, b = b0 + threadIdx.x;
+        if (e < n_el && b < B) P[(static_cast<size_t>(a) * n_el + e) * n_freq + f0 + b] = scale * tile[threadIdx.x][y];
     }
 }
 
@@ -461,7 +497,8 @@ cudaError_t fft2_planes(float2* a, float2* b, int B, int n0, int n1, int sign, c
 }
 
 cudaError_t launch_beam_planes(const double* nu, int B, int na, int ne, double d_az, double d_el, double R,
-                               double t_edge_db, float2* F, float2* work, float* peak, cudaStream_t stream) {
+                               double t_edge_db, float2* F, float2* work, float* peak, cudaStream_t stream,
+                               bool normalise) {
     const long long plane = static_cast<long long>(na) * ne;
     const unsigned bx = static_cast<unsigned>((plane + kPrepThreads - 1) / kPrepThreads < 64 ? (plane + kPrepThreads - 1) / kPrepThreads : 64);
     aperture_kernel<<<dim3(bx, B), kPrepThreads, 0, stream>>>(F, nu, na, ne, static_cast<float>(1.0 / (na * d_az)),
@@ -472,7 +509,7 @@ cudaError_t launch_beam_planes(const double* nu, int B, int na, int ne, double d
     e = cudaMemsetAsync(peak, 0, static_cast<size_t>(B) * sizeof(float), stream);
     if (e != cudaSuccess) return e;
     power_max_kernel<<<dim3(bx, B), kPrepThreads, 0, stream>>>(F, plane, peak);
-    scale_planes_kernel<<<grid_for(plane * B), kPrepThreads, 0, stream>>>(F, plane, B, peak);
+    if (normalise) scale_planes_kernel<<<dim3(bx, B), kPrepThreads, 0, stream>>>(F, plane, peak);
     return cudaGetLastError();
 }
 
@@ -481,21 +518,27 @@ cudaError_t launch_convolve_source_batch(const float* I, float* P, const double*
                                          double t_edge_db, float2* K, float2* S, float2* work, float* peak,
                                          cudaStream_t stream) {
     const int na = 2 * n_az, ne = 2 * n_el;
-    const long long n = static_cast<long long>(B) * na * ne;
-    cudaError_t e = launch_beam_planes(nu + f0, B, na, ne, d_az, d_el, R, t_edge_db, K, work, peak, stream);
+    if (na > 65535) return cudaErrorInvalidValue;   // the plane kernels put the padded azimuth rows on grid z
+    // |F|^2 left unnormalised: its peak divides the product below
+    cudaError_t e = launch_beam_planes(nu + f0, B, na, ne, d_az, d_el, R, t_edge_db, K, work, peak, stream, false);
     if (e != cudaSuccess) return e;
     e = fft2_planes(K, work, B, na, ne, -1, stream);                      // transform of the beam kernel
     if (e != cudaSuccess) return e;
-    source_planes_kernel<<<grid_for(n), kPrepThreads, 0, stream>>>(I, S, B, f0, n_freq, n_az, n_el, el0, d_el);
+    source_planes_kernel<<<dim3((ne + 31) / 32, (B + 31) / 32, na), dim3(32, 8), 0, stream>>>(I, S, B, f0, n_freq, n_az,
+                                                                                          n_el, el0, d_el);
     e = fft2_planes(S, work, B, na, ne, -1, stream);
     if (e != cudaSuccess) return e;
-    multiply_kernel<<<grid_for(n), kPrepThreads, 0, stream>>>(S, K, n);
+    {
+        const long long plane = static_cast<long long>(na) * ne;
+        const unsigned bx = static_cast<unsigned>((plane + kPrepThreads - 1) / kPrepThreads < 64 ? (plane + kPrepThreads - 1) / kPrepThreads : 64);
+        multiply_scaled_kernel<<<dim3(bx, B), kPrepThreads, 0, stream>>>(S, K, plane, peak);
+    }
     e = fft2_planes(S, work, B, na, ne, +1, stream);
     if (e != cudaSuccess) return e;
     const double A_p = 3.141592653589793 * R * R;
     const float scale = static_cast<float>(A_p * d_az * d_el / (static_cast<double>(na) * ne));   // with 1/(na ne)
-    gather_planes_kernel<<<grid_for(static_cast<long long>(B) * n_az * n_el), kPrepThreads, 0, stream>>>(
-        S, P, B, f0, n_freq, n_az, n_el, scale);
+    gather_planes_kernel<<<dim3((n_el + 31) / 32, (B + 31) / 32, n_az), dim3(32, 8), 0, stream>>>(S, P, B, f0, n_freq,
+                                                                                                n_az, n_el, scale);
     return cudaGetLastError();
 }
 
