@@ -381,9 +381,12 @@ __device__ __forceinline__ void dft16(float2 (&x)[16]) {
     for (int k = 0; k < 16; ++k) x[k] = y[k];
 }
 
+// Pruned: only the first 16 n_in16 points of a vector are read (the rest are zero) and only the first
+// 16 n_out16 outputs are written (the rest are not needed).
 template <int SIGN>
 __global__ void __launch_bounds__(kPrepThreads, 2) fft256_kernel(float2* a, long long nvec, long long kstride, int log2pp,
-                                                               long long vstride, long long plane_stride) {
+                                                               long long vstride, long long plane_stride, int n_in16,
+                                                               int n_out16) {
     __shared__ float2 sm[16 * kF16VS];
     __shared__ float2 tw[256];                       // W256^e
     const bool columns = kstride != 1;
@@ -402,7 +405,7 @@ __global__ void __launch_bounds__(kPrepThreads, 2) fft256_kernel(float2* a, long
         float2* base = a + (live ? (v >> log2pp) * plane_stride + (v & pp_mask) * vstride : 0);
         float2 x[16];
 #pragma unroll
-        for (int m = 0; m < 16; ++m) x[m] = live ? base[(q + 16 * m) * kstride] : make_float2(0.f, 0.f);
+        for (int m = 0; m < 16; ++m) x[m] = live && m < n_in16 ? base[(q + 16 * m) * kstride] : make_float2(0.f, 0.f);
         dft16<SIGN>(x);                              // Z_j[k1] at x[k1], j = q
 #pragma unroll
         for (int k1 = 0; k1 < 16; ++k1) sm[vl * kF16VS + k1 * kF16RS + q] = cmul(x[k1], tw[(q * k1) & 255]);
@@ -412,7 +415,8 @@ __global__ void __launch_bounds__(kPrepThreads, 2) fft256_kernel(float2* a, long
         dft16<SIGN>(x);                              // X[k1 + 16 k2] at x[k2]
         if (live)
 #pragma unroll
-            for (int k2 = 0; k2 < 16; ++k2) base[(q + 16 * k2) * kstride] = x[k2];
+            for (int k2 = 0; k2 < 16; ++k2)
+                if (k2 < n_out16) base[(q + 16 * k2) * kstride] = x[k2];
         __syncthreads();                             // the next group's stores reuse sm
     }
 }
@@ -423,19 +427,22 @@ static int ilog2(long long x) {
     return l;
 }
 
+// n_in / n_out (256-point path only; 0 = n): points read and outputs written per vector.
 static cudaError_t fft_smem(float2* a, long long nvec, int n, long long kstride, long long per_plane,
-                            long long vstride, long long plane_stride, int sign, cudaStream_t stream) {
+                            long long vstride, long long plane_stride, int sign, cudaStream_t stream, int n_in = 0,
+                            int n_out = 0) {
     if (n <= 1) return cudaSuccess;                // a one-point transform is the identity
     if (n == 256) {                                // two radix-16 passes in registers
         long long grid = (nvec + 15) / 16;
         if (grid > 148LL * 16) grid = 148LL * 16;
         const int log2pp = ilog2(per_plane);
+        const int in16 = (n_in > 0 ? n_in : n) / 16, out16 = (n_out > 0 ? n_out : n) / 16;
         if (sign < 0)
             fft256_kernel<-1><<<static_cast<unsigned>(grid), kPrepThreads, 0, stream>>>(a, nvec, kstride, log2pp,
-                                                                                      vstride, plane_stride);
+                                                                                      vstride, plane_stride, in16, out16);
         else
             fft256_kernel<1><<<static_cast<unsigned>(grid), kPrepThreads, 0, stream>>>(a, nvec, kstride, log2pp,
-                                                                                     vstride, plane_stride);
+                                                                                     vstride, plane_stride, in16, out16);
         return cudaGetLastError();
     }
     const int log2n = ilog2(n), log2pp = ilog2(per_plane);
@@ -496,6 +503,23 @@ cudaError_t fft2_planes(float2* a, float2* b, int B, int n0, int n1, int sign, c
     return cudaGetLastError();
 }
 
+// 2-D transform of B planes [n0][n1] of which only rows < in0 and columns < in1 hold non-zero values,
+// keeping only outputs in rows < out0 and columns < out1 (the rest of the planes are left as they
+// were).  256 x 256 planes with multiples of 16: the row pass runs over rows < in0 only, reading their
+// first in1 points and writing their first out1 outputs, and the column pass over columns < out1,
+// reading rows < in0 and writing rows < out0.  Other sizes: the full transform.
+static cudaError_t fft2_planes_pruned(float2* a, float2* b, int B, int n0, int n1, int sign, int in0, int in1,
+                                      int out0, int out1, cudaStream_t stream) {
+    const bool ok = n0 == 256 && n1 == 256 && in0 > 0 && in1 > 0 && out0 > 0 && out1 > 0 && in0 <= 256 && in1 <= 256 &&
+                    out0 <= 256 && out1 <= 256 && (in0 & (in0 - 1)) == 0 && (out1 & (out1 - 1)) == 0 && in1 % 16 == 0 &&
+                    out0 % 16 == 0;
+    if (!ok) return fft2_planes(a, b, B, n0, n1, sign, stream);
+    const long long plane = 256LL * 256;
+    cudaError_t e = fft_smem(a, static_cast<long long>(B) * in0, 256, 1, in0, 256, plane, sign, stream, in1, out1);   // rows
+    if (e != cudaSuccess) return e;
+    return fft_smem(a, static_cast<long long>(B) * out1, 256, 256, out1, 1, plane, sign, stream, in0, out0);       // columns
+}
+
 cudaError_t launch_beam_planes(const double* nu, int B, int na, int ne, double d_az, double d_el, double R,
                                double t_edge_db, float2* F, float2* work, float* peak, cudaStream_t stream,
                                bool normalise) {
@@ -526,14 +550,14 @@ cudaError_t launch_convolve_source_batch(const float* I, float* P, const double*
     if (e != cudaSuccess) return e;
     source_planes_kernel<<<dim3((ne + 31) / 32, (B + 31) / 32, na), dim3(32, 8), 0, stream>>>(I, S, B, f0, n_freq, n_az,
                                                                                           n_el, el0, d_el);
-    e = fft2_planes(S, work, B, na, ne, -1, stream);
+    e = fft2_planes_pruned(S, work, B, na, ne, -1, n_az, n_el, na, ne, stream);    // the cube fills a quarter of the plane
     if (e != cudaSuccess) return e;
     {
         const long long plane = static_cast<long long>(na) * ne;
         const unsigned bx = static_cast<unsigned>((plane + kPrepThreads - 1) / kPrepThreads < 64 ? (plane + kPrepThreads - 1) / kPrepThreads : 64);
         multiply_scaled_kernel<<<dim3(bx, B), kPrepThreads, 0, stream>>>(S, K, plane, peak);
     }
-    e = fft2_planes(S, work, B, na, ne, +1, stream);
+    e = fft2_planes_pruned(S, work, B, na, ne, +1, na, ne, n_az, n_el, stream);   // only the cube's cells are gathered
     if (e != cudaSuccess) return e;
     const double A_p = 3.141592653589793 * R * R;
     const float scale = static_cast<float>(A_p * d_az * d_el / (static_cast<double>(na) * ne));   // with 1/(na ne)
