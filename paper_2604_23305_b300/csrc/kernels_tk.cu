@@ -33,29 +33,40 @@ __global__ void __launch_bounds__(kTkThreads) tk_spectrum_kernel(float2* __restr
                                                                  uint32_t k0, uint32_t k1) {
     const long long n_pairs = static_cast<long long>(n_pix) * P;
     const float fstep = static_cast<float>(f_sample / M);
-    for (long long pair = blockIdx.y; pair < n_pairs; pair += gridDim.y) {
+    __shared__ float s_amp[2], s_ha[2];
+    for (long long pair = blockIdx.y; pair < n_pairs; pair += gridDim.y) {      // uniform over the block
         const int i = static_cast<int>(pair / P), c = static_cast<int>(pair - static_cast<long long>(i) * P);
+        // the pair's amplitudes, once per block: FP64 square roots and divisions run at 1/64 of the FP32
+        // rate here, and formed by every thread they were most of the kernel
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            const int ch = 2 * c + threadIdx.x;
+            const bool live = ch < n_ch && A[ch] > 0.0;
+            s_amp[threadIdx.x] = live ? static_cast<float>(sqrt(M * f_sample * A[ch] / 4.0) / M) : 0.f;
+            s_ha[threadIdx.x] = live ? -0.5f * static_cast<float>(alpha[ch]) : 0.f;
+        }
+        __syncthreads();
         float amp[2], ha[2];
         bool on[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            const int ch = 2 * c + e;
-            on[e] = ch < n_ch && A[ch] > 0.0;
-            amp[e] = on[e] ? static_cast<float>(sqrt(M * f_sample * A[ch] / 4.0) / M) : 0.f;
-            ha[e] = on[e] ? -0.5f * static_cast<float>(alpha[ch]) : 0.f;
+            amp[e] = s_amp[e];
+            ha[e] = s_ha[e];
+            on[e] = amp[e] > 0.f;
         }
         float2* z = Z + pair * M;
-        for (long long q = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; 2 * q <= M / 2;
-             q += static_cast<long long>(gridDim.x) * blockDim.x) {
+        // bins j = 2q, 2q + 1 <= M / 2 < 2^30: 32-bit indices (a 64-bit integer's conversion to float
+        // runs on the FP64 pipe, which it had kept ~70 % busy)
+        for (int q = blockIdx.x * blockDim.x + threadIdx.x; 2 * q <= M / 2; q += gridDim.x * blockDim.x) {
             uint4 x[2];
 #pragma unroll
             for (int e = 0; e < 2; ++e)
-                x[e] = philox4x32_10(make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32),
-                                                static_cast<uint32_t>(i), 0x40000000u | static_cast<uint32_t>(2 * c + e)),
+                x[e] = philox4x32_10(make_uint4(static_cast<uint32_t>(q), 0u, static_cast<uint32_t>(i),
+                                                0x40000000u | static_cast<uint32_t>(2 * c + e)),
                                      k0, k1);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const long long j = 2 * q + h;
+                const int j = 2 * q + h;
                 if (j > M / 2) break;
                 const float lf = j > 0 ? log2f(static_cast<float>(j) * fstep) : 0.f;
                 float2 cf[2];
