@@ -56,7 +56,10 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms from before the warm-up steps (the
+    tool takes a moment to start) and kept for the timed region: mark(True) / mark(False) bracket it,
+    and summary() uses the samples taken between the two marks (those within 0.3 s of the window when
+    it holds none, e.g. a timed region shorter than one sampling period)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -65,12 +68,16 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines: list[str] = []
+        self.lines: list[tuple[float, str]] = []
+        self.window = [None, None]
+
+    def mark(self, start: bool):
+        self.window[0 if start else 1] = time.monotonic()
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -80,7 +87,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -93,7 +100,16 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
+        t0, t1 = self.window
+        lines = []
+        if t0 is not None and t1 is not None:
+            for pad in (0.1, 0.3):                   # the window, then a sampling period or three around it
+                lines = [ln for t, ln in self.lines if t0 - (pad - 0.1) <= t <= t1 + pad]
+                if lines:
+                    break
+        if not lines:
+            lines = [ln for _, ln in self.lines]
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -321,7 +337,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="ifu25")
@@ -381,6 +397,7 @@ def main():
     tune = plan.autotune(nt_sample=4096) if args.precision == "bf16x3" and not args.no_autotune else None
     out = torch.empty((nt, plan.n_pix, plan.n_ch), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    clk = ClockSampler(local).__enter__()          # running before the warm-up; the timed region is marked
     for _ in range(max(args.warmup, 3)):
         plan.run(0, nt, out)
     torch.cuda.synchronize()
@@ -389,15 +406,17 @@ def main():
     plan.set_timing(True)
 
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        barrier()
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            plan.run(0, nt, out)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
+    barrier()
+    torch.cuda.synchronize()
+    clk.mark(True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.run(0, nt, out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk.mark(False)
+    barrier()
+    clk.__exit__(None, None, None)
     elapsed_s = ranks_max(ev0.elapsed_time(ev1) / 1e3)
     phase_ms, runs, launches = plan.get_timing()
     plan.set_timing(False)
