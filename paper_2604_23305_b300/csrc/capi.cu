@@ -262,26 +262,21 @@ gateau_status fetch_floats(const float* src, size_t n, int mem, std::vector<floa
     return GATEAU_OK;
 }
 
-// Contraction operands in device units (w in GHz, X in kelvin), FP64 [n_ch][Kp]:
+// Contraction operands in device units (w in GHz, X in kelvin), FP64 per (channel, point):
 //   H = eta w_GHz;  G = H gamma (nu_GHz + beta);  Q = eta^2 w_GHz
-// with gamma = h 1e9 / k_B and beta = 2 Delta_Al / (eta_pb h 1e9) (Sect. 2.5 Eq. 16, Sect. 2.6 Eq. 17).
-void filter_operands(const gateau_plan* p, std::vector<double>& H, std::vector<double>& G, std::vector<double>& Q) {
+// with gamma = h 1e9 / k_B and beta = 2 Delta_Al / (eta_pb h 1e9) (Sect. 2.5 Eq. 16, Sect. 2.6 Eq. 17),
+// formed per element where they are used (the reference integrals, the FP32 operands, the split-BF16
+// tiles) rather than stored as three [n_ch][Kp] FP64 matrices.
+FilterOperands filter_operands(const gateau_plan* p) {
     const gateau_plan_desc& d = p->desc;
-    const int nf = d.n_freq, Kp = p->Kp, n_ch = p->n_ch;
-    const double gamma = kH * 1e9 / kKB;
-    const double beta = 2.0 * d.delta_al_J / (d.eta_pb * kH * 1e9);
-    H.assign(static_cast<size_t>(n_ch) * Kp, 0.0);
-    G.assign(H.size(), 0.0);
-    Q.assign(H.size(), 0.0);
-    for (int c = 0; c < n_ch; ++c)
-        for (int k = 0; k < nf; ++k) {
-            const double eta = p->eta_filt[static_cast<size_t>(c) * nf + k];
-            const double wg = p->w[k] * 1e-9;
-            const size_t i = static_cast<size_t>(c) * Kp + k;
-            H[i] = eta * wg;
-            G[i] = H[i] * gamma * (p->nu[k] * 1e-9 + beta);
-            Q[i] = eta * eta * wg;
-        }
+    FilterOperands f;
+    f.eta = p->eta_filt.data();
+    f.w = p->w.data();
+    f.nu = p->nu.data();
+    f.nf = d.n_freq;
+    f.gamma = kH * 1e9 / kKB;
+    f.beta = 2.0 * d.delta_al_J / (d.eta_pb * kH * 1e9);
+    return f;
 }
 
 // Transmission of the reference sky per point: exp(-csc(theta_0) tau_z) at the screen's mean PWV,
@@ -337,17 +332,17 @@ gateau_status build_reference(gateau_plan* p) {
     GATEAU_CUDA(cudaMemcpy(p->d_c.as<float>() + 3 * static_cast<size_t>(Kp), cv.data(), cv.size() * sizeof(float),
                            cudaMemcpyHostToDevice));
 
-    std::vector<double> H, G, Q;
-    filter_operands(p, H, G, Q);
+    FilterOperands fo = filter_operands(p);
+    fo.xref = xref.data();
     const int stride = p->n_ch_pad;
     std::vector<float> rv(2 * static_cast<size_t>(stride), 0.f);
     for (int c = 0; c < n_ch; ++c) {
         double s_ref = 0.0, n_ref = 0.0;
         for (int k = 0; k < nf; ++k) {
-            const size_t i = static_cast<size_t>(c) * Kp + k;
-            s_ref += H[i] * xref[k];
-            n_ref += (G[i] + Q[i] * xref[k]) * xref[k];
-            G[i] += 2.0 * Q[i] * xref[k];
+            double h, g, q;
+            fo.at(c, k, h, g, q);
+            s_ref += h * xref[k];
+            n_ref += (g + q * xref[k]) * xref[k];
         }
         rv[c] = static_cast<float>(kKB * 1e9 * s_ref);     // P_KID of the reference (W)
         rv[stride + c] = static_cast<float>(n_ref);
@@ -358,11 +353,15 @@ gateau_status build_reference(gateau_plan* p) {
     if (d.precision == GATEAU_PREC_FP32) {
         std::vector<float> hgq(3 * static_cast<size_t>(p->n_ch_pad) * Kp, 0.f);
         const size_t mat = static_cast<size_t>(p->n_ch_pad) * Kp;
-        for (size_t i = 0; i < H.size(); ++i) {
-            hgq[i] = static_cast<float>(H[i]);
-            hgq[mat + i] = static_cast<float>(G[i]);
-            hgq[2 * mat + i] = static_cast<float>(Q[i]);
-        }
+        for (int c = 0; c < n_ch; ++c)
+            for (int k = 0; k < nf; ++k) {
+                double h, g, q;
+                fo.at(c, k, h, g, q);
+                const size_t i = static_cast<size_t>(c) * Kp + k;
+                hgq[i] = static_cast<float>(h);
+                hgq[mat + i] = static_cast<float>(fo.gprime(g, q, k));
+                hgq[2 * mat + i] = static_cast<float>(q);
+            }
         GATEAU_CUDA(grow(p, p->d_HGQ, hgq.size() * sizeof(float)));
         GATEAU_CUDA(cudaMemcpy(p->d_HGQ.p, hgq.data(), hgq.size() * sizeof(float), cudaMemcpyHostToDevice));
     } else {
@@ -375,8 +374,7 @@ gateau_status build_reference(gateau_plan* p) {
         p->fused.ring_b = p->tile_ring_b > 0 ? p->tile_ring_b : kDefaultRingB;
         std::vector<uint16_t> tiled;
         size_t stage_elems = 0;
-        fused_tile_operands(H.data(), G.data(), Q.data(), n_ch, Kp, p->fused.n_half, p->fused.n_groups, tiled,
-                            stage_elems);
+        fused_tile_operands(fo, n_ch, Kp, p->fused.n_half, p->fused.n_groups, tiled, stage_elems);
         GATEAU_CUDA(grow(p, p->d_fusedB, tiled.size() * sizeof(uint16_t)));
         GATEAU_CUDA(cudaMemcpy(p->d_fusedB.p, tiled.data(), tiled.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
         p->fused.B = p->d_fusedB.as<uint16_t>();

@@ -158,8 +158,27 @@ bool fused_encode_input_maps(const float* tau, int n_pwv, const float* cube, int
                              TensorMapBytes* tm_tau, TensorMapBytes* tm_cube, std::string& err);
 size_t fused_smem_bytes();
 int fused_kstage();
-void fused_tile_operands(const double* H, const double* G, const double* Q, int n_ch, int Kp,
-                         int n_half, int n_groups, std::vector<uint16_t>& out, size_t& stage_elems);
+// The contraction operands of channel c at point k (k < n_freq; zero past it), in device units (w in
+// GHz, X in kelvin): H = eta w, G = H gamma (nu_GHz + beta), Q = eta^2 w (Sect. 2.5 Eq. 16, Sect. 2.6
+// Eq. 17), and G' = G + 2 Q X_ref for the reference-spectrum difference.
+struct FilterOperands {
+    const double* eta = nullptr;      // [n_ch][nf] filter transmission
+    const double* w = nullptr;        // [nf] trapezoid weights (Hz)
+    const double* nu = nullptr;       // [nf] frequencies (Hz)
+    const double* xref = nullptr;     // [nf] reference spectrum (kelvin), for G'
+    int nf = 0;
+    double gamma = 0, beta = 0;
+    void at(int c, int k, double& h, double& g, double& q) const {
+        const double e = eta[static_cast<size_t>(c) * nf + k];
+        const double wg = w[k] * 1e-9;
+        h = e * wg;
+        g = h * gamma * (nu[k] * 1e-9 + beta);
+        q = e * e * wg;
+    }
+    double gprime(double g, double q, int k) const { return g + 2.0 * q * xref[k]; }
+};
+void fused_tile_operands(const FilterOperands& f, int n_ch, int Kp, int n_half, int n_groups,
+                         std::vector<uint16_t>& out, size_t& stage_elems);
 
 // Pink noise: chunked linear-recurrence scan adding into out.
 struct PinkWork {

@@ -112,9 +112,9 @@ float bf16_to_f32(uint16_t h) {
     return f;
 }
 
-// Host: lay out H_hi, H_lo, G, Q (FP64 [n_ch][Kp]) as [group][kstage][matrix][block].
-void fused_tile_operands(const double* H, const double* G, const double* Q, int n_ch, int Kp, int n_half,
-                         int n_groups, std::vector<uint16_t>& out, size_t& stage_elems) {
+// Host: lay out H_hi, H_lo, G', Q (formed per element, FP64) as [group][kstage][matrix][block].
+void fused_tile_operands(const FilterOperands& f, int n_ch, int Kp, int n_half, int n_groups,
+                         std::vector<uint16_t>& out, size_t& stage_elems) {
     const int n_ks = Kp / kKStage;
     const size_t mat_elems = static_cast<size_t>(n_half) * kKStage;
     stage_elems = mat_elems * kBMats;
@@ -126,14 +126,17 @@ void fused_tile_operands(const double* H, const double* G, const double* Q, int 
                 const int ch = g * n_half + r;
                 if (ch >= n_ch) continue;
                 for (int kk = 0; kk < kKStage; ++kk) {
-                    const size_t src = static_cast<size_t>(ch) * Kp + ks * kKStage + kk;
+                    const int k = ks * kKStage + kk;
+                    if (k >= f.nf) continue;                 // zero past the grid (out is zeroed)
+                    double h, g, q;
+                    f.at(ch, k, h, g, q);
                     const size_t off = core_offset(r, kk, n_half) / 2;
-                    const uint16_t hhi = f32_to_bf16_rn(static_cast<float>(H[src]));
-                    const double res = H[src] - static_cast<double>(bf16_to_f32(hhi));
+                    const uint16_t hhi = f32_to_bf16_rn(static_cast<float>(h));
+                    const double res = h - static_cast<double>(bf16_to_f32(hhi));
                     blk[0 * mat_elems + off] = hhi;
                     blk[1 * mat_elems + off] = f32_to_bf16_rn(static_cast<float>(res));
-                    blk[2 * mat_elems + off] = f32_to_bf16_rn(static_cast<float>(G[src]));
-                    blk[3 * mat_elems + off] = f32_to_bf16_rn(static_cast<float>(Q[src]));
+                    blk[2 * mat_elems + off] = f32_to_bf16_rn(static_cast<float>(f.gprime(g, q, k)));
+                    blk[3 * mat_elems + off] = f32_to_bf16_rn(static_cast<float>(q));
                 }
             }
         }
