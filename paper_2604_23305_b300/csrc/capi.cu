@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <map>
 #include <memory>
@@ -136,10 +137,8 @@ struct gateau_plan {
     double pitch = 0;
     int n_pwv = 0;
     double pwv_min = 0, dpwv = 0;
-    std::vector<double> tau_host;     // zenith opacity [n_pwv][n_freq] as set (FP64)
-    std::vector<float> table_raw;     // the table as last set (values before any conversion)
-    std::vector<float> tau_f;         // tau_host rounded to float (the device rows of a transmission table)
-    bool table_is_opacity = false;
+    std::vector<float> table_raw;     // the table [n_pwv][n_freq] as last set (values before any conversion)
+    bool table_is_opacity = false;    // table_raw holds opacities (else transmissions, tau = -ln t)
     double screen_mean = 0;           // mean PWV of the screen (mm)
     std::vector<StageSpec> stages;
     int disp_kind = 0, n_ch = 0;
@@ -280,12 +279,19 @@ FilterOperands filter_operands(const gateau_plan* p) {
 }
 
 // Transmission of the reference sky per point: exp(-csc(theta_0) tau_z) at the screen's mean PWV,
+// Zenith opacity of table entry i in FP64: the value itself, or -ln t of a transmission t (floored
+// at 1e-30, so that a zero transmission stays finite).
+static double table_opacity(const gateau_plan* p, size_t i) {
+    const double v = p->table_raw[i];
+    return p->table_is_opacity ? v : -log(std::max(v, 1e-30));
+}
+
 // tau_z interpolated linearly between the table's PWV rows (clamped to the table), Eq. 10 at the
 // scan's base elevation.  1 before the table is set.
 std::vector<double> reference_transmission(const gateau_plan* p) {
     const int nf = p->desc.n_freq;
     std::vector<double> eref(nf, 1.0);
-    if (p->tau_host.empty() || p->n_pwv < 2) return eref;
+    if (p->table_raw.empty() || p->n_pwv < 2) return eref;
     double u = (p->screen_mean - p->pwv_min) / p->dpwv;
     u = std::min(std::max(u, 0.0), static_cast<double>(p->n_pwv - 1));
     const int j = std::min(static_cast<int>(floor(u)), p->n_pwv - 2);
@@ -293,8 +299,8 @@ std::vector<double> reference_transmission(const gateau_plan* p) {
     const double sn = sin(p->theta0);
     const double csc = sn > 1e-3 ? 1.0 / sn : 1.0;      // elevations below 0.06 deg: a zenith reference
     for (int k = 0; k < nf; ++k) {
-        const double tau = (1.0 - f) * p->tau_host[static_cast<size_t>(j) * nf + k] +
-                           f * p->tau_host[static_cast<size_t>(j + 1) * nf + k];
+        const double tau = (1.0 - f) * table_opacity(p, static_cast<size_t>(j) * nf + k) +
+                           f * table_opacity(p, static_cast<size_t>(j + 1) * nf + k);
         eref[k] = exp(-csc * tau);
     }
     return eref;
@@ -937,27 +943,30 @@ gateau_status gateau_set_atmosphere_table(gateau_plan* p, const float* table, in
         if (st != GATEAU_OK) return st;
         hv = h.data();
     }
-    // The FP64 opacities (the reference spectrum and the skydip read them) are formed again only
-    // when the values change; the device rows are uploaded on every call.
+    // The table is checked and kept (the reference spectrum converts the two rows it reads to FP64)
+    // only when its values change; the device rows are uploaded on every call.
     const bool same = p->has_table && p->n_pwv == n_pwv && p->table_is_opacity == (is_opacity != 0) &&
                       p->table_raw.size() == n && memcmp(p->table_raw.data(), hv, n * sizeof(float)) == 0;
+    std::vector<float> tf;                  // a transmission table's opacities rounded to float
     if (!same) {
-        std::vector<double> tau(n);
-        std::vector<float> tf(n);
-        for (int j = 0; j < n_pwv; ++j)
-            for (size_t k = 0; k < nf; ++k) {
-                double v = hv[j * nf + k];
-                if (!is_opacity) v = -log(std::max(v, 1e-30));
-                if (!(v >= 0.0) || !std::isfinite(v)) return fail(GATEAU_EINVAL, "opacity must be finite and >= 0 (row %d, point %zu)", j, k);
-                tau[j * nf + k] = v;
-                tf[j * nf + k] = static_cast<float>(v);
+        if (is_opacity) {
+            bool ok = true;                 // NaN fails v >= 0, +inf fails v <= FLT_MAX
+            for (size_t i = 0; i < n; ++i) ok &= (hv[i] >= 0.f) & (hv[i] <= FLT_MAX);
+            if (!ok)
+                for (size_t i = 0; i < n; ++i)
+                    if (!(hv[i] >= 0.f && hv[i] <= FLT_MAX))
+                        return fail(GATEAU_EINVAL, "opacity must be finite and >= 0 (row %zu, point %zu)", i / nf, i % nf);
+        } else {
+            tf.resize(n);
+            for (size_t i = 0; i < n; ++i) {
+                const double v = -log(std::max(static_cast<double>(hv[i]), 1e-30));
+                if (!(v >= 0.0) || !std::isfinite(v))
+                    return fail(GATEAU_EINVAL, "opacity must be finite and >= 0 (row %zu, point %zu)", i / nf, i % nf);
+                tf[i] = static_cast<float>(v);
             }
-        if (tau != p->tau_host) {
-            p->ref_dirty = true;
-            if (p->pink_auto) p->dirty = true;
         }
-        p->tau_host = std::move(tau);
-        p->tau_f = std::move(tf);
+        p->ref_dirty = true;
+        if (p->pink_auto) p->dirty = true;
         p->table_raw.assign(hv, hv + n);
         p->table_is_opacity = is_opacity != 0;
     }
@@ -969,10 +978,15 @@ gateau_status gateau_set_atmosphere_table(gateau_plan* p, const float* table, in
     // [n_pwv][2][Kp] -- row 2j tau_j, row 2j+1 tau_{j+1} - tau_j (0 for the last j) -- by a kernel.
     GATEAU_CUDA(grow(p, p->d_tau_rows, n * sizeof(float)));
     GATEAU_CUDA(grow(p, p->d_tau, static_cast<size_t>(2 * n_pwv) * Kp * sizeof(float)));
-    if (is_opacity)
+    if (is_opacity) {
         GATEAU_CUDA(cudaMemcpy(p->d_tau_rows.p, table, n * sizeof(float), kind_of(mem)));
-    else
-        GATEAU_CUDA(cudaMemcpy(p->d_tau_rows.p, p->tau_f.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    } else {
+        if (same) {                         // unchanged transmissions: round the kept table again
+            tf.resize(n);
+            for (size_t i = 0; i < n; ++i) tf[i] = static_cast<float>(table_opacity(p, i));
+        }
+        GATEAU_CUDA(cudaMemcpy(p->d_tau_rows.p, tf.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    }
     GATEAU_CUDA(launch_tau_interleave(p->d_tau_rows.as<float>(), n_pwv, static_cast<int>(nf), static_cast<int>(Kp),
                                       p->d_tau.as<float>(), nullptr));
     GATEAU_CUDA(cudaStreamSynchronize(nullptr));

@@ -397,6 +397,39 @@ def test_empty_negative_and_oversized_runs_are_refused():
     assert rel_err(got.cpu().numpy().astype(np.float64), ref["p_kid"]) < SIGNAL_TOL["bf16x3"]
 
 
+def test_table_reset_matches_fresh_plan():
+    """Setting the opacity table again on a prepared plan: the same values leave the output as it
+    was; changed opacities, and the same opacities given as transmissions (tau = -ln t, Eq. 10),
+    give what a fresh plan built on that table gives, bit for bit, and setting the first table
+    back restores the first output."""
+    sc = W.scenario("single_pixel_small", nt_total=400)
+    atm = sc["atmosphere"]
+
+    def run(plan):
+        out = plan.run(0, 400)
+        torch.cuda.synchronize()
+        return out.clone()
+
+    p = Plan(sc, precision="bf16x3", white=False, pink=False)
+    first = run(p)
+    p.set_table(dict(atm, table=atm["table"].copy()))
+    assert torch.equal(run(p), first)
+    changed = dict(atm, table=(atm["table"] * 1.25).astype(np.float32))
+    trans = dict(atm, table=np.exp(-atm["table"].astype(np.float64)).astype(np.float32), table_is_opacity=False)
+    for new_atm in (changed, trans):
+        p.set_table(new_atm)
+        got = run(p)
+        fresh = Plan(dict(sc, atmosphere=new_atm), precision="bf16x3", white=False, pink=False)
+        want = run(fresh)
+        fresh.close()
+        assert torch.equal(got, want)
+        if new_atm is changed:
+            assert not torch.equal(got, first)
+    p.set_table(atm)
+    assert torch.equal(run(p), first)
+    assert p.status() & ~L.STATUS_PWV_CLAMPED == 0
+
+
 # ---------------------------------------------------------------- full size, sampled
 
 def test_full_size_ifu_sampled_rows():
