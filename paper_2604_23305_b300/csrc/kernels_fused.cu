@@ -327,6 +327,37 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
+// Non-blocking test of a phase (mbarrier.test_wait: the thread is never suspended).
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded polling wait for the single-thread roles on the kernel's critical chain (the MMA issuer
+// waiting for stage data, the filter-operand loader waiting for a free B slot): polling with
+// test_wait sees a completed phase sooner than a thread suspended in try_wait is resumed, which
+// measured ~0.7 ms less per ifu25 launch.  Budget and abort as in mbar_wait.
+__device__ __forceinline__ bool mbar_wait_poll(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                               unsigned int* status, long long budget) {
+    if (mbar_test(bar, parity)) return true;
+    const long long t_start = clock64();
+    while (true) {
+        for (int i = 0; i < 16; ++i)
+            if (mbar_test(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t_start > budget) {
+            *abort_flag = 1;
+            atomicOr(status, GATEAU_STATUS_WAIT_TIMEOUT);
+            return false;
+        }
+    }
+}
+
 // Bounded wait for a long-pending phase (the epilogue's wait for a finished item): between
 // polls the thread sleeps, so idle waiters do not take shared-memory issue slots from the
 // roles on the critical path.
@@ -427,13 +458,29 @@ __device__ __forceinline__ void tc_commit_pair(uint32_t bar) {
         : "memory");
 }
 
-// D[tmem] (+)= A[smem] * B[smem]^T, M=128, N from idesc, K=16, bf16 in, f32 accumulate.
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                       uint32_t accumulate) {
+// One 16-point stage of the fused contraction, issued by one thread in one block: the three S
+// products D_hi H_hi, D_lo H_hi, D_hi H_lo into d_sig and the two N products D_hi G', bf16(D_hi^2) Q
+// into d_noi (M = 128, N and the types from idesc, K = 16).  Descriptors come as their low words
+// (start address and leading byte offset; the slot offsets are added there, without carry since
+// shared addresses stay below 256 KB) and the common high word (stride byte offset, version):
+// the issuing thread is on the kernel's critical path, so the block keeps its work small.
+// acc = 0 overwrites the accumulators (the first stage of an item); the other products accumulate.
+__device__ __forceinline__ void tc_mma_stage(uint32_t d_sig, uint32_t d_noi, uint32_t xhi, uint32_t xlo,
+                                             uint32_t xsq, uint32_t hhi, uint32_t hlo, uint32_t gmat,
+                                             uint32_t qmat, uint32_t dhi, uint32_t idesc, uint32_t acc) {
     asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        "{\n.reg .pred p, t;\n.reg .b64 a0, a1, a2, b0, b1, b2, b3;\n"
+        "setp.ne.b32 p, %11, 0;\n"
+        "setp.eq.b32 t, %11, %11;\n"
+        "mov.b64 a0, {%2, %9};\nmov.b64 a1, {%3, %9};\nmov.b64 a2, {%4, %9};\n"
+        "mov.b64 b0, {%5, %9};\nmov.b64 b1, {%6, %9};\nmov.b64 b2, {%7, %9};\nmov.b64 b3, {%8, %9};\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a0, b0, %10, p;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b0, %10, t;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a0, b1, %10, t;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%1], a0, b2, %10, p;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%1], a2, b3, %10, t;\n}" ::"r"(d_sig),
+        "r"(d_noi), "r"(xhi), "r"(xlo), "r"(xsq), "r"(hhi), "r"(hlo), "r"(gmat), "r"(qmat), "r"(dhi), "r"(idesc),
+        "r"(acc)
         : "memory");
 }
 
@@ -843,16 +890,19 @@ __global__ void __launch_bounds__(kThreads, 1) fused_bf16x3_kernel(const __grid_
                 const uint32_t expect = bytes + (share ? static_cast<uint32_t>(kAMats * kTileM * kKStage) : 0u);
                 bool ok = true;
                 for (int ks = 0; ks < n_ks; ++ks) {
+                    // the copy's addresses are formed before the wait for its slot
+                    const uint32_t dst = smem_u32(smem + sp.b_off + s * sp.b_bytes);
+                    const uint16_t* op = src + ks * J.F.stage_elems;
+                    const uint32_t bar = full_a(sa);
                     if (g >= NSB) {
-                        if (!mbar_wait((sf & 1) ? empty_bar(sf) : bfree_first(sf), pf, abort_flag, status0, L.wait_cycles)) {
+                        if (!mbar_wait_poll((sf & 1) ? empty_bar(sf) : bfree_first(sf), pf, abort_flag, status0, L.wait_cycles)) {
                             ok = false;
                             break;
                         }
                         if (++sf == NS) { sf = 0; pf ^= 1u; }
                     }
-                    mbar_arrive_expect_tx(full_a(sa), expect);
-                    bulk_g2s(smem_u32(smem + sp.b_off + s * sp.b_bytes), src + ks * J.F.stage_elems, bytes,
-                             full_a(sa));
+                    mbar_arrive_expect_tx(bar, expect);
+                    bulk_g2s(dst, op, bytes, bar);
                     ++g;
                     if (++s == NSB) s = 0;
                     if (++sa == NS) sa = 0;
@@ -938,8 +988,11 @@ __global__ void __launch_bounds__(kThreads, 1) fused_bf16x3_kernel(const __grid_
             // slot-0 descriptors and the per-slot steps of the start-address field
             const uint32_t a_mat = kTileM * kKStage * 2;                // bytes per A matrix
             const uint32_t a_base = smem_u32(smem), b_base = smem_u32(smem + sp.b_off);
-            const uint64_t dx0 = smem_desc(a_base + 0 * a_mat, 128, 256), dx1 = smem_desc(a_base + 1 * a_mat, 128, 256),
-                           dx2 = smem_desc(a_base + 2 * a_mat, 128, 256);
+            // descriptor low words of slot 0 (start address, leading byte offset) and the common high word
+            const uint32_t dx0 = static_cast<uint32_t>(smem_desc(a_base + 0 * a_mat, 128, 256)),
+                           dx1 = static_cast<uint32_t>(smem_desc(a_base + 1 * a_mat, 128, 256)),
+                           dx2 = static_cast<uint32_t>(smem_desc(a_base + 2 * a_mat, 128, 256));
+            const uint32_t dhi = static_cast<uint32_t>(smem_desc(a_base, 128, 256) >> 32);
             const uint32_t a_step = static_cast<uint32_t>(sp.a_bytes >> 4), b_step = static_cast<uint32_t>(sp.b_bytes >> 4);
             int s = 0, sb = 0;
             uint32_t par = 0;
@@ -951,39 +1004,38 @@ __global__ void __launch_bounds__(kThreads, 1) fused_bf16x3_kernel(const __grid_
                 const int n_ks = J.T.Kp / kKStage;
                 const uint32_t idesc = make_idesc(J.F.n_half);
                 const uint32_t b_mat = static_cast<uint32_t>(J.F.n_half) * kKStage * 2;
-                const uint64_t dh0 = smem_desc(b_base + 0 * b_mat, 128, 256), dh1 = smem_desc(b_base + 1 * b_mat, 128, 256),
-                               dh2 = smem_desc(b_base + 2 * b_mat, 128, 256), dh3 = smem_desc(b_base + 3 * b_mat, 128, 256);
+                const uint32_t dh0 = static_cast<uint32_t>(smem_desc(b_base + 0 * b_mat, 128, 256)),
+                               dh1 = static_cast<uint32_t>(smem_desc(b_base + 1 * b_mat, 128, 256)),
+                               dh2 = static_cast<uint32_t>(smem_desc(b_base + 2 * b_mat, 128, 256)),
+                               dh3 = static_cast<uint32_t>(smem_desc(b_base + 3 * b_mat, 128, 256));
                 if (j > 0) {
                     ok = mbar_wait(acc_empty, static_cast<uint32_t>((j - 1) & 1), abort_flag, status0, L.wait_cycles);
                     if (!ok) break;
                     tc_fence_after();
                 }
                 for (int ks = 0; ks < n_ks; ks += 2) {               // n_ks is even (Kp % 32 == 0)
-                    if (!mbar_wait(full_a(s), par, abort_flag, status0, L.wait_cycles)) {
+                    // What the pair's MMAs and commits need is formed before the wait, so that they
+                    // go out as soon as the stage data are in.  Descriptors of A slots s, s + 1 and
+                    // B slots sb, sb1: the slot-0 low words plus the slot offset in 16-byte units
+                    // (start-address field, bits 0-13; no carry: shared addresses stay below 256 KB).
+                    const int sb1 = sb + 1 == NSB ? 0 : sb + 1;
+                    const uint32_t da0 = static_cast<uint32_t>(s) * a_step, da1 = da0 + a_step;
+                    const uint32_t db0 = static_cast<uint32_t>(sb) * b_step, db1 = static_cast<uint32_t>(sb1) * b_step;
+                    const uint32_t bar_full = full_a(s), bar_first = bfree_first(s), bar_free = empty_bar(s);
+                    const uint32_t acc0 = ks > 0 ? 1u : 0u;
+                    if (!mbar_wait_poll(bar_full, par, abort_flag, status0, L.wait_cycles)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        // descriptors of A slot s + h and B slot sb: the slot-0 descriptors plus the
-                        // slot offset in 16-byte units (start-address field, bits 0-13; no carry:
-                        // shared addresses stay below 256 KB)
-                        const uint64_t da = static_cast<uint64_t>((s + h) * a_step);
-                        const uint64_t db = static_cast<uint64_t>(sb * b_step);
-                        const uint64_t xhi = dx0 + da, xlo = dx1 + da, xsq = dx2 + da;
-                        const uint64_t hhi = dh0 + db, hlo = dh1 + db, gmat = dh2 + db, qmat = dh3 + db;
-                        const uint32_t acc = (ks > 0 || h > 0) ? 1u : 0u;
-                        tc_mma(d_sig, xhi, hhi, idesc, acc);
-                        tc_mma(d_sig, xlo, hhi, idesc, 1u);
-                        tc_mma(d_sig, xhi, hlo, idesc, 1u);
-                        tc_mma(d_noi, xhi, gmat, idesc, acc);
-                        tc_mma(d_noi, xsq, qmat, idesc, 1u);
-                        if (h == 0) tc_commit(bfree_first(s));   // the first stage's B slot
-                        if (++sb == NSB) sb = 0;
-                    }
-                    if (share) tc_commit_pair(empty_bar(s));   // A slots s, s+1 free in both CTAs
-                    else tc_commit(empty_bar(s));              // A slots s, s+1 free once these MMAs finish
+                    tc_mma_stage(d_sig, d_noi, dx0 + da0, dx1 + da0, dx2 + da0, dh0 + db0, dh1 + db0, dh2 + db0,
+                                 dh3 + db0, dhi, idesc, acc0);
+                    tc_commit(bar_first);                      // the first stage's B slot
+                    tc_mma_stage(d_sig, d_noi, dx0 + da1, dx1 + da1, dx2 + da1, dh0 + db1, dh1 + db1, dh2 + db1,
+                                 dh3 + db1, dhi, idesc, 1u);
+                    if (share) tc_commit_pair(bar_free);       // A slots s, s+1 free in both CTAs
+                    else tc_commit(bar_free);                  // A slots s, s+1 free once these MMAs finish
+                    sb = sb1 + 1 == NSB ? 0 : sb1 + 1;
                     s += 2;
                     ++n_pairs;
                     if (s == NS) { s = 0; par ^= 1u; }
