@@ -69,6 +69,7 @@ constexpr int kInSlots = 6;          // input-ring depth (stages of staged gathe
 // point do not conflict.
 constexpr int kBoxW = 20;
 constexpr int kCubeBoxBytes = kCubeBoxAz * kCubeBoxEl * kBoxW * 4;    // 3840
+constexpr int kCubeBoxBytesS = kCubeBoxAz * kCubeBoxElS * kBoxW * 4;  // 1920: the small box, at the slot's start
 constexpr int kTauBoxBytes = 2 * kTauBoxRows * kBoxW * 4;             // (tau_j, dtau_j) rows: 1280
 constexpr int kConstBytes = 2 * kKStage * 4;                          // c_ref and c1 of the stage
 constexpr int kTauOff = kCubeBoxBytes;
@@ -144,7 +145,8 @@ void fused_tile_operands(const FilterOperands& f, int n_ch, int Kp, int n_half, 
 
 // Host: tensor maps of the opacity table and the cube for the staged gathers.
 bool fused_encode_input_maps(const float* tau, int n_pwv, const float* cube, int n_az, int n_el, int Kp,
-                             TensorMapBytes* tm_tau, TensorMapBytes* tm_cube, std::string& err) {
+                             TensorMapBytes* tm_tau, TensorMapBytes* tm_cube, TensorMapBytes* tm_cube_s,
+                             std::string& err) {
     static_assert(sizeof(CUtensorMap) == sizeof(TensorMapBytes), "tensor map size");
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -172,13 +174,13 @@ bool fused_encode_input_maps(const float* tau, int n_pwv, const float* cube, int
             return false;
         }
     }
-    {
+    for (int small = 0; small < 2; ++small) {
         const cuuint64_t dims[3] = {static_cast<cuuint64_t>(Kp), static_cast<cuuint64_t>(n_el),
                                     static_cast<cuuint64_t>(n_az)};
         const cuuint64_t strides[2] = {static_cast<cuuint64_t>(Kp) * 4, static_cast<cuuint64_t>(Kp) * 4 * n_el};
-        const cuuint32_t box[3] = {kBoxW, kCubeBoxEl, kCubeBoxAz};
-        CUresult r = encode(reinterpret_cast<CUtensorMap*>(tm_cube), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-                            const_cast<float*>(cube), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        const cuuint32_t box[3] = {kBoxW, static_cast<cuuint32_t>(small ? kCubeBoxElS : kCubeBoxEl), kCubeBoxAz};
+        CUresult r = encode(reinterpret_cast<CUtensorMap*>(small ? tm_cube_s : tm_cube), CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                            3, const_cast<float*>(cube), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
@@ -566,7 +568,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // the tensor copies).  Items are numbered job by job; a CTA (or a cluster, for shared tiles) takes
 // every gridDim-th item of that numbering, whatever job it belongs to.
 struct __align__(128) FusedJob {   // (CUtensorMap is 128-byte aligned)
-    CUtensorMap tm_tau, tm_cube;       // staged inputs of this plan
+    CUtensorMap tm_tau, tm_cube, tm_cube_s;   // staged inputs of this plan (the cube's full and small boxes)
     DevTables T;
     FusedOperands F;
     const RowParams* rows;
@@ -577,7 +579,7 @@ struct __align__(128) FusedJob {   // (CUtensorMap is 128-byte aligned)
     long long item0, n_items;          // this job's items in the launch's numbering
 };
 
-constexpr int kMaxJobs = 32;           // 32 jobs of 896 bytes stay inside the 32 KB of kernel parameters
+constexpr int kMaxJobs = 31;           // 31 jobs of 1024 bytes stay inside the 32 KB of kernel parameters
 
 template <int NJ>
 struct FusedLaunch {
@@ -930,7 +932,9 @@ __global__ void __launch_bounds__(kThreads, 1) fused_bf16x3_kernel(const __grid_
                 const TileInfo ti = J.tiles[tile];
                 const bool tau_box = J.F.tma_inputs && (ti.flags & TILE_TAU_FITS);
                 const bool cube_box = J.F.tma_inputs && (ti.flags & TILE_CUBE_FITS);
-                const uint32_t bytes = kConstBytes + (tau_box ? kTauBoxBytes : 0) + (cube_box ? kCubeBoxBytes : 0);
+                const bool small = (ti.flags & TILE_CUBE_SMALL) != 0;   // the tile's rows stay in one cell row
+                const uint32_t bytes = kConstBytes + (tau_box ? kTauBoxBytes : 0) +
+                                       (cube_box ? (small ? kCubeBoxBytesS : kCubeBoxBytes) : 0);
                 bool ok = true;
                 for (int ks = 0; ks < n_ks; ++ks) {
                     if (g >= kInSlots && !mbar_wait(empty_in(s), ph ^ 1u, abort_flag, status0, L.wait_cycles)) {
@@ -941,7 +945,9 @@ __global__ void __launch_bounds__(kThreads, 1) fused_bf16x3_kernel(const __grid_
                     mbar_arrive_expect_tx(full_in(s), bytes);
                     bulk_g2s(smem_u32(slot + kConstOff), J.F.c_tiled + static_cast<size_t>(ks) * 2 * kKStage,
                              kConstBytes, full_in(s));
-                    if (cube_box) tensor3d_g2s(smem_u32(slot), &J.tm_cube, ks * kKStage, ti.ie0, ti.ia0, full_in(s));
+                    if (cube_box)
+                        tensor3d_g2s(smem_u32(slot), small ? &J.tm_cube_s : &J.tm_cube, ks * kKStage, ti.ie0, ti.ia0,
+                                     full_in(s));
                     if (tau_box)
                         tensor2d_g2s(smem_u32(slot + kTauOff), &J.tm_tau, ks * kKStage, 2 * ti.j0, full_in(s));
                     ++g;
@@ -1095,6 +1101,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_bf16x3_kernel(const __grid_
         constexpr int kZSkip = 2, kZEvery = share ? 3 : 8;
         RowC rc[2];
         bool same_tau = false, same_cube = false;
+        int cstride = kCubeBoxEl * kBoxW;            // floats from a staged texel to its azimuth neighbour (the tile's box)
         long long z_row0 = 0;
         int z_pix = 0, z_chb = 0;
         const FusedJob* Jp = &L.job[0];              // the job of the item being built
@@ -1112,6 +1119,8 @@ __global__ void __launch_bounds__(kThreads, 1) fused_bf16x3_kernel(const __grid_
                 z_pix = pix;
                 z_chb = grp * J.F.n_half;
                 const TileInfo ti = J.tiles[tile];
+                const int box_el = (ti.flags & TILE_CUBE_SMALL) ? kCubeBoxElS : kCubeBoxEl;
+                cstride = box_el * kBoxW;
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
                     const int r = rr[i];
@@ -1134,13 +1143,13 @@ __global__ void __launch_bounds__(kThreads, 1) fused_bf16x3_kernel(const __grid_
                     const int da = has_src ? (rp.src_cell >> 16) - ti.ia0 : 0;
                     const int de = has_src ? (rp.src_cell & 0xffff) - ti.ie0 : 0;
                     const bool cube_box = has_src && J.F.tma_inputs && (ti.flags & TILE_CUBE_FITS) && da >= 0 &&
-                                          da <= kCubeBoxAz - 2 && de >= 0 && de <= kCubeBoxEl - 2;
+                                          da <= kCubeBoxAz - 2 && de >= 0 && de <= box_el - 2;
                     RowC& c = rc[i];
                     c.flags = (has_src ? kHasSrc : 0) | (tau_box ? kTauBox : 0) | (cube_box ? kCubeBox : 0);
                     c.tau_j = rp.tau_j;
                     c.src_idx = has_src ? rp.src_idx : 0;
                     c.sA = 2 * dj * kBoxW;
-                    c.sC00 = (da * kCubeBoxEl + de) * kBoxW;
+                    c.sC00 = (da * box_el + de) * kBoxW;
                     const float fa = rp.src_fa, fe = rp.src_fe;
                     c.w00 = (1.f - fa) * (1.f - fe); c.w10 = fa * (1.f - fe); c.w01 = (1.f - fa) * fe; c.w11 = fa * fe;
                     // eta_atm = exp(-csc tau) = 2^(a tau_j + b dtau_j) with a = -csc log2(e), b = a f
@@ -1187,9 +1196,9 @@ __global__ void __launch_bounds__(kThreads, 1) fused_bf16x3_kernel(const __grid_
                         if (c.flags & kCubeBox) {
                             const float* b = slot + c.sC00 + 4 * quad;
                             q00 = ld4(b);
-                            q10 = ld4(b + kCubeBoxEl * kBoxW);
+                            q10 = ld4(b + cstride);
                             q01 = ld4(b + kBoxW);
-                            q11 = ld4(b + kCubeBoxEl * kBoxW + kBoxW);
+                            q11 = ld4(b + cstride + kBoxW);
                         } else if (c.flags & kHasSrc) {
                             const DevTables& T = Jp->T;
                             const float* g00 = T.cube + c.src_idx + kq;
@@ -1343,6 +1352,7 @@ static cudaError_t launch_jobs(const FusedRunDesc* runs, int n, int n_sm, cudaSt
         FusedJob& J = L.job[k];
         memcpy(&J.tm_tau, &r.tm_tau, sizeof(J.tm_tau));
         memcpy(&J.tm_cube, &r.tm_cube, sizeof(J.tm_cube));
+        memcpy(&J.tm_cube_s, &r.tm_cube_s, sizeof(J.tm_cube_s));
         J.T = r.T;
         J.F = F;
         J.rows = r.rows;
@@ -1440,21 +1450,5 @@ cudaError_t launch_fused_runs(const FusedRunDesc* runs, int n, int n_sm, cudaStr
 }
 
 int fused_max_jobs() { return kMaxJobs; }
-
-cudaError_t launch_fused_bf16x3(const DevTables& T, const FusedOperands& F, const TensorMapBytes& tm_tau,
-                                const TensorMapBytes& tm_cube, const RowParams* rows, const TileInfo* tiles,
-                                long long t0, long long nt, float* out, int n_sm, cudaStream_t stream) {
-    FusedRunDesc r;
-    r.T = T;
-    r.F = F;
-    r.tm_tau = tm_tau;
-    r.tm_cube = tm_cube;
-    r.rows = rows;
-    r.tiles = tiles;
-    r.t0 = t0;
-    r.nt = nt;
-    r.out = out;
-    return launch_fused_runs(&r, 1, n_sm, stream);
-}
 
 }  // namespace gateau

@@ -218,6 +218,7 @@ __global__ void __launch_bounds__(kTileRows) row_setup_kernel(DevTables T, long 
                 if (v[6]) {
                     f |= TILE_HAS_SOURCE;
                     if (v[3] + 1 - v[2] <= kCubeBoxAz - 1 && v[5] + 1 - v[4] <= kCubeBoxEl - 1) f |= TILE_CUBE_FITS;
+                    if (v[5] + 1 - v[4] <= kCubeBoxElS - 1) f |= TILE_CUBE_SMALL;   // every row in one cell row
                 }
                 ti.flags = f;
                 tiles[static_cast<long long>(i) * tpp + b] = ti;
