@@ -436,7 +436,7 @@ gateau_status gateau_common_mode(gateau_plan* plan, long long t0, long long nt, 
  * batch's plans share persistent launches of the fused kernel -- one launch for
  * the plans with two channel groups (177-352 channels: 2-CTA clusters) and one
  * for the others, each over every work item (time tile x spaxel x channel
- * group) of up to 31 plans -- so uneven requests fill the GPU together; the
+ * group) of up to 28 plans -- so uneven requests fill the GPU together; the
  * row setup and the noise phases stay per plan.  FP32 plans run one by one.
  * The phase timing of gateau_plan_get_timing reports a shared launch under
  * each of its plans; the launch count counts it once.  0 < n <= 256; the whole

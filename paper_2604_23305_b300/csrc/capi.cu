@@ -177,7 +177,7 @@ struct gateau_plan {
     bool cube_scale_dirty = true;    // d_cube = d_cube_raw * c2 / k_B must be recomputed
     DevBuf d_rows, d_tiles, d_X, d_agg, d_stage[2];
     FusedOperands fused{};
-    TensorMapBytes tm_tau{}, tm_cube{}, tm_cube_s{};
+    TensorMapBytes tm_tau{}, tm_tau_s{}, tm_cube{}, tm_cube_s{};
     bool maps_dirty = true;
     int n_ch_pad = 0;
     int n_sm = 148;
@@ -682,7 +682,7 @@ gateau_status run_rows(gateau_plan* p, long long t0, long long nt, cudaStream_t 
         if (p->maps_dirty) {
             std::string err;
             p->fused.tma_inputs = fused_encode_input_maps(p->d_tau.as<float>(), p->n_pwv, p->d_cube.as<float>(),
-                                                          p->n_az, p->n_el, p->Kp, &p->tm_tau, &p->tm_cube,
+                                                          p->n_az, p->n_el, p->Kp, &p->tm_tau, &p->tm_tau_s, &p->tm_cube,
                                                           &p->tm_cube_s, err)
                                       ? 1
                                       : 0;
@@ -702,6 +702,7 @@ FusedRunDesc fused_run(const gateau_plan* p, long long t0, long long nt, float* 
     r.T = make_tables(p);
     r.F = p->fused;
     r.tm_tau = p->tm_tau;
+    r.tm_tau_s = p->tm_tau_s;
     r.tm_cube = p->tm_cube;
     r.tm_cube_s = p->tm_cube_s;
     r.rows = p->d_rows.as<RowParams>();

@@ -33,9 +33,10 @@ struct __align__(16) RowParams {
 // that both can be staged in shared memory by tensor copies.
 constexpr int kTileRows = 128;
 constexpr int kTauBoxRows = 8;                // opacity rows per staged box
+constexpr int kTauBoxRowsS = 2;               // opacity rows of the small box (a tile spanning one or two rows)
 constexpr int kCubeBoxAz = 12, kCubeBoxEl = 4; // cube texels per staged box (a 128-sample tile of a 30"/s raster spans ~8 x 2 cells)
 constexpr int kCubeBoxElS = 2;                 // elevation rows of the small box (a tile whose rows stay in one cell row)
-enum { TILE_TAU_FITS = 1, TILE_CUBE_FITS = 2, TILE_HAS_SOURCE = 4, TILE_CUBE_SMALL = 8 };
+enum { TILE_TAU_FITS = 1, TILE_CUBE_FITS = 2, TILE_HAS_SOURCE = 4, TILE_CUBE_SMALL = 8, TILE_TAU_SMALL = 16 };
 struct __align__(16) TileInfo {
     int j0;           // lowest opacity row of the tile
     int ia0, ie0;     // lowest cube cell of the tile's source rows
@@ -138,7 +139,7 @@ cudaError_t launch_contract_fp32(const DevTables& T, const float* X, long long r
 struct FusedRunDesc {
     DevTables T;
     FusedOperands F;
-    TensorMapBytes tm_tau, tm_cube, tm_cube_s;    // cube: the full box and the small one
+    TensorMapBytes tm_tau, tm_tau_s, tm_cube, tm_cube_s;   // the full boxes and the small ones
     const RowParams* rows;
     const TileInfo* tiles;
     long long t0, nt;
@@ -153,7 +154,8 @@ int fused_ring_depths(int n_half, int ring_b, int* nsa);
 // Encodes the tensor maps of the opacity table [n_pwv][Kp] and the cube [n_az][n_el][Kp] (its
 // full and small boxes; driver entry point looked up at run time); false if the driver cannot.
 bool fused_encode_input_maps(const float* tau, int n_pwv, const float* cube, int n_az, int n_el, int Kp,
-                             TensorMapBytes* tm_tau, TensorMapBytes* tm_cube, TensorMapBytes* tm_cube_s,
+                             TensorMapBytes* tm_tau, TensorMapBytes* tm_tau_s, TensorMapBytes* tm_cube,
+                             TensorMapBytes* tm_cube_s,
                              std::string& err);
 size_t fused_smem_bytes();
 int fused_kstage();

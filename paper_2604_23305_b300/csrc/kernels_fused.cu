@@ -71,6 +71,7 @@ constexpr int kBoxW = 20;
 constexpr int kCubeBoxBytes = kCubeBoxAz * kCubeBoxEl * kBoxW * 4;    // 3840
 constexpr int kCubeBoxBytesS = kCubeBoxAz * kCubeBoxElS * kBoxW * 4;  // 1920: the small box, at the slot's start
 constexpr int kTauBoxBytes = 2 * kTauBoxRows * kBoxW * 4;             // (tau_j, dtau_j) rows: 1280
+constexpr int kTauBoxBytesS = 2 * kTauBoxRowsS * kBoxW * 4;           // the small box: 320
 constexpr int kConstBytes = 2 * kKStage * 4;                          // c_ref and c1 of the stage
 constexpr int kTauOff = kCubeBoxBytes;
 constexpr int kConstOff = kCubeBoxBytes + kTauBoxBytes;
@@ -145,7 +146,8 @@ void fused_tile_operands(const FilterOperands& f, int n_ch, int Kp, int n_half, 
 
 // Host: tensor maps of the opacity table and the cube for the staged gathers.
 bool fused_encode_input_maps(const float* tau, int n_pwv, const float* cube, int n_az, int n_el, int Kp,
-                             TensorMapBytes* tm_tau, TensorMapBytes* tm_cube, TensorMapBytes* tm_cube_s,
+                             TensorMapBytes* tm_tau, TensorMapBytes* tm_tau_s, TensorMapBytes* tm_cube,
+                             TensorMapBytes* tm_cube_s,
                              std::string& err) {
     static_assert(sizeof(CUtensorMap) == sizeof(TensorMapBytes), "tensor map size");
     void* fn = nullptr;
@@ -161,11 +163,11 @@ bool fused_encode_input_maps(const float* tau, int n_pwv, const float* cube, int
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
     Encode encode = reinterpret_cast<Encode>(fn);
     const cuuint32_t estr[3] = {1, 1, 1};
-    {
+    for (int small = 0; small < 2; ++small) {
         const cuuint64_t dims[2] = {static_cast<cuuint64_t>(Kp), static_cast<cuuint64_t>(2 * n_pwv)};
         const cuuint64_t strides[1] = {static_cast<cuuint64_t>(Kp) * 4};
-        const cuuint32_t box[2] = {kBoxW, 2 * kTauBoxRows};
-        CUresult r = encode(reinterpret_cast<CUtensorMap*>(tm_tau), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+        const cuuint32_t box[2] = {kBoxW, static_cast<cuuint32_t>(2 * (small ? kTauBoxRowsS : kTauBoxRows))};
+        CUresult r = encode(reinterpret_cast<CUtensorMap*>(small ? tm_tau_s : tm_tau), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                             const_cast<float*>(tau), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -568,7 +570,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // the tensor copies).  Items are numbered job by job; a CTA (or a cluster, for shared tiles) takes
 // every gridDim-th item of that numbering, whatever job it belongs to.
 struct __align__(128) FusedJob {   // (CUtensorMap is 128-byte aligned)
-    CUtensorMap tm_tau, tm_cube, tm_cube_s;   // staged inputs of this plan (the cube's full and small boxes)
+    CUtensorMap tm_tau, tm_tau_s, tm_cube, tm_cube_s;   // staged inputs of this plan (full and small boxes)
     DevTables T;
     FusedOperands F;
     const RowParams* rows;
@@ -579,7 +581,7 @@ struct __align__(128) FusedJob {   // (CUtensorMap is 128-byte aligned)
     long long item0, n_items;          // this job's items in the launch's numbering
 };
 
-constexpr int kMaxJobs = 31;           // 31 jobs of 1024 bytes stay inside the 32 KB of kernel parameters
+constexpr int kMaxJobs = 28;           // 28 jobs of 1152 bytes stay inside the 32 KB of kernel parameters
 
 template <int NJ>
 struct FusedLaunch {
@@ -933,7 +935,8 @@ __global__ void __launch_bounds__(kThreads, 1) fused_bf16x3_kernel(const __grid_
                 const bool tau_box = J.F.tma_inputs && (ti.flags & TILE_TAU_FITS);
                 const bool cube_box = J.F.tma_inputs && (ti.flags & TILE_CUBE_FITS);
                 const bool small = (ti.flags & TILE_CUBE_SMALL) != 0;   // the tile's rows stay in one cell row
-                const uint32_t bytes = kConstBytes + (tau_box ? kTauBoxBytes : 0) +
+                const bool tsmall = (ti.flags & TILE_TAU_SMALL) != 0;   // and span one or two opacity rows
+                const uint32_t bytes = kConstBytes + (tau_box ? (tsmall ? kTauBoxBytesS : kTauBoxBytes) : 0) +
                                        (cube_box ? (small ? kCubeBoxBytesS : kCubeBoxBytes) : 0);
                 bool ok = true;
                 for (int ks = 0; ks < n_ks; ++ks) {
@@ -949,7 +952,8 @@ __global__ void __launch_bounds__(kThreads, 1) fused_bf16x3_kernel(const __grid_
                         tensor3d_g2s(smem_u32(slot), small ? &J.tm_cube_s : &J.tm_cube, ks * kKStage, ti.ie0, ti.ia0,
                                      full_in(s));
                     if (tau_box)
-                        tensor2d_g2s(smem_u32(slot + kTauOff), &J.tm_tau, ks * kKStage, 2 * ti.j0, full_in(s));
+                        tensor2d_g2s(smem_u32(slot + kTauOff), tsmall ? &J.tm_tau_s : &J.tm_tau, ks * kKStage, 2 * ti.j0,
+                                     full_in(s));
                     ++g;
                     if (++s == kInSlots) { s = 0; ph ^= 1u; }
                 }
@@ -1139,7 +1143,8 @@ __global__ void __launch_bounds__(kThreads, 1) fused_bf16x3_kernel(const __grid_
                     const bool has_src = valid && rp.src_idx >= 0;
                     // staged boxes, with a range check that sends a row to the global path otherwise
                     const int dj = rp.tau_j - ti.j0;
-                    const bool tau_box = J.F.tma_inputs && (ti.flags & TILE_TAU_FITS) && dj >= 0 && dj <= kTauBoxRows - 1;
+                    const bool tau_box = J.F.tma_inputs && (ti.flags & TILE_TAU_FITS) && dj >= 0 &&
+                                         dj <= ((ti.flags & TILE_TAU_SMALL) ? kTauBoxRowsS : kTauBoxRows) - 1;
                     const int da = has_src ? (rp.src_cell >> 16) - ti.ia0 : 0;
                     const int de = has_src ? (rp.src_cell & 0xffff) - ti.ie0 : 0;
                     const bool cube_box = has_src && J.F.tma_inputs && (ti.flags & TILE_CUBE_FITS) && da >= 0 &&
@@ -1351,6 +1356,7 @@ static cudaError_t launch_jobs(const FusedRunDesc* runs, int n, int n_sm, cudaSt
             return cudaErrorInvalidConfiguration;
         FusedJob& J = L.job[k];
         memcpy(&J.tm_tau, &r.tm_tau, sizeof(J.tm_tau));
+        memcpy(&J.tm_tau_s, &r.tm_tau_s, sizeof(J.tm_tau_s));
         memcpy(&J.tm_cube, &r.tm_cube, sizeof(J.tm_cube));
         memcpy(&J.tm_cube_s, &r.tm_cube_s, sizeof(J.tm_cube_s));
         J.T = r.T;

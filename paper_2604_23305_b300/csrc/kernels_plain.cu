@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(kTileRows) row_setup_kernel(DevTables T, long 
                 ti.ie0 = v[6] ? v[4] : 0;
                 int f = 0;
                 if (v[1] - v[0] <= kTauBoxRows - 1) f |= TILE_TAU_FITS;
+                if (v[1] - v[0] <= kTauBoxRowsS - 1) f |= TILE_TAU_SMALL;
                 if (v[6]) {
                     f |= TILE_HAS_SOURCE;
                     if (v[3] + 1 - v[2] <= kCubeBoxAz - 1 && v[5] + 1 - v[4] <= kCubeBoxEl - 1) f |= TILE_CUBE_FITS;
