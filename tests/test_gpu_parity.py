@@ -347,6 +347,26 @@ def _mut_max_channels(s):
     s["noise"]["pink_alpha"] = np.resize(np.asarray(s["noise"]["pink_alpha"]), 4096)
 
 
+def _mut_el_drift(s):
+    """A custom scan drifting 6"/s in azimuth and elevation over the 4.5" cells of the small cube: each
+    128-sample tile spans two or three rows of cube cells, so the fused kernel stages the full
+    12 x 4-texel cube box (not the 12 x 2 one of single-row tiles) and both sizes of opacity box."""
+    n = s["nt_total"]
+    t = np.arange(n) / s["f_sample"]
+    v = 6.0 * W.ARCSEC
+    s["scan"] = dict(kind="custom", params=(), phi0=0.0, theta0=s["scan"]["theta0"],
+                     custom=np.stack([v * t, v * (t - t.mean())], 1))
+
+
+def _mut_pwv_ripple(s):
+    """A 0.3 mm PWV ripple with a 12-cell (6 m) period across the screen: within a tile the line of
+    sight crosses more opacity-table rows than the staged box holds, so every row reads its
+    opacities from global memory."""
+    scr = np.asarray(s["atmosphere"]["screen"], dtype=np.float64)
+    ix = np.arange(scr.shape[1])[None, :]
+    s["atmosphere"]["screen"] = (scr + 0.3 * np.sin(2 * np.pi * ix / 12.0)).astype(np.float32)
+
+
 EDGE = {
     "64_spaxels_daisy": ("ifu25", 40001, 45, _mut_64_spaxels_daisy),
     "wide_offsets": ("ifu25", 120007, 37, _mut_wide_offsets),
@@ -359,6 +379,8 @@ EDGE = {
     "1_channel_2_freqs": ("single_pixel_small", 0, 33, _mut_one_channel_two_freqs),
     "one_sample": ("ifu25", 77, 1, None),
     "4096_channels": ("single_pixel_small", 3, 61, _mut_max_channels),
+    "el_drift_full_boxes": ("single_pixel_small", 0, 384, _mut_el_drift),
+    "pwv_ripple": ("single_pixel_small", 0, 384, _mut_pwv_ripple),
 }
 
 
