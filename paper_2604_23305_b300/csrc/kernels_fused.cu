@@ -23,7 +23,9 @@
 //
 // Warp roles (512 threads, one CTA per SM, persistent over work items):
 //   warp 0        : one thread issuing bulk copies of the pre-tiled filter operands (B ring)
-//   warp 1        : TMEM allocator + single-thread tcgen05.mma issuer
+//   warp 1        : TMEM allocator + single-thread tcgen05.mma issuer (a stage's five MMAs in one
+//                   asm block; it and the warp-0 loader poll their barriers: both threads are on
+//                   the kernel's critical chain)
 //   warp 2        : one thread issuing tensor copies of the tile's opacity rows and cube texel
 //                   box (input ring); each spinning role has a warp of its own
 //   warp 3        : shared tiles only: one thread copying this CTA's finished rows of each
@@ -35,8 +37,9 @@
 //   warps 12..15  : shared tiles: a third producer group; independent CTAs: epilogue only.
 //                   The epilogue of each item is shared by warps 4..15 (three per TMEM quadrant)
 // The input ring runs ahead of the producers, the A/B ring behind them, so the
-// producers read their gathers from shared memory.  Tiles whose opacity rows or
-// cube texels do not fit the staged boxes fall back to global loads.
+// producers read their gathers from shared memory.  A tile whose rows span one or two
+// opacity-table rows, or stay in one row of cube cells, stages the smaller box of each
+// (less for the SM to take in per stage); rows outside the staged boxes read global memory.
 // Every wait is bounded: on time-out the kernel records GATEAU_STATUS_WAIT_TIMEOUT,
 // stops all roles, waits (bounded) for its own copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
